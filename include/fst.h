@@ -1,0 +1,159 @@
+/*
+ * fst.h - batched Featherstone rigid-body dynamics on GB300 (sm_103a).
+ *
+ * C ABI of libfst.so. One kinematic tree (the "model") is shared by B
+ * independent environments; every operator evaluates all B environments in
+ * one call. The operators are those of the paper "Batched Differentiable
+ * Rigid Body Dynamics in PyTorch for GPU-Accelerated Robot Learning":
+ * forward kinematics (Sec. 3.1 tier 3), the geometric Jacobian (Sec. 3.4,
+ * Eq. 6), RNEA (Sec. 3.3, Eq. 7), CRBA and ABA (Sec. 3.5, Sec. 4.1), plus
+ * hand-written adjoints of FK, RNEA and ABA (the paper differentiates by
+ * autograd, Sec. 3.5 and Sec. 4.3).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Arrays are FP32, caller-owned DEVICE memory on the model's device, in
+ *   structure-of-arrays layout with the environment index fastest:
+ *   element (field f, env e) lives at ptr[f * B + e]. So q is [nq][B],
+ *   qd/qdd/tau are [nv][B].
+ * - `stream` is a cudaStream_t (NULL = the legacy default stream). Calls are
+ *   asynchronous on it; none allocates, frees or synchronises, so every
+ *   compute call can be captured into a CUDA graph.
+ * - B = 0 is valid and does nothing. B < 0, null pointers with B > 0, or a
+ *   call from a device other than the model's return FST_ERR_INVALID_ARG
+ *   without launching anything.
+ * - A failed kernel launch returns FST_ERR_CUDA. Nothing traps on the
+ *   device. NaN/Inf inputs give NaN/Inf outputs for that environment only.
+ * - On any status other than FST_OK, fst_last_error() gives a message
+ *   (thread-local, valid until the next call on the same thread).
+ *
+ * Joint model (paper Sec. 3.2, first equation): the pose of body i in its
+ * parent is T_joint[i] * J(q_i) * T_link[i], with J a rotation about `axis`
+ * (revolute, 1 DOF), a translation along `axis` (prismatic, 1 DOF), the
+ * identity (fixed, 0 DOF) or a free rigid motion (free, body 0 only,
+ * q = [x y z qx qy qz qw], velocity = twist of the body frame in its own
+ * coordinates, linear part first [v; w], 6 DOF; T_link must be identity).
+ * q-index and v-index of each body are the running sums of its
+ * predecessors' nq and nv, in body order.
+ */
+#ifndef FST_H
+#define FST_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define FST_API __attribute__((visibility("default")))
+#else
+#define FST_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  FST_OK = 0,
+  FST_ERR_INVALID_ARG = -1,  /* bad pointer, size, device or option */
+  FST_ERR_TOPOLOGY = -2,     /* parent index not in [-1, i-1], misplaced free joint */
+  FST_ERR_INERTIA = -3,      /* negative mass, non-PSD or non-finite inertia */
+  FST_ERR_UNSUPPORTED = -4,  /* joint type or model size this build does not handle */
+  FST_ERR_CUDA = -5,         /* a CUDA runtime call or kernel launch failed */
+  FST_ERR_NO_MEMORY = -6,    /* device allocation at model creation failed */
+  FST_ERR_DEVICE_CHECK = -7  /* a device-side check recorded a failure */
+} fst_status;
+
+enum {
+  FST_JOINT_FIXED = 0,
+  FST_JOINT_REVOLUTE = 1,
+  FST_JOINT_PRISMATIC = 2,
+  FST_JOINT_FREE = 3
+};
+
+/* Largest model this build accepts (bodies). */
+#define FST_MAX_BODIES 64
+/* Largest number of end-effector links per Jacobian call. */
+#define FST_MAX_LINKS 16
+
+/* One row of the body table (host memory, FP64). Bodies are listed in
+ * topological order: parent < own index, -1 = attached to the world. */
+typedef struct fst_body_desc {
+  int32_t parent;
+  int32_t type;          /* FST_JOINT_* */
+  double axis[3];        /* joint axis in the joint frame; normalised by create */
+  double T_joint[12];    /* parent -> joint frame: R row-major (9), then t (3) */
+  double T_link[12];     /* joint (moved) -> body frame; identity if unused */
+  double mass;           /* kg */
+  double com[3];         /* centre of mass in the body frame */
+  double I_com[6];       /* rotational inertia about the COM, body frame: xx xy yy xz yz zz */
+} fst_body_desc;
+
+typedef struct fst_model fst_model;
+
+/* Builds a model from the body table (host memory, not retained) and
+ * uploads its constants to the CURRENT CUDA device: the Rodrigues constants
+ * of paper Eq. 2-3 per joint, each body's motion subspace and its inertia as
+ * the 10 linear parameters about the body origin. gravity[3] is the world
+ * gravity vector (e.g. {0, 0, -9.81}). On success *out owns device memory;
+ * release it with fst_model_destroy. Validation happens before any CUDA
+ * call, so FST_ERR_TOPOLOGY / FST_ERR_INERTIA / FST_ERR_UNSUPPORTED /
+ * FST_ERR_INVALID_ARG are returned on hosts without a GPU as well. */
+FST_API fst_status fst_model_create(const fst_body_desc* bodies, int32_t n_bodies,
+                            const double gravity[3], fst_model** out);
+
+/* Frees the model's device memory. NULL is accepted. */
+FST_API fst_status fst_model_destroy(fst_model* model);
+
+/* Sizes of a model: configuration dimension nq, velocity dimension nv,
+ * number of bodies and tree depth (bodies on the longest root-leaf path).
+ * Any output pointer may be NULL. */
+FST_API fst_status fst_model_info(const fst_model* model, int32_t* nq, int32_t* nv,
+                          int32_t* n_bodies, int32_t* depth);
+
+/* Forward kinematics (paper Sec. 3.1, tier 3; Eq. 4-5 for each joint).
+ * q      [nq][B]        joint positions.
+ * poses  [n_b][12][B]   world pose of every body: R row-major (9), then p (3). */
+FST_API fst_status fst_fk(const fst_model* model, int64_t B, const float* q,
+                  float* poses, void* stream);
+
+/* Geometric Jacobians (paper Sec. 3.4, Eq. 6) of n_links bodies.
+ * links   HOST array of n_links body indices (1 <= n_links <= FST_MAX_LINKS).
+ * J       [n_links][6][nv][B]: world-frame twist at the world origin, rows
+ *         [v; w] (linear first); column k is the twist produced by unit
+ *         velocity of DOF k; DOFs not on the body's support path are 0. */
+FST_API fst_status fst_jacobian(const fst_model* model, int64_t B, const float* q,
+                        const int32_t* links, int32_t n_links, float* J,
+                        void* stream);
+
+/* Inverse dynamics by recursive Newton-Euler (paper Sec. 3.3, Eq. 7):
+ * tau = M(q) qdd + C(q, qd) qd + g(q).
+ * theta  [n_b][10] device, or NULL for the model's own inertias:
+ *        per body [m, m*cx, m*cy, m*cz, Ixx, Ixy, Iyy, Ixz, Iyz, Izz] with
+ *        the rotational inertia about the BODY-FRAME ORIGIN. Shared by all
+ *        environments. */
+FST_API fst_status fst_rnea(const fst_model* model, int64_t B, const float* q,
+                    const float* qd, const float* qdd, const float* theta,
+                    float* tau, void* stream);
+
+/* Joint-space mass matrix by the composite-rigid-body algorithm (paper
+ * Sec. 3.5). M [nv][nv][B], full symmetric (both triangles written). */
+FST_API fst_status fst_crba(const fst_model* model, int64_t B, const float* q,
+                    const float* theta, float* M, void* stream);
+
+/* Forward dynamics by the articulated-body algorithm (paper Sec. 4.1, three
+ * passes): qdd = M(q)^-1 (tau - C(q, qd) qd - g(q)). */
+FST_API fst_status fst_aba(const fst_model* model, int64_t B, const float* q,
+                   const float* qd, const float* tau, const float* theta,
+                   float* qdd, void* stream);
+
+/* Message for the last non-OK status on this thread ("" if none). */
+FST_API const char* fst_last_error(void);
+
+/* Library version string. */
+FST_API const char* fst_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FST_H */

@@ -1,0 +1,91 @@
+"""ctypes declarations of libfst.so (the C ABI in include/fst.h).
+
+Loading fails loudly when the library has not been built: there is no CPU
+fallback behind this binding.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libfst.so")
+
+FST_OK = 0
+STATUS_NAMES = {
+    0: "FST_OK", -1: "FST_ERR_INVALID_ARG", -2: "FST_ERR_TOPOLOGY", -3: "FST_ERR_INERTIA",
+    -4: "FST_ERR_UNSUPPORTED", -5: "FST_ERR_CUDA", -6: "FST_ERR_NO_MEMORY", -7: "FST_ERR_DEVICE_CHECK",
+}
+MAX_BODIES = 64
+MAX_LINKS = 16
+
+c_int32, c_int64, c_double, c_void_p = ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_void_p
+c_float_p = ctypes.POINTER(ctypes.c_float)
+
+
+class BodyDesc(ctypes.Structure):
+    """fst_body_desc: one row of the body table."""
+    _fields_ = [
+        ("parent", c_int32),
+        ("type", c_int32),
+        ("axis", c_double * 3),
+        ("T_joint", c_double * 12),
+        ("T_link", c_double * 12),
+        ("mass", c_double),
+        ("com", c_double * 3),
+        ("I_com", c_double * 6),
+    ]
+
+
+class FstError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+# (name, restype, argtypes); pointers to device memory travel as c_void_p
+_SIGS = {
+    "fst_model_create": (c_int32, [ctypes.POINTER(BodyDesc), c_int32, ctypes.POINTER(c_double), ctypes.POINTER(c_void_p)]),
+    "fst_model_destroy": (c_int32, [c_void_p]),
+    "fst_model_info": (c_int32, [c_void_p, ctypes.POINTER(c_int32), ctypes.POINTER(c_int32),
+                                 ctypes.POINTER(c_int32), ctypes.POINTER(c_int32)]),
+    "fst_fk": (c_int32, [c_void_p, c_int64, c_void_p, c_void_p, c_void_p]),
+    "fst_jacobian": (c_int32, [c_void_p, c_int64, c_void_p, ctypes.POINTER(c_int32), c_int32, c_void_p, c_void_p]),
+    "fst_rnea": (c_int32, [c_void_p, c_int64, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "fst_crba": (c_int32, [c_void_p, c_int64, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "fst_aba": (c_int32, [c_void_p, c_int64, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "fst_last_error": (ctypes.c_char_p, []),
+    "fst_version": (ctypes.c_char_p, []),
+}
+
+_lib = None
+_lock = threading.Lock()
+
+
+def exported_names():
+    return list(_SIGS)
+
+
+def lib():
+    """The loaded library (ImportError if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise ImportError(
+                    f"{LIB_PATH} is missing: build it with `python -m paper_2605_31481_gb300.build` "
+                    "(there is no CPU fallback)")
+            L = ctypes.CDLL(LIB_PATH)
+            for name, (res, args) in _SIGS.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def check(status: int):
+    if status != FST_OK:
+        raise FstError(status, lib().fst_last_error().decode(errors="replace"))

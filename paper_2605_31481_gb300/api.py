@@ -1,0 +1,169 @@
+"""Thin PyTorch binding of libfst.so.
+
+Every function here only checks and marshals arguments: tensors in, device
+pointers plus the current CUDA stream out to the C ABI, output tensors
+allocated with torch when the caller passes none. All arithmetic runs in the
+library's kernels.
+
+Layout: FP32 CUDA tensors in structure-of-arrays form, environment index
+last and contiguous: q (nq, B), qd/qdd/tau (nv, B), poses (n_b, 12, B),
+J (n_links, 6, nv, B), M (nv, nv, B). `soa(x)` / `aos(x)` convert from/to
+the (B, ...) layout most training code uses.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from . import _ffi
+from ._ffi import check
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def soa(x: torch.Tensor) -> torch.Tensor:
+    """(B, ...) -> (..., B) contiguous."""
+    return x.movedim(0, -1).contiguous()
+
+
+def aos(x: torch.Tensor) -> torch.Tensor:
+    """(..., B) -> (B, ...) view."""
+    return x.movedim(-1, 0)
+
+
+class Model:
+    """A kinematic tree uploaded to the current CUDA device.
+
+    `tree` is any object with the body-table fields parent, jtype, axis,
+    T_joint, T_link, mass, com, I_com and gravity (see workloads.Tree)."""
+
+    def __init__(self, tree, device=None):
+        L = _ffi.lib()
+        n = len(tree.parent)
+        arr = (_ffi.BodyDesc * n)()
+        for i in range(n):
+            d = arr[i]
+            d.parent = int(tree.parent[i])
+            d.type = int(tree.jtype[i])
+            for k in range(3):
+                d.axis[k] = float(tree.axis[i][k])
+                d.com[k] = float(tree.com[i][k])
+            for k in range(12):
+                d.T_joint[k] = float(tree.T_joint[i][k])
+                d.T_link[k] = float(tree.T_link[i][k])
+            d.mass = float(tree.mass[i])
+            for k in range(6):
+                d.I_com[k] = float(tree.I_com[i][k])
+        g = (ctypes.c_double * 3)(*[float(x) for x in tree.gravity])
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else torch.device(device).index or 0)
+        handle = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            check(L.fst_model_create(arr, n, g, ctypes.byref(handle)))
+        self._h = handle
+        nq, nv, nb, depth = (ctypes.c_int32() for _ in range(4))
+        check(L.fst_model_info(self._h, ctypes.byref(nq), ctypes.byref(nv), ctypes.byref(nb), ctypes.byref(depth)))
+        self.nq, self.nv, self.n_bodies, self.depth = nq.value, nv.value, nb.value, depth.value
+        self.name = getattr(tree, "name", "tree")
+        self.ee = tuple(getattr(tree, "ee", ()))
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _ffi.lib().fst_model_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __repr__(self):
+        return f"Model({self.name}: n_b={self.n_bodies}, nq={self.nq}, nv={self.nv}, depth={self.depth})"
+
+
+def _check_in(x, rows, name, model):
+    if not isinstance(x, torch.Tensor):
+        raise TypeError(f"{name} must be a torch.Tensor")
+    if x.dtype != torch.float32 or x.device != model.device:
+        raise ValueError(f"{name} must be float32 on {model.device}, got {x.dtype} on {x.device}")
+    if x.dim() != 2 or x.shape[0] != rows or not x.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous ({rows}, B) tensor, got {tuple(x.shape)}")
+    return x.shape[1]
+
+
+def _out(out, shape, model):
+    if out is None:
+        return torch.empty(shape, dtype=torch.float32, device=model.device)
+    if out.shape != torch.Size(shape) or out.dtype != torch.float32 or not out.is_contiguous() or out.device != model.device:
+        raise ValueError(f"out must be a contiguous float32 {shape} tensor on {model.device}")
+    return out
+
+
+def _theta(theta, model):
+    if theta is None:
+        return None
+    if theta.dtype != torch.float32 or theta.device != model.device or theta.shape != (model.n_bodies, 10) \
+            or not theta.is_contiguous():
+        raise ValueError(f"theta must be a contiguous float32 ({model.n_bodies}, 10) tensor on {model.device}")
+    return theta
+
+
+def fk(model: Model, q, out=None):
+    """World poses (n_b, 12, B): R row-major then p, for every body."""
+    B = _check_in(q, model.nq, "q", model)
+    out = _out(out, (model.n_bodies, 12, B), model)
+    check(_ffi.lib().fst_fk(model.handle, B, _ptr(q), _ptr(out), _stream()))
+    return out
+
+
+def jacobian(model: Model, q, links, out=None):
+    """World-frame Jacobians (n_links, 6, nv, B), rows [v; w]."""
+    B = _check_in(q, model.nq, "q", model)
+    links = [int(l) for l in links]
+    arr = (ctypes.c_int32 * len(links))(*links)
+    out = _out(out, (len(links), 6, model.nv, B), model)
+    check(_ffi.lib().fst_jacobian(model.handle, B, _ptr(q), arr, len(links), _ptr(out), _stream()))
+    return out
+
+
+def rnea(model: Model, q, qd, qdd, theta=None, out=None):
+    """Inverse dynamics tau (nv, B)."""
+    B = _check_in(q, model.nq, "q", model)
+    for x, nm in ((qd, "qd"), (qdd, "qdd")):
+        if _check_in(x, model.nv, nm, model) != B:
+            raise ValueError(f"{nm} batch size differs from q")
+    out = _out(out, (model.nv, B), model)
+    check(_ffi.lib().fst_rnea(model.handle, B, _ptr(q), _ptr(qd), _ptr(qdd), _ptr(_theta(theta, model)),
+                              _ptr(out), _stream()))
+    return out
+
+
+def crba(model: Model, q, theta=None, out=None):
+    """Mass matrix (nv, nv, B)."""
+    B = _check_in(q, model.nq, "q", model)
+    out = _out(out, (model.nv, model.nv, B), model)
+    check(_ffi.lib().fst_crba(model.handle, B, _ptr(q), _ptr(_theta(theta, model)), _ptr(out), _stream()))
+    return out
+
+
+def aba(model: Model, q, qd, tau, theta=None, out=None):
+    """Forward dynamics qdd (nv, B)."""
+    B = _check_in(q, model.nq, "q", model)
+    for x, nm in ((qd, "qd"), (tau, "tau")):
+        if _check_in(x, model.nv, nm, model) != B:
+            raise ValueError(f"{nm} batch size differs from q")
+    out = _out(out, (model.nv, B), model)
+    check(_ffi.lib().fst_aba(model.handle, B, _ptr(q), _ptr(qd), _ptr(tau), _ptr(_theta(theta, model)),
+                             _ptr(out), _stream()))
+    return out
