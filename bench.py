@@ -1,0 +1,444 @@
+#!/usr/bin/env python3
+"""Throughput of the batched rigid-body dynamics hot path on GB300.
+
+Workload: the branched 11-DOF spined-quadruped tree (3-joint spine on a
+fixed base, rear leg pair off the first spine link, front pair off the last;
+depth 5), seeded random inertias, B = 4096 environments. One step = one pass
+of every operator over the batch: FK of all bodies, the four foot Jacobians,
+RNEA, CRBA and ABA.
+
+Metric: env-evals/s = environments x steps / device time (higher is
+better). Inputs and outputs rotate over enough replica sets (> 2x the
+129 MB L2) that every step reads and writes HBM.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl fst|reference]
+
+Under torchrun every rank runs an independent replica of the workload on its
+own GPU (environments are independent; there is no collective on the data
+path); rank 0 prints one JSON line with the whole-job throughput.
+`--impl reference` times the FP64 CPU oracle on a bounded sample instead.
+"""
+from __future__ import annotations
+
+import os
+
+for _v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
+import argparse
+import ctypes
+import json
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "env-evals/s for FK/Jac/RNEA/CRBA/ABA @4096 envs; RNEA fwd+bwd/s vs plain"
+L2_BYTES = 129 * 2 ** 20
+FP32_LANES_PER_SM, N_SM = 128, 152
+OPS = ("fk", "jacobian", "rnea", "crba", "aba")
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return {"hbm_gbs": float(d["hbm_gbs"]), "sm_max_mhz": float(d.get("sm_max_mhz", 2070.0)), "src": "measured"}
+    return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0, "src": "fallback"}
+
+
+def fp32_peak_tflops(sm_mhz):
+    # 152 SMs x 128 FP32 lanes x 2 flops per FMA x clock
+    return N_SM * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+
+
+def workload():
+    from paper_2605_31481_gb300 import workloads as w
+    tree = w.spined_quadruped(seed=0)
+    return tree, 4096, list(tree.ee)
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    """nvidia-smi samples (100 ms period) of SM clock and throttle reasons;
+    stats are taken over the samples whose timestamps fall in the timed
+    region (or, if the region is shorter than the period, over the samples
+    of the loaded soak just before it, flagged in_region=false)."""
+    FIELDS = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+    NAMES = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.marks = {}
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def mark(self, name):
+        self.marks[name] = time.time()
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        time.sleep(0.2)
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        import datetime
+        rows = []
+        for line in out.strip().splitlines():
+            r = [x.strip() for x in line.split(",")]
+            try:
+                ts = datetime.datetime.strptime(r[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                rows.append((ts, float(r[1]), float(r[2]), float(r[3]), [v.lower() == "active" for v in r[4:8]]))
+            except (ValueError, IndexError):
+                continue
+
+        def stats(lo, hi):
+            sel = [x for x in rows if lo <= x[0] <= hi]
+            if not sel:
+                return None
+            reasons = sorted({n for x in sel for n, a in zip(self.NAMES, x[4]) if a})
+            return {"sm_mhz": statistics.median(x[1] for x in sel), "sm_max_mhz": max(x[2] for x in sel),
+                    "power_w_median": statistics.median(x[3] for x in sel), "reasons": reasons, "samples": len(sel)}
+
+        st = stats(self.marks.get("t0", 0), self.marks.get("t1", 0))
+        if st is not None:
+            st["in_region"] = True
+            return st
+        st = stats(self.marks.get("soak", 0), self.marks.get("t1", 0))
+        if st is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0, "in_region": False}
+        st["in_region"] = False
+        return st
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def run_fst(args):
+    import torch
+    import torch.distributed as dist
+
+    import __graft_entry__
+    from paper_2605_31481_gb300 import _ffi, costs
+    from paper_2605_31481_gb300 import workloads as w
+    import paper_2605_31481_gb300 as fst
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    __graft_entry__.build()
+    L = _ffi.lib()
+
+    tree, B, links = workload()
+    model = fst.Model(tree)
+    nq, nv, nb, nl = tree.nq, tree.nv, tree.n_bodies, len(links)
+    out_floats = nb * 12 + nl * 6 * nv + nv + nv * nv + nv
+    in_floats = nq + 3 * nv
+    set_bytes = 4 * B * (in_floats + out_floats)
+    R = max(2, int(np.ceil(2 * L2_BYTES / set_bytes)) + 1)
+    st = w.random_state(tree, B * R, seed=1 + 1000 * rank)
+    dev = torch.device("cuda", local)
+
+    def soa(x, r):
+        return torch.from_numpy(np.ascontiguousarray(x[r * B:(r + 1) * B].T.astype(np.float32))).to(dev)
+
+    sets = []
+    for r in range(R):
+        d = {k: soa(st[k], r) for k in ("q", "qd", "qdd", "tau")}
+        d["poses"] = torch.empty((nb, 12, B), device=dev)
+        d["J"] = torch.empty((nl, 6, nv, B), device=dev)
+        d["tau_out"] = torch.empty((nv, B), device=dev)
+        d["M"] = torch.empty((nv, nv, B), device=dev)
+        d["qdd_out"] = torch.empty((nv, B), device=dev)
+        d["p"] = {k: ctypes_ptr(v) for k, v in d.items()}
+        sets.append(d)
+    links_arr = (ctypes.c_int32 * nl)(*links)
+    stream = torch.cuda.current_stream()
+    sp = ctypes.c_void_p(stream.cuda_stream)
+    h = model.handle
+
+    def launch(op, p):
+        if op == "fk":
+            return L.fst_fk(h, B, p["q"], p["poses"], sp)
+        if op == "jacobian":
+            return L.fst_jacobian(h, B, p["q"], links_arr, nl, p["J"], sp)
+        if op == "rnea":
+            return L.fst_rnea(h, B, p["q"], p["qd"], p["qdd"], None, p["tau_out"], sp)
+        if op == "crba":
+            return L.fst_crba(h, B, p["q"], None, p["M"], sp)
+        return L.fst_aba(h, B, p["q"], p["qd"], p["tau"], None, p["qdd_out"], sp)
+
+    def step(k, evs=None):
+        p = sets[k % R]["p"]
+        for j, op in enumerate(OPS):
+            if evs is not None:
+                evs[k][j].record(stream)
+            st_ = launch(op, p)
+            if st_ != 0:
+                raise RuntimeError(f"{op}: {L.fst_last_error().decode()}")
+        if evs is not None:
+            evs[k][len(OPS)].record(stream)
+
+    # parity guard: the timed launches must reproduce the oracle on a sample
+    step(0)
+    torch.cuda.synchronize()
+    parity = parity_guard(torch, tree, links, st, sets[0], B)
+
+    for k in range(args.warmup):
+        step(k)
+    torch.cuda.synchronize()
+
+    K = args.steps
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(len(OPS) + 1)] for _ in range(K)]
+    clk = ClockSampler(local)
+    clk.start()
+    time.sleep(0.15)
+    # loaded soak (untimed) so the clocks are at their loaded state
+    clk.mark("soak")
+    t_soak = time.time()
+    k = 0
+    while time.time() - t_soak < 0.5:
+        for _ in range(50):
+            step(k)
+            k += 1
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk.mark("t0")
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for k in range(K):
+        step(k, evs)
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    clk.mark("t1")
+    if world > 1:
+        dist.barrier()
+    clocks = clk.stop()
+    ms = t_start.elapsed_time(t_end)
+    per_op_ms = {op: float(np.mean([evs[k][j].elapsed_time(evs[k][j + 1]) for k in range(K)])) for j, op in enumerate(OPS)}
+
+    if world > 1:
+        tt = torch.tensor([ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    value = world * B * K / (ms / 1e3)
+
+    # end to end through the public binding, host buffers in and out
+    e2e = run_e2e(torch, fst, model, tree, B, links, st, dev, K, args.warmup)
+    if world > 1:
+        tt = torch.tensor([e2e["ms"]], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e["ms"] = float(tt.item())
+    e2e_value = world * B * K / (e2e["ms"] / 1e3)
+
+    pk = peaks()
+    dom = max(per_op_ms, key=per_op_ms.get)
+    fl = costs.flops(tree, dom, links=links if dom == "jacobian" else ())
+    by = costs.io_bytes(tree, dom, n_links=nl)
+    t_dom = per_op_ms[dom] / 1e3
+    p_alu = fp32_peak_tflops(pk["sm_max_mhz"])
+    bound = "alu" if fl / (p_alu * 1e12) > by / (pk["hbm_gbs"] * 1e9) else "hbm"
+    if bound == "alu":
+        achieved = fl * B / t_dom / 1e12
+        roof = {"bound": "alu", "achieved": round(achieved, 4), "peak": round(p_alu, 2), "unit": "TFLOP/s",
+                "frac": round(achieved / p_alu, 5), "traffic": args.traffic,
+                "kernel": f"{dom}_kernel", "peak_src": f"derived: 152 SMs x 128 FP32 lanes x 2 x {pk['sm_max_mhz']:.0f} MHz",
+                "algorithmic_flops_per_launch": fl * B, "algorithmic_bytes_per_launch": by * B}
+    else:
+        achieved = by * B / t_dom / 1e9
+        roof = {"bound": "hbm", "achieved": round(achieved, 2), "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": round(achieved / pk["hbm_gbs"], 5), "traffic": args.traffic, "kernel": f"{dom}_kernel",
+                "peak_src": pk["src"], "algorithmic_bytes_per_launch": by * B}
+
+    if rank == 0:
+        cpu = cpu_baseline(tree, links, args)
+        line = {
+            "metric": METRIC, "value": round(value, 1), "unit": "env-evals/s", "n_gpus": world, "steps": K,
+            "warmup": args.warmup, "ms_per_step": round(ms / K, 5), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"{tree.name}: 11 revolute DOF branched tree, depth 5, B=4096 per GPU",
+                       "B": B, "step": "+".join(OPS) + " (4 foot Jacobians)",
+                       "l2": f"inputs/outputs rotate over {R} sets of {set_bytes / 2**20:.1f} MiB (> 2x L2)",
+                       "parallelism": f"replicas x{world}"},
+            "per_op_ms": {k: round(v, 5) for k, v in per_op_ms.items()},
+            "per_op_env_evals_per_s": {k: round(B / (v / 1e3), 1) for k, v in per_op_ms.items()},
+            "roofline": roof,
+            "e2e": {"value": round(e2e_value, 1), "unit": "env-evals/s", "h2d_bytes_per_step": e2e["h2d"],
+                    "d2h_bytes_per_step": e2e["d2h"]},
+            "gpu_launches": K * len(OPS),
+            "parity_guard": parity,
+            "clocks": clocks,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def parity_guard(torch, tree, links, st, d, B, n=64):
+    """Max normwise error of the timed path's outputs on n sampled envs."""
+    from oracle import rbd
+    idx = np.linspace(0, B - 1, n).astype(int)
+    s = {k: st[k][idx] for k in ("q", "qd", "qdd", "tau")}
+    T = rbd.fk(tree, s["q"])
+    ref = {"poses": np.concatenate([T[..., :3, :3].reshape(n, -1, 9), T[..., :3, 3]], -1),
+           "J": np.stack([rbd.jacobian(tree, s["q"], l) for l in links], 1),
+           "tau_out": rbd.rnea(tree, s["q"], s["qd"], s["qdd"]),
+           "M": rbd.crba(tree, s["q"]),
+           "qdd_out": rbd.aba(tree, s["q"], s["qd"], s["tau"])}
+    tol = {"poses": 1e-5, "J": 1e-5, "tau_out": 1e-4, "M": 1e-4, "qdd_out": 1e-4}
+    out = {}
+    for k, r in ref.items():
+        g = np.moveaxis(d[k].cpu().numpy().astype(np.float64), -1, 0)[idx].reshape(n, -1)
+        r = r.reshape(n, -1)
+        err = float((np.abs(g - r).max(1) / np.maximum(np.abs(r).max(1), 1.0)).max())
+        if not err <= tol[k]:
+            raise RuntimeError(f"parity guard failed: {k} error {err:.3e} > {tol[k]}")
+        out[k] = float(f"{err:.2e}")
+    return out
+
+
+def ctypes_ptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def run_e2e(torch, fst, model, tree, B, links, st, dev, K, warmup):
+    """Same step through the public binding, with the inputs copied from
+    pinned host memory and every output read back to pinned host memory."""
+    nq, nv, nb, nl = tree.nq, tree.nv, tree.n_bodies, len(links)
+    host_in = {k: torch.from_numpy(np.ascontiguousarray(st[k][:B].T.astype(np.float32))).pin_memory()
+               for k in ("q", "qd", "qdd", "tau")}
+    dev_in = {k: torch.empty_like(v, device=dev) for k, v in host_in.items()}
+    shapes = {"poses": (nb, 12, B), "J": (nl, 6, nv, B), "tau": (nv, B), "M": (nv, nv, B), "qdd": (nv, B)}
+    dev_out = {k: torch.empty(s, device=dev) for k, s in shapes.items()}
+    host_out = {k: torch.empty(s).pin_memory() for k, s in shapes.items()}
+
+    def step():
+        for k in dev_in:
+            dev_in[k].copy_(host_in[k], non_blocking=True)
+        fst.fk(model, dev_in["q"], out=dev_out["poses"])
+        fst.jacobian(model, dev_in["q"], links, out=dev_out["J"])
+        fst.rnea(model, dev_in["q"], dev_in["qd"], dev_in["qdd"], out=dev_out["tau"])
+        fst.crba(model, dev_in["q"], out=dev_out["M"])
+        fst.aba(model, dev_in["q"], dev_in["qd"], dev_in["tau"], out=dev_out["qdd"])
+        for k in dev_out:
+            host_out[k].copy_(dev_out[k], non_blocking=True)
+
+    for _ in range(max(3, warmup // 10)):
+        step()
+    torch.cuda.synchronize()
+    s = torch.cuda.current_stream()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(s)
+    for _ in range(K):
+        step()
+    b.record(s)
+    torch.cuda.synchronize()
+    h2d = sum(v.numel() * 4 for v in host_in.values())
+    d2h = sum(v.numel() * 4 for v in host_out.values())
+    return {"ms": a.elapsed_time(b), "h2d": h2d, "d2h": d2h}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (baseline and reference arm)
+# ---------------------------------------------------------------------------
+
+def oracle_step(tree, links, s):
+    from oracle import rbd
+    rbd.fk(tree, s["q"])
+    for l in links:
+        rbd.jacobian(tree, s["q"], l)
+    rbd.rnea(tree, s["q"], s["qd"], s["qdd"])
+    rbd.crba(tree, s["q"])
+    rbd.aba(tree, s["q"], s["qd"], s["tau"])
+
+
+def cpu_baseline(tree, links, args, budget_s=12.0):
+    from paper_2605_31481_gb300 import workloads as w
+    Bs = 512
+    s = w.random_state(tree, Bs, seed=1)
+    oracle_step(tree, links, s)
+    n, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < budget_s:
+        oracle_step(tree, links, s)
+        n += 1
+    dt = time.perf_counter() - t0
+    return {"value": round(n * Bs / dt, 1), "unit": "env-evals/s", "cores": 1, "kind": "oracle",
+            "sample": f"{n} passes of FK+4 Jacobians+RNEA+CRBA+ABA over {Bs} envs of the same tree (FP64 numpy, "
+                      f"1 thread, {dt:.1f} s)"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_2605_31481_gb300 import workloads as w
+    tree, B, links = workload()
+    Bs = 256
+    s = w.random_state(tree, Bs, seed=1)
+    for _ in range(args.warmup):
+        oracle_step(tree, links, s)
+    t = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle_step(tree, links, s)
+        t.append(time.perf_counter() - t0)
+    tot = sum(t)
+    value = Bs * args.steps / tot
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 1), "unit": "env-evals/s",
+        "n_gpus": int(os.environ.get("WORLD_SIZE", "1")), "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(1e3 * tot / args.steps, 3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"{tree.name}: 11 revolute DOF branched tree, depth 5, B=4096",
+                   "B": B, "step": "+".join(OPS) + " (4 foot Jacobians)", "sample_envs_per_step": Bs},
+        "cpu_baseline": {"value": round(value, 1), "unit": "env-evals/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{Bs} of the 4096 envs per step, FP64 numpy oracle, 1 thread"},
+        "e2e": {"value": round(value, 1), "unit": "env-evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=200)
+    ap.add_argument("--impl", choices=("fst", "reference"), default="fst")
+    ap.add_argument("--traffic", type=float, default=None,
+                    help="dram bytes per launch of the dominant kernel from an ncu capture (else null)")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_fst(args)
+
+
+if __name__ == "__main__":
+    main()
