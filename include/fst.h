@@ -146,6 +146,31 @@ FST_API fst_status fst_aba(const fst_model* model, int64_t B, const float* q,
                    const float* qd, const float* tau, const float* theta,
                    float* qdd, void* stream);
 
+/* Inputs and outputs of fst_eval. Inputs: q always; qd and qdd when tau_out
+ * is requested; qd and tau when qdd_out is requested. Outputs: any subset,
+ * NULL = not computed. links/n_links (HOST array) are used when J is set. */
+typedef struct fst_eval_io {
+  const float* q;        /* [nq][B] */
+  const float* qd;       /* [nv][B] */
+  const float* qdd;      /* [nv][B] */
+  const float* tau;      /* [nv][B] */
+  float* poses;          /* [n_b][12][B]        as fst_fk */
+  float* J;              /* [n_links][6][nv][B] as fst_jacobian */
+  const int32_t* links;
+  int32_t n_links;
+  float* tau_out;        /* [nv][B]             as fst_rnea (inputs q, qd, qdd) */
+  float* M;              /* [nv][nv][B]         as fst_crba */
+  float* qdd_out;        /* [nv][B]             as fst_aba (inputs q, qd, tau) */
+} fst_eval_io;
+
+/* Every requested operator of one batch in ONE launch. The paper computes
+ * only the kinematic tiers a query needs (Sec. 3.1); here the operators
+ * whose outputs are NULL are skipped and the others run side by side on the
+ * GPU, one group of thread blocks per operator. Results are bit-identical
+ * to the per-operator calls. theta as in fst_rnea. */
+FST_API fst_status fst_eval(const fst_model* model, int64_t B, const fst_eval_io* io,
+                            const float* theta, void* stream);
+
 /* Message for the last non-OK status on this thread ("" if none). */
 FST_API const char* fst_last_error(void);
 

@@ -43,6 +43,15 @@ class FstError(RuntimeError):
         self.status = status
 
 
+class EvalIO(ctypes.Structure):
+    """fst_eval_io: inputs and requested outputs of one fused evaluation."""
+    _fields_ = [
+        ("q", c_void_p), ("qd", c_void_p), ("qdd", c_void_p), ("tau", c_void_p),
+        ("poses", c_void_p), ("J", c_void_p), ("links", ctypes.POINTER(c_int32)), ("n_links", c_int32),
+        ("tau_out", c_void_p), ("M", c_void_p), ("qdd_out", c_void_p),
+    ]
+
+
 # (name, restype, argtypes); pointers to device memory travel as c_void_p
 _SIGS = {
     "fst_model_create": (c_int32, [ctypes.POINTER(BodyDesc), c_int32, ctypes.POINTER(c_double), ctypes.POINTER(c_void_p)]),
@@ -54,6 +63,7 @@ _SIGS = {
     "fst_rnea": (c_int32, [c_void_p, c_int64, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "fst_crba": (c_int32, [c_void_p, c_int64, c_void_p, c_void_p, c_void_p, c_void_p]),
     "fst_aba": (c_int32, [c_void_p, c_int64, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "fst_eval": (c_int32, [c_void_p, c_int64, ctypes.POINTER(EvalIO), c_void_p, c_void_p]),
     "fst_last_error": (ctypes.c_char_p, []),
     "fst_version": (ctypes.c_char_p, []),
 }

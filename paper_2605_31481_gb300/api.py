@@ -167,3 +167,49 @@ def aba(model: Model, q, qd, tau, theta=None, out=None):
     check(_ffi.lib().fst_aba(model.handle, B, _ptr(q), _ptr(qd), _ptr(tau), _ptr(_theta(theta, model)),
                              _ptr(out), _stream()))
     return out
+
+
+def eval(model: Model, q, qd=None, qdd=None, tau=None, *, fk=False, links=None, rnea=False, crba=False,
+         aba=False, theta=None, out=None):
+    """Every requested operator in one fused launch (fst_eval).
+
+    fk=True requests poses; links=[...] the Jacobians of those bodies;
+    rnea=True tau (needs qd, qdd); crba=True M; aba=True qdd (needs qd, tau).
+    Returns a dict with the requested outputs ("poses", "J", "tau", "M",
+    "qdd"); `out` may supply preallocated tensors under the same keys."""
+    B = _check_in(q, model.nq, "q", model)
+    out = dict(out or {})
+    io = _ffi.EvalIO()
+    io.q = q.data_ptr()
+    if rnea or aba:
+        _check_in(qd, model.nv, "qd", model)
+        io.qd = qd.data_ptr()
+    if rnea:
+        _check_in(qdd, model.nv, "qdd", model)
+        io.qdd = qdd.data_ptr()
+    if aba:
+        _check_in(tau, model.nv, "tau", model)
+        io.tau = tau.data_ptr()
+    res = {}
+    if fk:
+        res["poses"] = _out(out.get("poses"), (model.n_bodies, 12, B), model)
+        io.poses = res["poses"].data_ptr()
+    link_arr = None
+    if links:
+        links = [int(l) for l in links]
+        link_arr = (ctypes.c_int32 * len(links))(*links)
+        res["J"] = _out(out.get("J"), (len(links), 6, model.nv, B), model)
+        io.J = res["J"].data_ptr()
+        io.links = link_arr
+        io.n_links = len(links)
+    if rnea:
+        res["tau"] = _out(out.get("tau"), (model.nv, B), model)
+        io.tau_out = res["tau"].data_ptr()
+    if crba:
+        res["M"] = _out(out.get("M"), (model.nv, model.nv, B), model)
+        io.M = res["M"].data_ptr()
+    if aba:
+        res["qdd"] = _out(out.get("qdd"), (model.nv, B), model)
+        io.qdd_out = res["qdd"].data_ptr()
+    check(_ffi.lib().fst_eval(model.handle, B, ctypes.byref(io), _ptr(_theta(theta, model)), _stream()))
+    return res

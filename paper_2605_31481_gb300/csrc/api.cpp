@@ -190,4 +190,50 @@ fst_status fst_aba(const fst_model* m, int64_t B, const float* q, const float* q
   return finish(fn, launch_aba(view_of(m, theta), B, q, qd, tau, qdd, launch_of(B, stream)));
 }
 
+fst_status fst_eval(const fst_model* m, int64_t B, const fst_eval_io* io, const float* theta, void* stream) {
+  static const char* fn = "fst_eval";
+  if (!io) return set_error(FST_ERR_INVALID_ARG, "fst_eval: null io");
+  bool skip;
+  FST_CHECK(check_call(fn, m, B, &skip));
+  EvalArgs a{};
+  a.q = io->q;
+  a.qd = io->qd;
+  a.qdd = io->qdd;
+  a.tau = io->tau;
+  a.poses = io->poses;
+  a.J = io->J;
+  a.tau_out = io->tau_out;
+  a.M = io->M;
+  a.qdd_out = io->qdd_out;
+  if (io->J) {
+    if (!io->links || io->n_links < 1 || io->n_links > FST_MAX_LINKS)
+      return set_error(FST_ERR_INVALID_ARG, "fst_eval: J needs 1 <= n_links <= FST_MAX_LINKS links");
+    a.links.n = io->n_links;
+    for (int l = 0; l < io->n_links; ++l) {
+      if (io->links[l] < 0 || io->links[l] >= m->n) return set_error(FST_ERR_INVALID_ARG, "fst_eval: link index out of range");
+      a.links.idx[l] = io->links[l];
+    }
+  }
+  const bool dyn = m->nv > 0;
+  if (io->qdd_out && dyn) {
+    FST_CHECK(need(fn, io->qd, "qd"));
+    FST_CHECK(need(fn, io->tau, "tau"));
+    a.roles[a.n_roles++] = ROLE_ABA;
+  }
+  if (io->M && dyn) a.roles[a.n_roles++] = ROLE_CRBA;
+  if (io->tau_out && dyn) {
+    FST_CHECK(need(fn, io->qd, "qd"));
+    FST_CHECK(need(fn, io->qdd, "qdd"));
+    a.roles[a.n_roles++] = ROLE_RNEA;
+  }
+  if (io->poses || (io->J && dyn)) {
+    if (!io->poses) a.poses = nullptr;
+    if (!dyn) a.J = nullptr;
+    a.roles[a.n_roles++] = ROLE_KIN;
+  }
+  if (skip || a.n_roles == 0) return FST_OK;
+  if (m->nq) FST_CHECK(need(fn, io->q, "q"));
+  return finish(fn, launch_eval(view_of(m, theta), B, a, launch_of(B, stream)));
+}
+
 }  // extern "C"

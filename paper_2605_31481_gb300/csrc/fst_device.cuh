@@ -304,6 +304,16 @@ __device__ __forceinline__ SmemModel stage_model(const ModelView& mv, float4* sm
 
 __host__ __device__ inline size_t smem_bytes(int n) { return (size_t)n * (sizeof(BodyC) + sizeof(BodyI)); }
 
+// Dynamic shared memory of a kernel: the model, then a float tile of
+// `rows` staged input rows for each of the block's environments.
+__host__ __device__ inline size_t smem_bytes(int n, int rows, int block) {
+  return smem_bytes(n) + (size_t)rows * block * sizeof(float);
+}
+
+__device__ __forceinline__ float* smem_tile(float4* smem, int n) {
+  return reinterpret_cast<float*>(reinterpret_cast<char*>(smem) + smem_bytes(n));
+}
+
 // Rotation matrix of the quaternion (x, y, z, w), normalised first.
 __device__ __forceinline__ void quat_R(float x, float y, float z, float w, float* R) {
   float s = rsqrtf(fmaf(x, x, fmaf(y, y, fmaf(z, z, w * w))));
@@ -322,33 +332,57 @@ __device__ __forceinline__ void quat_R(float x, float y, float z, float w, float
   R[8] = 1.f - 2.f * (x * x + y * y);
 }
 
+// One environment's column of a staged [field][envs-per-block] tile in
+// shared memory: element k is p[k * ld]. Consecutive threads hold
+// consecutive environments, so a warp's accesses hit 32 distinct banks.
+struct Col {
+  const float* p;
+  int ld;
+  __device__ __forceinline__ float operator[](int k) const { return p[k * ld]; }
+};
+
+// Asynchronous 4-byte global -> shared copies (no register staging, so a
+// thread issues all of its environment's loads before waiting on any).
+__device__ __forceinline__ void cp_async4(float* smem_dst, const float* gmem_src) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// Stages rows [0, rows) of a [rows][B] array for this thread's environment
+// into tile[row * blockDim.x + threadIdx.x]. Only the calling thread reads
+// its own column afterwards, so the thread's own wait is enough.
+__device__ __forceinline__ Col stage_rows(float* tile, const float* __restrict__ src, int rows, int64_t B, int64_t e) {
+  float* dst = tile + threadIdx.x;
+  for (int k = 0; k < rows; ++k) cp_async4(dst + k * blockDim.x, src + (int64_t)k * B + e);
+  return Col{dst, (int)blockDim.x};
+}
+
 // Pose of body i in its parent from q (paper Eq. 4-5 for revolute joints).
 // sin q and 1 - cos q come from one sincos of q/2: sin q = 2 s c,
 // 1 - cos q = 2 s^2, which keeps 1 - cos q accurate near q = 0.
-__device__ __forceinline__ Xf joint_X(const BodyC& c, const BodyI& b, const float* __restrict__ q, int64_t B,
-                                      int64_t e) {
+__device__ __forceinline__ Xf joint_X(const BodyC& c, const BodyI& b, const Col& q) {
   Xf X;
   if (b.type == FST_JOINT_REVOLUTE) {
-    float qi = __ldg(q + (int64_t)b.qi * B + e);
+    const float qi = q[b.qi];
     float sh, ch;
     sincosf(0.5f * qi, &sh, &ch);
-    float s = 2.f * sh * ch;
-    float omc = 2.f * sh * sh;
+    const float s = 2.f * sh * ch;
+    const float omc = 2.f * sh * sh;
 #pragma unroll
     for (int k = 0; k < 9; ++k) X.R[k] = fmaf(omc, c.Bm[k], fmaf(s, c.A[k], c.R0[k]));
 #pragma unroll
     for (int k = 0; k < 3; ++k) X.t[k] = fmaf(omc, c.b[k], fmaf(s, c.a[k], c.t0[k]));
   } else if (b.type == FST_JOINT_PRISMATIC) {
-    float qi = __ldg(q + (int64_t)b.qi * B + e);
+    const float qi = q[b.qi];
 #pragma unroll
     for (int k = 0; k < 9; ++k) X.R[k] = c.R0[k];
 #pragma unroll
     for (int k = 0; k < 3; ++k) X.t[k] = fmaf(qi, c.a[k], c.t0[k]);
   } else if (b.type == FST_JOINT_FREE) {
-    const float* qb = q + (int64_t)b.qi * B + e;
-    float p[3] = {__ldg(qb), __ldg(qb + B), __ldg(qb + 2 * B)};
+    const float p[3] = {q[b.qi], q[b.qi + 1], q[b.qi + 2]};
     float Rq[9];
-    quat_R(__ldg(qb + 3 * B), __ldg(qb + 4 * B), __ldg(qb + 5 * B), __ldg(qb + 6 * B), Rq);
+    quat_R(q[b.qi + 3], q[b.qi + 4], q[b.qi + 5], q[b.qi + 6], Rq);
     // T_joint * (Rq, p)
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
@@ -368,18 +402,12 @@ __device__ __forceinline__ Xf joint_X(const BodyC& c, const BodyI& b, const floa
 
 __device__ __forceinline__ SV S_of(const BodyC& c) { return SV{f3{c.S[0], c.S[1], c.S[2]}, f3{c.S[3], c.S[4], c.S[5]}}; }
 
-// S_i x_i for joint-space x ([nv][B] layout); the free joint maps its
-// velocity coordinates [v; w] to spatial (w, v).
-__device__ __forceinline__ SV S_times(const BodyC& c, const BodyI& b, const float* __restrict__ x, int64_t B,
-                                      int64_t e) {
-  if (b.type == FST_JOINT_REVOLUTE || b.type == FST_JOINT_PRISMATIC) {
-    float xi = __ldg(x + (int64_t)b.vi * B + e);
-    return xi * S_of(c);
-  }
-  if (b.type == FST_JOINT_FREE) {
-    const float* p = x + (int64_t)b.vi * B + e;
-    return SV{f3{__ldg(p + 3 * B), __ldg(p + 4 * B), __ldg(p + 5 * B)}, f3{__ldg(p), __ldg(p + B), __ldg(p + 2 * B)}};
-  }
+// S_i x_i for a joint-space column x; the free joint maps its velocity
+// coordinates [v; w] to spatial (w, v).
+__device__ __forceinline__ SV S_times(const BodyC& c, const BodyI& b, const Col& x) {
+  if (b.type == FST_JOINT_REVOLUTE || b.type == FST_JOINT_PRISMATIC) return x[b.vi] * S_of(c);
+  if (b.type == FST_JOINT_FREE)
+    return SV{f3{x[b.vi + 3], x[b.vi + 4], x[b.vi + 5]}, f3{x[b.vi], x[b.vi + 1], x[b.vi + 2]}};
   return sv_zero();
 }
 

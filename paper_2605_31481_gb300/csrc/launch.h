@@ -3,6 +3,10 @@
 
 #include <cuda_runtime.h>
 
+#include <cstdlib>
+#include <mutex>
+#include <unordered_map>
+
 #include "fst_internal.h"
 
 namespace fst {
@@ -10,6 +14,25 @@ namespace fst {
 struct LinkList {
   int n;
   int idx[FST_MAX_LINKS];
+};
+
+// Operators of the fused evaluation kernel, in launch order (longest first,
+// so the slowest role's blocks are dispatched first).
+enum Role { ROLE_ABA = 0, ROLE_CRBA = 1, ROLE_RNEA = 2, ROLE_KIN = 3 };
+
+struct EvalArgs {
+  const float* q;
+  const float* qd;
+  const float* qdd;
+  const float* tau;
+  float* poses;
+  float* J;
+  float* tau_out;
+  float* M;
+  float* qdd_out;
+  LinkList links;
+  int roles[4];
+  int n_roles;
 };
 
 struct Launch {
@@ -43,6 +66,27 @@ inline int default_block(int64_t B) {
 
 inline unsigned grid_for(int64_t B, int block) { return (unsigned)((B + block - 1) / block); }
 
+// Per-kernel launch attributes, set once per kernel (and again only when a
+// launch needs more dynamic shared memory than configured so far):
+//  * the dynamic shared-memory limit, when above the 48 KB default;
+//  * the shared-memory carveout: just enough shared memory for ~4 resident
+//    blocks, leaving the rest of the 256 KB unified L1 for the per-thread
+//    sweep state (local memory). FST_SMEM_CARVEOUT=<percent> overrides it.
+template <typename K>
+inline void prepare(K* kernel, size_t smem) {
+  static std::mutex mu;
+  static std::unordered_map<const void*, size_t> done;
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = done.find((const void*)kernel);
+  if (it != done.end() && it->second >= smem) return;
+  if (smem > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int pct = (int)((4 * smem * 100 + 228 * 1024 - 1) / (228 * 1024));
+  if (const char* env = std::getenv("FST_SMEM_CARVEOUT")) pct = std::atoi(env);
+  pct = pct < 0 ? 0 : (pct > 100 ? 100 : pct);
+  cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+  done[(const void*)kernel] = smem;
+}
+
 // Kernel launchers (return the cudaGetLastError() after the launch).
 cudaError_t launch_fk(const ModelView& mv, int64_t B, const float* q, float* poses, const Launch& L);
 cudaError_t launch_jacobian(const ModelView& mv, int64_t B, const float* q, const LinkList& links, float* J,
@@ -51,6 +95,7 @@ cudaError_t launch_rnea(const ModelView& mv, int64_t B, const float* q, const fl
                         float* tau, const Launch& L);
 cudaError_t launch_crba(const ModelView& mv, int64_t B, const float* q, float* M,
                         const Launch& L);
+cudaError_t launch_eval(const ModelView& mv, int64_t B, const EvalArgs& a, const Launch& L);
 cudaError_t launch_aba(const ModelView& mv, int64_t B, const float* q, const float* qd, const float* tau,
                        float* qdd, const Launch& L);
 

@@ -1,0 +1,357 @@
+// Per-environment bodies of the five operators. Each runs in one thread,
+// reads its environment's inputs from a staged shared-memory column and
+// writes its outputs straight to global memory (coalesced across the warp:
+// consecutive threads hold consecutive environments of a [field][B] array).
+// The per-operator kernels and the fused evaluation kernel both call these,
+// so every launch form computes bit-identical results.
+#pragma once
+
+#include "fst_device.cuh"
+#include "launch.h"
+
+namespace fst {
+
+__device__ __forceinline__ SV world_accel(const ModelView& mv) {
+  return SV{f3{0.f, 0.f, 0.f}, f3{mv.a0[0], mv.a0[1], mv.a0[2]}};
+}
+
+// world pose of body i from its parent's world pose and its local transform
+__device__ __forceinline__ void compose(const float* Rp, const float* pp, const Xf& X, float* R, float* p) {
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+#pragma unroll
+    for (int cc = 0; cc < 3; ++cc)
+      R[3 * r + cc] = fmaf(Rp[3 * r], X.R[cc], fmaf(Rp[3 * r + 1], X.R[3 + cc], Rp[3 * r + 2] * X.R[6 + cc]));
+    p[r] = fmaf(Rp[3 * r], X.t[0], fmaf(Rp[3 * r + 1], X.t[1], fmaf(Rp[3 * r + 2], X.t[2], pp[r])));
+  }
+}
+
+// Forward kinematics (tier 3 of the paper's cache, Sec. 3.1), world poses
+// kept in Rw/pw for the caller (the Jacobian reuses them).
+template <int NB>
+__device__ __forceinline__ void world_poses(const SmemModel& sm, const Col& q, float (&Rw)[NB][9], float (&pw)[NB][3],
+                                            float* __restrict__ poses, int64_t B, int64_t e) {
+  for (int i = 0; i < sm.n; ++i) {
+    const BodyI bi = sm.i[i];
+    const Xf X = joint_X(sm.c[i], bi, q);
+    if (bi.parent < 0) {
+#pragma unroll
+      for (int k = 0; k < 9; ++k) Rw[i][k] = X.R[k];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) pw[i][k] = X.t[k];
+    } else {
+      compose(Rw[bi.parent], pw[bi.parent], X, Rw[i], pw[i]);
+    }
+    if (poses) {
+      float* out = poses + (int64_t)i * 12 * B + e;
+#pragma unroll
+      for (int k = 0; k < 9; ++k) out[(int64_t)k * B] = Rw[i][k];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) out[(int64_t)(9 + k) * B] = pw[i][k];
+    }
+  }
+}
+
+template <int NB>
+__device__ __forceinline__ void fk_env(const SmemModel& sm, const Col& q, float* __restrict__ poses, int64_t B,
+                                       int64_t e) {
+  float Rw[NB][9];
+  float pw[NB][3];
+  world_poses<NB>(sm, q, Rw, pw, poses, B, e);
+}
+
+// Jacobian columns straight from the world poses (paper Sec. 3.4, Eq. 6):
+// w = R_k S_w, v = R_k S_v + p_k x w, i.e. [o_k x z_k; z_k] for a revolute
+// joint with o_k on its axis. Rows are [v; w]; off-path DOFs are zero.
+template <int NB>
+__device__ __forceinline__ void jac_env(const SmemModel& sm, const Col& q, int nv, const LinkList& links,
+                                        float* __restrict__ poses, float* __restrict__ J, int64_t B, int64_t e) {
+  float Rw[NB][9];
+  float pw[NB][3];
+  world_poses<NB>(sm, q, Rw, pw, poses, B, e);
+  for (int l = 0; l < links.n; ++l) {
+    const unsigned long long mask = sm.c[links.idx[l]].anc;
+    float* Jl = J + (int64_t)l * 6 * nv * B + e;
+    for (int k = 0; k < sm.n; ++k) {
+      const BodyI bk = sm.i[k];
+      const int nvk = nv_of(bk.type);
+      if (nvk == 0) continue;
+      const bool on_path = (mask >> k) & 1ull;
+      const f3 p = f3{pw[k][0], pw[k][1], pw[k][2]};
+      if (nvk == 1) {
+        float col[6] = {0, 0, 0, 0, 0, 0};
+        if (on_path) {
+          const SV s = S_of(sm.c[k]);
+          const f3 w = Rmul(Rw[k], s.w);
+          const f3 v = Rmul(Rw[k], s.v) + cross(p, w);
+          col[0] = v.x; col[1] = v.y; col[2] = v.z;
+          col[3] = w.x; col[4] = w.y; col[5] = w.z;
+        }
+#pragma unroll
+        for (int r = 0; r < 6; ++r) Jl[((int64_t)r * nv + bk.vi) * B] = col[r];
+      } else {  // free base: velocity [v; w] in body coordinates
+#pragma unroll
+        for (int j = 0; j < 6; ++j) {
+          float col[6] = {0, 0, 0, 0, 0, 0};
+          if (on_path) {
+            const int a = j % 3;
+            const f3 Re = f3{Rw[k][a], Rw[k][3 + a], Rw[k][6 + a]};  // R e_a
+            if (j < 3) {
+              col[0] = Re.x; col[1] = Re.y; col[2] = Re.z;
+            } else {
+              const f3 v = cross(p, Re);
+              col[0] = v.x; col[1] = v.y; col[2] = v.z;
+              col[3] = Re.x; col[4] = Re.y; col[5] = Re.z;
+            }
+          }
+#pragma unroll
+          for (int r = 0; r < 6; ++r) Jl[((int64_t)r * nv + bk.vi + j) * B] = col[r];
+        }
+      }
+    }
+  }
+}
+
+// Recursive Newton-Euler (paper Sec. 3.3, Eq. 7 for the velocity sweep):
+//   v_i = X_i v_p + S_i qd_i
+//   a_i = X_i a_p + S_i qdd_i + v_i x S_i qd_i     (a of the world = -g)
+//   f_i = I_i a_i + v_i x* I_i v_i
+// then leaf to root: tau_i = S_i^T f_i, f_p += X_i^T f_i.
+template <int NB>
+__device__ __forceinline__ void rnea_env(const SmemModel& sm, SV a0, const Col& q, const Col& qd, const Col& qdd,
+                                         float* __restrict__ tau, int64_t B, int64_t e) {
+  Xf X[NB];
+  SV v[NB], a[NB], f[NB];
+  for (int i = 0; i < sm.n; ++i) {
+    const BodyC& c = sm.c[i];
+    const BodyI bi = sm.i[i];
+    X[i] = joint_X(c, bi, q);
+    const SV vJ = S_times(c, bi, qd);
+    const SV aJ = S_times(c, bi, qdd);
+    SV vi, ai;
+    if (bi.parent < 0) {
+      vi = vJ;
+      ai = X_motion(X[i], a0) + aJ;
+    } else {
+      vi = X_motion(X[i], v[bi.parent]) + vJ;
+      ai = X_motion(X[i], a[bi.parent]) + aJ + crm(vi, vJ);
+    }
+    const In10 I = in_load(c.theta);
+    v[i] = vi;
+    a[i] = ai;
+    f[i] = in_mul(I, ai) + crf(vi, in_mul(I, vi));
+  }
+  for (int i = sm.n - 1; i >= 0; --i) {
+    const BodyI bi = sm.i[i];
+    ST_store(sm.c[i], bi, f[i], tau, B, e);
+    if (bi.parent >= 0) f[bi.parent] = f[bi.parent] + XT_force(X[i], f[i]);
+  }
+}
+
+// Composite-rigid-body algorithm: composite inertias leaf to root
+// (I^c_p += X_i^T I^c_i X_i, kept as 10 parameters because a sum of rigid
+// bodies is a rigid body), then F = I^c_i S_i carried up the support path:
+// M_ij = S_j^T F. Structural zeros are written too.
+template <int NB>
+__device__ __forceinline__ void crba_env(const SmemModel& sm, const Col& q, int nv, float* __restrict__ M, int64_t B,
+                                         int64_t e) {
+  Xf X[NB];
+  In10 Ic[NB];
+  for (int i = 0; i < sm.n; ++i) {
+    X[i] = joint_X(sm.c[i], sm.i[i], q);
+    Ic[i] = in_load(sm.c[i].theta);
+  }
+  for (int i = sm.n - 1; i > 0; --i) {
+    const int p = sm.i[i].parent;
+    if (p >= 0) in_add(Ic[p], in_to_parent(X[i], Ic[i]));
+  }
+  float* Me = M + e;
+  for (int i = 0; i < sm.n; ++i) {
+    const BodyI bi = sm.i[i];
+    if (bi.type == FST_JOINT_REVOLUTE || bi.type == FST_JOINT_PRISMATIC) {
+      SV F = in_mul(Ic[i], S_of(sm.c[i]));
+      Me[((int64_t)bi.vi * nv + bi.vi) * B] = dot(S_of(sm.c[i]), F);
+      int j = i;
+      while (sm.i[j].parent >= 0) {
+        F = XT_force(X[j], F);
+        j = sm.i[j].parent;
+        const BodyI bj = sm.i[j];
+        if (bj.type == FST_JOINT_REVOLUTE || bj.type == FST_JOINT_PRISMATIC) {
+          const float mij = dot(S_of(sm.c[j]), F);
+          Me[((int64_t)bi.vi * nv + bj.vi) * B] = mij;
+          Me[((int64_t)bj.vi * nv + bi.vi) * B] = mij;
+        } else if (bj.type == FST_JOINT_FREE) {
+          const float col[6] = {F.v.x, F.v.y, F.v.z, F.w.x, F.w.y, F.w.z};
+#pragma unroll
+          for (int r = 0; r < 6; ++r) {
+            Me[((int64_t)(bj.vi + r) * nv + bi.vi) * B] = col[r];
+            Me[((int64_t)bi.vi * nv + bj.vi + r) * B] = col[r];
+          }
+        }
+      }
+    } else if (bi.type == FST_JOINT_FREE) {
+      // base block: the composite inertia with rows/cols ordered [v; w]
+      const In10& I = Ic[i];
+      const float blk[6][6] = {
+          {I.m, 0.f, 0.f, 0.f, I.h.z, -I.h.y},
+          {0.f, I.m, 0.f, -I.h.z, 0.f, I.h.x},
+          {0.f, 0.f, I.m, I.h.y, -I.h.x, 0.f},
+          {0.f, -I.h.z, I.h.y, I.I[0], I.I[1], I.I[3]},
+          {I.h.z, 0.f, -I.h.x, I.I[1], I.I[2], I.I[4]},
+          {-I.h.y, I.h.x, 0.f, I.I[3], I.I[4], I.I[5]},
+      };
+#pragma unroll
+      for (int r = 0; r < 6; ++r)
+#pragma unroll
+        for (int cc = 0; cc < 6; ++cc) Me[((int64_t)(bi.vi + r) * nv + bi.vi + cc) * B] = blk[r][cc];
+    }
+  }
+  for (int i = 1; i < sm.n; ++i) {
+    const BodyI bi = sm.i[i];
+    const int ni = nv_of(bi.type);
+    if (ni == 0) continue;
+    const unsigned long long anc_i = sm.c[i].anc;
+    for (int j = 0; j < i; ++j) {
+      const BodyI bj = sm.i[j];
+      const int nj = nv_of(bj.type);
+      if (nj == 0 || ((anc_i >> j) & 1ull)) continue;
+      for (int r = 0; r < ni; ++r)
+        for (int cc = 0; cc < nj; ++cc) {
+          Me[((int64_t)(bi.vi + r) * nv + bj.vi + cc) * B] = 0.f;
+          Me[((int64_t)(bj.vi + cc) * nv + bi.vi + r) * B] = 0.f;
+        }
+    }
+  }
+}
+
+// Cholesky solve of a symmetric positive-definite 6x6 spatial system.
+__device__ __forceinline__ SV sym6_solve(const Sym6& s, SV rhs) {
+  float A[6][6];
+  const float Af[9] = {s.A[0], s.A[1], s.A[3], s.A[1], s.A[2], s.A[4], s.A[3], s.A[4], s.A[5]};
+  const float Cf[9] = {s.C[0], s.C[1], s.C[3], s.C[1], s.C[2], s.C[4], s.C[3], s.C[4], s.C[5]};
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      A[r][c] = Af[3 * r + c];
+      A[r][3 + c] = s.Bk[3 * r + c];
+      A[3 + r][c] = s.Bk[3 * c + r];
+      A[3 + r][3 + c] = Cf[3 * r + c];
+    }
+  float L[6][6];
+  float inv[6];
+#pragma unroll
+  for (int j = 0; j < 6; ++j) {
+    float d = A[j][j];
+#pragma unroll
+    for (int k = 0; k < j; ++k) d = fmaf(-L[j][k], L[j][k], d);
+    const float ljj = sqrtf(d);
+    inv[j] = 1.0f / ljj;
+    L[j][j] = ljj;
+#pragma unroll
+    for (int i = j + 1; i < 6; ++i) {
+      float x = A[i][j];
+#pragma unroll
+      for (int k = 0; k < j; ++k) x = fmaf(-L[i][k], L[j][k], x);
+      L[i][j] = x * inv[j];
+    }
+  }
+  float y[6] = {rhs.w.x, rhs.w.y, rhs.w.z, rhs.v.x, rhs.v.y, rhs.v.z};
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+#pragma unroll
+    for (int k = 0; k < i; ++k) y[i] = fmaf(-L[i][k], y[k], y[i]);
+    y[i] *= inv[i];
+  }
+#pragma unroll
+  for (int i = 5; i >= 0; --i) {
+#pragma unroll
+    for (int k = i + 1; k < 6; ++k) y[i] = fmaf(-L[k][i], y[k], y[i]);
+    y[i] *= inv[i];
+  }
+  return SV{f3{y[0], y[1], y[2]}, f3{y[3], y[4], y[5]}};
+}
+
+// Articulated-body algorithm, three passes (paper Sec. 4.1):
+//  1. root to leaf: v_i, bias acceleration c_i = v_i x S_i qd_i,
+//     I^A_i = I_i, p^A_i = v_i x* I_i v_i
+//  2. leaf to root: U = I^A S, D = S^T U, u = tau - S^T p^A,
+//     I^a = I^A - U U^T / D, p^a = p^A + I^a c + U u / D,
+//     I^A_p += X^T I^a X, p^A_p += X^T p^a
+//  3. root to leaf: a' = X a_p + c, qdd = (u - U^T a') / D, a = a' + S qdd
+// A free base solves its 6x6 articulated inertia directly.
+template <int NB>
+__device__ __forceinline__ void aba_env(const SmemModel& sm, SV a0, const Col& q, const Col& qd, const Col& tau,
+                                        float* __restrict__ qdd, int64_t B, int64_t e) {
+  Xf X[NB];
+  SV va[NB];  // velocity in pass 1, acceleration in pass 3
+  SV cb[NB], pA[NB], U[NB];
+  Sym6 IA[NB];
+  float invD[NB], u[NB];
+  for (int i = 0; i < sm.n; ++i) {
+    const BodyC& c = sm.c[i];
+    const BodyI bi = sm.i[i];
+    X[i] = joint_X(c, bi, q);
+    const SV vJ = S_times(c, bi, qd);
+    SV vi;
+    if (bi.parent < 0) {
+      vi = vJ;
+      cb[i] = sv_zero();
+    } else {
+      vi = X_motion(X[i], va[bi.parent]) + vJ;
+      cb[i] = crm(vi, vJ);
+    }
+    va[i] = vi;
+    const In10 I = in_load(c.theta);
+    IA[i] = sym6_from_in(I);
+    pA[i] = crf(vi, in_mul(I, vi));
+  }
+  for (int i = sm.n - 1; i >= 0; --i) {
+    const BodyI bi = sm.i[i];
+    if (bi.type == FST_JOINT_FREE) continue;  // the root: solved in pass 3
+    Sym6 Ia = IA[i];
+    SV pa = pA[i];
+    if (bi.type != FST_JOINT_FIXED) {
+      const SV S = S_of(sm.c[i]);
+      const SV Ui = sym6_mul(IA[i], S);
+      const float iD = 1.0f / dot(S, Ui);
+      const float ui = tau[bi.vi] - dot(S, pA[i]);
+      U[i] = Ui;
+      invD[i] = iD;
+      u[i] = ui;
+      if (bi.parent < 0) continue;
+      sym6_rank1_sub(Ia, Ui, iD);
+      pa = pa + sym6_mul(Ia, cb[i]) + (ui * iD) * Ui;
+    } else {
+      if (bi.parent < 0) continue;
+      pa = pa + sym6_mul(Ia, cb[i]);
+    }
+    sym6_add(IA[bi.parent], sym6_to_parent(X[i], Ia));
+    pA[bi.parent] = pA[bi.parent] + XT_force(X[i], pa);
+  }
+  for (int i = 0; i < sm.n; ++i) {
+    const BodyI bi = sm.i[i];
+    const SV ap = bi.parent < 0 ? a0 : va[bi.parent];
+    SV ai = X_motion(X[i], ap) + cb[i];
+    if (bi.type == FST_JOINT_REVOLUTE || bi.type == FST_JOINT_PRISMATIC) {
+      const float qi = (u[i] - dot(U[i], ai)) * invD[i];
+      qdd[(int64_t)bi.vi * B + e] = qi;
+      ai = ai + qi * S_of(sm.c[i]);
+    } else if (bi.type == FST_JOINT_FREE) {
+      const SV tf = SV{f3{tau[bi.vi + 3], tau[bi.vi + 4], tau[bi.vi + 5]}, f3{tau[bi.vi], tau[bi.vi + 1], tau[bi.vi + 2]}};
+      const SV anew = sym6_solve(IA[i], tf - pA[i]);
+      const SV x = anew - ai;
+      float* o = qdd + (int64_t)bi.vi * B + e;
+      o[0] = x.v.x;
+      o[B] = x.v.y;
+      o[2 * B] = x.v.z;
+      o[3 * B] = x.w.x;
+      o[4 * B] = x.w.y;
+      o[5 * B] = x.w.z;
+      ai = anew;
+    }
+    va[i] = ai;
+  }
+}
+
+}  // namespace fst

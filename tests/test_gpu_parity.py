@@ -155,3 +155,25 @@ def test_invalid_calls_return_errors(torch_cuda):
     L = _ffi.lib()
     assert L.fst_fk(m.handle, 16, None, None, None) == -1
     assert L.fst_fk(m.handle, -1, None, None, None) == -1
+
+
+@pytest.mark.parametrize("name", ["quadruped11", "humanoid29", "general8"])
+def test_fused_eval_is_bitwise_equal_to_per_op_calls(torch_cuda, name):
+    import torch
+    from paper_2605_31481_gb300 import api
+    tree = TREES[name]()
+    B = 777
+    s = w.random_state(tree, B, seed=2)
+    m = api.Model(tree)
+    q, qd, qdd, tau = (to_soa_cuda(s[k], torch) for k in ("q", "qd", "qdd", "tau"))
+    ee = list(tree.ee)
+    res = api.eval(m, q, qd, qdd, tau, fk=True, links=ee, rnea=True, crba=True, aba=True)
+    ref = {"poses": api.fk(m, q), "J": api.jacobian(m, q, ee), "tau": api.rnea(m, q, qd, qdd),
+           "M": api.crba(m, q), "qdd": api.aba(m, q, qd, tau)}
+    for k in ref:
+        assert torch.equal(res[k], ref[k]), k
+    # subsets: only the requested outputs are produced
+    only = api.eval(m, q, qd, qdd, tau, rnea=True)
+    assert set(only) == {"tau"} and torch.equal(only["tau"], ref["tau"])
+    kin = api.eval(m, q, links=ee)
+    assert set(kin) == {"J"} and torch.equal(kin["J"], ref["J"])
