@@ -171,6 +171,56 @@ typedef struct fst_eval_io {
 FST_API fst_status fst_eval(const fst_model* model, int64_t B, const fst_eval_io* io,
                             const float* theta, void* stream);
 
+/* ---------------------------------------------------------------------------
+ * Adjoints (vector-Jacobian products). The paper obtains gradients with
+ * autograd (Sec. 3.5) and identifies link masses through the RNEA gradient
+ * (Sec. 4.3); these entry points compute the same products with hand-written
+ * reverse sweeps. Any output pointer may be NULL (that cotangent is not
+ * computed). theta_bar is [n_b][10] in the theta layout of fst_rnea, summed
+ * over all B environments and OVERWRITTEN (not accumulated); it is reduced
+ * deterministically (no floating-point atomics), so repeated calls give
+ * bit-identical results. Computing theta_bar needs caller-allocated device
+ * scratch of fst_adjoint_scratch_bytes() bytes; scratch may be NULL when
+ * theta_bar is NULL. Too small a scratch returns FST_ERR_INVALID_ARG.
+ * The free joint's q_bar is the gradient with respect to the 7 raw
+ * coordinates [x y z qx qy qz qw] (through the quaternion normalisation).
+ * ------------------------------------------------------------------------- */
+
+/* Device scratch bytes the adjoints need for B environments. */
+FST_API fst_status fst_adjoint_scratch_bytes(const fst_model* model, int64_t B, size_t* bytes);
+
+/* FK: q_bar [nq][B] = (d poses / d q)^T poses_bar, poses_bar [n_b][12][B]. */
+FST_API fst_status fst_fk_vjp(const fst_model* model, int64_t B, const float* q,
+                              const float* poses_bar, float* q_bar, void* stream);
+
+/* RNEA: cotangents of tau = RNEA(q, qd, qdd; theta) for tau_bar [nv][B]:
+ * q_bar [nq][B], qd_bar [nv][B], qdd_bar [nv][B] (= M tau_bar), theta_bar. */
+FST_API fst_status fst_rnea_vjp(const fst_model* model, int64_t B, const float* q,
+                                const float* qd, const float* qdd, const float* theta,
+                                const float* tau_bar, float* q_bar, float* qd_bar,
+                                float* qdd_bar, float* theta_bar, void* scratch,
+                                size_t scratch_bytes, void* stream);
+
+/* ABA: cotangents of qdd = ABA(q, qd, tau; theta) for qdd_bar [nv][B].
+ * qdd [nv][B] must be the forward result for the same inputs. Uses
+ * tau_bar = M^-1 qdd_bar and {q_bar, qd_bar, theta_bar} = -RNEA-VJP at qdd. */
+FST_API fst_status fst_aba_vjp(const fst_model* model, int64_t B, const float* q,
+                               const float* qd, const float* qdd, const float* theta,
+                               const float* qdd_bar, float* q_bar, float* qd_bar,
+                               float* tau_bar, float* theta_bar, void* scratch,
+                               size_t scratch_bytes, void* stream);
+
+/* System-identification loss L = sum_env sum_i (tau_i - tau_meas_i)^2,
+ * tau = RNEA(q, qd, qdd; theta) (paper Sec. 4.3), and its gradient, in one
+ * pass that keeps the forward state on chip. loss_theta_bar [n_b*10 + 1]
+ * (device) receives dL/dtheta followed by L. q_bar / qd_bar [.][B] optional.
+ * scratch is required. */
+FST_API fst_status fst_rnea_loss_grad(const fst_model* model, int64_t B, const float* q,
+                                      const float* qd, const float* qdd, const float* theta,
+                                      const float* tau_meas, float* loss_theta_bar,
+                                      float* q_bar, float* qd_bar, void* scratch,
+                                      size_t scratch_bytes, void* stream);
+
 /* Message for the last non-OK status on this thread ("" if none). */
 FST_API const char* fst_last_error(void);
 

@@ -213,3 +213,93 @@ def eval(model: Model, q, qd=None, qdd=None, tau=None, *, fk=False, links=None, 
         io.qdd_out = res["qdd"].data_ptr()
     check(_ffi.lib().fst_eval(model.handle, B, ctypes.byref(io), _ptr(_theta(theta, model)), _stream()))
     return res
+
+
+# ---------------------------------------------------------------------------
+# adjoints
+# ---------------------------------------------------------------------------
+
+def adjoint_scratch(model: Model, B: int) -> torch.Tensor:
+    """Device scratch for the thetabar partial sums of B environments."""
+    n = ctypes.c_size_t()
+    check(_ffi.lib().fst_adjoint_scratch_bytes(model.handle, int(B), ctypes.byref(n)))
+    return torch.empty(max(int(n.value), 4), dtype=torch.uint8, device=model.device)
+
+
+def _scratch(model, B, scratch):
+    if scratch is None:
+        scratch = adjoint_scratch(model, B)
+    return _ptr(scratch), scratch.numel() * scratch.element_size()
+
+
+def fk_vjp(model: Model, q, poses_bar, out=None):
+    """q_bar (nq, B) for the cotangent poses_bar (n_b, 12, B) of fk()."""
+    B = _check_in(q, model.nq, "q", model)
+    if poses_bar.shape != (model.n_bodies, 12, B) or not poses_bar.is_contiguous() or poses_bar.dtype != torch.float32:
+        raise ValueError(f"poses_bar must be a contiguous float32 ({model.n_bodies}, 12, {B}) tensor")
+    out = _out(out, (model.nq, B), model)
+    check(_ffi.lib().fst_fk_vjp(model.handle, B, _ptr(q), _ptr(poses_bar), _ptr(out), _stream()))
+    return out
+
+
+def rnea_vjp(model: Model, q, qd, qdd, tau_bar, theta=None, *, q_bar=True, qd_bar=True, qdd_bar=True,
+             theta_bar=True, scratch=None):
+    """Cotangents of rnea() for tau_bar (nv, B). Returns a dict with the
+    requested keys among "q", "qd", "qdd" ((nq|nv, B)) and "theta" (n_b, 10,
+    summed over environments)."""
+    B = _check_in(q, model.nq, "q", model)
+    for x, nm in ((qd, "qd"), (qdd, "qdd"), (tau_bar, "tau_bar")):
+        _check_in(x, model.nv, nm, model)
+    res = {}
+    if q_bar:
+        res["q"] = _out(None, (model.nq, B), model)
+    if qd_bar:
+        res["qd"] = _out(None, (model.nv, B), model)
+    if qdd_bar:
+        res["qdd"] = _out(None, (model.nv, B), model)
+    if theta_bar:
+        res["theta"] = _out(None, (model.n_bodies, 10), model)
+    sp, sb = _scratch(model, B, scratch) if theta_bar else (None, 0)
+    check(_ffi.lib().fst_rnea_vjp(model.handle, B, _ptr(q), _ptr(qd), _ptr(qdd), _ptr(_theta(theta, model)),
+                                  _ptr(tau_bar), _ptr(res.get("q")), _ptr(res.get("qd")), _ptr(res.get("qdd")),
+                                  _ptr(res.get("theta")), sp, sb, _stream()))
+    return res
+
+
+def aba_vjp(model: Model, q, qd, qdd, qdd_bar, theta=None, *, q_bar=True, qd_bar=True, tau_bar=True,
+            theta_bar=True, scratch=None):
+    """Cotangents of aba() for qdd_bar (nv, B); qdd is aba()'s result.
+    Returns a dict with keys among "q", "qd", "tau", "theta"."""
+    B = _check_in(q, model.nq, "q", model)
+    for x, nm in ((qd, "qd"), (qdd, "qdd"), (qdd_bar, "qdd_bar")):
+        _check_in(x, model.nv, nm, model)
+    res = {}
+    if q_bar:
+        res["q"] = _out(None, (model.nq, B), model)
+    if qd_bar:
+        res["qd"] = _out(None, (model.nv, B), model)
+    if tau_bar:
+        res["tau"] = _out(None, (model.nv, B), model)
+    if theta_bar:
+        res["theta"] = _out(None, (model.n_bodies, 10), model)
+    sp, sb = _scratch(model, B, scratch) if theta_bar else (None, 0)
+    check(_ffi.lib().fst_aba_vjp(model.handle, B, _ptr(q), _ptr(qd), _ptr(qdd), _ptr(_theta(theta, model)),
+                                 _ptr(qdd_bar), _ptr(res.get("q")), _ptr(res.get("qd")), _ptr(res.get("tau")),
+                                 _ptr(res.get("theta")), sp, sb, _stream()))
+    return res
+
+
+def rnea_loss_grad(model: Model, q, qd, qdd, tau_meas, theta=None, *, q_bar=False, qd_bar=False, scratch=None,
+                   out=None):
+    """L = sum (rnea(q, qd, qdd; theta) - tau_meas)^2 and dL/dtheta in one
+    pass. Returns (L as a 0-d tensor, theta_bar (n_b, 10), q_bar, qd_bar)."""
+    B = _check_in(q, model.nq, "q", model)
+    for x, nm in ((qd, "qd"), (qdd, "qdd"), (tau_meas, "tau_meas")):
+        _check_in(x, model.nv, nm, model)
+    buf = _out(out, (model.n_bodies * 10 + 1,), model)
+    qb = _out(None, (model.nq, B), model) if q_bar else None
+    qdb = _out(None, (model.nv, B), model) if qd_bar else None
+    sp, sb = _scratch(model, B, scratch)
+    check(_ffi.lib().fst_rnea_loss_grad(model.handle, B, _ptr(q), _ptr(qd), _ptr(qdd), _ptr(_theta(theta, model)),
+                                        _ptr(tau_meas), _ptr(buf), _ptr(qb), _ptr(qdb), sp, sb, _stream()))
+    return buf[-1], buf[:-1].view(model.n_bodies, 10), qb, qdb

@@ -236,4 +236,88 @@ fst_status fst_eval(const fst_model* m, int64_t B, const fst_eval_io* io, const 
   return finish(fn, launch_eval(view_of(m, theta), B, a, launch_of(B, stream)));
 }
 
+fst_status fst_adjoint_scratch_bytes(const fst_model* m, int64_t B, size_t* bytes) {
+  if (!m || !bytes || B < 0) return set_error(FST_ERR_INVALID_ARG, "fst_adjoint_scratch_bytes: bad argument");
+  *bytes = vjp_scratch_floats(m->n, B) * sizeof(float);
+  return FST_OK;
+}
+
+namespace {
+fst_status need_scratch(const char* fn, const fst_model* m, int64_t B, const void* scratch, size_t bytes) {
+  if (!scratch) return set_error(FST_ERR_INVALID_ARG, std::string(fn) + ": theta_bar needs scratch");
+  if (bytes < vjp_scratch_floats(m->n, B) * sizeof(float))
+    return set_error(FST_ERR_INVALID_ARG, std::string(fn) + ": scratch smaller than fst_adjoint_scratch_bytes()");
+  return FST_OK;
+}
+}  // namespace
+
+fst_status fst_fk_vjp(const fst_model* m, int64_t B, const float* q, const float* poses_bar, float* q_bar,
+                      void* stream) {
+  static const char* fn = "fst_fk_vjp";
+  bool skip;
+  FST_CHECK(check_call(fn, m, B, &skip));
+  if (skip || m->nq == 0 || !q_bar) return FST_OK;
+  FST_CHECK(need(fn, q, "q"));
+  FST_CHECK(need(fn, poses_bar, "poses_bar"));
+  return finish(fn, launch_fk_vjp(view_of(m, nullptr), B, q, poses_bar, q_bar, (cudaStream_t)stream));
+}
+
+fst_status fst_rnea_vjp(const fst_model* m, int64_t B, const float* q, const float* qd, const float* qdd,
+                        const float* theta, const float* tau_bar, float* q_bar, float* qd_bar, float* qdd_bar,
+                        float* theta_bar, void* scratch, size_t scratch_bytes, void* stream) {
+  static const char* fn = "fst_rnea_vjp";
+  bool skip;
+  FST_CHECK(check_call(fn, m, B, &skip));
+  if (theta_bar) FST_CHECK(need_scratch(fn, m, B, scratch, scratch_bytes));
+  if (skip || m->nv == 0) {
+    if (theta_bar && m->n) cudaMemsetAsync(theta_bar, 0, sizeof(float) * m->n * 10, (cudaStream_t)stream);
+    return FST_OK;
+  }
+  FST_CHECK(need(fn, q, "q"));
+  FST_CHECK(need(fn, qd, "qd"));
+  FST_CHECK(need(fn, qdd, "qdd"));
+  FST_CHECK(need(fn, tau_bar, "tau_bar"));
+  return finish(fn, launch_rnea_vjp(view_of(m, theta), B, q, qd, qdd, tau_bar, q_bar, qd_bar, qdd_bar, theta_bar,
+                                    (float*)scratch, (cudaStream_t)stream));
+}
+
+fst_status fst_aba_vjp(const fst_model* m, int64_t B, const float* q, const float* qd, const float* qdd,
+                       const float* theta, const float* qdd_bar, float* q_bar, float* qd_bar, float* tau_bar,
+                       float* theta_bar, void* scratch, size_t scratch_bytes, void* stream) {
+  static const char* fn = "fst_aba_vjp";
+  bool skip;
+  FST_CHECK(check_call(fn, m, B, &skip));
+  if (theta_bar) FST_CHECK(need_scratch(fn, m, B, scratch, scratch_bytes));
+  if (skip || m->nv == 0) {
+    if (theta_bar && m->n) cudaMemsetAsync(theta_bar, 0, sizeof(float) * m->n * 10, (cudaStream_t)stream);
+    return FST_OK;
+  }
+  FST_CHECK(need(fn, q, "q"));
+  FST_CHECK(need(fn, qd, "qd"));
+  FST_CHECK(need(fn, qdd, "qdd"));
+  FST_CHECK(need(fn, qdd_bar, "qdd_bar"));
+  return finish(fn, launch_aba_vjp(view_of(m, theta), B, q, qd, qdd, qdd_bar, q_bar, qd_bar, tau_bar, theta_bar,
+                                   (float*)scratch, (cudaStream_t)stream));
+}
+
+fst_status fst_rnea_loss_grad(const fst_model* m, int64_t B, const float* q, const float* qd, const float* qdd,
+                              const float* theta, const float* tau_meas, float* loss_theta_bar, float* q_bar,
+                              float* qd_bar, void* scratch, size_t scratch_bytes, void* stream) {
+  static const char* fn = "fst_rnea_loss_grad";
+  bool skip;
+  FST_CHECK(check_call(fn, m, B, &skip));
+  FST_CHECK(need(fn, loss_theta_bar, "loss_theta_bar"));
+  FST_CHECK(need_scratch(fn, m, B, scratch, scratch_bytes));
+  if (skip || m->nv == 0) {
+    cudaMemsetAsync(loss_theta_bar, 0, sizeof(float) * (m->n * 10 + 1), (cudaStream_t)stream);
+    return FST_OK;
+  }
+  FST_CHECK(need(fn, q, "q"));
+  FST_CHECK(need(fn, qd, "qd"));
+  FST_CHECK(need(fn, qdd, "qdd"));
+  FST_CHECK(need(fn, tau_meas, "tau_meas"));
+  return finish(fn, launch_rnea_loss_grad(view_of(m, theta), B, q, qd, qdd, tau_meas, loss_theta_bar, q_bar, qd_bar,
+                                          (float*)scratch, (cudaStream_t)stream));
+}
+
 }  // extern "C"

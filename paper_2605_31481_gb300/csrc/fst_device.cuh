@@ -278,10 +278,25 @@ __device__ __forceinline__ Sym6 sym6_to_parent(const Xf& X, const Sym6& s) {
 // model staging and joint transforms
 // ---------------------------------------------------------------------------
 
+// Loops over bodies: left rolled in the generic kernels (the topology is
+// read at run time from shared memory), fully unrolled when a kernel is
+// compiled for one fixed tree (then every body index is a compile-time
+// constant and the per-body sweep state can live in registers).
+#ifdef FST_FIXED_TOPOLOGY
+#define FST_UNROLL _Pragma("unroll")
+#else
+#define FST_UNROLL _Pragma("unroll 1")
+#endif
+
+// Run-time topology: the model staged in shared memory. Any type with the
+// same three accessors (n, C, I) can drive the operator templates.
 struct SmemModel {
   const BodyC* c;
   const BodyI* i;
-  int n;
+  int n_;
+  __device__ __forceinline__ int n() const { return n_; }
+  __device__ __forceinline__ const BodyC& C(int k) const { return c[k]; }
+  __device__ __forceinline__ BodyI I(int k) const { return i[k]; }
 };
 
 // Copies the model constants (and the inertia override, if any) to shared

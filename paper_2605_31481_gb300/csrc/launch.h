@@ -99,4 +99,19 @@ cudaError_t launch_eval(const ModelView& mv, int64_t B, const EvalArgs& a, const
 cudaError_t launch_aba(const ModelView& mv, int64_t B, const float* q, const float* qd, const float* tau,
                        float* qdd, const Launch& L);
 
+// Adjoints (adjoint.cu). scratch: vjp_scratch_floats(n, B) floats of device
+// memory for the per-block partial sums of thetabar (and the loss).
+size_t vjp_scratch_floats(int n, int64_t B);
+cudaError_t launch_fk_vjp(const ModelView& mv, int64_t B, const float* q, const float* pbar, float* qbar,
+                          cudaStream_t s);
+cudaError_t launch_rnea_vjp(const ModelView& mv, int64_t B, const float* q, const float* qd, const float* qdd,
+                            const float* tbar, float* qbar, float* qdbar, float* qddbar, float* thbar, float* scratch,
+                            cudaStream_t s);
+cudaError_t launch_aba_vjp(const ModelView& mv, int64_t B, const float* q, const float* qd, const float* qdd,
+                           const float* qddbar, float* qbar, float* qdbar, float* taubar, float* thbar, float* scratch,
+                           cudaStream_t s);
+cudaError_t launch_rnea_loss_grad(const ModelView& mv, int64_t B, const float* q, const float* qd, const float* qdd,
+                                  const float* tau_meas, float* loss_theta, float* qbar, float* qdbar, float* scratch,
+                                  cudaStream_t s);
+
 }  // namespace fst

@@ -2,8 +2,12 @@
 // reads its environment's inputs from a staged shared-memory column and
 // writes its outputs straight to global memory (coalesced across the warp:
 // consecutive threads hold consecutive environments of a [field][B] array).
-// The per-operator kernels and the fused evaluation kernel both call these,
-// so every launch form computes bit-identical results.
+//
+// Every body is a template over the topology accessor TP (n(), C(i), I(i)):
+// the generic kernels pass the run-time model in shared memory, a kernel
+// compiled for one fixed tree passes compile-time constants. The per-op
+// kernels and the fused evaluation kernel call the same bodies, so every
+// launch form computes bit-identical results.
 #pragma once
 
 #include "fst_device.cuh"
@@ -15,7 +19,7 @@ __device__ __forceinline__ SV world_accel(const ModelView& mv) {
   return SV{f3{0.f, 0.f, 0.f}, f3{mv.a0[0], mv.a0[1], mv.a0[2]}};
 }
 
-// world pose of body i from its parent's world pose and its local transform
+// world pose of a body from its parent's world pose and its local transform
 __device__ __forceinline__ void compose(const float* Rp, const float* pp, const Xf& X, float* R, float* p) {
 #pragma unroll
   for (int r = 0; r < 3; ++r) {
@@ -26,14 +30,16 @@ __device__ __forceinline__ void compose(const float* Rp, const float* pp, const 
   }
 }
 
-// Forward kinematics (tier 3 of the paper's cache, Sec. 3.1), world poses
-// kept in Rw/pw for the caller (the Jacobian reuses them).
-template <int NB>
-__device__ __forceinline__ void world_poses(const SmemModel& sm, const Col& q, float (&Rw)[NB][9], float (&pw)[NB][3],
+// Forward kinematics (tier 3 of the paper's cache, Sec. 3.1); world poses
+// are kept in Rw/pw for the caller (the Jacobian reuses them) and written to
+// `poses` when it is not null.
+template <int NB, class TP>
+__device__ __forceinline__ void world_poses(const TP& tp, const Col& q, float (&Rw)[NB][9], float (&pw)[NB][3],
                                             float* __restrict__ poses, int64_t B, int64_t e) {
-  for (int i = 0; i < sm.n; ++i) {
-    const BodyI bi = sm.i[i];
-    const Xf X = joint_X(sm.c[i], bi, q);
+  FST_UNROLL
+  for (int i = 0; i < tp.n(); ++i) {
+    const BodyI bi = tp.I(i);
+    const Xf X = joint_X(tp.C(i), bi, q);
     if (bi.parent < 0) {
 #pragma unroll
       for (int k = 0; k < 9; ++k) Rw[i][k] = X.R[k];
@@ -52,28 +58,28 @@ __device__ __forceinline__ void world_poses(const SmemModel& sm, const Col& q, f
   }
 }
 
-template <int NB>
-__device__ __forceinline__ void fk_env(const SmemModel& sm, const Col& q, float* __restrict__ poses, int64_t B,
-                                       int64_t e) {
+template <int NB, class TP>
+__device__ __forceinline__ void fk_env(const TP& tp, const Col& q, float* __restrict__ poses, int64_t B, int64_t e) {
   float Rw[NB][9];
   float pw[NB][3];
-  world_poses<NB>(sm, q, Rw, pw, poses, B, e);
+  world_poses<NB>(tp, q, Rw, pw, poses, B, e);
 }
 
 // Jacobian columns straight from the world poses (paper Sec. 3.4, Eq. 6):
 // w = R_k S_w, v = R_k S_v + p_k x w, i.e. [o_k x z_k; z_k] for a revolute
 // joint with o_k on its axis. Rows are [v; w]; off-path DOFs are zero.
-template <int NB>
-__device__ __forceinline__ void jac_env(const SmemModel& sm, const Col& q, int nv, const LinkList& links,
+template <int NB, class TP>
+__device__ __forceinline__ void jac_env(const TP& tp, const Col& q, int nv, const LinkList& links,
                                         float* __restrict__ poses, float* __restrict__ J, int64_t B, int64_t e) {
   float Rw[NB][9];
   float pw[NB][3];
-  world_poses<NB>(sm, q, Rw, pw, poses, B, e);
+  world_poses<NB>(tp, q, Rw, pw, poses, B, e);
   for (int l = 0; l < links.n; ++l) {
-    const unsigned long long mask = sm.c[links.idx[l]].anc;
+    const unsigned long long mask = tp.C(links.idx[l]).anc;
     float* Jl = J + (int64_t)l * 6 * nv * B + e;
-    for (int k = 0; k < sm.n; ++k) {
-      const BodyI bk = sm.i[k];
+    FST_UNROLL
+    for (int k = 0; k < tp.n(); ++k) {
+      const BodyI bk = tp.I(k);
       const int nvk = nv_of(bk.type);
       if (nvk == 0) continue;
       const bool on_path = (mask >> k) & 1ull;
@@ -81,7 +87,7 @@ __device__ __forceinline__ void jac_env(const SmemModel& sm, const Col& q, int n
       if (nvk == 1) {
         float col[6] = {0, 0, 0, 0, 0, 0};
         if (on_path) {
-          const SV s = S_of(sm.c[k]);
+          const SV s = S_of(tp.C(k));
           const f3 w = Rmul(Rw[k], s.w);
           const f3 v = Rmul(Rw[k], s.v) + cross(p, w);
           col[0] = v.x; col[1] = v.y; col[2] = v.z;
@@ -112,19 +118,17 @@ __device__ __forceinline__ void jac_env(const SmemModel& sm, const Col& q, int n
   }
 }
 
-// Recursive Newton-Euler (paper Sec. 3.3, Eq. 7 for the velocity sweep):
+// Forward sweep of RNEA (paper Sec. 3.3, Eq. 7 for the velocities):
 //   v_i = X_i v_p + S_i qd_i
 //   a_i = X_i a_p + S_i qdd_i + v_i x S_i qd_i     (a of the world = -g)
 //   f_i = I_i a_i + v_i x* I_i v_i
-// then leaf to root: tau_i = S_i^T f_i, f_p += X_i^T f_i.
-template <int NB>
-__device__ __forceinline__ void rnea_env(const SmemModel& sm, SV a0, const Col& q, const Col& qd, const Col& qdd,
-                                         float* __restrict__ tau, int64_t B, int64_t e) {
-  Xf X[NB];
-  SV v[NB], a[NB], f[NB];
-  for (int i = 0; i < sm.n; ++i) {
-    const BodyC& c = sm.c[i];
-    const BodyI bi = sm.i[i];
+template <int NB, class TP>
+__device__ __forceinline__ void rnea_forward(const TP& tp, SV a0, const Col& q, const Col& qd, const Col& qdd,
+                                             Xf (&X)[NB], SV (&v)[NB], SV (&a)[NB], SV (&f)[NB]) {
+  FST_UNROLL
+  for (int i = 0; i < tp.n(); ++i) {
+    const BodyC& c = tp.C(i);
+    const BodyI bi = tp.I(i);
     X[i] = joint_X(c, bi, q);
     const SV vJ = S_times(c, bi, qd);
     const SV aJ = S_times(c, bi, qdd);
@@ -141,43 +145,68 @@ __device__ __forceinline__ void rnea_env(const SmemModel& sm, SV a0, const Col& 
     a[i] = ai;
     f[i] = in_mul(I, ai) + crf(vi, in_mul(I, vi));
   }
-  for (int i = sm.n - 1; i >= 0; --i) {
-    const BodyI bi = sm.i[i];
-    ST_store(sm.c[i], bi, f[i], tau, B, e);
+}
+
+// Backward sweep of RNEA, leaf to root: F_i = f_i + sum_children X_c^T F_c,
+// tau_i = S_i^T F_i. f is accumulated in place into F.
+template <int NB, class TP>
+__device__ __forceinline__ void rnea_backward(const TP& tp, const Xf (&X)[NB], SV (&f)[NB], float* __restrict__ tau,
+                                              int64_t B, int64_t e) {
+  FST_UNROLL
+  for (int i = tp.n() - 1; i >= 0; --i) {
+    const BodyI bi = tp.I(i);
+    if (tau) ST_store(tp.C(i), bi, f[i], tau, B, e);
     if (bi.parent >= 0) f[bi.parent] = f[bi.parent] + XT_force(X[i], f[i]);
   }
+}
+
+template <int NB, class TP>
+__device__ __forceinline__ void rnea_env(const TP& tp, SV a0, const Col& q, const Col& qd, const Col& qdd,
+                                         float* __restrict__ tau, int64_t B, int64_t e) {
+  Xf X[NB];
+  SV v[NB], a[NB], f[NB];
+  rnea_forward<NB>(tp, a0, q, qd, qdd, X, v, a, f);
+  rnea_backward<NB>(tp, X, f, tau, B, e);
 }
 
 // Composite-rigid-body algorithm: composite inertias leaf to root
 // (I^c_p += X_i^T I^c_i X_i, kept as 10 parameters because a sum of rigid
 // bodies is a rigid body), then F = I^c_i S_i carried up the support path:
-// M_ij = S_j^T F. Structural zeros are written too.
-template <int NB>
-__device__ __forceinline__ void crba_env(const SmemModel& sm, const Col& q, int nv, float* __restrict__ M, int64_t B,
+// M_ij = S_j^T F. Ancestors have smaller indices than their descendants, so
+// walking j = i-1 .. 0 over the support-path bitmask visits the path from i
+// to the root in order. Structural zeros are written too.
+template <int NB, class TP>
+__device__ __forceinline__ void crba_env(const TP& tp, const Col& q, int nv, float* __restrict__ M, int64_t B,
                                          int64_t e) {
   Xf X[NB];
   In10 Ic[NB];
-  for (int i = 0; i < sm.n; ++i) {
-    X[i] = joint_X(sm.c[i], sm.i[i], q);
-    Ic[i] = in_load(sm.c[i].theta);
+  FST_UNROLL
+  for (int i = 0; i < tp.n(); ++i) {
+    X[i] = joint_X(tp.C(i), tp.I(i), q);
+    Ic[i] = in_load(tp.C(i).theta);
   }
-  for (int i = sm.n - 1; i > 0; --i) {
-    const int p = sm.i[i].parent;
+  FST_UNROLL
+  for (int i = tp.n() - 1; i > 0; --i) {
+    const int p = tp.I(i).parent;
     if (p >= 0) in_add(Ic[p], in_to_parent(X[i], Ic[i]));
   }
   float* Me = M + e;
-  for (int i = 0; i < sm.n; ++i) {
-    const BodyI bi = sm.i[i];
+  FST_UNROLL
+  for (int i = 0; i < tp.n(); ++i) {
+    const BodyI bi = tp.I(i);
     if (bi.type == FST_JOINT_REVOLUTE || bi.type == FST_JOINT_PRISMATIC) {
-      SV F = in_mul(Ic[i], S_of(sm.c[i]));
-      Me[((int64_t)bi.vi * nv + bi.vi) * B] = dot(S_of(sm.c[i]), F);
-      int j = i;
-      while (sm.i[j].parent >= 0) {
-        F = XT_force(X[j], F);
-        j = sm.i[j].parent;
-        const BodyI bj = sm.i[j];
+      SV F = in_mul(Ic[i], S_of(tp.C(i)));
+      Me[((int64_t)bi.vi * nv + bi.vi) * B] = dot(S_of(tp.C(i)), F);
+      const unsigned long long anc = tp.C(i).anc;
+      int k = i;
+      FST_UNROLL
+      for (int j = i - 1; j >= 0; --j) {
+        if (!((anc >> j) & 1ull)) continue;
+        F = XT_force(X[k], F);
+        k = j;
+        const BodyI bj = tp.I(j);
         if (bj.type == FST_JOINT_REVOLUTE || bj.type == FST_JOINT_PRISMATIC) {
-          const float mij = dot(S_of(sm.c[j]), F);
+          const float mij = dot(S_of(tp.C(j)), F);
           Me[((int64_t)bi.vi * nv + bj.vi) * B] = mij;
           Me[((int64_t)bj.vi * nv + bi.vi) * B] = mij;
         } else if (bj.type == FST_JOINT_FREE) {
@@ -206,13 +235,15 @@ __device__ __forceinline__ void crba_env(const SmemModel& sm, const Col& q, int 
         for (int cc = 0; cc < 6; ++cc) Me[((int64_t)(bi.vi + r) * nv + bi.vi + cc) * B] = blk[r][cc];
     }
   }
-  for (int i = 1; i < sm.n; ++i) {
-    const BodyI bi = sm.i[i];
+  FST_UNROLL
+  for (int i = 1; i < tp.n(); ++i) {
+    const BodyI bi = tp.I(i);
     const int ni = nv_of(bi.type);
     if (ni == 0) continue;
-    const unsigned long long anc_i = sm.c[i].anc;
+    const unsigned long long anc_i = tp.C(i).anc;
+    FST_UNROLL
     for (int j = 0; j < i; ++j) {
-      const BodyI bj = sm.i[j];
+      const BodyI bj = tp.I(j);
       const int nj = nv_of(bj.type);
       if (nj == 0 || ((anc_i >> j) & 1ull)) continue;
       for (int r = 0; r < ni; ++r)
@@ -280,18 +311,32 @@ __device__ __forceinline__ SV sym6_solve(const Sym6& s, SV rhs) {
 //     I^A_p += X^T I^a X, p^A_p += X^T p^a
 //  3. root to leaf: a' = X a_p + c, qdd = (u - U^T a') / D, a = a' + S qdd
 // A free base solves its 6x6 articulated inertia directly.
-template <int NB>
-__device__ __forceinline__ void aba_env(const SmemModel& sm, SV a0, const Col& q, const Col& qd, const Col& tau,
-                                        float* __restrict__ qdd, int64_t B, int64_t e) {
+// With qd_zero set, qd is taken as 0 (no velocity terms at all); the adjoint
+// of ABA uses that with a0 = 0 to apply M(q)^-1.
+// The result is written to qdd (global, [nv][B]) and, if qdd_col is not
+// null, also to that shared-memory column.
+template <int NB, class TP>
+__device__ __forceinline__ void aba_env(const TP& tp, SV a0, const Col& q, const Col& qd, const Col& tau,
+                                        float* __restrict__ qdd, int64_t B, int64_t e, bool qd_zero = false,
+                                        float* qdd_col = nullptr, int qdd_ld = 0) {
   Xf X[NB];
   SV va[NB];  // velocity in pass 1, acceleration in pass 3
   SV cb[NB], pA[NB], U[NB];
   Sym6 IA[NB];
   float invD[NB], u[NB];
-  for (int i = 0; i < sm.n; ++i) {
-    const BodyC& c = sm.c[i];
-    const BodyI bi = sm.i[i];
+  FST_UNROLL
+  for (int i = 0; i < tp.n(); ++i) {
+    const BodyC& c = tp.C(i);
+    const BodyI bi = tp.I(i);
     X[i] = joint_X(c, bi, q);
+    const In10 I = in_load(c.theta);
+    IA[i] = sym6_from_in(I);
+    if (qd_zero) {
+      va[i] = sv_zero();
+      cb[i] = sv_zero();
+      pA[i] = sv_zero();
+      continue;
+    }
     const SV vJ = S_times(c, bi, qd);
     SV vi;
     if (bi.parent < 0) {
@@ -302,17 +347,16 @@ __device__ __forceinline__ void aba_env(const SmemModel& sm, SV a0, const Col& q
       cb[i] = crm(vi, vJ);
     }
     va[i] = vi;
-    const In10 I = in_load(c.theta);
-    IA[i] = sym6_from_in(I);
     pA[i] = crf(vi, in_mul(I, vi));
   }
-  for (int i = sm.n - 1; i >= 0; --i) {
-    const BodyI bi = sm.i[i];
+  FST_UNROLL
+  for (int i = tp.n() - 1; i >= 0; --i) {
+    const BodyI bi = tp.I(i);
     if (bi.type == FST_JOINT_FREE) continue;  // the root: solved in pass 3
     Sym6 Ia = IA[i];
     SV pa = pA[i];
     if (bi.type != FST_JOINT_FIXED) {
-      const SV S = S_of(sm.c[i]);
+      const SV S = S_of(tp.C(i));
       const SV Ui = sym6_mul(IA[i], S);
       const float iD = 1.0f / dot(S, Ui);
       const float ui = tau[bi.vi] - dot(S, pA[i]);
@@ -329,25 +373,26 @@ __device__ __forceinline__ void aba_env(const SmemModel& sm, SV a0, const Col& q
     sym6_add(IA[bi.parent], sym6_to_parent(X[i], Ia));
     pA[bi.parent] = pA[bi.parent] + XT_force(X[i], pa);
   }
-  for (int i = 0; i < sm.n; ++i) {
-    const BodyI bi = sm.i[i];
+  FST_UNROLL
+  for (int i = 0; i < tp.n(); ++i) {
+    const BodyI bi = tp.I(i);
     const SV ap = bi.parent < 0 ? a0 : va[bi.parent];
     SV ai = X_motion(X[i], ap) + cb[i];
     if (bi.type == FST_JOINT_REVOLUTE || bi.type == FST_JOINT_PRISMATIC) {
       const float qi = (u[i] - dot(U[i], ai)) * invD[i];
-      qdd[(int64_t)bi.vi * B + e] = qi;
-      ai = ai + qi * S_of(sm.c[i]);
+      if (qdd) qdd[(int64_t)bi.vi * B + e] = qi;
+      if (qdd_col) qdd_col[bi.vi * qdd_ld] = qi;
+      ai = ai + qi * S_of(tp.C(i));
     } else if (bi.type == FST_JOINT_FREE) {
       const SV tf = SV{f3{tau[bi.vi + 3], tau[bi.vi + 4], tau[bi.vi + 5]}, f3{tau[bi.vi], tau[bi.vi + 1], tau[bi.vi + 2]}};
       const SV anew = sym6_solve(IA[i], tf - pA[i]);
       const SV x = anew - ai;
-      float* o = qdd + (int64_t)bi.vi * B + e;
-      o[0] = x.v.x;
-      o[B] = x.v.y;
-      o[2 * B] = x.v.z;
-      o[3 * B] = x.w.x;
-      o[4 * B] = x.w.y;
-      o[5 * B] = x.w.z;
+      const float xo[6] = {x.v.x, x.v.y, x.v.z, x.w.x, x.w.y, x.w.z};
+#pragma unroll
+      for (int r = 0; r < 6; ++r) {
+        if (qdd) qdd[(int64_t)(bi.vi + r) * B + e] = xo[r];
+        if (qdd_col) qdd_col[(bi.vi + r) * qdd_ld] = xo[r];
+      }
       ai = anew;
     }
     va[i] = ai;

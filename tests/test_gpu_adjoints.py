@@ -1,0 +1,162 @@
+"""Hand-written adjoint kernels (through the C ABI) against the oracle's
+reference gradients (complex-step derivatives and the regressor), plus the
+determinism of the thetabar reduction and the autograd wrappers."""
+import numpy as np
+import pytest
+
+from oracle import rbd, derivs
+from paper_2605_31481_gb300 import workloads as w
+from tests._helpers import env_err, from_soa, to_soa_cuda, oracle_poses
+from tests.test_gpu_parity import TREES
+
+pytestmark = pytest.mark.gpu
+
+GTOL = 2e-4          # per-environment normwise relative error of q/qd/qdd/tau cotangents
+THTOL = 2e-4         # thetabar relative to its largest entry
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2605_31481_gb300 import build
+    build.build(quiet=True)
+    return torch
+
+
+def _th_err(g, r):
+    return np.abs(np.asarray(g, np.float64) - r).max() / max(np.abs(r).max(), 1e-30)
+
+
+@pytest.mark.parametrize("name", ["chain7", "quadruped11", "humanoid29", "general8"])
+def test_rnea_vjp_matches_oracle(torch_cuda, name):
+    torch = torch_cuda
+    from paper_2605_31481_gb300 import api
+    tree = TREES[name]()
+    B = 161                                    # 5 tiles of 32 plus a tail of 1
+    s = w.random_state(tree, B, seed=3)
+    rng = np.random.default_rng(1)
+    tb = rng.standard_normal((B, tree.nv))
+    m = api.Model(tree)
+    q, qd, qdd, tbar = (to_soa_cuda(x, torch) for x in (s["q"], s["qd"], s["qdd"], tb))
+    res = api.rnea_vjp(m, q, qd, qdd, tbar)
+    torch.cuda.synchronize()
+    rq, rqd, rqdd, rth = derivs.rnea_vjp(tree, s["q"], s["qd"], s["qdd"], tb)
+    for k, ref in (("q", rq), ("qd", rqd), ("qdd", rqdd)):
+        err = env_err(from_soa(res[k]), ref)
+        assert err.max() <= GTOL, f"{name} {k}: {err.max():.3e}"
+    assert _th_err(res["theta"].cpu().numpy(), rth) <= THTOL
+
+
+@pytest.mark.parametrize("name", ["chain7", "quadruped11", "humanoid29", "general8"])
+def test_aba_vjp_matches_oracle(torch_cuda, name):
+    torch = torch_cuda
+    from paper_2605_31481_gb300 import api
+    tree = TREES[name]()
+    B = 97
+    s = w.random_state(tree, B, seed=4)
+    rng = np.random.default_rng(2)
+    qb = rng.standard_normal((B, tree.nv))
+    m = api.Model(tree)
+    q, qd, tau, qbar = (to_soa_cuda(x, torch) for x in (s["q"], s["qd"], s["tau"], qb))
+    qdd = api.aba(m, q, qd, tau)
+    res = api.aba_vjp(m, q, qd, qdd, qbar)
+    torch.cuda.synchronize()
+    rq, rqd, rtau, rth = derivs.aba_vjp(tree, s["q"], s["qd"], s["tau"], qb)
+    for k, ref in (("q", rq), ("qd", rqd), ("tau", rtau)):
+        err = env_err(from_soa(res[k]), ref)
+        assert err.max() <= 10 * GTOL, f"{name} {k}: {err.max():.3e}"
+    assert _th_err(res["theta"].cpu().numpy(), rth) <= 10 * THTOL
+
+
+@pytest.mark.parametrize("name", ["chain7", "quadruped11", "humanoid29", "general8"])
+def test_fk_vjp_matches_oracle(torch_cuda, name):
+    torch = torch_cuda
+    from paper_2605_31481_gb300 import api
+    tree = TREES[name]()
+    B = 70
+    s = w.random_state(tree, B, seed=5)
+    rng = np.random.default_rng(3)
+    pb = rng.standard_normal((B, tree.n_bodies, 12))
+    m = api.Model(tree)
+    q = to_soa_cuda(s["q"], torch)
+    pbar = torch.from_numpy(np.ascontiguousarray(np.moveaxis(pb, 0, -1).astype(np.float32))).cuda()
+    qbar = api.fk_vjp(m, q, pbar)
+    torch.cuda.synchronize()
+    ref = derivs.fk_vjp(tree, s["q"], pb)
+    err = env_err(from_soa(qbar), ref)
+    assert err.max() <= GTOL, f"{name}: {err.max():.3e}"
+
+
+def test_loss_grad_matches_oracle_and_is_deterministic(torch_cuda):
+    torch = torch_cuda
+    from paper_2605_31481_gb300 import api
+    tree = TREES["chain7"]()
+    B = 8192 + 13
+    s = w.random_state(tree, B, seed=6)
+    rng = np.random.default_rng(4)
+    tau_true = rbd.rnea(tree, s["q"], s["qd"], s["qdd"])
+    tau_meas = tau_true * (1 + 0.05 * rng.standard_normal(tau_true.shape))
+    m = api.Model(tree)
+    q, qd, qdd, tm = (to_soa_cuda(x, torch) for x in (s["q"], s["qd"], s["qdd"], tau_meas))
+    th = rbd.Model(tree).theta() * (1 + rng.uniform(-0.3, 0.3, (tree.n_bodies, 10)))
+    tht = torch.from_numpy(th.astype(np.float32)).cuda()
+    L, thb, qb, qdb = api.rnea_loss_grad(m, q, qd, qdd, tm, theta=tht, q_bar=True, qd_bar=True)
+    L2, thb2, _, _ = api.rnea_loss_grad(m, q, qd, qdd, tm, theta=tht)
+    torch.cuda.synchronize()
+    assert torch.equal(thb, thb2) and torch.equal(L, L2)          # bit-reproducible
+    r = rbd.rnea(tree, s["q"], s["qd"], s["qdd"], theta=th) - tau_meas
+    L_ref = np.sum(r * r)
+    assert abs(float(L) - L_ref) / L_ref < 1e-4
+    idx = np.arange(0, B, 97)
+    rq, rqd, _, _ = derivs.rnea_vjp(tree, s["q"][idx], s["qd"][idx], s["qdd"][idx], 2 * r[idx], theta=th)
+    assert env_err(from_soa(qb)[idx], rq).max() <= GTOL
+    assert env_err(from_soa(qdb)[idx], rqd).max() <= GTOL
+    Y = derivs.regressor(tree, s["q"], s["qd"], s["qdd"])
+    th_ref = np.einsum("bi,bink->nk", 2 * r, Y)
+    assert _th_err(thb.cpu().numpy(), th_ref) <= THTOL
+
+
+def test_theta_bar_is_bit_reproducible(torch_cuda):
+    torch = torch_cuda
+    from paper_2605_31481_gb300 import api
+    tree = TREES["quadruped11"]()
+    B = 4096
+    s = w.random_state(tree, B, seed=7)
+    m = api.Model(tree)
+    q, qd, qdd, tb = (to_soa_cuda(s[k], torch) for k in ("q", "qd", "qdd", "tau"))
+    a = api.rnea_vjp(m, q, qd, qdd, tb)["theta"]
+    b = api.rnea_vjp(m, q, qd, qdd, tb)["theta"]
+    assert torch.equal(a, b)
+
+
+def test_autograd_wrappers(torch_cuda):
+    torch = torch_cuda
+    from paper_2605_31481_gb300 import api, autograd
+    tree = TREES["quadruped11"]()
+    B = 300
+    s = w.random_state(tree, B, seed=8)
+    m = api.Model(tree)
+    q, qd, qdd, tau = (to_soa_cuda(s[k], torch).requires_grad_() for k in ("q", "qd", "qdd", "tau"))
+    th0 = torch.from_numpy(rbd.Model(tree).theta().astype(np.float32)).cuda().requires_grad_()
+    out = autograd.rnea(m, q, qd, qdd, th0)
+    g = torch.randn_like(out)
+    out.backward(g)
+    ref = api.rnea_vjp(m, q.detach(), qd.detach(), qdd.detach(), g, theta=th0.detach())
+    for t, k in ((q, "q"), (qd, "qd"), (qdd, "qdd"), (th0, "theta")):
+        assert torch.equal(t.grad, ref[k]), k
+    # FK and ABA through autograd against the oracle
+    q2 = to_soa_cuda(s["q"], torch).requires_grad_()
+    poses = autograd.fk(m, q2)
+    pb = torch.randn_like(poses)
+    poses.backward(pb)
+    ref = derivs.fk_vjp(tree, s["q"], np.moveaxis(pb.cpu().numpy().astype(np.float64), -1, 0))
+    assert env_err(from_soa(q2.grad), ref).max() <= GTOL
+    tau2 = to_soa_cuda(s["tau"], torch).requires_grad_()
+    qdd2 = autograd.aba(m, to_soa_cuda(s["q"], torch), to_soa_cuda(s["qd"], torch), tau2)
+    gq = torch.randn_like(qdd2)
+    qdd2.backward(gq)
+    M = rbd.crba(tree, s["q"])
+    lam = np.linalg.solve(M, np.moveaxis(gq.cpu().numpy().astype(np.float64), -1, 0)[..., None])[..., 0]
+    assert env_err(from_soa(tau2.grad), lam).max() <= 10 * GTOL
