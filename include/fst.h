@@ -221,6 +221,29 @@ FST_API fst_status fst_rnea_loss_grad(const fst_model* model, int64_t B, const f
                                       float* q_bar, float* qd_bar, void* scratch,
                                       size_t scratch_bytes, void* stream);
 
+/* fst_rnea_vjp for callers that cannot allocate device memory (the paper
+ * has no counterpart; this is a deployment convenience). Some callers cannot
+ * call cudaMalloc or hand over a scratch buffer: code whose device memory is
+ * owned by a pool or arena, real-time loops where an allocation and its
+ * implicit synchronisation are not allowed, plugins that only see their
+ * input and output tensors. This variant takes the scratch for theta_bar's
+ * partial sums from a 4 MiB array that the library keeps in device memory
+ * (held by every GPU that loads the library until the process exits) and
+ * allocates nothing. Inputs and outputs are as fst_rnea_vjp and are still
+ * the caller's.
+ * Limits: theta_bar needs ceil(B/32) * (10 n_b + 1) <= 1,048,576 floats
+ * (about B = 300,000 for 11 bodies); a larger B with theta_bar set returns
+ * FST_ERR_INVALID_ARG before any launch. All calls share the array: calls
+ * whose kernels overlap on the GPU (unordered streams) race and give wrong
+ * theta_bar; sequential calls are fine and need no clearing. The first call
+ * on a device looks up the array's device address (cudaGetSymbolAddress with
+ * that device current) and caches it; make that first call before any
+ * stream capture. */
+FST_API fst_status fst_rnea_vjp_noalloc(const fst_model* model, int64_t B, const float* q,
+                                        const float* qd, const float* qdd, const float* theta,
+                                        const float* tau_bar, float* q_bar, float* qd_bar,
+                                        float* qdd_bar, float* theta_bar, void* stream);
+
 /* Message for the last non-OK status on this thread ("" if none). */
 FST_API const char* fst_last_error(void);
 
