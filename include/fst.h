@@ -110,6 +110,37 @@ FST_API fst_status fst_model_destroy(fst_model* model);
 FST_API fst_status fst_model_info(const fst_model* model, int32_t* nq, int32_t* nv,
                           int32_t* n_bodies, int32_t* depth);
 
+/* Kernel kinds for fst_model_specialize (bit masks; 0 = all). */
+#define FST_SPEC_FK (1u << 0)
+#define FST_SPEC_JACOBIAN (1u << 1)
+#define FST_SPEC_RNEA (1u << 2)
+#define FST_SPEC_CRBA (1u << 3)
+#define FST_SPEC_ABA (1u << 4)
+#define FST_SPEC_EVAL (1u << 5)
+#define FST_SPEC_FK_VJP (1u << 6)
+#define FST_SPEC_RNEA_VJP (1u << 7)
+#define FST_SPEC_ABA_VJP (1u << 8)
+#define FST_SPEC_LOSS_GRAD (1u << 9)
+#define FST_SPEC_ALL 0x3ffu
+
+/* Compiles kernels specialised for this model's tree (run-time compilation
+ * with NVRTC for the current GPU). The paper folds the fixed joint offsets
+ * into precomputed constants at build time (Sec. 3.2); this goes one step
+ * further and bakes the whole tree into the kernel: the topology becomes a
+ * compile-time constant, every body loop is unrolled and the sweep state
+ * stays in registers. Afterwards, calls of the selected kinds on this model
+ * run the specialised kernels (same results within FP32 rounding; the
+ * inertial parameters, including a theta override, are still read at run
+ * time). Synchronous: about a second per kind on first use; compiled code
+ * is cached on disk ($FST_JIT_CACHE, default ~/.cache/fst_jit). Call it
+ * before capturing a stream. Returns FST_ERR_UNSUPPORTED (and changes
+ * nothing) when NVRTC or the CUDA driver entry points are unavailable; the
+ * generic kernels keep serving every call. */
+FST_API fst_status fst_model_specialize(fst_model* model, uint32_t kinds);
+
+/* Bit mask of the specialised kinds currently in use for this model. */
+FST_API fst_status fst_model_specialized(const fst_model* model, uint32_t* kinds);
+
 /* Forward kinematics (paper Sec. 3.1, tier 3; Eq. 4-5 for each joint).
  * q      [nq][B]        joint positions.
  * poses  [n_b][12][B]   world pose of every body: R row-major (9), then p (3). */

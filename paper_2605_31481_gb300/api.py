@@ -44,7 +44,7 @@ class Model:
     `tree` is any object with the body-table fields parent, jtype, axis,
     T_joint, T_link, mass, com, I_com and gravity (see workloads.Tree)."""
 
-    def __init__(self, tree, device=None):
+    def __init__(self, tree, device=None, specialize=False):
         L = _ffi.lib()
         n = len(tree.parent)
         arr = (_ffi.BodyDesc * n)()
@@ -72,6 +72,22 @@ class Model:
         self.nq, self.nv, self.n_bodies, self.depth = nq.value, nv.value, nb.value, depth.value
         self.name = getattr(tree, "name", "tree")
         self.ee = tuple(getattr(tree, "ee", ()))
+        if specialize:
+            self.specialize(None if specialize is True else specialize)
+
+    def specialize(self, kinds=None):
+        """Compile kernels specialised for this tree (fst_model_specialize);
+        `kinds` is an iterable of names from _ffi.SPEC_KINDS, None = all."""
+        mask = 0 if kinds is None else sum(1 << _ffi.SPEC_KINDS.index(k) for k in kinds)
+        with torch.cuda.device(self.device):
+            check(_ffi.lib().fst_model_specialize(self._h, mask))
+        return self.specialized()
+
+    def specialized(self):
+        """Names of the kernel kinds that run specialised for this model."""
+        m = ctypes.c_uint32()
+        check(_ffi.lib().fst_model_specialized(self._h, ctypes.byref(m)))
+        return tuple(k for i, k in enumerate(_ffi.SPEC_KINDS) if (m.value >> i) & 1)
 
     @property
     def handle(self):

@@ -34,6 +34,32 @@ def nvcc_path() -> str:
     raise RuntimeError("nvcc not found: the CUDA toolkit is required to build libfst.so")
 
 
+# Device headers embedded into the library for run-time specialisation
+# (NVRTC compiles them again for one fixed tree; see csrc/jit.cpp).
+JIT_HEADERS = ["fst_layout.h", "fst_device.cuh", "ops.cuh", "adjoint.cuh", "jit_kernels.cuh"]
+EMBED = "jit_embed.cpp"
+
+
+def _gen_embed() -> str:
+    parts = ["// generated by build.py: device headers for run-time specialisation", "namespace fst {",
+             f"extern const int kJitHeaderCount = {len(JIT_HEADERS)};",
+             "extern const char* const kJitHeaderNames[] = {" + ", ".join(f'"{h}"' for h in JIT_HEADERS) + "};",
+             "extern const char* const kJitHeaderSources[] = {"]
+    for h in JIT_HEADERS:
+        with open(os.path.join(CSRC, h)) as fh:
+            text = fh.read()
+        if ")fst_embed\"" in text:
+            raise RuntimeError(f"{h} contains the raw-string delimiter")
+        parts.append('R"fst_embed(' + text + ')fst_embed",')
+    parts += ["};", "}  // namespace fst", ""]
+    src = "\n".join(parts)
+    path = os.path.join(BUILD, EMBED)
+    if not os.path.exists(path) or open(path).read() != src:
+        with open(path, "w") as fh:
+            fh.write(src)
+    return path
+
+
 def _sources():
     return sorted(f for f in os.listdir(CSRC) if f.endswith((".cu", ".cpp")))
 
@@ -49,7 +75,7 @@ def _headers_digest() -> str:
 
 
 def _compile(nvcc, src, flags, hdr, force):
-    path = os.path.join(CSRC, src)
+    path = os.path.join(BUILD if src == EMBED else CSRC, src)
     obj = os.path.join(BUILD, src + ".o")
     stamp = obj + ".stamp"
     with open(path, "rb") as fh:
@@ -74,7 +100,8 @@ def build(verbose_ptxas: bool = False, force: bool = False, quiet: bool = False)
     if verbose_ptxas:
         flags += ["-Xptxas", "-v"]
     hdr = _headers_digest()
-    srcs = _sources()
+    _gen_embed()
+    srcs = _sources() + [EMBED]
     changed = False
     with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
         for src, log, did in ex.map(lambda s: _compile(nvcc, s, flags, hdr, force), srcs):
@@ -84,7 +111,7 @@ def build(verbose_ptxas: bool = False, force: bool = False, quiet: bool = False)
     if changed or force or not os.path.exists(LIB):
         objs = [os.path.join(BUILD, s + ".o") for s in srcs]
         tmp = LIB + ".tmp"
-        cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs]
+        cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-ldl"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

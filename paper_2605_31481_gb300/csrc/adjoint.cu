@@ -7,6 +7,7 @@
 // partials in block order. No floating-point atomics, so the result is
 // bit-reproducible run to run.
 #include "adjoint.cuh"
+#include "launch.h"
 
 namespace fst {
 namespace {
@@ -213,6 +214,10 @@ cudaError_t reduce(const float* partial, int nblk, int P, float* out, cudaStream
 }
 
 }  // namespace
+
+cudaError_t launch_partial_reduce(const float* partial, int nblk, int P, float* out, cudaStream_t s) {
+  return reduce(partial, nblk, P, out, s);
+}
 
 size_t vjp_scratch_floats(int n, int64_t B) { return (size_t)((B + 31) / 32) * (n * 10 + 1); }
 

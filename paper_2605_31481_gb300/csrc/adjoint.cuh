@@ -124,7 +124,7 @@ __device__ __forceinline__ void rnea_vjp_reverse(const TP& tp, SV a0, const Col&
   for (int i = tp.n() - 1; i >= 0; --i) {
     const BodyC& c = tp.C(i);
     const BodyI bi = tp.I(i);
-    const In10 I = in_load(c.theta);
+    const In10 I = in_load(tp.theta(i));
     const SV fb = Fb[i];
     // f = I a + v x* h,  h = I v
     const SV h = in_mul(I, v[i]);

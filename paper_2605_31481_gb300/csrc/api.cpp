@@ -7,6 +7,7 @@
 #include <string>
 
 #include "fst_internal.h"
+#include "jit.h"
 #include "launch.h"
 
 namespace fst {
@@ -62,6 +63,21 @@ fst_status finish(const char* fn, cudaError_t err) {
   return FST_OK;
 }
 
+// Launches a specialised kernel: one environment per thread, `rows` staged
+// input rows per environment plus `P` floats per warp of reduction slots in
+// shared memory; gy = blockIdx.y extent. *nblk receives the grid's x size.
+template <typename... A>
+cudaError_t jit_go(const fst_model* m, int kind, int64_t B, int rows, int P, unsigned gy, cudaStream_t s,
+                   unsigned* nblk, A... args) {
+  int T = default_block(B);
+  auto smem = [&](int t) { return (size_t)rows * t * sizeof(float) + (size_t)(t / 32) * P * sizeof(float); };
+  while (T > 32 && smem(T) > 96 * 1024) T /= 2;
+  const dim3 grid(grid_for(B, T), gy);
+  if (nblk) *nblk = grid.x;
+  void* argv[] = {(void*)&args...};
+  return jit_launch(m, kind, grid, T, smem(T), s, argv);
+}
+
 }  // namespace
 }  // namespace fst
 
@@ -109,9 +125,23 @@ fst_status fst_model_create(const fst_body_desc* bodies, int32_t n_bodies, const
 
 fst_status fst_model_destroy(fst_model* m) {
   if (!m) return FST_OK;
+  jit_release(m);
   if (m->dc) cudaFree(m->dc);
   if (m->di) cudaFree(m->di);
   delete m;
+  return FST_OK;
+}
+
+fst_status fst_model_specialize(fst_model* m, uint32_t kinds) {
+  if (!m) return set_error(FST_ERR_INVALID_ARG, "fst_model_specialize: null model");
+  if (kinds == 0) kinds = FST_SPEC_ALL;
+  if (kinds & ~(uint32_t)FST_SPEC_ALL) return set_error(FST_ERR_INVALID_ARG, "fst_model_specialize: unknown kind bits");
+  return jit_specialize(m, kinds);
+}
+
+fst_status fst_model_specialized(const fst_model* m, uint32_t* kinds) {
+  if (!m || !kinds) return set_error(FST_ERR_INVALID_ARG, "fst_model_specialized: null argument");
+  *kinds = jit_mask(m);
   return FST_OK;
 }
 
@@ -131,7 +161,10 @@ fst_status fst_fk(const fst_model* m, int64_t B, const float* q, float* poses, v
   if (skip) return FST_OK;
   if (m->nq) FST_CHECK(need(fn, q, "q"));
   FST_CHECK(need(fn, poses, "poses"));
-  return finish(fn, launch_fk(view_of(m, nullptr), B, q, poses, launch_of(B, stream)));
+  const ModelView mv = view_of(m, nullptr);
+  if (jit_has(m, JK_FK))
+    return finish(fn, jit_go(m, JK_FK, B, m->nq, 0, 1, (cudaStream_t)stream, nullptr, mv, B, q, poses));
+  return finish(fn, launch_fk(mv, B, q, poses, launch_of(B, stream)));
 }
 
 fst_status fst_jacobian(const fst_model* m, int64_t B, const float* q, const int32_t* links, int32_t n_links,
@@ -151,7 +184,10 @@ fst_status fst_jacobian(const fst_model* m, int64_t B, const float* q, const int
   if (skip || m->nv == 0) return FST_OK;
   FST_CHECK(need(fn, q, "q"));
   FST_CHECK(need(fn, J, "J"));
-  return finish(fn, launch_jacobian(view_of(m, nullptr), B, q, L, J, launch_of(B, stream)));
+  const ModelView mv = view_of(m, nullptr);
+  if (jit_has(m, JK_JACOBIAN))
+    return finish(fn, jit_go(m, JK_JACOBIAN, B, m->nq, 0, 1, (cudaStream_t)stream, nullptr, mv, B, q, L, J));
+  return finish(fn, launch_jacobian(mv, B, q, L, J, launch_of(B, stream)));
 }
 
 fst_status fst_rnea(const fst_model* m, int64_t B, const float* q, const float* qd, const float* qdd,
@@ -164,7 +200,11 @@ fst_status fst_rnea(const fst_model* m, int64_t B, const float* q, const float* 
   FST_CHECK(need(fn, qd, "qd"));
   FST_CHECK(need(fn, qdd, "qdd"));
   FST_CHECK(need(fn, tau, "tau"));
-  return finish(fn, launch_rnea(view_of(m, theta), B, q, qd, qdd, tau, launch_of(B, stream)));
+  const ModelView mv = view_of(m, theta);
+  if (jit_has(m, JK_RNEA))
+    return finish(fn, jit_go(m, JK_RNEA, B, m->nq + 2 * m->nv, 0, 1, (cudaStream_t)stream, nullptr, mv, B, q, qd,
+                             qdd, tau));
+  return finish(fn, launch_rnea(mv, B, q, qd, qdd, tau, launch_of(B, stream)));
 }
 
 fst_status fst_crba(const fst_model* m, int64_t B, const float* q, const float* theta, float* M, void* stream) {
@@ -174,7 +214,10 @@ fst_status fst_crba(const fst_model* m, int64_t B, const float* q, const float* 
   if (skip || m->nv == 0) return FST_OK;
   FST_CHECK(need(fn, q, "q"));
   FST_CHECK(need(fn, M, "M"));
-  return finish(fn, launch_crba(view_of(m, theta), B, q, M, launch_of(B, stream)));
+  const ModelView mv = view_of(m, theta);
+  if (jit_has(m, JK_CRBA))
+    return finish(fn, jit_go(m, JK_CRBA, B, m->nq, 0, 1, (cudaStream_t)stream, nullptr, mv, B, q, M));
+  return finish(fn, launch_crba(mv, B, q, M, launch_of(B, stream)));
 }
 
 fst_status fst_aba(const fst_model* m, int64_t B, const float* q, const float* qd, const float* tau,
@@ -187,7 +230,11 @@ fst_status fst_aba(const fst_model* m, int64_t B, const float* q, const float* q
   FST_CHECK(need(fn, qd, "qd"));
   FST_CHECK(need(fn, tau, "tau"));
   FST_CHECK(need(fn, qdd, "qdd"));
-  return finish(fn, launch_aba(view_of(m, theta), B, q, qd, tau, qdd, launch_of(B, stream)));
+  const ModelView mv = view_of(m, theta);
+  if (jit_has(m, JK_ABA))
+    return finish(fn, jit_go(m, JK_ABA, B, m->nq + 2 * m->nv, 0, 1, (cudaStream_t)stream, nullptr, mv, B, q, qd,
+                             tau, qdd));
+  return finish(fn, launch_aba(mv, B, q, qd, tau, qdd, launch_of(B, stream)));
 }
 
 fst_status fst_eval(const fst_model* m, int64_t B, const fst_eval_io* io, const float* theta, void* stream) {
@@ -233,7 +280,11 @@ fst_status fst_eval(const fst_model* m, int64_t B, const fst_eval_io* io, const 
   }
   if (skip || a.n_roles == 0) return FST_OK;
   if (m->nq) FST_CHECK(need(fn, io->q, "q"));
-  return finish(fn, launch_eval(view_of(m, theta), B, a, launch_of(B, stream)));
+  const ModelView mv = view_of(m, theta);
+  if (jit_has(m, JK_EVAL))
+    return finish(fn, jit_go(m, JK_EVAL, B, m->nq + 2 * m->nv, 0, (unsigned)a.n_roles, (cudaStream_t)stream, nullptr,
+                             mv, B, a));
+  return finish(fn, launch_eval(mv, B, a, launch_of(B, stream)));
 }
 
 fst_status fst_adjoint_scratch_bytes(const fst_model* m, int64_t B, size_t* bytes) {
@@ -259,7 +310,11 @@ fst_status fst_fk_vjp(const fst_model* m, int64_t B, const float* q, const float
   if (skip || m->nq == 0 || !q_bar) return FST_OK;
   FST_CHECK(need(fn, q, "q"));
   FST_CHECK(need(fn, poses_bar, "poses_bar"));
-  return finish(fn, launch_fk_vjp(view_of(m, nullptr), B, q, poses_bar, q_bar, (cudaStream_t)stream));
+  const ModelView mv = view_of(m, nullptr);
+  if (jit_has(m, JK_FK_VJP))
+    return finish(fn, jit_go(m, JK_FK_VJP, B, m->nq + 12 * m->n, 0, 1, (cudaStream_t)stream, nullptr, mv, B, q,
+                             poses_bar, q_bar));
+  return finish(fn, launch_fk_vjp(mv, B, q, poses_bar, q_bar, (cudaStream_t)stream));
 }
 
 fst_status fst_rnea_vjp(const fst_model* m, int64_t B, const float* q, const float* qd, const float* qdd,
@@ -277,7 +332,17 @@ fst_status fst_rnea_vjp(const fst_model* m, int64_t B, const float* q, const flo
   FST_CHECK(need(fn, qd, "qd"));
   FST_CHECK(need(fn, qdd, "qdd"));
   FST_CHECK(need(fn, tau_bar, "tau_bar"));
-  return finish(fn, launch_rnea_vjp(view_of(m, theta), B, q, qd, qdd, tau_bar, q_bar, qd_bar, qdd_bar, theta_bar,
+  const ModelView mv = view_of(m, theta);
+  if (jit_has(m, JK_RNEA_VJP)) {
+    unsigned nblk = 0;
+    float* partial = theta_bar ? (float*)scratch : nullptr;
+    const int P = theta_bar ? m->n * 10 : 0;
+    cudaError_t err = jit_go(m, JK_RNEA_VJP, B, m->nq + 3 * m->nv, P, 1, (cudaStream_t)stream, &nblk, mv, B, q, qd,
+                             qdd, tau_bar, q_bar, qd_bar, qdd_bar, partial);
+    if (err == cudaSuccess && theta_bar) err = launch_partial_reduce(partial, (int)nblk, P, theta_bar, (cudaStream_t)stream);
+    return finish(fn, err);
+  }
+  return finish(fn, launch_rnea_vjp(mv, B, q, qd, qdd, tau_bar, q_bar, qd_bar, qdd_bar, theta_bar,
                                     (float*)scratch, (cudaStream_t)stream));
 }
 
@@ -296,7 +361,17 @@ fst_status fst_aba_vjp(const fst_model* m, int64_t B, const float* q, const floa
   FST_CHECK(need(fn, qd, "qd"));
   FST_CHECK(need(fn, qdd, "qdd"));
   FST_CHECK(need(fn, qdd_bar, "qdd_bar"));
-  return finish(fn, launch_aba_vjp(view_of(m, theta), B, q, qd, qdd, qdd_bar, q_bar, qd_bar, tau_bar, theta_bar,
+  const ModelView mv = view_of(m, theta);
+  if (jit_has(m, JK_ABA_VJP)) {
+    unsigned nblk = 0;
+    float* partial = theta_bar ? (float*)scratch : nullptr;
+    const int P = theta_bar ? m->n * 10 : 0;
+    cudaError_t err = jit_go(m, JK_ABA_VJP, B, m->nq + 4 * m->nv, P, 1, (cudaStream_t)stream, &nblk, mv, B, q, qd,
+                             qdd, qdd_bar, q_bar, qd_bar, tau_bar, partial);
+    if (err == cudaSuccess && theta_bar) err = launch_partial_reduce(partial, (int)nblk, P, theta_bar, (cudaStream_t)stream);
+    return finish(fn, err);
+  }
+  return finish(fn, launch_aba_vjp(mv, B, q, qd, qdd, qdd_bar, q_bar, qd_bar, tau_bar, theta_bar,
                                    (float*)scratch, (cudaStream_t)stream));
 }
 
@@ -316,7 +391,16 @@ fst_status fst_rnea_loss_grad(const fst_model* m, int64_t B, const float* q, con
   FST_CHECK(need(fn, qd, "qd"));
   FST_CHECK(need(fn, qdd, "qdd"));
   FST_CHECK(need(fn, tau_meas, "tau_meas"));
-  return finish(fn, launch_rnea_loss_grad(view_of(m, theta), B, q, qd, qdd, tau_meas, loss_theta_bar, q_bar, qd_bar,
+  const ModelView mv = view_of(m, theta);
+  if (jit_has(m, JK_LOSS_GRAD)) {
+    unsigned nblk = 0;
+    const int P = m->n * 10 + 1;
+    cudaError_t err = jit_go(m, JK_LOSS_GRAD, B, m->nq + 3 * m->nv, P, 1, (cudaStream_t)stream, &nblk, mv, B, q, qd,
+                             qdd, tau_meas, q_bar, qd_bar, (float*)scratch);
+    if (err == cudaSuccess) err = launch_partial_reduce((float*)scratch, (int)nblk, P, loss_theta_bar, (cudaStream_t)stream);
+    return finish(fn, err);
+  }
+  return finish(fn, launch_rnea_loss_grad(mv, B, q, qd, qdd, tau_meas, loss_theta_bar, q_bar, qd_bar,
                                           (float*)scratch, (cudaStream_t)stream));
 }
 

@@ -6,6 +6,7 @@
 // the same word (a broadcast), and the environment's inputs are staged into
 // shared memory with asynchronous copies before the sweep starts.
 #include "ops.cuh"
+#include "launch.h"
 
 namespace fst {
 namespace {

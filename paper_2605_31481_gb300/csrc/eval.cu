@@ -9,6 +9,7 @@
 // together fill it, and the launch takes as long as its slowest role rather
 // than the sum of all of them.
 #include "ops.cuh"
+#include "launch.h"
 
 namespace fst {
 namespace {

@@ -8,9 +8,11 @@
 // are a handful of 3x3 operations on registers).
 #pragma once
 
+#ifndef __CUDACC_RTC__
 #include <cuda_runtime.h>
+#endif
 
-#include "fst_internal.h"
+#include "fst_layout.h"
 
 namespace fst {
 
@@ -297,6 +299,8 @@ struct SmemModel {
   __device__ __forceinline__ int n() const { return n_; }
   __device__ __forceinline__ const BodyC& C(int k) const { return c[k]; }
   __device__ __forceinline__ BodyI I(int k) const { return i[k]; }
+  // inertial parameters (the override, if any, was staged in place)
+  __device__ __forceinline__ const float* theta(int k) const { return c[k].theta; }
 };
 
 // Copies the model constants (and the inertia override, if any) to shared

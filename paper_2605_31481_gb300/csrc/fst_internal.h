@@ -6,49 +6,11 @@
 #include <vector>
 
 #include "../../include/fst.h"
+#include "fst_layout.h"
 
 namespace fst {
-
-// Per-body FP32 constants, 64 floats (256 B) so a body is 16 float4 loads.
-// Revolute (paper Eq. 2-3, all in the parent frame):
-//   R_pc = R0 + sin(q) A + (1 - cos q) Bm,  t_pc = t0 + sin(q) a + (1 - cos q) b
-// Prismatic: R_pc = R0, t_pc = t0 + q a.   Fixed: R_pc = R0, t_pc = t0.
-// Free (body 0 only): R0 = R of T_joint, t0 = t of T_joint; the joint's own
-//   pose comes from q.
-// S: motion subspace of a 1-DOF joint in body coordinates, [w; v].
-// theta: 10 inertial parameters about the body origin [m, h(3), I(6)].
-// anc: support-path bitmask (drives the zero blocks of J and M).
-struct BodyC {
-  float R0[9];
-  float A[9];
-  float Bm[9];
-  float t0[3];
-  float a[3];
-  float b[3];
-  float S[6];
-  float theta[10];
-  unsigned long long anc;  // bit j set: body j is on this body's support path (itself included)
-  float pad[10];
-};
-static_assert(sizeof(BodyC) == 256, "BodyC must stay 256 bytes");
-
-struct BodyI {
-  int32_t parent;
-  int32_t type;
-  int32_t qi;
-  int32_t vi;
-};
-
-// Everything a kernel needs to find the model; passed by value.
-struct ModelView {
-  const BodyC* c;        // device, n entries
-  const BodyI* i;        // device, n entries
-  const float* theta;    // device [n][10] override, or nullptr
-  int n, nq, nv, depth;
-  float a0[3];           // linear part of the world's spatial acceleration: -gravity
-};
-
-}  // namespace fst
+struct JitState;
+}
 
 struct fst_model {
   int n = 0, nq = 0, nv = 0, depth = 0;
@@ -61,6 +23,7 @@ struct fst_model {
   std::vector<int> level;            // 1-based depth of each body
   fst::BodyC* dc = nullptr;
   fst::BodyI* di = nullptr;
+  fst::JitState* jit = nullptr;      // run-time specialised kernels, if any
 };
 
 namespace fst {

@@ -1,0 +1,84 @@
+// Device-safe layout shared by the host model builder, the kernels and the
+// run-time specialised (NVRTC) kernels: no host-only headers here.
+#pragma once
+
+#ifdef __CUDACC_RTC__
+typedef long long int64_t;
+typedef int int32_t;
+typedef unsigned long long uint64_t;
+typedef unsigned long size_t;
+#define FST_MAX_BODIES 64
+#define FST_MAX_LINKS 16
+enum { FST_JOINT_FIXED = 0, FST_JOINT_REVOLUTE = 1, FST_JOINT_PRISMATIC = 2, FST_JOINT_FREE = 3 };
+#else
+#include <cstdint>
+
+#include "../../include/fst.h"
+#endif
+
+namespace fst {
+
+// Per-body FP32 constants, 64 floats (256 B) so a body is 16 float4 loads.
+// Revolute (paper Eq. 2-3, all in the parent frame):
+//   R_pc = R0 + sin(q) A + (1 - cos q) Bm,  t_pc = t0 + sin(q) a + (1 - cos q) b
+// Prismatic: R_pc = R0, t_pc = t0 + q a.   Fixed: R_pc = R0, t_pc = t0.
+// Free (body 0 only): R0 = R of T_joint, t0 = t of T_joint; the joint's own
+//   pose comes from q.
+// S: motion subspace of a 1-DOF joint in body coordinates, [w; v].
+// theta: 10 inertial parameters about the body origin [m, h(3), I(6)].
+// anc: support-path bitmask (drives the zero blocks of J and M).
+struct BodyC {
+  float R0[9];
+  float A[9];
+  float Bm[9];
+  float t0[3];
+  float a[3];
+  float b[3];
+  float S[6];
+  float theta[10];
+  unsigned long long anc;  // bit j set: body j is on this body's support path (itself included)
+  float pad[10];
+};
+static_assert(sizeof(BodyC) == 256, "BodyC must stay 256 bytes");
+
+struct BodyI {
+  int32_t parent;
+  int32_t type;
+  int32_t qi;
+  int32_t vi;
+};
+
+// Everything a kernel needs to find the model; passed by value.
+struct ModelView {
+  const BodyC* c;        // device, n entries
+  const BodyI* i;        // device, n entries
+  const float* theta;    // device [n][10] override, or nullptr
+  int n, nq, nv, depth;
+  float a0[3];           // linear part of the world's spatial acceleration: -gravity
+};
+
+struct LinkList {
+  int n;
+  int idx[FST_MAX_LINKS];
+};
+
+// Operators of the fused evaluation kernel, in launch order (longest first,
+// so the slowest role's blocks are dispatched first).
+enum Role { ROLE_ABA = 0, ROLE_CRBA = 1, ROLE_RNEA = 2, ROLE_KIN = 3 };
+
+struct EvalArgs {
+  const float* q;
+  const float* qd;
+  const float* qdd;
+  const float* tau;
+  float* poses;
+  float* J;
+  float* tau_out;
+  float* M;
+  float* qdd_out;
+  LinkList links;
+  int roles[4];
+  int n_roles;
+};
+
+}  // namespace fst

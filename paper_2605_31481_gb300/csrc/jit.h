@@ -1,0 +1,32 @@
+// Run-time specialised kernels (jit.cpp): which kernels exist per model and
+// how to launch them.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "fst_internal.h"
+
+namespace fst {
+
+// Kernel kinds; bit k of a specialisation mask selects kind k.
+enum JitKind {
+  JK_FK = 0,
+  JK_JACOBIAN,
+  JK_RNEA,
+  JK_CRBA,
+  JK_ABA,
+  JK_EVAL,
+  JK_FK_VJP,
+  JK_RNEA_VJP,
+  JK_ABA_VJP,
+  JK_LOSS_GRAD,
+  JK_COUNT
+};
+
+fst_status jit_specialize(fst_model* m, unsigned mask);
+void jit_release(fst_model* m);
+unsigned jit_mask(const fst_model* m);
+bool jit_has(const fst_model* m, int kind);
+cudaError_t jit_launch(const fst_model* m, int kind, dim3 grid, int block, size_t smem, cudaStream_t s, void** args);
+
+}  // namespace fst

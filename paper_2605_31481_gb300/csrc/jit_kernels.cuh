@@ -1,0 +1,289 @@
+// Kernels specialised for one fixed tree, compiled at run time by NVRTC.
+//
+// The host generator (jit.cpp) writes a prelude that defines FST_N (the
+// number of bodies), the model constants kC/kI as initialised device
+// constants, and one FST_JIT_* macro naming the kernel to build, then
+// includes this file. The kernels call the same operator templates as the
+// generic kernels, with a compile-time topology: every body loop is fully
+// unrolled, every parent index is a constant, and the per-body sweep state
+// lives in registers instead of per-thread local memory. Only the inertial
+// parameters are read at run time (from the override or the model's device
+// copy), so one compiled module serves every parameter set.
+#pragma once
+
+#include "adjoint.cuh"
+
+namespace fst {
+
+struct FixedTopo {
+  const float* th;  // inertial parameters of body k at th + k * ts
+  int ts;
+  __device__ __forceinline__ static constexpr int n() { return FST_N; }
+  __device__ __forceinline__ const BodyC& C(int k) const { return kC[k]; }
+  __device__ __forceinline__ BodyI I(int k) const { return kI[k]; }
+  __device__ __forceinline__ const float* theta(int k) const { return th + k * ts; }
+};
+
+__device__ __forceinline__ FixedTopo fixed_topo(const ModelView& mv) {
+  if (mv.theta) return FixedTopo{mv.theta, 10};
+  return FixedTopo{mv.c[0].theta, (int)(sizeof(BodyC) / sizeof(float))};
+}
+
+__device__ __forceinline__ Col jit_stage_or_zero(float* tile, const float* __restrict__ src, int rows, int64_t B,
+                                                 int64_t e, bool act) {
+  if (act) return stage_rows(tile, src, rows, B, e);
+  float* dst = tile + threadIdx.x;
+  for (int k = 0; k < rows; ++k) dst[k * blockDim.x] = 0.f;
+  return Col{dst, (int)blockDim.x};
+}
+
+__device__ __forceinline__ void jit_write_partial(const float* slots, int P, float* partial) {
+  const int warps = blockDim.x / 32;
+  for (int p = threadIdx.x; p < P; p += blockDim.x) {
+    float s = 0.f;
+    for (int w = 0; w < warps; ++w) s += slots[w * P + p];
+    partial[(int64_t)blockIdx.x * P + p] = s;
+  }
+}
+
+}  // namespace fst
+
+using namespace fst;
+
+#define FST_JIT_PROLOGUE                                              \
+  extern __shared__ float4 smem[];                                    \
+  float* tile = reinterpret_cast<float*>(smem);                       \
+  const int T = blockDim.x;                                           \
+  const int64_t e = (int64_t)blockIdx.x * T + threadIdx.x;            \
+  const bool act = e < B;                                             \
+  (void)T;                                                            \
+  (void)act
+
+#ifdef FST_JIT_FK
+extern "C" __global__ void __launch_bounds__(128) fst_jit_kernel(ModelView mv, int64_t B, const float* __restrict__ q,
+                                                                 float* __restrict__ poses) {
+  FST_JIT_PROLOGUE;
+  if (!act) return;
+  const Col cq = stage_rows(tile, q, mv.nq, B, e);
+  cp_async_wait_all();
+  fk_env<FST_N>(fixed_topo(mv), cq, poses, B, e);
+}
+#endif
+
+#ifdef FST_JIT_JACOBIAN
+extern "C" __global__ void __launch_bounds__(128) fst_jit_kernel(ModelView mv, int64_t B, const float* __restrict__ q,
+                                                                 LinkList links, float* __restrict__ J) {
+  FST_JIT_PROLOGUE;
+  if (!act) return;
+  const Col cq = stage_rows(tile, q, mv.nq, B, e);
+  cp_async_wait_all();
+  jac_env<FST_N>(fixed_topo(mv), cq, mv.nv, links, nullptr, J, B, e);
+}
+#endif
+
+#ifdef FST_JIT_RNEA
+extern "C" __global__ void __launch_bounds__(128) fst_jit_kernel(ModelView mv, int64_t B, const float* __restrict__ q,
+                                                                 const float* __restrict__ qd,
+                                                                 const float* __restrict__ qdd,
+                                                                 float* __restrict__ tau) {
+  FST_JIT_PROLOGUE;
+  if (!act) return;
+  const Col cq = stage_rows(tile, q, mv.nq, B, e);
+  const Col cqd = stage_rows(tile + mv.nq * T, qd, mv.nv, B, e);
+  const Col cqdd = stage_rows(tile + (mv.nq + mv.nv) * T, qdd, mv.nv, B, e);
+  cp_async_wait_all();
+  rnea_env<FST_N>(fixed_topo(mv), world_accel(mv), cq, cqd, cqdd, tau, B, e);
+}
+#endif
+
+#ifdef FST_JIT_CRBA
+extern "C" __global__ void __launch_bounds__(128) fst_jit_kernel(ModelView mv, int64_t B, const float* __restrict__ q,
+                                                                 float* __restrict__ M) {
+  FST_JIT_PROLOGUE;
+  if (!act) return;
+  const Col cq = stage_rows(tile, q, mv.nq, B, e);
+  cp_async_wait_all();
+  crba_env<FST_N>(fixed_topo(mv), cq, mv.nv, M, B, e);
+}
+#endif
+
+#ifdef FST_JIT_ABA
+extern "C" __global__ void __launch_bounds__(128) fst_jit_kernel(ModelView mv, int64_t B, const float* __restrict__ q,
+                                                                 const float* __restrict__ qd,
+                                                                 const float* __restrict__ tau,
+                                                                 float* __restrict__ qdd) {
+  FST_JIT_PROLOGUE;
+  if (!act) return;
+  const Col cq = stage_rows(tile, q, mv.nq, B, e);
+  const Col cqd = stage_rows(tile + mv.nq * T, qd, mv.nv, B, e);
+  const Col ctau = stage_rows(tile + (mv.nq + mv.nv) * T, tau, mv.nv, B, e);
+  cp_async_wait_all();
+  aba_env<FST_N>(fixed_topo(mv), world_accel(mv), cq, cqd, ctau, qdd, B, e);
+}
+#endif
+
+#ifdef FST_JIT_EVAL
+extern "C" __global__ void __launch_bounds__(128) fst_jit_kernel(ModelView mv, int64_t B, EvalArgs a) {
+  FST_JIT_PROLOGUE;
+  if (!act) return;
+  const int role = a.roles[blockIdx.y];
+  const Col cq = stage_rows(tile, a.q, mv.nq, B, e);
+  Col c1{}, c2{};
+  if (role == ROLE_RNEA) {
+    c1 = stage_rows(tile + mv.nq * T, a.qd, mv.nv, B, e);
+    c2 = stage_rows(tile + (mv.nq + mv.nv) * T, a.qdd, mv.nv, B, e);
+  } else if (role == ROLE_ABA) {
+    c1 = stage_rows(tile + mv.nq * T, a.qd, mv.nv, B, e);
+    c2 = stage_rows(tile + (mv.nq + mv.nv) * T, a.tau, mv.nv, B, e);
+  }
+  cp_async_wait_all();
+  const FixedTopo tp = fixed_topo(mv);
+  switch (role) {
+    case ROLE_ABA:
+      aba_env<FST_N>(tp, world_accel(mv), cq, c1, c2, a.qdd_out, B, e);
+      break;
+    case ROLE_CRBA:
+      crba_env<FST_N>(tp, cq, mv.nv, a.M, B, e);
+      break;
+    case ROLE_RNEA:
+      rnea_env<FST_N>(tp, world_accel(mv), cq, c1, c2, a.tau_out, B, e);
+      break;
+    default:
+      if (a.J)
+        jac_env<FST_N>(tp, cq, mv.nv, a.links, a.poses, a.J, B, e);
+      else
+        fk_env<FST_N>(tp, cq, a.poses, B, e);
+      break;
+  }
+}
+#endif
+
+#ifdef FST_JIT_FK_VJP
+extern "C" __global__ void __launch_bounds__(128) fst_jit_kernel(ModelView mv, int64_t B, const float* __restrict__ q,
+                                                                 const float* __restrict__ pbar,
+                                                                 float* __restrict__ qbar) {
+  FST_JIT_PROLOGUE;
+  if (!act) return;
+  const Col cq = stage_rows(tile, q, mv.nq, B, e);
+  const Col cpb = stage_rows(tile + mv.nq * T, pbar, mv.n * 12, B, e);
+  cp_async_wait_all();
+  fk_vjp_env<FST_N>(fixed_topo(mv), cq, cpb, qbar, B, e);
+}
+#endif
+
+#ifdef FST_JIT_RNEA_VJP
+extern "C" __global__ void __launch_bounds__(128) fst_jit_kernel(ModelView mv, int64_t B, const float* __restrict__ q,
+                                                                 const float* __restrict__ qd,
+                                                                 const float* __restrict__ qdd,
+                                                                 const float* __restrict__ tbar, float* qbar,
+                                                                 float* qdbar, float* qddbar, float* partial) {
+  FST_JIT_PROLOGUE;
+  const int rows = mv.nq + 3 * mv.nv;
+  const Col cq = jit_stage_or_zero(tile, q, mv.nq, B, e, act);
+  const Col cqd = jit_stage_or_zero(tile + mv.nq * T, qd, mv.nv, B, e, act);
+  const Col cqdd = jit_stage_or_zero(tile + (mv.nq + mv.nv) * T, qdd, mv.nv, B, e, act);
+  const Col ctb = jit_stage_or_zero(tile + (mv.nq + 2 * mv.nv) * T, tbar, mv.nv, B, e, act);
+  const int P = FST_N * 10;
+  float* slots = partial ? tile + rows * T : nullptr;
+  if (slots)
+    for (int k = threadIdx.x; k < (T / 32) * P; k += T) slots[k] = 0.f;
+  cp_async_wait_all();
+  __syncthreads();
+  VjpOut o{qbar, qdbar, qddbar, slots ? slots + (threadIdx.x / 32) * P : nullptr, 1.f, act};
+  rnea_vjp_env<FST_N>(fixed_topo(mv), world_accel(mv), cq, cqd, cqdd, ctb, o, B, e);
+  if (partial) {
+    __syncthreads();
+    jit_write_partial(slots, P, partial);
+  }
+}
+#endif
+
+#ifdef FST_JIT_ABA_VJP
+extern "C" __global__ void __launch_bounds__(128) fst_jit_kernel(ModelView mv, int64_t B, const float* __restrict__ q,
+                                                                 const float* __restrict__ qd,
+                                                                 const float* __restrict__ qdd,
+                                                                 const float* __restrict__ qddbar, float* qbar,
+                                                                 float* qdbar, float* taubar, float* partial) {
+  FST_JIT_PROLOGUE;
+  const int rows = mv.nq + 4 * mv.nv;
+  const Col cq = jit_stage_or_zero(tile, q, mv.nq, B, e, act);
+  const Col cqd = jit_stage_or_zero(tile + mv.nq * T, qd, mv.nv, B, e, act);
+  const Col cqdd = jit_stage_or_zero(tile + (mv.nq + mv.nv) * T, qdd, mv.nv, B, e, act);
+  const Col cqb = jit_stage_or_zero(tile + (mv.nq + 2 * mv.nv) * T, qddbar, mv.nv, B, e, act);
+  float* lam = tile + (mv.nq + 3 * mv.nv) * T + threadIdx.x;
+  const int P = FST_N * 10;
+  float* slots = partial ? tile + rows * T : nullptr;
+  if (slots)
+    for (int k = threadIdx.x; k < (T / 32) * P; k += T) slots[k] = 0.f;
+  cp_async_wait_all();
+  __syncthreads();
+  const FixedTopo tp = fixed_topo(mv);
+  aba_env<FST_N>(tp, sv_zero(), cq, cqd, cqb, nullptr, B, e, true, lam, T);
+  const Col clam{lam, T};
+  if (taubar && act)
+    for (int k = 0; k < mv.nv; ++k) taubar[(int64_t)k * B + e] = clam[k];
+  VjpOut o{qbar, qdbar, nullptr, slots ? slots + (threadIdx.x / 32) * P : nullptr, -1.f, act};
+  rnea_vjp_env<FST_N>(tp, world_accel(mv), cq, cqd, cqdd, clam, o, B, e);
+  if (partial) {
+    __syncthreads();
+    jit_write_partial(slots, P, partial);
+  }
+}
+#endif
+
+#ifdef FST_JIT_LOSS_GRAD
+extern "C" __global__ void __launch_bounds__(128) fst_jit_kernel(ModelView mv, int64_t B, const float* __restrict__ q,
+                                                                 const float* __restrict__ qd,
+                                                                 const float* __restrict__ qdd,
+                                                                 const float* __restrict__ tau_meas, float* qbar,
+                                                                 float* qdbar, float* partial) {
+  FST_JIT_PROLOGUE;
+  const int rows = mv.nq + 3 * mv.nv;
+  const Col cq = jit_stage_or_zero(tile, q, mv.nq, B, e, act);
+  const Col cqd = jit_stage_or_zero(tile + mv.nq * T, qd, mv.nv, B, e, act);
+  const Col cqdd = jit_stage_or_zero(tile + (mv.nq + mv.nv) * T, qdd, mv.nv, B, e, act);
+  jit_stage_or_zero(tile + (mv.nq + 2 * mv.nv) * T, tau_meas, mv.nv, B, e, act);
+  const int P = FST_N * 10 + 1;
+  float* slots = tile + rows * T;
+  for (int k = threadIdx.x; k < (T / 32) * P; k += T) slots[k] = 0.f;
+  cp_async_wait_all();
+  __syncthreads();
+  const FixedTopo tp = fixed_topo(mv);
+  const SV a0 = world_accel(mv);
+  Xf X[FST_N];
+  SV v[FST_N], a[FST_N], F[FST_N];
+  rnea_forward<FST_N>(tp, a0, cq, cqd, cqdd, X, v, a, F);
+  rnea_backward<FST_N>(tp, X, F, nullptr, B, e);
+  float* tb = tile + (mv.nq + 2 * mv.nv) * T + threadIdx.x;
+  float loss = 0.f;
+#pragma unroll
+  for (int i = 0; i < FST_N; ++i) {
+    const BodyI bi = tp.I(i);
+    const int nvi = nv_of(bi.type);
+    if (nvi == 0) continue;
+    float tau6[6];
+    if (nvi == 1) {
+      tau6[0] = dot(S_of(tp.C(i)), F[i]);
+    } else {
+      tau6[0] = F[i].v.x; tau6[1] = F[i].v.y; tau6[2] = F[i].v.z;
+      tau6[3] = F[i].w.x; tau6[4] = F[i].w.y; tau6[5] = F[i].w.z;
+    }
+#pragma unroll
+    for (int r = 0; r < 6; ++r) {
+      if (r >= nvi) break;
+      const float res = tau6[r] - tb[(bi.vi + r) * T];
+      loss = fmaf(res, res, loss);
+      tb[(bi.vi + r) * T] = 2.f * res;
+    }
+  }
+  float* wslot = slots + (threadIdx.x / 32) * P;
+  float lg = act ? loss : 0.f;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) lg += __shfl_xor_sync(0xffffffffu, lg, off);
+  if ((threadIdx.x & 31) == 0) wslot[P - 1] += lg;
+  VjpOut o{qbar, qdbar, nullptr, wslot, 1.f, act};
+  rnea_vjp_reverse<FST_N>(tp, a0, cq, cqd, X, v, a, F, Col{tb, T}, o, B, e);
+  __syncthreads();
+  jit_write_partial(slots, P, partial);
+}
+#endif

@@ -1,6 +1,7 @@
 // Forward kinematics and geometric Jacobian kernels, one environment per
 // thread (bodies in ops.cuh).
 #include "ops.cuh"
+#include "launch.h"
 
 namespace fst {
 namespace {

@@ -11,30 +11,6 @@
 
 namespace fst {
 
-struct LinkList {
-  int n;
-  int idx[FST_MAX_LINKS];
-};
-
-// Operators of the fused evaluation kernel, in launch order (longest first,
-// so the slowest role's blocks are dispatched first).
-enum Role { ROLE_ABA = 0, ROLE_CRBA = 1, ROLE_RNEA = 2, ROLE_KIN = 3 };
-
-struct EvalArgs {
-  const float* q;
-  const float* qd;
-  const float* qdd;
-  const float* tau;
-  float* poses;
-  float* J;
-  float* tau_out;
-  float* M;
-  float* qdd_out;
-  LinkList links;
-  int roles[4];
-  int n_roles;
-};
-
 struct Launch {
   int block;          // threads per block (environments per block for 1 env/thread)
   cudaStream_t stream;
@@ -102,6 +78,8 @@ cudaError_t launch_aba(const ModelView& mv, int64_t B, const float* q, const flo
 // Adjoints (adjoint.cu). scratch: vjp_scratch_floats(n, B) floats of device
 // memory for the per-block partial sums of thetabar (and the loss).
 size_t vjp_scratch_floats(int n, int64_t B);
+// out[p] = sum over b < nblk of partial[b * P + p] (in block order)
+cudaError_t launch_partial_reduce(const float* partial, int nblk, int P, float* out, cudaStream_t s);
 cudaError_t launch_fk_vjp(const ModelView& mv, int64_t B, const float* q, const float* pbar, float* qbar,
                           cudaStream_t s);
 cudaError_t launch_rnea_vjp(const ModelView& mv, int64_t B, const float* q, const float* qd, const float* qdd,

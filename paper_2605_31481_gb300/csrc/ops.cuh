@@ -11,7 +11,6 @@
 #pragma once
 
 #include "fst_device.cuh"
-#include "launch.h"
 
 namespace fst {
 
@@ -140,7 +139,7 @@ __device__ __forceinline__ void rnea_forward(const TP& tp, SV a0, const Col& q, 
       vi = X_motion(X[i], v[bi.parent]) + vJ;
       ai = X_motion(X[i], a[bi.parent]) + aJ + crm(vi, vJ);
     }
-    const In10 I = in_load(c.theta);
+    const In10 I = in_load(tp.theta(i));
     v[i] = vi;
     a[i] = ai;
     f[i] = in_mul(I, ai) + crf(vi, in_mul(I, vi));
@@ -183,7 +182,7 @@ __device__ __forceinline__ void crba_env(const TP& tp, const Col& q, int nv, flo
   FST_UNROLL
   for (int i = 0; i < tp.n(); ++i) {
     X[i] = joint_X(tp.C(i), tp.I(i), q);
-    Ic[i] = in_load(tp.C(i).theta);
+    Ic[i] = in_load(tp.theta(i));
   }
   FST_UNROLL
   for (int i = tp.n() - 1; i > 0; --i) {
@@ -329,7 +328,7 @@ __device__ __forceinline__ void aba_env(const TP& tp, SV a0, const Col& q, const
     const BodyC& c = tp.C(i);
     const BodyI bi = tp.I(i);
     X[i] = joint_X(c, bi, q);
-    const In10 I = in_load(c.theta);
+    const In10 I = in_load(tp.theta(i));
     IA[i] = sym6_from_in(I);
     if (qd_zero) {
       va[i] = sv_zero();
