@@ -38,6 +38,9 @@ extern const char* const kJitHeaderSources[];
 
 namespace {
 
+const char* const kKindName[JK_COUNT] = {"fst_jit_fk",      "fst_jit_jacobian", "fst_jit_rnea",     "fst_jit_crba",
+                                         "fst_jit_aba",     "fst_jit_eval",     "fst_jit_fk_vjp",   "fst_jit_rnea_vjp",
+                                         "fst_jit_aba_vjp", "fst_jit_loss_grad"};
 const char* const kKindMacro[JK_COUNT] = {"FST_JIT_FK",      "FST_JIT_JACOBIAN", "FST_JIT_RNEA",     "FST_JIT_CRBA",
                                           "FST_JIT_ABA",     "FST_JIT_EVAL",     "FST_JIT_FK_VJP",   "FST_JIT_RNEA_VJP",
                                           "FST_JIT_ABA_VJP", "FST_JIT_LOSS_GRAD"};
@@ -131,6 +134,7 @@ void put_floats(std::ostringstream& os, const float* p, int n) {
 std::string make_source(const fst_model* m, int kind) {
   std::ostringstream os;
   os << "#define FST_FIXED_TOPOLOGY 1\n#define FST_N " << m->n << "\n#define " << kKindMacro[kind] << " 1\n"
+     << "#define FST_JIT_NAME " << kKindName[kind] << "\n"
      << "#include \"fst_layout.h\"\nnamespace fst {\nstatic __device__ const BodyC kC[" << m->n << "] = {\n";
   for (int i = 0; i < m->n; ++i) {
     const BodyC& c = m->hc[i];
@@ -278,7 +282,7 @@ fst_status jit_specialize(fst_model* m, unsigned mask) {
     if (D.load(&mod, j.cubin.data()) != CUDA_SUCCESS)
       return set_error(FST_ERR_CUDA, "fst_model_specialize: cuModuleLoadData failed");
     CUfunction fn;
-    if (D.get(&fn, mod, "fst_jit_kernel") != CUDA_SUCCESS) {
+    if (D.get(&fn, mod, kKindName[j.kind]) != CUDA_SUCCESS) {
       D.unload(mod);
       return set_error(FST_ERR_CUDA, "fst_model_specialize: kernel not found in the compiled module");
     }
