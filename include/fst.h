@@ -138,6 +138,19 @@ FST_API fst_status fst_model_info(const fst_model* model, int32_t* nq, int32_t* 
  * generic kernels keep serving every call. */
 FST_API fst_status fst_model_specialize(fst_model* model, uint32_t kinds);
 
+/* Launch configuration of the selected kinds (FST_SPEC_* mask, 0 = all) on
+ * this model: threads per block (32, 64, 128 or 256; 0 = built-in heuristic)
+ * and which kernel variant runs (AUTO = specialised when compiled, else
+ * generic). One environment per thread either way and results agree within
+ * FP32 rounding; only speed changes. SPECIALIZED for a kind that
+ * fst_model_specialize has not compiled returns FST_ERR_INVALID_ARG. The
+ * autotuner in the Python package measures the candidates per kind and batch
+ * size and sets the fastest. */
+#define FST_VARIANT_AUTO 0
+#define FST_VARIANT_GENERIC 1
+#define FST_VARIANT_SPECIALIZED 2
+FST_API fst_status fst_model_set_launch(fst_model* model, uint32_t kinds, int32_t block, int32_t variant);
+
 /* Bit mask of the specialised kinds currently in use for this model. */
 FST_API fst_status fst_model_specialized(const fst_model* model, uint32_t* kinds);
 

@@ -18,6 +18,7 @@ STATUS_NAMES = {
 }
 MAX_BODIES = 64
 MAX_LINKS = 16
+VARIANTS = {"auto": 0, "generic": 1, "specialized": 2}
 SPEC_KINDS = ("fk", "jacobian", "rnea", "crba", "aba", "eval", "fk_vjp", "rnea_vjp", "aba_vjp", "loss_grad")
 
 c_int32, c_int64, c_double, c_void_p = ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_void_p
@@ -61,6 +62,7 @@ _SIGS = {
                                  ctypes.POINTER(c_int32), ctypes.POINTER(c_int32)]),
     "fst_model_specialize": (c_int32, [c_void_p, ctypes.c_uint32]),
     "fst_model_specialized": (c_int32, [c_void_p, ctypes.POINTER(ctypes.c_uint32)]),
+    "fst_model_set_launch": (c_int32, [c_void_p, ctypes.c_uint32, c_int32, c_int32]),
     "fst_fk": (c_int32, [c_void_p, c_int64, c_void_p, c_void_p, c_void_p]),
     "fst_jacobian": (c_int32, [c_void_p, c_int64, c_void_p, ctypes.POINTER(c_int32), c_int32, c_void_p, c_void_p]),
     "fst_rnea": (c_int32, [c_void_p, c_int64, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),

@@ -13,7 +13,9 @@ the (B, ...) layout most training code uses.
 from __future__ import annotations
 
 import ctypes
+import hashlib
 
+import numpy as np
 import torch
 
 from . import _ffi
@@ -72,6 +74,10 @@ class Model:
         self.nq, self.nv, self.n_bodies, self.depth = nq.value, nv.value, nb.value, depth.value
         self.name = getattr(tree, "name", "tree")
         self.ee = tuple(getattr(tree, "ee", ()))
+        h = hashlib.sha1()
+        for f in ("parent", "jtype", "axis", "T_joint", "T_link", "mass", "com", "I_com", "gravity"):
+            h.update(np.ascontiguousarray(np.asarray(getattr(tree, f), dtype=np.float64)).tobytes())
+        self.fingerprint = h.hexdigest()[:16]
         if specialize:
             self.specialize(None if specialize is True else specialize)
 
@@ -82,6 +88,14 @@ class Model:
         with torch.cuda.device(self.device):
             check(_ffi.lib().fst_model_specialize(self._h, mask))
         return self.specialized()
+
+    def set_launch(self, kinds=None, block=0, variant="auto"):
+        """Launch configuration (fst_model_set_launch) of the given kernel
+        kinds (names from _ffi.SPEC_KINDS, None = all): threads per block
+        (0 = built-in heuristic) and variant ("auto", "generic",
+        "specialized")."""
+        mask = 0 if kinds is None else sum(1 << _ffi.SPEC_KINDS.index(k) for k in kinds)
+        check(_ffi.lib().fst_model_set_launch(self._h, mask, int(block), _ffi.VARIANTS[variant]))
 
     def specialized(self):
         """Names of the kernel kinds that run specialised for this model."""

@@ -1,0 +1,198 @@
+"""Autotuner for the launch configuration of the kernels.
+
+For one model and batch size it measures, on the current GPU, every
+candidate configuration of each kernel kind — variant (generic kernels with
+the tree in shared memory, or kernels specialised for the tree) and
+environments per block (32, 64, 128, 256; one environment per thread) — and
+keeps the fastest via fst_model_set_launch. For a multi-operator step it also
+decides between the fused launch (fst_eval, operators side by side) and the
+operators one after another: fusing pays at small B, where one operator
+leaves most SMs idle, and costs at large B, where one register allocation
+for all operators lowers occupancy.
+
+Timings replay a CUDA graph of repeated launches, so host launch overhead is
+excluded. Choices are cached in a JSON file (FST_TUNE_CACHE, default
+~/.cache/fst_tune.json) keyed by the tree's fingerprint, the kind, B and the
+GPU name.
+"""
+from __future__ import annotations
+
+import json
+import os
+import threading
+
+import torch
+
+from . import api
+from . import _ffi
+
+CANDIDATE_BLOCKS = (32, 64, 128, 256)
+FORWARD_KINDS = ("fk", "jacobian", "rnea", "crba", "aba")
+_lock = threading.Lock()
+
+
+def _cache_path():
+    return os.environ.get("FST_TUNE_CACHE", os.path.join(os.path.expanduser("~"), ".cache", "fst_tune.json"))
+
+
+def _load_cache():
+    try:
+        with open(_cache_path()) as fh:
+            return json.load(fh)
+    except (OSError, ValueError):
+        return {}
+
+
+def _store_cache(entries):
+    path = _cache_path()
+    with _lock:
+        data = _load_cache()
+        data.update(entries)
+        os.makedirs(os.path.dirname(path), exist_ok=True)
+        tmp = f"{path}.{os.getpid()}.tmp"
+        with open(tmp, "w") as fh:
+            json.dump(data, fh, indent=1, sort_keys=True)
+        os.replace(tmp, path)
+
+
+def graph_time_us(fn, n=20, reps=10):
+    """Mean device time of fn() in microseconds, from a CUDA graph of n
+    calls replayed reps times (fn must only enqueue work)."""
+    for _ in range(2):
+        fn()
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        for _ in range(n):
+            fn()
+    g.replay()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(reps):
+        g.replay()
+    b.record()
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) * 1e3 / (n * reps)
+
+
+class Buffers:
+    """Synthetic device inputs and outputs for timing one model at batch B."""
+
+    def __init__(self, model, B, links):
+        dev = model.device
+        gen = torch.Generator(device=dev).manual_seed(0)
+        r = lambda *s: torch.randn(*s, device=dev, generator=gen)
+        self.q = r(model.nq, B)   # a free base's quaternion rows are normalised in the kernels
+        self.qd, self.qdd, self.tau = r(model.nv, B), r(model.nv, B), r(model.nv, B)
+        self.links = list(links)
+        self.out = {"poses": torch.empty(model.n_bodies, 12, B, device=dev),
+                    "J": torch.empty(len(self.links), 6, model.nv, B, device=dev),
+                    "tau": torch.empty(model.nv, B, device=dev), "M": torch.empty(model.nv, model.nv, B, device=dev),
+                    "qdd": torch.empty(model.nv, B, device=dev)}
+        self.tbar = r(model.nv, B)
+        self.pbar = r(model.n_bodies, 12, B)
+        self.scratch = api.adjoint_scratch(model, B)
+        self.qdd_fwd = torch.empty(model.nv, B, device=dev)
+
+
+def _op(model, kind, buf):
+    m, b = model, buf
+    if kind == "fk":
+        return lambda: api.fk(m, b.q, out=b.out["poses"])
+    if kind == "jacobian":
+        return lambda: api.jacobian(m, b.q, b.links, out=b.out["J"])
+    if kind == "rnea":
+        return lambda: api.rnea(m, b.q, b.qd, b.qdd, out=b.out["tau"])
+    if kind == "crba":
+        return lambda: api.crba(m, b.q, out=b.out["M"])
+    if kind == "aba":
+        return lambda: api.aba(m, b.q, b.qd, b.tau, out=b.out["qdd"])
+    if kind == "eval":
+        return lambda: api.eval(m, b.q, b.qd, b.qdd, b.tau, fk=True, links=b.links, rnea=True, crba=True, aba=True,
+                                out=b.out)
+    if kind == "rnea_vjp":
+        return lambda: api.rnea_vjp(m, b.q, b.qd, b.qdd, b.tbar, scratch=b.scratch)
+    if kind == "fk_vjp":
+        return lambda: api.fk_vjp(m, b.q, b.pbar)
+    if kind == "aba_vjp":
+        return lambda: api.aba_vjp(m, b.q, b.qd, b.qdd_fwd, b.tbar, scratch=b.scratch)
+    if kind == "loss_grad":
+        return lambda: api.rnea_loss_grad(m, b.q, b.qd, b.qdd, b.tau, scratch=b.scratch)
+    raise ValueError(kind)
+
+
+def _key(model, kind, B):
+    return f"{model.fingerprint}|{kind}|{B}|{torch.cuda.get_device_name(model.device)}|{_ffi.lib().fst_version().decode()}"
+
+
+def tune(model, B, kinds=FORWARD_KINDS + ("eval",), links=None, use_cache=True, verbose=False):
+    """Pick and set the fastest (variant, block) for each kind at batch B.
+    Returns {kind: {"variant", "block", "us", "candidates"}}."""
+    links = list(links if links is not None else (model.ee or (model.n_bodies - 1,)))
+    cache = _load_cache() if use_cache else {}
+    spec = set(model.specialized())
+    buf = None
+    result, new = {}, {}
+    for kind in kinds:
+        key = _key(model, kind, B)
+        hit = cache.get(key)
+        if hit and (hit["variant"] != "specialized" or kind in spec):
+            model.set_launch([kind], hit["block"], hit["variant"])
+            result[kind] = hit
+            continue
+        if buf is None:
+            buf = Buffers(model, B, links)
+            if "aba_vjp" in kinds:
+                api.aba(model, buf.q, buf.qd, buf.tau, out=buf.qdd_fwd)
+        fn = _op(model, kind, buf)
+        cands = {}
+        for variant in ("generic", "specialized") if kind in spec else ("generic",):
+            for block in CANDIDATE_BLOCKS:
+                model.set_launch([kind], block, variant)
+                cands[f"{variant}/{block}"] = graph_time_us(fn)
+        best = min(cands, key=cands.get)
+        variant, block = best.split("/")
+        model.set_launch([kind], int(block), variant)
+        entry = {"variant": variant, "block": int(block), "us": round(cands[best], 3),
+                 "candidates": {k: round(v, 3) for k, v in cands.items()}}
+        result[kind] = new[key] = entry
+        if verbose:
+            print(f"[autotune] {model.name} B={B} {kind}: {best} {cands[best]:.2f} us")
+    if new and use_cache:
+        _store_cache(new)
+    return result
+
+
+class StepPlan:
+    """How to run the five forward operators on one batch: one fused launch
+    (fst_eval) or the per-operator kernels in sequence, whichever the tuner
+    measured faster (each already at its tuned configuration)."""
+
+    def __init__(self, model, B, links=None, use_cache=True, verbose=False):
+        self.model = model
+        self.links = list(links if links is not None else model.ee)
+        self.tuned = tune(model, B, FORWARD_KINDS + ("eval",), links=self.links, use_cache=use_cache,
+                          verbose=verbose)
+        fused = self.tuned["eval"]["us"]
+        seq = sum(self.tuned[k]["us"] for k in FORWARD_KINDS)
+        self.fused = fused <= seq
+        self.expected_us = min(fused, seq)
+        self.sequential_us = seq
+        self.fused_us = fused
+
+    def __call__(self, q, qd, qdd, tau, out):
+        m = self.model
+        if self.fused:
+            return api.eval(m, q, qd, qdd, tau, fk=True, links=self.links, rnea=True, crba=True, aba=True, out=out)
+        api.fk(m, q, out=out["poses"])
+        api.jacobian(m, q, self.links, out=out["J"])
+        api.rnea(m, q, qd, qdd, out=out["tau"])
+        api.crba(m, q, out=out["M"])
+        api.aba(m, q, qd, tau, out=out["qdd"])
+        return out
+
+    def describe(self):
+        return {"mode": "fused" if self.fused else "sequential", "fused_us": round(self.fused_us, 3),
+                "sequential_us": round(self.sequential_us, 3),
+                "kinds": {k: f"{v['variant']}/{v['block']}" for k, v in self.tuned.items()}}

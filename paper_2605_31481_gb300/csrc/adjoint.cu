@@ -47,7 +47,7 @@ __device__ __forceinline__ void write_partial(const float* slots, int P, float* 
 }
 
 template <int NB>
-__global__ void __launch_bounds__(128) rnea_vjp_kernel(ModelView mv, int64_t B, const float* __restrict__ q,
+__global__ void __launch_bounds__(256) rnea_vjp_kernel(ModelView mv, int64_t B, const float* __restrict__ q,
                                                        const float* __restrict__ qd, const float* __restrict__ qdd,
                                                        const float* __restrict__ tbar, float* qbar, float* qdbar,
                                                        float* qddbar, float* partial) {
@@ -77,7 +77,7 @@ __global__ void __launch_bounds__(128) rnea_vjp_kernel(ModelView mv, int64_t B, 
 // ABA adjoint: lambda = M^-1 qddbar by an ABA sweep (qd = 0, no gravity),
 // then minus the RNEA adjoint at the forward solution qdd with taubar = lambda.
 template <int NB>
-__global__ void __launch_bounds__(128) aba_vjp_kernel(ModelView mv, int64_t B, const float* __restrict__ q,
+__global__ void __launch_bounds__(256) aba_vjp_kernel(ModelView mv, int64_t B, const float* __restrict__ q,
                                                       const float* __restrict__ qd, const float* __restrict__ qdd,
                                                       const float* __restrict__ qddbar, float* qbar, float* qdbar,
                                                       float* taubar, float* partial) {
@@ -115,7 +115,7 @@ __global__ void __launch_bounds__(128) aba_vjp_kernel(ModelView mv, int64_t B, c
 // state stays on chip between the forward sweep and the reverse sweeps.
 // The block's share of L goes to partial[P] (after the P theta values).
 template <int NB>
-__global__ void __launch_bounds__(128) rnea_loss_grad_kernel(ModelView mv, int64_t B, const float* __restrict__ q,
+__global__ void __launch_bounds__(256) rnea_loss_grad_kernel(ModelView mv, int64_t B, const float* __restrict__ q,
                                                              const float* __restrict__ qd,
                                                              const float* __restrict__ qdd,
                                                              const float* __restrict__ tau_meas, float* qbar,
@@ -173,7 +173,7 @@ __global__ void __launch_bounds__(128) rnea_loss_grad_kernel(ModelView mv, int64
 }
 
 template <int NB>
-__global__ void __launch_bounds__(128) fk_vjp_kernel(ModelView mv, int64_t B, const float* __restrict__ q,
+__global__ void __launch_bounds__(256) fk_vjp_kernel(ModelView mv, int64_t B, const float* __restrict__ q,
                                                      const float* __restrict__ pbar, float* __restrict__ qbar) {
   extern __shared__ float4 smem[];
   const int T = blockDim.x;

@@ -56,7 +56,15 @@ fst_status need(const char* fn, const void* p, const char* name) {
   return set_error(FST_ERR_INVALID_ARG, std::string(fn) + ": null " + name);
 }
 
-Launch launch_of(int64_t B, void* stream) { return Launch{default_block(B), (cudaStream_t)stream}; }
+// Whether a call of this kind runs the specialised kernel: it must exist,
+// and the kind must not be pinned to the generic variant.
+bool use_jit(const fst_model* m, int kind) { return m->variant[kind] != FST_VARIANT_GENERIC && jit_has(m, kind); }
+
+int block_of(const fst_model* m, int kind, int64_t B) { return m->block[kind] ? m->block[kind] : default_block(B); }
+
+Launch launch_of(const fst_model* m, int kind, int64_t B, void* stream) {
+  return Launch{block_of(m, kind, B), (cudaStream_t)stream};
+}
 
 fst_status finish(const char* fn, cudaError_t err) {
   if (err != cudaSuccess) return cuda_error(fn, err);
@@ -69,7 +77,7 @@ fst_status finish(const char* fn, cudaError_t err) {
 template <typename... A>
 cudaError_t jit_go(const fst_model* m, int kind, int64_t B, int rows, int P, unsigned gy, cudaStream_t s,
                    unsigned* nblk, A... args) {
-  int T = default_block(B);
+  int T = block_of(m, kind, B);
   auto smem = [&](int t) { return (size_t)rows * t * sizeof(float) + (size_t)(t / 32) * P * sizeof(float); };
   while (T > 32 && smem(T) > 96 * 1024) T /= 2;
   const dim3 grid(grid_for(B, T), gy);
@@ -139,6 +147,25 @@ fst_status fst_model_specialize(fst_model* m, uint32_t kinds) {
   return jit_specialize(m, kinds);
 }
 
+fst_status fst_model_set_launch(fst_model* m, uint32_t kinds, int32_t block, int32_t variant) {
+  if (!m) return set_error(FST_ERR_INVALID_ARG, "fst_model_set_launch: null model");
+  if (block != 0 && block != 32 && block != 64 && block != 128 && block != 256)
+    return set_error(FST_ERR_INVALID_ARG, "fst_model_set_launch: block must be 0, 32, 64, 128 or 256");
+  if (variant < FST_VARIANT_AUTO || variant > FST_VARIANT_SPECIALIZED)
+    return set_error(FST_ERR_INVALID_ARG, "fst_model_set_launch: unknown variant");
+  if (kinds == 0) kinds = FST_SPEC_ALL;
+  if (kinds & ~(uint32_t)FST_SPEC_ALL) return set_error(FST_ERR_INVALID_ARG, "fst_model_set_launch: unknown kind bits");
+  for (int k = 0; k < JK_COUNT; ++k)
+    if (((kinds >> k) & 1u) && variant == FST_VARIANT_SPECIALIZED && !jit_has(m, k))
+      return set_error(FST_ERR_INVALID_ARG, "fst_model_set_launch: a selected kind is not specialised yet");
+  for (int k = 0; k < JK_COUNT; ++k)
+    if ((kinds >> k) & 1u) {
+      m->block[k] = block;
+      m->variant[k] = variant;
+    }
+  return FST_OK;
+}
+
 fst_status fst_model_specialized(const fst_model* m, uint32_t* kinds) {
   if (!m || !kinds) return set_error(FST_ERR_INVALID_ARG, "fst_model_specialized: null argument");
   *kinds = jit_mask(m);
@@ -162,9 +189,9 @@ fst_status fst_fk(const fst_model* m, int64_t B, const float* q, float* poses, v
   if (m->nq) FST_CHECK(need(fn, q, "q"));
   FST_CHECK(need(fn, poses, "poses"));
   const ModelView mv = view_of(m, nullptr);
-  if (jit_has(m, JK_FK))
+  if (use_jit(m, JK_FK))
     return finish(fn, jit_go(m, JK_FK, B, m->nq, 0, 1, (cudaStream_t)stream, nullptr, mv, B, q, poses));
-  return finish(fn, launch_fk(mv, B, q, poses, launch_of(B, stream)));
+  return finish(fn, launch_fk(mv, B, q, poses, launch_of(m, JK_FK, B, stream)));
 }
 
 fst_status fst_jacobian(const fst_model* m, int64_t B, const float* q, const int32_t* links, int32_t n_links,
@@ -185,9 +212,9 @@ fst_status fst_jacobian(const fst_model* m, int64_t B, const float* q, const int
   FST_CHECK(need(fn, q, "q"));
   FST_CHECK(need(fn, J, "J"));
   const ModelView mv = view_of(m, nullptr);
-  if (jit_has(m, JK_JACOBIAN))
+  if (use_jit(m, JK_JACOBIAN))
     return finish(fn, jit_go(m, JK_JACOBIAN, B, m->nq, 0, 1, (cudaStream_t)stream, nullptr, mv, B, q, L, J));
-  return finish(fn, launch_jacobian(mv, B, q, L, J, launch_of(B, stream)));
+  return finish(fn, launch_jacobian(mv, B, q, L, J, launch_of(m, JK_JACOBIAN, B, stream)));
 }
 
 fst_status fst_rnea(const fst_model* m, int64_t B, const float* q, const float* qd, const float* qdd,
@@ -201,10 +228,10 @@ fst_status fst_rnea(const fst_model* m, int64_t B, const float* q, const float* 
   FST_CHECK(need(fn, qdd, "qdd"));
   FST_CHECK(need(fn, tau, "tau"));
   const ModelView mv = view_of(m, theta);
-  if (jit_has(m, JK_RNEA))
+  if (use_jit(m, JK_RNEA))
     return finish(fn, jit_go(m, JK_RNEA, B, m->nq + 2 * m->nv, 0, 1, (cudaStream_t)stream, nullptr, mv, B, q, qd,
                              qdd, tau));
-  return finish(fn, launch_rnea(mv, B, q, qd, qdd, tau, launch_of(B, stream)));
+  return finish(fn, launch_rnea(mv, B, q, qd, qdd, tau, launch_of(m, JK_RNEA, B, stream)));
 }
 
 fst_status fst_crba(const fst_model* m, int64_t B, const float* q, const float* theta, float* M, void* stream) {
@@ -215,9 +242,9 @@ fst_status fst_crba(const fst_model* m, int64_t B, const float* q, const float* 
   FST_CHECK(need(fn, q, "q"));
   FST_CHECK(need(fn, M, "M"));
   const ModelView mv = view_of(m, theta);
-  if (jit_has(m, JK_CRBA))
+  if (use_jit(m, JK_CRBA))
     return finish(fn, jit_go(m, JK_CRBA, B, m->nq, 0, 1, (cudaStream_t)stream, nullptr, mv, B, q, M));
-  return finish(fn, launch_crba(mv, B, q, M, launch_of(B, stream)));
+  return finish(fn, launch_crba(mv, B, q, M, launch_of(m, JK_CRBA, B, stream)));
 }
 
 fst_status fst_aba(const fst_model* m, int64_t B, const float* q, const float* qd, const float* tau,
@@ -231,10 +258,10 @@ fst_status fst_aba(const fst_model* m, int64_t B, const float* q, const float* q
   FST_CHECK(need(fn, tau, "tau"));
   FST_CHECK(need(fn, qdd, "qdd"));
   const ModelView mv = view_of(m, theta);
-  if (jit_has(m, JK_ABA))
+  if (use_jit(m, JK_ABA))
     return finish(fn, jit_go(m, JK_ABA, B, m->nq + 2 * m->nv, 0, 1, (cudaStream_t)stream, nullptr, mv, B, q, qd,
                              tau, qdd));
-  return finish(fn, launch_aba(mv, B, q, qd, tau, qdd, launch_of(B, stream)));
+  return finish(fn, launch_aba(mv, B, q, qd, tau, qdd, launch_of(m, JK_ABA, B, stream)));
 }
 
 fst_status fst_eval(const fst_model* m, int64_t B, const fst_eval_io* io, const float* theta, void* stream) {
@@ -281,10 +308,10 @@ fst_status fst_eval(const fst_model* m, int64_t B, const fst_eval_io* io, const 
   if (skip || a.n_roles == 0) return FST_OK;
   if (m->nq) FST_CHECK(need(fn, io->q, "q"));
   const ModelView mv = view_of(m, theta);
-  if (jit_has(m, JK_EVAL))
+  if (use_jit(m, JK_EVAL))
     return finish(fn, jit_go(m, JK_EVAL, B, m->nq + 2 * m->nv, 0, (unsigned)a.n_roles, (cudaStream_t)stream, nullptr,
                              mv, B, a));
-  return finish(fn, launch_eval(mv, B, a, launch_of(B, stream)));
+  return finish(fn, launch_eval(mv, B, a, launch_of(m, JK_EVAL, B, stream)));
 }
 
 fst_status fst_adjoint_scratch_bytes(const fst_model* m, int64_t B, size_t* bytes) {
@@ -311,7 +338,7 @@ fst_status fst_fk_vjp(const fst_model* m, int64_t B, const float* q, const float
   FST_CHECK(need(fn, q, "q"));
   FST_CHECK(need(fn, poses_bar, "poses_bar"));
   const ModelView mv = view_of(m, nullptr);
-  if (jit_has(m, JK_FK_VJP))
+  if (use_jit(m, JK_FK_VJP))
     return finish(fn, jit_go(m, JK_FK_VJP, B, m->nq + 12 * m->n, 0, 1, (cudaStream_t)stream, nullptr, mv, B, q,
                              poses_bar, q_bar));
   return finish(fn, launch_fk_vjp(mv, B, q, poses_bar, q_bar, (cudaStream_t)stream));
@@ -333,7 +360,7 @@ fst_status fst_rnea_vjp(const fst_model* m, int64_t B, const float* q, const flo
   FST_CHECK(need(fn, qdd, "qdd"));
   FST_CHECK(need(fn, tau_bar, "tau_bar"));
   const ModelView mv = view_of(m, theta);
-  if (jit_has(m, JK_RNEA_VJP)) {
+  if (use_jit(m, JK_RNEA_VJP)) {
     unsigned nblk = 0;
     float* partial = theta_bar ? (float*)scratch : nullptr;
     const int P = theta_bar ? m->n * 10 : 0;
@@ -362,7 +389,7 @@ fst_status fst_aba_vjp(const fst_model* m, int64_t B, const float* q, const floa
   FST_CHECK(need(fn, qdd, "qdd"));
   FST_CHECK(need(fn, qdd_bar, "qdd_bar"));
   const ModelView mv = view_of(m, theta);
-  if (jit_has(m, JK_ABA_VJP)) {
+  if (use_jit(m, JK_ABA_VJP)) {
     unsigned nblk = 0;
     float* partial = theta_bar ? (float*)scratch : nullptr;
     const int P = theta_bar ? m->n * 10 : 0;
@@ -392,7 +419,7 @@ fst_status fst_rnea_loss_grad(const fst_model* m, int64_t B, const float* q, con
   FST_CHECK(need(fn, qdd, "qdd"));
   FST_CHECK(need(fn, tau_meas, "tau_meas"));
   const ModelView mv = view_of(m, theta);
-  if (jit_has(m, JK_LOSS_GRAD)) {
+  if (use_jit(m, JK_LOSS_GRAD)) {
     unsigned nblk = 0;
     const int P = m->n * 10 + 1;
     cudaError_t err = jit_go(m, JK_LOSS_GRAD, B, m->nq + 3 * m->nv, P, 1, (cudaStream_t)stream, &nblk, mv, B, q, qd,

@@ -12,7 +12,7 @@ namespace fst {
 namespace {
 
 template <int NB>
-__global__ void __launch_bounds__(128) rnea_kernel(ModelView mv, int64_t B, const float* __restrict__ q,
+__global__ void __launch_bounds__(256) rnea_kernel(ModelView mv, int64_t B, const float* __restrict__ q,
                                                    const float* __restrict__ qd, const float* __restrict__ qdd,
                                                    float* __restrict__ tau) {
   extern __shared__ float4 smem[];
@@ -32,7 +32,7 @@ __global__ void __launch_bounds__(128) rnea_kernel(ModelView mv, int64_t B, cons
 }
 
 template <int NB>
-__global__ void __launch_bounds__(128) crba_kernel(ModelView mv, int64_t B, const float* __restrict__ q,
+__global__ void __launch_bounds__(256) crba_kernel(ModelView mv, int64_t B, const float* __restrict__ q,
                                                    float* __restrict__ M) {
   extern __shared__ float4 smem[];
   float* tile = smem_tile(smem, mv.n);
@@ -47,7 +47,7 @@ __global__ void __launch_bounds__(128) crba_kernel(ModelView mv, int64_t B, cons
 }
 
 template <int NB>
-__global__ void __launch_bounds__(128) aba_kernel(ModelView mv, int64_t B, const float* __restrict__ q,
+__global__ void __launch_bounds__(256) aba_kernel(ModelView mv, int64_t B, const float* __restrict__ q,
                                                   const float* __restrict__ qd, const float* __restrict__ tau,
                                                   float* __restrict__ qdd) {
   extern __shared__ float4 smem[];

@@ -15,7 +15,7 @@ namespace fst {
 namespace {
 
 template <int NB>
-__global__ void __launch_bounds__(128) eval_kernel(ModelView mv, int64_t B, EvalArgs a) {
+__global__ void __launch_bounds__(256) eval_kernel(ModelView mv, int64_t B, EvalArgs a) {
   extern __shared__ float4 smem[];
   float* tile = smem_tile(smem, mv.n);
   const int role = a.roles[blockIdx.y];

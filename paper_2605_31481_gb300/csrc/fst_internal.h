@@ -24,6 +24,8 @@ struct fst_model {
   fst::BodyC* dc = nullptr;
   fst::BodyI* di = nullptr;
   fst::JitState* jit = nullptr;      // run-time specialised kernels, if any
+  int block[16] = {0};               // threads per block per kernel kind (0 = built-in heuristic)
+  int variant[16] = {0};             // per kind: 0 auto, 1 generic, 2 specialised (see fst_model_set_launch)
 };
 
 namespace fst {

@@ -60,7 +60,7 @@ using namespace fst;
   (void)act
 
 #ifdef FST_JIT_FK
-extern "C" __global__ void __launch_bounds__(128) FST_JIT_NAME(ModelView mv, int64_t B, const float* __restrict__ q,
+extern "C" __global__ void __launch_bounds__(256) FST_JIT_NAME(ModelView mv, int64_t B, const float* __restrict__ q,
                                                                  float* __restrict__ poses) {
   FST_JIT_PROLOGUE;
   if (!act) return;
@@ -71,7 +71,7 @@ extern "C" __global__ void __launch_bounds__(128) FST_JIT_NAME(ModelView mv, int
 #endif
 
 #ifdef FST_JIT_JACOBIAN
-extern "C" __global__ void __launch_bounds__(128) FST_JIT_NAME(ModelView mv, int64_t B, const float* __restrict__ q,
+extern "C" __global__ void __launch_bounds__(256) FST_JIT_NAME(ModelView mv, int64_t B, const float* __restrict__ q,
                                                                  LinkList links, float* __restrict__ J) {
   FST_JIT_PROLOGUE;
   if (!act) return;
@@ -82,7 +82,7 @@ extern "C" __global__ void __launch_bounds__(128) FST_JIT_NAME(ModelView mv, int
 #endif
 
 #ifdef FST_JIT_RNEA
-extern "C" __global__ void __launch_bounds__(128) FST_JIT_NAME(ModelView mv, int64_t B, const float* __restrict__ q,
+extern "C" __global__ void __launch_bounds__(256) FST_JIT_NAME(ModelView mv, int64_t B, const float* __restrict__ q,
                                                                  const float* __restrict__ qd,
                                                                  const float* __restrict__ qdd,
                                                                  float* __restrict__ tau) {
@@ -97,7 +97,7 @@ extern "C" __global__ void __launch_bounds__(128) FST_JIT_NAME(ModelView mv, int
 #endif
 
 #ifdef FST_JIT_CRBA
-extern "C" __global__ void __launch_bounds__(128) FST_JIT_NAME(ModelView mv, int64_t B, const float* __restrict__ q,
+extern "C" __global__ void __launch_bounds__(256) FST_JIT_NAME(ModelView mv, int64_t B, const float* __restrict__ q,
                                                                  float* __restrict__ M) {
   FST_JIT_PROLOGUE;
   if (!act) return;
@@ -108,7 +108,7 @@ extern "C" __global__ void __launch_bounds__(128) FST_JIT_NAME(ModelView mv, int
 #endif
 
 #ifdef FST_JIT_ABA
-extern "C" __global__ void __launch_bounds__(128) FST_JIT_NAME(ModelView mv, int64_t B, const float* __restrict__ q,
+extern "C" __global__ void __launch_bounds__(256) FST_JIT_NAME(ModelView mv, int64_t B, const float* __restrict__ q,
                                                                  const float* __restrict__ qd,
                                                                  const float* __restrict__ tau,
                                                                  float* __restrict__ qdd) {
@@ -123,7 +123,7 @@ extern "C" __global__ void __launch_bounds__(128) FST_JIT_NAME(ModelView mv, int
 #endif
 
 #ifdef FST_JIT_EVAL
-extern "C" __global__ void __launch_bounds__(128) FST_JIT_NAME(ModelView mv, int64_t B, EvalArgs a) {
+extern "C" __global__ void __launch_bounds__(256) FST_JIT_NAME(ModelView mv, int64_t B, EvalArgs a) {
   FST_JIT_PROLOGUE;
   if (!act) return;
   const int role = a.roles[blockIdx.y];
@@ -159,7 +159,7 @@ extern "C" __global__ void __launch_bounds__(128) FST_JIT_NAME(ModelView mv, int
 #endif
 
 #ifdef FST_JIT_FK_VJP
-extern "C" __global__ void __launch_bounds__(128) FST_JIT_NAME(ModelView mv, int64_t B, const float* __restrict__ q,
+extern "C" __global__ void __launch_bounds__(256) FST_JIT_NAME(ModelView mv, int64_t B, const float* __restrict__ q,
                                                                  const float* __restrict__ pbar,
                                                                  float* __restrict__ qbar) {
   FST_JIT_PROLOGUE;
@@ -172,7 +172,7 @@ extern "C" __global__ void __launch_bounds__(128) FST_JIT_NAME(ModelView mv, int
 #endif
 
 #ifdef FST_JIT_RNEA_VJP
-extern "C" __global__ void __launch_bounds__(128) FST_JIT_NAME(ModelView mv, int64_t B, const float* __restrict__ q,
+extern "C" __global__ void __launch_bounds__(256) FST_JIT_NAME(ModelView mv, int64_t B, const float* __restrict__ q,
                                                                  const float* __restrict__ qd,
                                                                  const float* __restrict__ qdd,
                                                                  const float* __restrict__ tbar, float* qbar,
@@ -199,7 +199,7 @@ extern "C" __global__ void __launch_bounds__(128) FST_JIT_NAME(ModelView mv, int
 #endif
 
 #ifdef FST_JIT_ABA_VJP
-extern "C" __global__ void __launch_bounds__(128) FST_JIT_NAME(ModelView mv, int64_t B, const float* __restrict__ q,
+extern "C" __global__ void __launch_bounds__(256) FST_JIT_NAME(ModelView mv, int64_t B, const float* __restrict__ q,
                                                                  const float* __restrict__ qd,
                                                                  const float* __restrict__ qdd,
                                                                  const float* __restrict__ qddbar, float* qbar,
@@ -232,7 +232,7 @@ extern "C" __global__ void __launch_bounds__(128) FST_JIT_NAME(ModelView mv, int
 #endif
 
 #ifdef FST_JIT_LOSS_GRAD
-extern "C" __global__ void __launch_bounds__(128) FST_JIT_NAME(ModelView mv, int64_t B, const float* __restrict__ q,
+extern "C" __global__ void __launch_bounds__(256) FST_JIT_NAME(ModelView mv, int64_t B, const float* __restrict__ q,
                                                                  const float* __restrict__ qd,
                                                                  const float* __restrict__ qdd,
                                                                  const float* __restrict__ tau_meas, float* qbar,

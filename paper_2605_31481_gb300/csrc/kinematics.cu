@@ -7,7 +7,7 @@ namespace fst {
 namespace {
 
 template <int NB>
-__global__ void __launch_bounds__(128) fk_kernel(ModelView mv, int64_t B, const float* __restrict__ q,
+__global__ void __launch_bounds__(256) fk_kernel(ModelView mv, int64_t B, const float* __restrict__ q,
                                                  float* __restrict__ poses) {
   extern __shared__ float4 smem[];
   float* tile = smem_tile(smem, mv.n);
@@ -22,7 +22,7 @@ __global__ void __launch_bounds__(128) fk_kernel(ModelView mv, int64_t B, const 
 }
 
 template <int NB>
-__global__ void __launch_bounds__(128) jac_kernel(ModelView mv, int64_t B, const float* __restrict__ q,
+__global__ void __launch_bounds__(256) jac_kernel(ModelView mv, int64_t B, const float* __restrict__ q,
                                                   LinkList links, float* __restrict__ J) {
   extern __shared__ float4 smem[];
   float* tile = smem_tile(smem, mv.n);
