@@ -294,6 +294,11 @@ def run_fst(args):
         roof = {"bound": "hbm", "achieved": round(achieved, 2), "peak": pk["hbm_gbs"], "unit": "GB/s",
                 "frac": round(achieved / pk["hbm_gbs"], 5), **common}
 
+    extras = {}
+    if rank == 0 and not args.no_extras:
+        extras["rnea_fwd_bwd"] = rnea_fwd_bwd(torch, fst, w)
+        extras["rl_step_graph"] = rl_step(torch, fst, w)
+        extras["humanoid_sweep"] = humanoid_sweep(torch, fst, w)
     if rank == 0:
         cpu = cpu_baseline(tree, links, args)
         line = {
@@ -315,10 +320,130 @@ def run_fst(args):
             "parity_guard": parity,
             "clocks": clocks,
             "cpu_baseline": cpu,
+            **extras,
         }
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
+
+
+def _graph_us(torch, fn, n=20, reps=10):
+    from paper_2605_31481_gb300.autotune import graph_time_us
+    return graph_time_us(fn, n=n, reps=reps)
+
+
+def rnea_fwd_bwd(torch, fst, w):
+    """RNEA forward + backward on the 7-DOF chain, B = 8192: the sysid loss
+    sum (RNEA - tau_meas)^2 and its gradient in one fused kernel, against the
+    plain sequence (RNEA kernel, the residual as a torch op, the RNEA adjoint
+    kernel). Both graph-replayed."""
+    tree = w.chain(7, seed=0)
+    B = 8192
+    m = fst.Model(tree)
+    try:
+        m.specialize(["rnea", "rnea_vjp", "loss_grad"])
+    except Exception:
+        pass
+    s = w.random_state(tree, B, seed=1)
+    cu = lambda x: torch.from_numpy(np.ascontiguousarray(x.T.astype(np.float32))).cuda()
+    q, qd, qdd, tm = cu(s["q"]), cu(s["qd"]), cu(s["qdd"]), cu(s["tau"])
+    from paper_2605_31481_gb300 import autotune
+    autotune.tune(m, B, kinds=("rnea", "rnea_vjp", "loss_grad"), use_cache=False)
+    scratch = fst.api.adjoint_scratch(m, B)
+    tau = torch.empty_like(tm)
+    buf = torch.empty(tree.n_bodies * 10 + 1, device="cuda")
+
+    def fused():
+        fst.api.rnea_loss_grad(m, q, qd, qdd, tm, q_bar=False, scratch=scratch, out=buf)
+
+    def plain():
+        fst.rnea(m, q, qd, qdd, out=tau)
+        tb = 2.0 * (tau - tm)
+        fst.api.rnea_vjp(m, q, qd, qdd, tb, q_bar=False, qd_bar=False, qdd_bar=False, scratch=scratch)
+
+    tf, tp = _graph_us(torch, fused), _graph_us(torch, plain)
+    return {"workload": "chain7, B=8192, loss sum (RNEA - tau_meas)^2 and d/dtheta",
+            "fused_us": round(tf, 3), "plain_us": round(tp, 3),
+            "fused_per_s": round(B / tf * 1e6, 1), "plain_per_s": round(B / tp * 1e6, 1),
+            "speedup": round(tp / tf, 3), "unit": "RNEA fwd+bwd env-evals/s"}
+
+
+def rl_step(torch, fst, w, steps=1000):
+    """One RL-style controller step on the 11-DOF tree, B = 4096: FK, the four
+    foot Jacobians, RNEA and the RNEA adjoint (cotangent tau), run eagerly
+    through the binding and replayed from one captured CUDA graph."""
+    tree = w.spined_quadruped(seed=0)
+    B = 4096
+    m = fst.Model(tree)
+    try:
+        m.specialize(["fk", "jacobian", "rnea", "rnea_vjp"])
+    except Exception:
+        pass
+    from paper_2605_31481_gb300 import autotune
+    autotune.tune(m, B, kinds=("fk", "jacobian", "rnea", "rnea_vjp"), use_cache=False)
+    s = w.random_state(tree, B, seed=2)
+    cu = lambda x: torch.from_numpy(np.ascontiguousarray(x.T.astype(np.float32))).cuda()
+    q, qd, qdd = cu(s["q"]), cu(s["qd"]), cu(s["qdd"])
+    poses = torch.empty(tree.n_bodies, 12, B, device="cuda")
+    J = torch.empty(4, 6, tree.nv, B, device="cuda")
+    tau = torch.empty(tree.nv, B, device="cuda")
+    scratch = fst.api.adjoint_scratch(m, B)
+
+    def step():
+        fst.fk(m, q, out=poses)
+        fst.jacobian(m, q, tree.ee, out=J)
+        fst.rnea(m, q, qd, qdd, out=tau)
+        fst.api.rnea_vjp(m, q, qd, qdd, tau, qdd_bar=False, theta_bar=False, scratch=scratch)
+
+    for _ in range(5):
+        step()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(steps):
+        step()
+    b.record()
+    torch.cuda.synchronize()
+    eager = a.elapsed_time(b) * 1e3 / steps
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        step()
+    g.replay()
+    torch.cuda.synchronize()
+    a.record()
+    for _ in range(steps):
+        g.replay()
+    b.record()
+    torch.cuda.synchronize()
+    graph = a.elapsed_time(b) * 1e3 / steps
+    return {"workload": "spined_quadruped11, B=4096: FK + 4 foot Jacobians + RNEA + RNEA adjoint", "steps": steps,
+            "eager_us_per_step": round(eager, 3), "graph_us_per_step": round(graph, 3),
+            "graph_steps_per_s": round(1e6 / graph, 1), "speedup": round(eager / graph, 3)}
+
+
+def humanoid_sweep(torch, fst, w, Bs=(1, 64, 1024, 4096, 16384, 65536)):
+    """The five operators on the floating-base 29-DOF humanoid across batch
+    sizes (tuned plan per B), env-evals/s of the whole step."""
+    tree = w.humanoid(seed=0)
+    m = fst.Model(tree)
+    try:
+        m.specialize(["fk", "jacobian", "rnea", "crba", "aba", "eval"])
+    except Exception:
+        pass
+    from paper_2605_31481_gb300.autotune import StepPlan
+    out = {}
+    for B in Bs:
+        s = w.random_state(tree, B, seed=1)
+        cu = lambda x: torch.from_numpy(np.ascontiguousarray(x.T.astype(np.float32))).cuda()
+        q, qd, qdd, tau = cu(s["q"]), cu(s["qd"]), cu(s["qdd"]), cu(s["tau"])
+        plan = StepPlan(m, B, links=tree.ee, use_cache=False)
+        o = {"poses": torch.empty(tree.n_bodies, 12, B, device="cuda"),
+             "J": torch.empty(len(tree.ee), 6, tree.nv, B, device="cuda"), "tau": torch.empty(tree.nv, B, device="cuda"),
+             "M": torch.empty(tree.nv, tree.nv, B, device="cuda"), "qdd": torch.empty(tree.nv, B, device="cuda")}
+        us = _graph_us(torch, lambda: plan(q, qd, qdd, tau, o))
+        out[str(B)] = {"us": round(us, 3), "env_evals_per_s": round(B / us * 1e6, 1), "plan": plan.describe()["mode"]}
+    return {"workload": "humanoid_float29 (free base + 23 revolute, depth 7): FK + 4 Jacobians + RNEA + CRBA + ABA",
+            "per_B": out}
 
 
 def per_op_times(torch, launch, sets, R, stream, K_op):
@@ -469,9 +594,11 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--steps", type=int, default=20000)
     ap.add_argument("--warmup", type=int, default=200)
     ap.add_argument("--impl", choices=("fst", "reference"), default="fst")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the secondary legs (fwd+bwd, RL-step graph, humanoid sweep) after the timed step")
     ap.add_argument("--traffic", type=float, default=None,
                     help="dram bytes per launch of the dominant kernel from an ncu capture (else null)")
     args = ap.parse_args()

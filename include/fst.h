@@ -288,6 +288,42 @@ FST_API fst_status fst_rnea_vjp_noalloc(const fst_model* model, int64_t B, const
                                         const float* tau_bar, float* q_bar, float* qd_bar,
                                         float* qdd_bar, float* theta_bar, void* stream);
 
+/* ---------------------------------------------------------------------------
+ * Mixed batches of several trees in ONE persistent launch. Not in the paper,
+ * which evaluates one robot at a time; a mixed batch would otherwise need one
+ * launch per tree and operator, each too small to fill the GPU.
+ * ------------------------------------------------------------------------- */
+#define FST_MAX_MULTI 16
+
+typedef struct fst_multi fst_multi;
+
+/* Per-tree inputs and outputs (device arrays as for the single-tree calls).
+ * A NULL output skips that operator for that tree; inputs as fst_eval. */
+typedef struct fst_multi_io {
+  int64_t B;
+  const float* q;
+  const float* qd;
+  const float* qdd;
+  const float* tau;
+  float* poses;    /* FK   [n_b][12][B] */
+  float* tau_out;  /* RNEA [nv][B] */
+  float* M;        /* CRBA [nv][nv][B] */
+  float* qdd_out;  /* ABA  [nv][B] */
+} fst_multi_io;
+
+/* Groups 1..FST_MAX_MULTI models (same device; they must outlive the group)
+ * and allocates its 4-byte device work counter. */
+FST_API fst_status fst_multi_create(const fst_model* const* models, int32_t n_models, fst_multi** out);
+FST_API fst_status fst_multi_destroy(fst_multi* multi);
+
+/* Evaluates the requested operators of every tree in one persistent launch
+ * (plus a 4-byte memset that resets the work counter; both are ordered on
+ * `stream` and can be captured into a CUDA graph). io has n_models entries,
+ * in the order given to fst_multi_create. Overlapping calls on the same
+ * group (unordered streams) race on its counter; create one group per
+ * stream for that. Results are bit-identical to the per-tree generic calls. */
+FST_API fst_status fst_multi_eval(fst_multi* multi, const fst_multi_io* io, void* stream);
+
 /* Message for the last non-OK status on this thread ("" if none). */
 FST_API const char* fst_last_error(void);
 

@@ -4,6 +4,6 @@ The compute path is libfst.so (hand-written CUDA, C ABI in include/fst.h);
 `api` is its thin PyTorch binding. Importing the package does not load the
 library; the first call does, and fails loudly if it has not been built.
 """
-from .api import Model, fk, jacobian, rnea, crba, aba, eval, soa, aos  # noqa: F401
+from .api import Model, MultiBatch, fk, jacobian, rnea, crba, aba, eval, soa, aos  # noqa: F401
 
-__all__ = ["Model", "fk", "jacobian", "rnea", "crba", "aba", "eval", "soa", "aos"]
+__all__ = ["Model", "MultiBatch", "fk", "jacobian", "rnea", "crba", "aba", "eval", "soa", "aos"]

@@ -54,6 +54,12 @@ class EvalIO(ctypes.Structure):
     ]
 
 
+class MultiIO(ctypes.Structure):
+    """fst_multi_io: one tree's inputs and requested outputs in a mixed batch."""
+    _fields_ = [("B", c_int64), ("q", c_void_p), ("qd", c_void_p), ("qdd", c_void_p), ("tau", c_void_p),
+                ("poses", c_void_p), ("tau_out", c_void_p), ("M", c_void_p), ("qdd_out", c_void_p)]
+
+
 # (name, restype, argtypes); pointers to device memory travel as c_void_p
 _SIGS = {
     "fst_model_create": (c_int32, [ctypes.POINTER(BodyDesc), c_int32, ctypes.POINTER(c_double), ctypes.POINTER(c_void_p)]),
@@ -79,6 +85,9 @@ _SIGS = {
                                      c_void_p, c_void_p, c_void_p, ctypes.c_size_t, c_void_p]),
     "fst_rnea_vjp_noalloc": (c_int32, [c_void_p, c_int64, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                        c_void_p, c_void_p, c_void_p, c_void_p]),
+    "fst_multi_create": (c_int32, [ctypes.POINTER(c_void_p), c_int32, ctypes.POINTER(c_void_p)]),
+    "fst_multi_destroy": (c_int32, [c_void_p]),
+    "fst_multi_eval": (c_int32, [c_void_p, ctypes.POINTER(MultiIO), c_void_p]),
     "fst_last_error": (ctypes.c_char_p, []),
     "fst_version": (ctypes.c_char_p, []),
 }

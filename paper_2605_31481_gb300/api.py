@@ -333,3 +333,65 @@ def rnea_loss_grad(model: Model, q, qd, qdd, tau_meas, theta=None, *, q_bar=Fals
     check(_ffi.lib().fst_rnea_loss_grad(model.handle, B, _ptr(q), _ptr(qd), _ptr(qdd), _ptr(_theta(theta, model)),
                                         _ptr(tau_meas), _ptr(buf), _ptr(qb), _ptr(qdb), sp, sb, _stream()))
     return buf[-1], buf[:-1].view(model.n_bodies, 10), qb, qdb
+
+
+# ---------------------------------------------------------------------------
+# mixed batches of several trees
+# ---------------------------------------------------------------------------
+
+class MultiBatch:
+    """Several models evaluated in one persistent launch (fst_multi_eval)."""
+
+    def __init__(self, models):
+        self.models = list(models)
+        arr = (ctypes.c_void_p * len(self.models))(*[m.handle.value for m in self.models])
+        h = ctypes.c_void_p()
+        check(_ffi.lib().fst_multi_create(arr, len(self.models), ctypes.byref(h)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _ffi.lib().fst_multi_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def eval(self, items):
+        """items[k] for models[k]: dict with "q" and, as needed, "qd", "qdd",
+        "tau", plus flags fk/rnea/crba/aba and optional preallocated outputs
+        under "out". Returns one dict of outputs per model."""
+        if len(items) != len(self.models):
+            raise ValueError("one item per model")
+        ios = (_ffi.MultiIO * len(items))()
+        results = []
+        for k, (m, it) in enumerate(zip(self.models, items)):
+            q = it["q"]
+            B = _check_in(q, m.nq, "q", m)
+            io = ios[k]
+            io.B = B
+            io.q = q.data_ptr()
+            for name in ("qd", "qdd", "tau"):
+                if it.get(name) is not None:
+                    _check_in(it[name], m.nv, name, m)
+                    setattr(io, name, it[name].data_ptr())
+            out = dict(it.get("out") or {})
+            res = {}
+            if it.get("fk"):
+                res["poses"] = _out(out.get("poses"), (m.n_bodies, 12, B), m)
+                io.poses = res["poses"].data_ptr()
+            if it.get("rnea"):
+                res["tau"] = _out(out.get("tau"), (m.nv, B), m)
+                io.tau_out = res["tau"].data_ptr()
+            if it.get("crba"):
+                res["M"] = _out(out.get("M"), (m.nv, m.nv, B), m)
+                io.M = res["M"].data_ptr()
+            if it.get("aba"):
+                res["qdd"] = _out(out.get("qdd"), (m.nv, B), m)
+                io.qdd_out = res["qdd"].data_ptr()
+            results.append(res)
+        check(_ffi.lib().fst_multi_eval(self._h, ios, _stream()))
+        return results

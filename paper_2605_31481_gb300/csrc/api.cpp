@@ -9,6 +9,7 @@
 #include "fst_internal.h"
 #include "jit.h"
 #include "launch.h"
+#include "multi.h"
 
 namespace fst {
 
@@ -429,6 +430,91 @@ fst_status fst_rnea_loss_grad(const fst_model* m, int64_t B, const float* q, con
   }
   return finish(fn, launch_rnea_loss_grad(mv, B, q, qd, qdd, tau_meas, loss_theta_bar, q_bar, qd_bar,
                                           (float*)scratch, (cudaStream_t)stream));
+}
+
+fst_status fst_multi_create(const fst_model* const* models, int32_t n_models, fst_multi** out) {
+  static const char* fn = "fst_multi_create";
+  if (!out || !models) return set_error(FST_ERR_INVALID_ARG, std::string(fn) + ": null argument");
+  *out = nullptr;
+  if (n_models < 1 || n_models > FST_MAX_MULTI)
+    return set_error(FST_ERR_INVALID_ARG, std::string(fn) + ": n_models must be in [1, FST_MAX_MULTI]");
+  for (int k = 0; k < n_models; ++k) {
+    if (!models[k]) return set_error(FST_ERR_INVALID_ARG, std::string(fn) + ": null model");
+    if (models[k]->device != models[0]->device)
+      return set_error(FST_ERR_INVALID_ARG, std::string(fn) + ": models live on different devices");
+  }
+  fst_multi* g = new (std::nothrow) fst_multi();
+  if (!g) return set_error(FST_ERR_NO_MEMORY, std::string(fn) + ": host allocation failed");
+  g->models.assign(models, models + n_models);
+  g->device = models[0]->device;
+  cudaError_t err = cudaMalloc((void**)&g->counter, sizeof(int));
+  if (err != cudaSuccess) {
+    delete g;
+    return cuda_error(fn, err);
+  }
+  *out = g;
+  return FST_OK;
+}
+
+fst_status fst_multi_destroy(fst_multi* g) {
+  if (!g) return FST_OK;
+  if (g->counter) cudaFree(g->counter);
+  delete g;
+  return FST_OK;
+}
+
+fst_status fst_multi_eval(fst_multi* g, const fst_multi_io* io, void* stream) {
+  static const char* fn = "fst_multi_eval";
+  if (!g || !io) return set_error(FST_ERR_INVALID_ARG, std::string(fn) + ": null argument");
+  int dev = -1;
+  cudaError_t err = cudaGetDevice(&dev);
+  if (err != cudaSuccess) return cuda_error(fn, err);
+  if (dev != g->device) return set_error(FST_ERR_INVALID_ARG, std::string(fn) + ": not the group's device");
+  const int n = (int)g->models.size();
+  MultiArgs a{};
+  a.counter = g->counter;
+  int max_n = 1;
+  for (int k = 0; k < n; ++k) {
+    const fst_model* m = g->models[k];
+    const fst_multi_io& x = io[k];
+    if (x.B < 0) return set_error(FST_ERR_INVALID_ARG, std::string(fn) + ": B must be >= 0");
+    if (x.B > 0 && m->nq && !x.q) return set_error(FST_ERR_INVALID_ARG, std::string(fn) + ": null q");
+    if (x.B > 0 && x.tau_out && (!x.qd || !x.qdd)) return set_error(FST_ERR_INVALID_ARG, std::string(fn) + ": RNEA needs qd and qdd");
+    if (x.B > 0 && x.qdd_out && (!x.qd || !x.tau)) return set_error(FST_ERR_INVALID_ARG, std::string(fn) + ": ABA needs qd and tau");
+    a.mv[k] = view_of(m, nullptr);
+    a.io[k] = MultiIO{x.q, x.qd, x.qdd, x.tau, x.poses, m->nv ? x.tau_out : nullptr, m->nv ? x.M : nullptr,
+                      m->nv ? x.qdd_out : nullptr, x.B};
+    if (m->n > max_n) max_n = m->n;
+    const int rows = m->nq + 2 * m->nv;
+    if (rows > a.max_rows) a.max_rows = rows;
+  }
+  // heaviest first: ABA, CRBA, RNEA, FK; within one, trees with most bodies first
+  std::vector<int> order(n);
+  for (int k = 0; k < n; ++k) order[k] = k;
+  for (int i = 1; i < n; ++i)
+    for (int j = i; j > 0 && g->models[order[j]]->n > g->models[order[j - 1]]->n; --j) std::swap(order[j], order[j - 1]);
+  const int T = g->block;
+  int seg = 0, items = 0;
+  const int roles[4] = {ROLE_ABA, ROLE_CRBA, ROLE_RNEA, ROLE_KIN};
+  for (int r : roles)
+    for (int k : order) {
+      const MultiIO& x = a.io[k];
+      const void* outp = r == ROLE_ABA ? (const void*)x.qdd_out
+                       : r == ROLE_CRBA ? (const void*)x.M
+                       : r == ROLE_RNEA ? (const void*)x.tau_out : (const void*)x.poses;
+      if (!outp || x.B == 0) continue;
+      a.seg_start[seg] = items;
+      a.seg_model[seg] = (unsigned char)k;
+      a.seg_op[seg] = (unsigned char)r;
+      items += (int)((x.B + T - 1) / T);
+      ++seg;
+    }
+  a.seg_start[seg] = items;
+  a.n_items = items;
+  a.model_bytes = (size_t)max_n * (sizeof(BodyC) + sizeof(BodyI));
+  a.model_bytes = (a.model_bytes + 15) / 16 * 16;
+  if (items == 0) return FST_OK;
+  return finish(fn, launch_multi(a, max_n, T, (cudaStream_t)stream));
 }
 
 }  // extern "C"
