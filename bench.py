@@ -299,6 +299,7 @@ def run_fst(args):
         extras["rnea_fwd_bwd"] = rnea_fwd_bwd(torch, fst, w)
         extras["rl_step_graph"] = rl_step(torch, fst, w)
         extras["humanoid_sweep"] = humanoid_sweep(torch, fst, w)
+        extras["multi_tree"] = multi_tree(torch, fst, w)
     if rank == 0:
         cpu = cpu_baseline(tree, links, args)
         line = {
@@ -444,6 +445,39 @@ def humanoid_sweep(torch, fst, w, Bs=(1, 64, 1024, 4096, 16384, 65536)):
         out[str(B)] = {"us": round(us, 3), "env_evals_per_s": round(B / us * 1e6, 1), "plan": plan.describe()["mode"]}
     return {"workload": "humanoid_float29 (free base + 23 revolute, depth 7): FK + 4 Jacobians + RNEA + CRBA + ABA",
             "per_B": out}
+
+
+def multi_tree(torch, fst, w, counts=(4096, 2048, 1024, 512, 256)):
+    """Mixed batch of five trees (7, 11, 12, 18, 23 revolute DOF; 7936
+    environments): FK + RNEA + CRBA + ABA of every tree in one persistent
+    launch, against one launch per tree and operator (generic kernels both
+    ways). Graph-replayed."""
+    trees = w.mixed_trees()
+    models = [fst.Model(t) for t in trees]
+    items, outs = [], []
+    for k, (t, B) in enumerate(zip(trees, counts)):
+        s = w.random_state(t, B, seed=20 + k)
+        cu = lambda x: torch.from_numpy(np.ascontiguousarray(x.T.astype(np.float32))).cuda()
+        o = {"poses": torch.empty(t.n_bodies, 12, B, device="cuda"), "tau": torch.empty(t.nv, B, device="cuda"),
+             "M": torch.empty(t.nv, t.nv, B, device="cuda"), "qdd": torch.empty(t.nv, B, device="cuda")}
+        items.append({"q": cu(s["q"]), "qd": cu(s["qd"]), "qdd": cu(s["qdd"]), "tau": cu(s["tau"]),
+                      "fk": True, "rnea": True, "crba": True, "aba": True, "out": o})
+    mb = fst.MultiBatch(models)
+
+    def separate():
+        for m, it in zip(models, items):
+            o = it["out"]
+            fst.fk(m, it["q"], out=o["poses"])
+            fst.rnea(m, it["q"], it["qd"], it["qdd"], out=o["tau"])
+            fst.crba(m, it["q"], out=o["M"])
+            fst.aba(m, it["q"], it["qd"], it["tau"], out=o["qdd"])
+
+    tp, ts = _graph_us(torch, lambda: mb.eval(items)), _graph_us(torch, separate)
+    n = sum(counts)
+    return {"workload": "5 trees (7/11/12/18/23 DOF) x (4096/2048/1024/512/256 envs): FK+RNEA+CRBA+ABA",
+            "persistent_us": round(tp, 3), "separate_us": round(ts, 3),
+            "persistent_env_evals_per_s": round(n / tp * 1e6, 1), "separate_env_evals_per_s": round(n / ts * 1e6, 1),
+            "speedup": round(ts / tp, 3), "launches": {"persistent": 1, "separate": 4 * len(trees)}}
 
 
 def per_op_times(torch, launch, sets, R, stream, K_op):
