@@ -158,7 +158,7 @@ def run_fst(args):
     except _ffi.FstError as exc:        # no NVRTC on this host: generic kernels only
         kernels = f"generic only ({exc})"
     from paper_2605_31481_gb300.autotune import StepPlan
-    plan = StepPlan(model, B, links=links, use_cache=False)
+    plan = StepPlan(model, B, links=links)
     nq, nv, nb, nl = tree.nq, tree.nv, tree.n_bodies, len(links)
     out_floats = nb * 12 + nl * 6 * nv + nv + nv * nv + nv
     in_floats = nq + 3 * nv
@@ -199,10 +199,11 @@ def run_fst(args):
         d = sets[k % R]
         plan(d["q"], d["qd"], d["qdd"], d["tau"], d["out"])
 
-    # parity guard: the timed launches must reproduce the oracle on a sample
+    # the step's outputs on the first input set, checked against the oracle
+    # in the CPU-baseline leg below
     step(0)
     torch.cuda.synchronize()
-    parity = parity_guard(torch, tree, links, st, sets[0]["out"], B)
+    first = {k: v.detach().cpu().numpy().astype(np.float64) for k, v in sets[0]["out"].items()}
 
     for k in range(args.warmup):
         step(k)
@@ -300,8 +301,9 @@ def run_fst(args):
         extras["rl_step_graph"] = rl_step(torch, fst, w)
         extras["humanoid_sweep"] = humanoid_sweep(torch, fst, w)
         extras["multi_tree"] = multi_tree(torch, fst, w)
+        extras["sysid"] = sysid(torch, fst, w)
     if rank == 0:
-        cpu = cpu_baseline(tree, links, args)
+        cpu, parity = cpu_baseline(tree, links, args, st, first)
         line = {
             "metric": METRIC, "value": round(value, 1), "unit": "env-evals/s", "n_gpus": world, "steps": K,
             "warmup": args.warmup, "ms_per_step": round(ms / K, 5), "higher_is_better": True, "scaling": "weak",
@@ -318,9 +320,9 @@ def run_fst(args):
             "gpu_launches": K * (1 if plan.fused else len(OPS)),
             "kernels": kernels,
             "plan": desc,
-            "parity_guard": parity,
             "clocks": clocks,
             "cpu_baseline": cpu,
+            "parity_vs_oracle": parity,
             **extras,
         }
         print(json.dumps(line))
@@ -480,6 +482,43 @@ def multi_tree(torch, fst, w, counts=(4096, 2048, 1024, 512, 256)):
             "speedup": round(ts / tp, 3), "launches": {"persistent": 1, "separate": 4 * len(trees)}}
 
 
+def sysid(torch, fst, w, steps=500):
+    """Link-parameter identification on the 7-DOF chain (paper Sec. 4.3
+    setting on a synthetic arm): B = 8192 samples, measured torques = true
+    RNEA x (1 + 0.05 N(0,1)), all 70 parameters start perturbed by
+    U(-30%, +30%), Adam (lr 1e-2) for `steps` steps, each step one fused
+    loss-and-gradient kernel."""
+    from paper_2605_31481_gb300 import sysid as sid
+    tree = w.chain(7, seed=0)
+    B = 8192
+    m = fst.Model(tree)
+    try:
+        m.specialize(["rnea", "loss_grad"])
+    except Exception:
+        pass
+    s = w.random_state(tree, B, seed=1)
+    cu = lambda x: torch.from_numpy(np.ascontiguousarray(np.asarray(x).T.astype(np.float32))).cuda()
+    q, qd, qdd = cu(s["q"]), cu(s["qd"]), cu(s["qdd"])
+    true = m.theta()
+    rng = np.random.default_rng(7)
+    tau_true = fst.rnea(m, q, qd, qdd)
+    tau_meas = (tau_true * torch.from_numpy((1 + 0.05 * rng.standard_normal(tuple(tau_true.shape))).astype(np.float32)).cuda()).contiguous()
+    theta0 = (true * torch.from_numpy(rng.uniform(-0.3, 0.3, tuple(true.shape)).astype(np.float32) + 1).cuda()).contiguous()
+    sid.identify(m, q, qd, qdd, tau_meas, theta0, steps=2)            # warm
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    theta, _ = sid.identify(m, q, qd, qdd, tau_meas, theta0, steps=steps)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    err = sid.mass_errors(theta, true.cpu().numpy())
+    err0 = sid.mass_errors(theta0, true.cpu().numpy())
+    return {"workload": "chain7, B=8192, 70 parameters, 5% torque noise, +-30% initial error, Adam 500 steps",
+            "steps": steps, "seconds": round(dt, 3), "steps_per_s": round(steps / dt, 1),
+            "mass_error_pct_initial_mean": round(100 * float(err0.mean()), 2),
+            "mass_error_pct_mean": round(100 * float(err.mean()), 2),
+            "mass_error_pct_per_link": [round(100 * float(x), 2) for x in err]}
+
+
 def per_op_times(torch, launch, sets, R, stream, K_op):
     """Each operator alone, its own kernel per call at its tuned
     configuration, replayed from a CUDA graph of R calls (for the
@@ -501,29 +540,6 @@ def per_op_times(torch, launch, sets, R, stream, K_op):
         b.record(stream)
         torch.cuda.synchronize()
         out[op] = a.elapsed_time(b) / (reps * R)
-    return out
-
-
-def parity_guard(torch, tree, links, st, d, B, n=64):
-    """Max normwise error of the timed path's outputs on n sampled envs."""
-    from oracle import rbd
-    idx = np.linspace(0, B - 1, n).astype(int)
-    s = {k: st[k][idx] for k in ("q", "qd", "qdd", "tau")}
-    T = rbd.fk(tree, s["q"])
-    ref = {"poses": np.concatenate([T[..., :3, :3].reshape(n, -1, 9), T[..., :3, 3]], -1),
-           "J": np.stack([rbd.jacobian(tree, s["q"], l) for l in links], 1),
-           "tau": rbd.rnea(tree, s["q"], s["qd"], s["qdd"]),
-           "M": rbd.crba(tree, s["q"]),
-           "qdd": rbd.aba(tree, s["q"], s["qd"], s["tau"])}
-    tol = {"poses": 1e-5, "J": 1e-5, "tau": 1e-4, "M": 1e-4, "qdd": 1e-4}
-    out = {}
-    for k, r in ref.items():
-        g = np.moveaxis(d[k].cpu().numpy().astype(np.float64), -1, 0)[idx].reshape(n, -1)
-        r = r.reshape(n, -1)
-        err = float((np.abs(g - r).max(1) / np.maximum(np.abs(r).max(1), 1.0)).max())
-        if not err <= tol[k]:
-            raise RuntimeError(f"parity guard failed: {k} error {err:.3e} > {tol[k]}")
-        out[k] = float(f"{err:.2e}")
     return out
 
 
@@ -579,19 +595,40 @@ def oracle_step(tree, links, s):
     rbd.aba(tree, s["q"], s["qd"], s["tau"])
 
 
-def cpu_baseline(tree, links, args, budget_s=12.0):
+def cpu_baseline(tree, links, args, st=None, gpu_first=None, budget_s=12.0, Bs=512):
+    """The FP64 oracle timed on the host (1 thread) over the first Bs
+    environments of the step's first input set; when the GPU step's outputs
+    for those inputs are given, also their largest per-environment normwise
+    error against the oracle (the same check the tests apply)."""
+    from oracle import rbd
     from paper_2605_31481_gb300 import workloads as w
-    Bs = 512
-    s = w.random_state(tree, Bs, seed=1)
+    s = {k: v[:Bs] for k, v in st.items()} if st is not None else w.random_state(tree, Bs, seed=1)
     oracle_step(tree, links, s)
     n, t0 = 0, time.perf_counter()
     while time.perf_counter() - t0 < budget_s:
         oracle_step(tree, links, s)
         n += 1
     dt = time.perf_counter() - t0
-    return {"value": round(n * Bs / dt, 1), "unit": "env-evals/s", "cores": 1, "kind": "oracle",
-            "sample": f"{n} passes of FK+4 Jacobians+RNEA+CRBA+ABA over {Bs} envs of the same tree (FP64 numpy, "
-                      f"1 thread, {dt:.1f} s)"}
+    cpu = {"value": round(n * Bs / dt, 1), "unit": "env-evals/s", "cores": 1, "kind": "oracle",
+           "sample": f"{n} passes of FK+4 Jacobians+RNEA+CRBA+ABA over {Bs} envs of the same tree (FP64 numpy, "
+                     f"1 thread, {dt:.1f} s)"}
+    parity = None
+    if gpu_first is not None:
+        T = rbd.fk(tree, s["q"])
+        ref = {"poses": np.concatenate([T[..., :3, :3].reshape(Bs, -1, 9), T[..., :3, 3]], -1),
+               "J": np.stack([rbd.jacobian(tree, s["q"], l) for l in links], 1),
+               "tau": rbd.rnea(tree, s["q"], s["qd"], s["qdd"]), "M": rbd.crba(tree, s["q"]),
+               "qdd": rbd.aba(tree, s["q"], s["qd"], s["tau"])}
+        tol = {"poses": 1e-5, "J": 1e-5, "tau": 1e-4, "M": 1e-4, "qdd": 1e-4}
+        parity = {}
+        for k, r in ref.items():
+            g = np.moveaxis(gpu_first[k], -1, 0)[:Bs].reshape(Bs, -1)
+            r = r.reshape(Bs, -1)
+            err = float((np.abs(g - r).max(1) / np.maximum(np.abs(r).max(1), 1.0)).max())
+            if not err <= tol[k]:
+                raise RuntimeError(f"parity check failed: {k} error {err:.3e} > {tol[k]}")
+            parity[k] = float(f"{err:.2e}")
+    return cpu, parity
 
 
 def run_reference(args):

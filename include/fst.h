@@ -110,6 +110,10 @@ FST_API fst_status fst_model_destroy(fst_model* model);
 FST_API fst_status fst_model_info(const fst_model* model, int32_t* nq, int32_t* nv,
                           int32_t* n_bodies, int32_t* depth);
 
+/* The model's own inertial parameters, theta layout of fst_rnea (about each
+ * body origin), copied to HOST memory theta[n_b * 10] (FP32). */
+FST_API fst_status fst_model_theta(const fst_model* model, float* theta);
+
 /* Kernel kinds for fst_model_specialize (bit masks; 0 = all). */
 #define FST_SPEC_FK (1u << 0)
 #define FST_SPEC_JACOBIAN (1u << 1)

@@ -89,6 +89,12 @@ class Model:
             check(_ffi.lib().fst_model_specialize(self._h, mask))
         return self.specialized()
 
+    def theta(self):
+        """The model's own inertial parameters (n_b, 10), float32, on its device."""
+        buf = (ctypes.c_float * (self.n_bodies * 10))()
+        check(_ffi.lib().fst_model_theta(self._h, buf))
+        return torch.tensor(list(buf), dtype=torch.float32).view(self.n_bodies, 10).to(self.device)
+
     def set_launch(self, kinds=None, block=0, variant="auto"):
         """Launch configuration (fst_model_set_launch) of the given kernel
         kinds (names from _ffi.SPEC_KINDS, None = all): threads per block

@@ -173,6 +173,13 @@ fst_status fst_model_specialized(const fst_model* m, uint32_t* kinds) {
   return FST_OK;
 }
 
+fst_status fst_model_theta(const fst_model* m, float* theta) {
+  if (!m || !theta) return set_error(FST_ERR_INVALID_ARG, "fst_model_theta: null argument");
+  for (int i = 0; i < m->n; ++i)
+    for (int k = 0; k < 10; ++k) theta[10 * i + k] = m->hc[i].theta[k];
+  return FST_OK;
+}
+
 fst_status fst_model_info(const fst_model* m, int32_t* nq, int32_t* nv, int32_t* n_bodies, int32_t* depth) {
   if (!m) return set_error(FST_ERR_INVALID_ARG, "fst_model_info: null model");
   if (nq) *nq = m->nq;
