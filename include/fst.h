@@ -144,15 +144,24 @@ FST_API fst_status fst_model_specialize(fst_model* model, uint32_t kinds);
 
 /* Launch configuration of the selected kinds (FST_SPEC_* mask, 0 = all) on
  * this model: threads per block (32, 64, 128 or 256; 0 = built-in heuristic)
- * and which kernel variant runs (AUTO = specialised when compiled, else
- * generic). One environment per thread either way and results agree within
- * FP32 rounding; only speed changes. SPECIALIZED for a kind that
- * fst_model_specialize has not compiled returns FST_ERR_INVALID_ARG. The
- * autotuner in the Python package measures the candidates per kind and batch
- * size and sets the fastest. */
+ * and which kernel variant runs:
+ *   AUTO        the specialised kernel when compiled, else the generic one;
+ *   GENERIC     one environment per thread, tree from shared memory;
+ *   SPECIALIZED one environment per thread, kernel compiled for this tree;
+ *   LEVEL       level-parallel (paper Sec. 3.3 on warps): 32 environments per
+ *               block, the block's block/32 warps split the bodies of each
+ *               tree level, per-body state in shared memory; FK, Jacobian,
+ *               RNEA, CRBA, ABA and eval only, and only while that state fits
+ *               in shared memory (about 28 bodies for ABA); otherwise the
+ *               generic kernel runs.
+ * Results agree within FP32 rounding; only speed changes. SPECIALIZED for a
+ * kind that fst_model_specialize has not compiled returns
+ * FST_ERR_INVALID_ARG. The autotuner in the Python package measures the
+ * candidates per kind and batch size and sets the fastest. */
 #define FST_VARIANT_AUTO 0
 #define FST_VARIANT_GENERIC 1
 #define FST_VARIANT_SPECIALIZED 2
+#define FST_VARIANT_LEVEL 3
 FST_API fst_status fst_model_set_launch(fst_model* model, uint32_t kinds, int32_t block, int32_t variant);
 
 /* Bit mask of the specialised kinds currently in use for this model. */

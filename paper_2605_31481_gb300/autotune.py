@@ -1,10 +1,12 @@
 """Autotuner for the launch configuration of the kernels.
 
 For one model and batch size it measures, on the current GPU, every
-candidate configuration of each kernel kind — variant (generic kernels with
-the tree in shared memory, or kernels specialised for the tree) and
-environments per block (32, 64, 128, 256; one environment per thread) — and
-keeps the fastest via fst_model_set_launch. For a multi-operator step it also
+candidate configuration of each kernel kind — the environment-to-thread
+mapping and kernel variant (one environment per thread with the tree in
+shared memory, one environment per thread with a kernel specialised for the
+tree, or level-parallel: 32 environments per block with the block's warps
+splitting each tree level) and the block size (32 to 256 threads) — and keeps
+the fastest via fst_model_set_launch. For a multi-operator step it also
 decides between the fused launch (fst_eval, operators side by side) and the
 operators one after another: fusing pays at small B, where one operator
 leaves most SMs idle, and costs at large B, where one register allocation
@@ -28,6 +30,7 @@ from . import _ffi
 
 CANDIDATE_BLOCKS = (32, 64, 128, 256)
 FORWARD_KINDS = ("fk", "jacobian", "rnea", "crba", "aba")
+LEVEL_KINDS = FORWARD_KINDS + ("eval",)   # kinds with a level-parallel variant
 _lock = threading.Lock()
 
 
@@ -147,7 +150,8 @@ def tune(model, B, kinds=FORWARD_KINDS + ("eval",), links=None, use_cache=True, 
                 api.aba(model, buf.q, buf.qd, buf.tau, out=buf.qdd_fwd)
         fn = _op(model, kind, buf)
         cands = {}
-        for variant in ("generic", "specialized") if kind in spec else ("generic",):
+        variants = ["generic"] + (["specialized"] if kind in spec else []) + (["level"] if kind in LEVEL_KINDS else [])
+        for variant in variants:
             for block in CANDIDATE_BLOCKS:
                 model.set_launch([kind], block, variant)
                 cands[f"{variant}/{block}"] = graph_time_us(fn)

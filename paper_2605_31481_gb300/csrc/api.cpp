@@ -58,8 +58,20 @@ fst_status need(const char* fn, const void* p, const char* name) {
 }
 
 // Whether a call of this kind runs the specialised kernel: it must exist,
-// and the kind must not be pinned to the generic variant.
-bool use_jit(const fst_model* m, int kind) { return m->variant[kind] != FST_VARIANT_GENERIC && jit_has(m, kind); }
+// and the kind must not be pinned to another variant.
+bool use_jit(const fst_model* m, int kind) {
+  return (m->variant[kind] == FST_VARIANT_AUTO || m->variant[kind] == FST_VARIANT_SPECIALIZED) && jit_has(m, kind);
+}
+
+// Whether a call of this kind runs the level-parallel kernel: selected, and
+// its shared memory (which grows with the number of bodies) fits.
+bool use_level(const fst_model* m, int kind, int level_kind) {
+  return m->variant[kind] == FST_VARIANT_LEVEL && level_smem_needed(view_of(m, nullptr), level_kind) <= kLevelSmemLimit;
+}
+
+// Threads per block of a level-parallel launch: a multiple of 32 (one warp
+// per share of a level), 32 environments per block.
+int level_block(const fst_model* m, int kind) { return m->block[kind] ? m->block[kind] : 128; }
 
 int block_of(const fst_model* m, int kind, int64_t B) { return m->block[kind] ? m->block[kind] : default_block(B); }
 
@@ -120,11 +132,14 @@ fst_status fst_model_create(const fst_body_desc* bodies, int32_t n_bodies, const
   if (err == cudaSuccess) err = cudaMalloc((void**)&m->di, sizeof(BodyI) * m->n);
   if (err == cudaSuccess) err = cudaMemcpy(m->dc, m->hc.data(), sizeof(BodyC) * m->n, cudaMemcpyHostToDevice);
   if (err == cudaSuccess) err = cudaMemcpy(m->di, m->hi.data(), sizeof(BodyI) * m->n, cudaMemcpyHostToDevice);
+  if (err == cudaSuccess) err = cudaMalloc((void**)&m->dt, sizeof(TopoLists));
+  if (err == cudaSuccess) err = cudaMemcpy(m->dt, &m->ht, sizeof(TopoLists), cudaMemcpyHostToDevice);
   if (err != cudaSuccess) {
     fst_status st = (err == cudaErrorMemoryAllocation) ? set_error(FST_ERR_NO_MEMORY, "fst_model_create: cudaMalloc failed")
                                                        : cuda_error("fst_model_create", err);
     if (m->dc) cudaFree(m->dc);
     if (m->di) cudaFree(m->di);
+    if (m->dt) cudaFree(m->dt);
     delete m;
     return st;
   }
@@ -137,6 +152,7 @@ fst_status fst_model_destroy(fst_model* m) {
   jit_release(m);
   if (m->dc) cudaFree(m->dc);
   if (m->di) cudaFree(m->di);
+  if (m->dt) cudaFree(m->dt);
   delete m;
   return FST_OK;
 }
@@ -152,13 +168,17 @@ fst_status fst_model_set_launch(fst_model* m, uint32_t kinds, int32_t block, int
   if (!m) return set_error(FST_ERR_INVALID_ARG, "fst_model_set_launch: null model");
   if (block != 0 && block != 32 && block != 64 && block != 128 && block != 256)
     return set_error(FST_ERR_INVALID_ARG, "fst_model_set_launch: block must be 0, 32, 64, 128 or 256");
-  if (variant < FST_VARIANT_AUTO || variant > FST_VARIANT_SPECIALIZED)
+  if (variant < FST_VARIANT_AUTO || variant > FST_VARIANT_LEVEL)
     return set_error(FST_ERR_INVALID_ARG, "fst_model_set_launch: unknown variant");
   if (kinds == 0) kinds = FST_SPEC_ALL;
   if (kinds & ~(uint32_t)FST_SPEC_ALL) return set_error(FST_ERR_INVALID_ARG, "fst_model_set_launch: unknown kind bits");
-  for (int k = 0; k < JK_COUNT; ++k)
+  for (int k = 0; k < JK_COUNT; ++k) {
     if (((kinds >> k) & 1u) && variant == FST_VARIANT_SPECIALIZED && !jit_has(m, k))
       return set_error(FST_ERR_INVALID_ARG, "fst_model_set_launch: a selected kind is not specialised yet");
+    if (((kinds >> k) & 1u) && variant == FST_VARIANT_LEVEL && k > JK_EVAL)
+      return set_error(FST_ERR_INVALID_ARG, "fst_model_set_launch: the level-parallel variant exists for FK, "
+                                            "Jacobian, RNEA, CRBA, ABA and eval only");
+  }
   for (int k = 0; k < JK_COUNT; ++k)
     if ((kinds >> k) & 1u) {
       m->block[k] = block;
@@ -197,6 +217,8 @@ fst_status fst_fk(const fst_model* m, int64_t B, const float* q, float* poses, v
   if (m->nq) FST_CHECK(need(fn, q, "q"));
   FST_CHECK(need(fn, poses, "poses"));
   const ModelView mv = view_of(m, nullptr);
+  if (use_level(m, JK_FK, LEVEL_FK))
+    return finish(fn, launch_fk_level(mv, B, q, poses, level_block(m, JK_FK), (cudaStream_t)stream));
   if (use_jit(m, JK_FK))
     return finish(fn, jit_go(m, JK_FK, B, m->nq, 0, 1, (cudaStream_t)stream, nullptr, mv, B, q, poses));
   return finish(fn, launch_fk(mv, B, q, poses, launch_of(m, JK_FK, B, stream)));
@@ -220,6 +242,8 @@ fst_status fst_jacobian(const fst_model* m, int64_t B, const float* q, const int
   FST_CHECK(need(fn, q, "q"));
   FST_CHECK(need(fn, J, "J"));
   const ModelView mv = view_of(m, nullptr);
+  if (use_level(m, JK_JACOBIAN, LEVEL_JAC))
+    return finish(fn, launch_jac_level(mv, B, q, L, J, level_block(m, JK_JACOBIAN), (cudaStream_t)stream));
   if (use_jit(m, JK_JACOBIAN))
     return finish(fn, jit_go(m, JK_JACOBIAN, B, m->nq, 0, 1, (cudaStream_t)stream, nullptr, mv, B, q, L, J));
   return finish(fn, launch_jacobian(mv, B, q, L, J, launch_of(m, JK_JACOBIAN, B, stream)));
@@ -236,6 +260,8 @@ fst_status fst_rnea(const fst_model* m, int64_t B, const float* q, const float* 
   FST_CHECK(need(fn, qdd, "qdd"));
   FST_CHECK(need(fn, tau, "tau"));
   const ModelView mv = view_of(m, theta);
+  if (use_level(m, JK_RNEA, LEVEL_RNEA))
+    return finish(fn, launch_rnea_level(mv, B, q, qd, qdd, tau, level_block(m, JK_RNEA), (cudaStream_t)stream));
   if (use_jit(m, JK_RNEA))
     return finish(fn, jit_go(m, JK_RNEA, B, m->nq + 2 * m->nv, 0, 1, (cudaStream_t)stream, nullptr, mv, B, q, qd,
                              qdd, tau));
@@ -250,6 +276,8 @@ fst_status fst_crba(const fst_model* m, int64_t B, const float* q, const float* 
   FST_CHECK(need(fn, q, "q"));
   FST_CHECK(need(fn, M, "M"));
   const ModelView mv = view_of(m, theta);
+  if (use_level(m, JK_CRBA, LEVEL_CRBA))
+    return finish(fn, launch_crba_level(mv, B, q, M, level_block(m, JK_CRBA), (cudaStream_t)stream));
   if (use_jit(m, JK_CRBA))
     return finish(fn, jit_go(m, JK_CRBA, B, m->nq, 0, 1, (cudaStream_t)stream, nullptr, mv, B, q, M));
   return finish(fn, launch_crba(mv, B, q, M, launch_of(m, JK_CRBA, B, stream)));
@@ -266,6 +294,8 @@ fst_status fst_aba(const fst_model* m, int64_t B, const float* q, const float* q
   FST_CHECK(need(fn, tau, "tau"));
   FST_CHECK(need(fn, qdd, "qdd"));
   const ModelView mv = view_of(m, theta);
+  if (use_level(m, JK_ABA, LEVEL_ABA))
+    return finish(fn, launch_aba_level(mv, B, q, qd, tau, qdd, level_block(m, JK_ABA), (cudaStream_t)stream));
   if (use_jit(m, JK_ABA))
     return finish(fn, jit_go(m, JK_ABA, B, m->nq + 2 * m->nv, 0, 1, (cudaStream_t)stream, nullptr, mv, B, q, qd,
                              tau, qdd));
@@ -316,6 +346,8 @@ fst_status fst_eval(const fst_model* m, int64_t B, const fst_eval_io* io, const 
   if (skip || a.n_roles == 0) return FST_OK;
   if (m->nq) FST_CHECK(need(fn, io->q, "q"));
   const ModelView mv = view_of(m, theta);
+  if (use_level(m, JK_EVAL, LEVEL_EVAL))
+    return finish(fn, launch_eval_level(mv, B, a, level_block(m, JK_EVAL), (cudaStream_t)stream));
   if (use_jit(m, JK_EVAL))
     return finish(fn, jit_go(m, JK_EVAL, B, m->nq + 2 * m->nv, 0, (unsigned)a.n_roles, (cudaStream_t)stream, nullptr,
                              mv, B, a));
@@ -518,7 +550,7 @@ fst_status fst_multi_eval(fst_multi* g, const fst_multi_io* io, void* stream) {
     }
   a.seg_start[seg] = items;
   a.n_items = items;
-  a.model_bytes = (size_t)max_n * (sizeof(BodyC) + sizeof(BodyI));
+  a.model_bytes = (size_t)max_n * (sizeof(BodyC) + sizeof(BodyI)) + (sizeof(TopoLists) + 15) / 16 * 16;
   a.model_bytes = (a.model_bytes + 15) / 16 * 16;
   if (items == 0) return FST_OK;
   return finish(fn, launch_multi(a, max_n, T, (cudaStream_t)stream));

@@ -291,16 +291,24 @@ __device__ __forceinline__ Sym6 sym6_to_parent(const Xf& X, const Sym6& s) {
 #endif
 
 // Run-time topology: the model staged in shared memory. Any type with the
-// same three accessors (n, C, I) can drive the operator templates.
+// same accessors (n, C, I, theta; depth and the level/child lists for the
+// level-parallel kernels) can drive the operator templates.
 struct SmemModel {
   const BodyC* c;
   const BodyI* i;
   int n_;
+  const TopoLists* t = nullptr;
+  int depth_ = 0;
   __device__ __forceinline__ int n() const { return n_; }
   __device__ __forceinline__ const BodyC& C(int k) const { return c[k]; }
   __device__ __forceinline__ BodyI I(int k) const { return i[k]; }
   // inertial parameters (the override, if any, was staged in place)
   __device__ __forceinline__ const float* theta(int k) const { return c[k].theta; }
+  __device__ __forceinline__ int depth() const { return depth_; }
+  __device__ __forceinline__ int level_begin(int l) const { return t->level_start[l]; }
+  __device__ __forceinline__ int level_body(int k) const { return t->level_body[k]; }
+  __device__ __forceinline__ int child_begin(int k) const { return t->child_start[k]; }
+  __device__ __forceinline__ int child(int k) const { return t->child[k]; }
 };
 
 // Copies the model constants (and the inertia override, if any) to shared
@@ -308,20 +316,26 @@ struct SmemModel {
 __device__ __forceinline__ SmemModel stage_model(const ModelView& mv, float4* smem) {
   BodyC* sc = reinterpret_cast<BodyC*>(smem);
   BodyI* si = reinterpret_cast<BodyI*>(sc + mv.n);
+  TopoLists* st = reinterpret_cast<TopoLists*>(si + mv.n);
   const float4* src = reinterpret_cast<const float4*>(mv.c);
   float4* dst = reinterpret_cast<float4*>(sc);
   const int nc4 = mv.n * (int)(sizeof(BodyC) / sizeof(float4));
   for (int k = threadIdx.x; k < nc4; k += blockDim.x) dst[k] = src[k];
   for (int k = threadIdx.x; k < mv.n; k += blockDim.x) si[k] = mv.i[k];
+  const int* ts = reinterpret_cast<const int*>(mv.topo);
+  int* td = reinterpret_cast<int*>(st);
+  for (int k = threadIdx.x; k < (int)(sizeof(TopoLists) / sizeof(int)); k += blockDim.x) td[k] = ts[k];
   if (mv.theta) {
     __syncthreads();
     for (int k = threadIdx.x; k < mv.n * 10; k += blockDim.x) sc[k / 10].theta[k % 10] = mv.theta[k];
   }
   __syncthreads();
-  return SmemModel{sc, si, mv.n};
+  return SmemModel{sc, si, mv.n, st, mv.depth};
 }
 
-__host__ __device__ inline size_t smem_bytes(int n) { return (size_t)n * (sizeof(BodyC) + sizeof(BodyI)); }
+__host__ __device__ inline size_t smem_bytes(int n) {
+  return (size_t)n * (sizeof(BodyC) + sizeof(BodyI)) + (sizeof(TopoLists) + 15) / 16 * 16;
+}
 
 // Dynamic shared memory of a kernel: the model, then a float tile of
 // `rows` staged input rows for each of the block's environments.

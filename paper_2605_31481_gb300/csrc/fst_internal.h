@@ -23,6 +23,8 @@ struct fst_model {
   std::vector<int> level;            // 1-based depth of each body
   fst::BodyC* dc = nullptr;
   fst::BodyI* di = nullptr;
+  fst::TopoLists ht{};               // level and child lists (host copy)
+  fst::TopoLists* dt = nullptr;      // device copy
   fst::JitState* jit = nullptr;      // run-time specialised kernels, if any
   int block[16] = {0};               // threads per block per kernel kind (0 = built-in heuristic)
   int variant[16] = {0};             // per kind: 0 auto, 1 generic, 2 specialised (see fst_model_set_launch)
@@ -37,6 +39,7 @@ inline ModelView view_of(const fst_model* m, const float* theta) {
   ModelView v;
   v.c = m->dc;
   v.i = m->di;
+  v.topo = m->dt;
   v.theta = theta;
   v.n = m->n;
   v.nq = m->nq;

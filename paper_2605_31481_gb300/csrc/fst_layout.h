@@ -48,10 +48,24 @@ struct BodyI {
   int32_t vi;
 };
 
+// Level and child lists of the tree (ints), used by the level-parallel
+// kernels: bodies of level l (root = level 0) are
+// level_body[level_start[l] .. level_start[l+1]), children of body i are
+// child[child_start[i] .. child_start[i+1]). Laid out in one int array:
+//   level_start (FST_MAX_BODIES + 1) | level_body (FST_MAX_BODIES) |
+//   child_start (FST_MAX_BODIES + 1) | child (FST_MAX_BODIES)
+struct TopoLists {
+  int level_start[FST_MAX_BODIES + 1];
+  int level_body[FST_MAX_BODIES];
+  int child_start[FST_MAX_BODIES + 1];
+  int child[FST_MAX_BODIES];
+};
+
 // Everything a kernel needs to find the model; passed by value.
 struct ModelView {
   const BodyC* c;        // device, n entries
   const BodyI* i;        // device, n entries
+  const TopoLists* topo; // device
   const float* theta;    // device [n][10] override, or nullptr
   int n, nq, nv, depth;
   float a0[3];           // linear part of the world's spatial acceleration: -gravity

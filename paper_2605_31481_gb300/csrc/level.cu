@@ -1,0 +1,163 @@
+// Level-parallel kernels (bodies in level.cuh): 32 environments per block,
+// W = blockDim.x / 32 warps splitting each level's bodies.
+//
+// Shared memory: model | input tile (rows x 32) | per-body state (F x n x 32).
+#include "launch.h"
+#include "level.cuh"
+
+namespace fst {
+namespace {
+
+__device__ __forceinline__ float* level_tile(float4* smem, int n) { return smem_tile(smem, n); }
+
+#define FST_LEVEL_PROLOGUE(rows, F)                                          \
+  extern __shared__ float4 smem[];                                          \
+  float* tile = level_tile(smem, mv.n);                                     \
+  const LaneState S{tile + (rows) * kLaneEnvs, (F)};                        \
+  const int lane = threadIdx.x & 31;                                        \
+  const int64_t e = (int64_t)blockIdx.x * kLaneEnvs + lane;                 \
+  const bool act = e < B
+
+#define FST_LEVEL_READY                            \
+  const SmemModel sm = stage_model(mv, smem);      \
+  cp_async_wait_all();                             \
+  __syncthreads()
+
+__global__ void __launch_bounds__(256) fk_level_kernel(ModelView mv, int64_t B, const float* __restrict__ q,
+                                                       float* __restrict__ poses) {
+  FST_LEVEL_PROLOGUE(mv.nq, kFkState);
+  stage_block_rows(tile, q, mv.nq, B, e);
+  FST_LEVEL_READY;
+  fk_level(sm, Col{tile + lane, kLaneEnvs}, S, poses, B, e, act);
+}
+
+__global__ void __launch_bounds__(256) jac_level_kernel(ModelView mv, int64_t B, const float* __restrict__ q,
+                                                        LinkList links, float* __restrict__ poses,
+                                                        float* __restrict__ J) {
+  FST_LEVEL_PROLOGUE(mv.nq, kFkState);
+  stage_block_rows(tile, q, mv.nq, B, e);
+  FST_LEVEL_READY;
+  fk_level(sm, Col{tile + lane, kLaneEnvs}, S, poses, B, e, act);
+  jac_columns(sm, mv.nv, links, S, J, B, e, act);
+}
+
+__global__ void __launch_bounds__(256) rnea_level_kernel(ModelView mv, int64_t B, const float* __restrict__ q,
+                                                         const float* __restrict__ qd, const float* __restrict__ qdd,
+                                                         float* __restrict__ tau) {
+  FST_LEVEL_PROLOGUE(mv.nq + 2 * mv.nv, kRneaState);
+  stage_block_rows(tile, q, mv.nq, B, e);
+  stage_block_rows(tile + mv.nq * kLaneEnvs, qd, mv.nv, B, e);
+  stage_block_rows(tile + (mv.nq + mv.nv) * kLaneEnvs, qdd, mv.nv, B, e);
+  FST_LEVEL_READY;
+  rnea_level(sm, world_accel(mv), Col{tile + lane, kLaneEnvs}, Col{tile + mv.nq * kLaneEnvs + lane, kLaneEnvs},
+             Col{tile + (mv.nq + mv.nv) * kLaneEnvs + lane, kLaneEnvs}, S, tau, B, e, act);
+}
+
+__global__ void __launch_bounds__(256) crba_level_kernel(ModelView mv, int64_t B, const float* __restrict__ q,
+                                                         float* __restrict__ M) {
+  FST_LEVEL_PROLOGUE(mv.nq, kCrbaState);
+  stage_block_rows(tile, q, mv.nq, B, e);
+  FST_LEVEL_READY;
+  crba_level(sm, Col{tile + lane, kLaneEnvs}, mv.nv, S, M, B, e, act);
+}
+
+__global__ void __launch_bounds__(256) aba_level_kernel(ModelView mv, int64_t B, const float* __restrict__ q,
+                                                        const float* __restrict__ qd, const float* __restrict__ tau,
+                                                        float* __restrict__ qdd) {
+  FST_LEVEL_PROLOGUE(mv.nq + 2 * mv.nv, kAbaState);
+  stage_block_rows(tile, q, mv.nq, B, e);
+  stage_block_rows(tile + mv.nq * kLaneEnvs, qd, mv.nv, B, e);
+  stage_block_rows(tile + (mv.nq + mv.nv) * kLaneEnvs, tau, mv.nv, B, e);
+  FST_LEVEL_READY;
+  aba_level(sm, world_accel(mv), Col{tile + lane, kLaneEnvs}, Col{tile + mv.nq * kLaneEnvs + lane, kLaneEnvs},
+            Col{tile + (mv.nq + mv.nv) * kLaneEnvs + lane, kLaneEnvs}, S, qdd, B, e, act);
+}
+
+// Fused evaluation with the level-parallel bodies: blockIdx.y is the role.
+__global__ void __launch_bounds__(256) eval_level_kernel(ModelView mv, int64_t B, EvalArgs a) {
+  const int role = a.roles[blockIdx.y];
+  const int F = role == ROLE_ABA ? kAbaState : role == ROLE_CRBA ? kCrbaState : role == ROLE_RNEA ? kRneaState : kFkState;
+  FST_LEVEL_PROLOGUE(mv.nq + 2 * mv.nv, F);
+  stage_block_rows(tile, a.q, mv.nq, B, e);
+  if (role == ROLE_RNEA) {
+    stage_block_rows(tile + mv.nq * kLaneEnvs, a.qd, mv.nv, B, e);
+    stage_block_rows(tile + (mv.nq + mv.nv) * kLaneEnvs, a.qdd, mv.nv, B, e);
+  } else if (role == ROLE_ABA) {
+    stage_block_rows(tile + mv.nq * kLaneEnvs, a.qd, mv.nv, B, e);
+    stage_block_rows(tile + (mv.nq + mv.nv) * kLaneEnvs, a.tau, mv.nv, B, e);
+  }
+  FST_LEVEL_READY;
+  const Col cq{tile + lane, kLaneEnvs};
+  const Col c1{tile + mv.nq * kLaneEnvs + lane, kLaneEnvs};
+  const Col c2{tile + (mv.nq + mv.nv) * kLaneEnvs + lane, kLaneEnvs};
+  switch (role) {
+    case ROLE_ABA:
+      aba_level(sm, world_accel(mv), cq, c1, c2, S, a.qdd_out, B, e, act);
+      break;
+    case ROLE_CRBA:
+      crba_level(sm, cq, mv.nv, S, a.M, B, e, act);
+      break;
+    case ROLE_RNEA:
+      rnea_level(sm, world_accel(mv), cq, c1, c2, S, a.tau_out, B, e, act);
+      break;
+    default:
+      fk_level(sm, cq, S, a.poses, B, e, act);
+      if (a.J) jac_columns(sm, mv.nv, a.links, S, a.J, B, e, act);
+      break;
+  }
+}
+
+size_t level_smem(const ModelView& mv, int rows, int F) {
+  return smem_bytes(mv.n) + (size_t)rows * kLaneEnvs * sizeof(float) + (size_t)F * mv.n * kLaneEnvs * sizeof(float);
+}
+
+template <typename K, typename... A>
+cudaError_t go(K* kernel, const ModelView& mv, int64_t B, size_t sh, int block, unsigned gy, cudaStream_t s,
+               A... args) {
+  if (sh > kLevelSmemLimit) return cudaErrorInvalidConfiguration;
+  prepare(kernel, sh);
+  kernel<<<dim3((unsigned)((B + kLaneEnvs - 1) / kLaneEnvs), gy), block, sh, s>>>(mv, B, args...);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t level_smem_needed(const ModelView& mv, int kind) {
+  switch (kind) {
+    case LEVEL_FK:
+    case LEVEL_JAC:
+      return level_smem(mv, mv.nq, kFkState);
+    case LEVEL_RNEA:
+      return level_smem(mv, mv.nq + 2 * mv.nv, kRneaState);
+    case LEVEL_CRBA:
+      return level_smem(mv, mv.nq, kCrbaState);
+    case LEVEL_ABA:
+      return level_smem(mv, mv.nq + 2 * mv.nv, kAbaState);
+    default:
+      return level_smem(mv, mv.nq + 2 * mv.nv, kAbaState);
+  }
+}
+
+cudaError_t launch_fk_level(const ModelView& mv, int64_t B, const float* q, float* poses, int block, cudaStream_t s) {
+  return go(fk_level_kernel, mv, B, level_smem_needed(mv, LEVEL_FK), block, 1, s, q, poses);
+}
+cudaError_t launch_jac_level(const ModelView& mv, int64_t B, const float* q, const LinkList& links, float* J,
+                             int block, cudaStream_t s) {
+  return go(jac_level_kernel, mv, B, level_smem_needed(mv, LEVEL_JAC), block, 1, s, q, links, (float*)nullptr, J);
+}
+cudaError_t launch_rnea_level(const ModelView& mv, int64_t B, const float* q, const float* qd, const float* qdd,
+                              float* tau, int block, cudaStream_t s) {
+  return go(rnea_level_kernel, mv, B, level_smem_needed(mv, LEVEL_RNEA), block, 1, s, q, qd, qdd, tau);
+}
+cudaError_t launch_crba_level(const ModelView& mv, int64_t B, const float* q, float* M, int block, cudaStream_t s) {
+  return go(crba_level_kernel, mv, B, level_smem_needed(mv, LEVEL_CRBA), block, 1, s, q, M);
+}
+cudaError_t launch_aba_level(const ModelView& mv, int64_t B, const float* q, const float* qd, const float* tau,
+                             float* qdd, int block, cudaStream_t s) {
+  return go(aba_level_kernel, mv, B, level_smem_needed(mv, LEVEL_ABA), block, 1, s, q, qd, tau, qdd);
+}
+cudaError_t launch_eval_level(const ModelView& mv, int64_t B, const EvalArgs& a, int block, cudaStream_t s) {
+  return go(eval_level_kernel, mv, B, level_smem_needed(mv, LEVEL_EVAL), block, (unsigned)a.n_roles, s, a);
+}
+
+}  // namespace fst

@@ -215,6 +215,22 @@ fst_status build_model_host(const fst_body_desc* bodies, int32_t n, const double
   m->nq = nq;
   m->nv = nv;
   m->depth = depth;
+  // level lists (stable: bodies of a level in body order) and child lists
+  TopoLists& T = m->ht;
+  int k = 0;
+  for (int l = 0; l < depth; ++l) {
+    T.level_start[l] = k;
+    for (int i = 0; i < n; ++i)
+      if (m->level[i] == l + 1) T.level_body[k++] = i;
+  }
+  T.level_start[depth] = k;
+  k = 0;
+  for (int i = 0; i < n; ++i) {
+    T.child_start[i] = k;
+    for (int j = i + 1; j < n; ++j)
+      if (bodies[j].parent == i) T.child[k++] = j;
+  }
+  T.child_start[n] = k;
   return FST_OK;
 }
 
