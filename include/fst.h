@@ -151,7 +151,8 @@ FST_API fst_status fst_model_specialize(fst_model* model, uint32_t kinds);
  *   LEVEL       level-parallel (paper Sec. 3.3 on warps): 32 environments per
  *               block, the block's block/32 warps split the bodies of each
  *               tree level, per-body state in shared memory; FK, Jacobian,
- *               RNEA, CRBA, ABA and eval only, and only while that state fits
+ *               RNEA, CRBA, ABA and eval only (a 0 mask then selects those
+ *               six), and only while that state fits
  *               in shared memory (about 28 bodies for ABA); otherwise the
  *               generic kernel runs.
  * Results agree within FP32 rounding; only speed changes. SPECIALIZED for a

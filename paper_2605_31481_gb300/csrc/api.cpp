@@ -170,7 +170,8 @@ fst_status fst_model_set_launch(fst_model* m, uint32_t kinds, int32_t block, int
     return set_error(FST_ERR_INVALID_ARG, "fst_model_set_launch: block must be 0, 32, 64, 128 or 256");
   if (variant < FST_VARIANT_AUTO || variant > FST_VARIANT_LEVEL)
     return set_error(FST_ERR_INVALID_ARG, "fst_model_set_launch: unknown variant");
-  if (kinds == 0) kinds = FST_SPEC_ALL;
+  // "all kinds" with the level variant means every kind that has one
+  if (kinds == 0) kinds = variant == FST_VARIANT_LEVEL ? (1u << (JK_EVAL + 1)) - 1u : FST_SPEC_ALL;
   if (kinds & ~(uint32_t)FST_SPEC_ALL) return set_error(FST_ERR_INVALID_ARG, "fst_model_set_launch: unknown kind bits");
   for (int k = 0; k < JK_COUNT; ++k) {
     if (((kinds >> k) & 1u) && variant == FST_VARIANT_SPECIALIZED && !jit_has(m, k))
