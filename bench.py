@@ -278,8 +278,11 @@ def run_fst(args):
     t_k = kernel_ms / 1e3
     bound = "alu" if fl / (p_alu * 1e12) > by / (pk["hbm_gbs"] * 1e9) else "hbm"
     desc = plan.describe()
-    common = {"kernel": ("fused eval kernel" if plan.fused else "per-operator kernels in sequence") +
-              f" ({desc['kinds']['eval' if plan.fused else 'aba']})", "traffic": args.traffic,
+    kname = {"fused": f"fused eval kernel ({desc['kinds']['eval']})",
+             "concurrent": "5 per-operator kernels on parallel graph branches (" +
+                           ", ".join(f"{k} {desc['kinds'][k]}" for k in OPS) + ")",
+             "sequential": "5 per-operator kernels in sequence"}[plan.mode]
+    common = {"kernel": kname, "traffic": args.traffic,
               "algorithmic_bytes_per_launch": by * B, "algorithmic_flops_per_launch": fl * B,
               "kernel_ms": round(kernel_ms, 5),
               "alu_frac": round(fl * B / t_k / 1e12 / p_alu, 5),
@@ -439,12 +442,12 @@ def humanoid_sweep(torch, fst, w, Bs=(1, 64, 1024, 4096, 16384, 65536)):
         s = w.random_state(tree, B, seed=1)
         cu = lambda x: torch.from_numpy(np.ascontiguousarray(x.T.astype(np.float32))).cuda()
         q, qd, qdd, tau = cu(s["q"]), cu(s["qd"]), cu(s["qdd"]), cu(s["tau"])
-        plan = StepPlan(m, B, links=tree.ee, use_cache=False)
+        plan = StepPlan(m, B, links=tree.ee)
         o = {"poses": torch.empty(tree.n_bodies, 12, B, device="cuda"),
              "J": torch.empty(len(tree.ee), 6, tree.nv, B, device="cuda"), "tau": torch.empty(tree.nv, B, device="cuda"),
              "M": torch.empty(tree.nv, tree.nv, B, device="cuda"), "qdd": torch.empty(tree.nv, B, device="cuda")}
         us = _graph_us(torch, lambda: plan(q, qd, qdd, tau, o))
-        out[str(B)] = {"us": round(us, 3), "env_evals_per_s": round(B / us * 1e6, 1), "plan": plan.describe()["mode"]}
+        out[str(B)] = {"us": round(us, 3), "env_evals_per_s": round(B / us * 1e6, 1), "plan": plan.mode}
     return {"workload": "humanoid_float29 (free base + 23 revolute, depth 7): FK + 4 Jacobians + RNEA + CRBA + ABA",
             "per_B": out}
 

@@ -169,34 +169,64 @@ def tune(model, B, kinds=FORWARD_KINDS + ("eval",), links=None, use_cache=True, 
 
 
 class StepPlan:
-    """How to run the five forward operators on one batch: one fused launch
-    (fst_eval) or the per-operator kernels in sequence, whichever the tuner
-    measured faster (each already at its tuned configuration)."""
+    """How to run the five forward operators on one batch, whichever the
+    tuner measured fastest (each operator already at its tuned
+    configuration):
+      fused       one launch (fst_eval), operators side by side in one kernel
+                  with one variant for all of them;
+      concurrent  each operator's own kernel (each at its best variant) on its
+                  own stream, forked from and joined back into the caller's
+                  stream, so they overlap on the GPU; captured into a CUDA
+                  graph these become parallel branches;
+      sequential  the per-operator kernels one after another."""
 
-    def __init__(self, model, B, links=None, use_cache=True, verbose=False):
+    MODES = ("fused", "concurrent", "sequential")
+
+    def __init__(self, model, B, links=None, use_cache=True, verbose=False, modes=MODES):
         self.model = model
         self.links = list(links if links is not None else model.ee)
         self.tuned = tune(model, B, FORWARD_KINDS + ("eval",), links=self.links, use_cache=use_cache,
                           verbose=verbose)
-        fused = self.tuned["eval"]["us"]
-        seq = sum(self.tuned[k]["us"] for k in FORWARD_KINDS)
-        self.fused = fused <= seq
-        self.expected_us = min(fused, seq)
-        self.sequential_us = seq
-        self.fused_us = fused
+        self.streams = [torch.cuda.Stream(device=model.device) for _ in FORWARD_KINDS]
+        buf = Buffers(model, B, self.links)
+        times = {}
+        for mode in modes:
+            self.mode = mode
+            times[mode] = graph_time_us(lambda: self(buf.q, buf.qd, buf.qdd, buf.tau, buf.out))
+        self.times = times
+        self.mode = min(times, key=times.get)
+        self.fused = self.mode == "fused"
+        self.expected_us = times[self.mode]
+
+    def _ops(self, q, qd, qdd, tau, out):
+        m = self.model
+        return (lambda: api.fk(m, q, out=out["poses"]),
+                lambda: api.jacobian(m, q, self.links, out=out["J"]),
+                lambda: api.rnea(m, q, qd, qdd, out=out["tau"]),
+                lambda: api.crba(m, q, out=out["M"]),
+                lambda: api.aba(m, q, qd, tau, out=out["qdd"]))
 
     def __call__(self, q, qd, qdd, tau, out):
         m = self.model
-        if self.fused:
+        if self.mode == "fused":
             return api.eval(m, q, qd, qdd, tau, fk=True, links=self.links, rnea=True, crba=True, aba=True, out=out)
-        api.fk(m, q, out=out["poses"])
-        api.jacobian(m, q, self.links, out=out["J"])
-        api.rnea(m, q, qd, qdd, out=out["tau"])
-        api.crba(m, q, out=out["M"])
-        api.aba(m, q, qd, tau, out=out["qdd"])
+        ops = self._ops(q, qd, qdd, tau, out)
+        if self.mode == "sequential":
+            for op in ops:
+                op()
+            return out
+        cur = torch.cuda.current_stream(m.device)
+        # longest first, so its blocks are dispatched first
+        order = sorted(range(len(ops)), key=lambda k: -self.tuned[FORWARD_KINDS[k]]["us"])
+        for k in order:
+            st = self.streams[k]
+            st.wait_stream(cur)
+            with torch.cuda.stream(st):
+                ops[k]()
+        for st in self.streams:
+            cur.wait_stream(st)
         return out
 
     def describe(self):
-        return {"mode": "fused" if self.fused else "sequential", "fused_us": round(self.fused_us, 3),
-                "sequential_us": round(self.sequential_us, 3),
+        return {"mode": self.mode, "us": {k: round(v, 3) for k, v in self.times.items()},
                 "kinds": {k: f"{v['variant']}/{v['block']}" for k, v in self.tuned.items()}}

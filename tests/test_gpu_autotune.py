@@ -74,8 +74,17 @@ def test_step_plan_matches_per_operator_calls(torch_cuda, tmp_path, monkeypatch)
     out = {"poses": torch.empty(tree.n_bodies, 12, B, device="cuda"),
            "J": torch.empty(4, 6, tree.nv, B, device="cuda"), "tau": torch.empty(tree.nv, B, device="cuda"),
            "M": torch.empty(tree.nv, tree.nv, B, device="cuda"), "qdd": torch.empty(tree.nv, B, device="cuda")}
-    plan(q, qd, qdd, tau, out)
-    assert plan.describe()["mode"] in ("fused", "sequential")
+    for mode in plan.MODES:
+        plan.mode = mode
+        for v in out.values():
+            v.zero_()
+        plan(q, qd, qdd, tau, out)
+        torch.cuda.synchronize()
+        ref = {"poses": api.fk(m, q), "J": api.jacobian(m, q, tree.ee), "tau": api.rnea(m, q, qd, qdd),
+               "M": api.crba(m, q), "qdd": api.aba(m, q, qd, tau)}
+        for k, tol in TOL.items():
+            assert env_err(from_soa(out[k]), from_soa(ref[k])).max() <= tol, (mode, k)
+    assert set(plan.describe()["us"]) == set(plan.MODES)
     ref = {"poses": api.fk(m, q), "J": api.jacobian(m, q, tree.ee), "tau": api.rnea(m, q, qd, qdd),
            "M": api.crba(m, q), "qdd": api.aba(m, q, qd, tau)}
     for k, tol in TOL.items():
