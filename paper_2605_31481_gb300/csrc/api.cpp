@@ -349,9 +349,36 @@ fst_status fst_eval(const fst_model* m, int64_t B, const fst_eval_io* io, const 
   const ModelView mv = view_of(m, theta);
   if (use_level(m, JK_EVAL, LEVEL_EVAL))
     return finish(fn, launch_eval_level(mv, B, a, level_block(m, JK_EVAL), (cudaStream_t)stream));
-  if (use_jit(m, JK_EVAL))
-    return finish(fn, jit_go(m, JK_EVAL, B, m->nq + 2 * m->nv, 0, (unsigned)a.n_roles, (cudaStream_t)stream, nullptr,
-                             mv, B, a));
+  if (use_jit(m, JK_EVAL)) {
+    // roles whose own operator is tuned level-parallel run that way here too
+    const int T = block_of(m, JK_EVAL, B);
+    const int rows = m->nq + 2 * m->nv;
+    size_t sh = 0;
+    int64_t gx = 0;
+    for (int r = 0; r < a.n_roles; ++r) {
+      const int role = a.roles[r];
+      const int kind = role == ROLE_ABA ? JK_ABA : role == ROLE_CRBA ? JK_CRBA : role == ROLE_RNEA ? JK_RNEA
+                                                                     : (a.J ? JK_JACOBIAN : JK_FK);
+      const int lk = role == ROLE_ABA ? LEVEL_ABA : role == ROLE_CRBA ? LEVEL_CRBA : role == ROLE_RNEA ? LEVEL_RNEA
+                                                                      : LEVEL_JAC;
+      size_t need;
+      int64_t blocks;
+      if (use_level(m, kind, lk)) {
+        a.level_mask |= 1 << role;
+        need = level_smem_needed(mv, lk) - (size_t)m->n * (sizeof(BodyC) + sizeof(BodyI)) -
+               (sizeof(TopoLists) + 15) / 16 * 16;  // no model copy in shared memory here
+        blocks = (B + 31) / 32;
+      } else {
+        need = (size_t)rows * T * sizeof(float);
+        blocks = (B + T - 1) / T;
+      }
+      if (need > sh) sh = need;
+      if (blocks > gx) gx = blocks;
+    }
+    void* argv[] = {(void*)&mv, (void*)&B, (void*)&a};
+    return finish(fn, jit_launch(m, JK_EVAL, dim3((unsigned)gx, (unsigned)a.n_roles), T, sh, (cudaStream_t)stream,
+                                 argv));
+  }
   return finish(fn, launch_eval(mv, B, a, launch_of(m, JK_EVAL, B, stream)));
 }
 

@@ -93,6 +93,7 @@ struct EvalArgs {
   LinkList links;
   int roles[4];
   int n_roles;
+  int level_mask;  // bit r: role r runs level-parallel (32 environments per block)
 };
 
 }  // namespace fst

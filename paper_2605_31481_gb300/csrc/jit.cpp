@@ -161,7 +161,19 @@ std::string make_source(const fst_model* m, int kind) {
     const BodyI& b = m->hi[i];
     os << (i ? "," : "") << "{" << b.parent << "," << b.type << "," << b.qi << "," << b.vi << "}";
   }
-  os << "};\n}  // namespace fst\n#include \"jit_kernels.cuh\"\n";
+  os << "};\n";
+  const TopoLists& T = m->ht;
+  auto ints = [&](const char* name, const int* v, int n) {
+    os << "static __device__ const int " << name << "[" << (n > 0 ? n : 1) << "] = {";
+    for (int k = 0; k < n; ++k) os << (k ? "," : "") << v[k];
+    if (n == 0) os << "0";
+    os << "};\n";
+  };
+  ints("kLevelStart", T.level_start, m->depth + 1);
+  ints("kLevelBody", T.level_body, m->n);
+  ints("kChildStart", T.child_start, m->n + 1);
+  ints("kChild", T.child, T.child_start[m->n]);
+  os << "}  // namespace fst\n#define FST_DEPTH " << m->depth << "\n#include \"jit_kernels.cuh\"\n";
   return os.str();
 }
 

@@ -12,6 +12,7 @@
 #pragma once
 
 #include "adjoint.cuh"
+#include "level.cuh"
 
 namespace fst {
 
@@ -22,6 +23,11 @@ struct FixedTopo {
   __device__ __forceinline__ const BodyC& C(int k) const { return kC[k]; }
   __device__ __forceinline__ BodyI I(int k) const { return kI[k]; }
   __device__ __forceinline__ const float* theta(int k) const { return th + k * ts; }
+  __device__ __forceinline__ static constexpr int depth() { return FST_DEPTH; }
+  __device__ __forceinline__ int level_begin(int l) const { return kLevelStart[l]; }
+  __device__ __forceinline__ int level_body(int k) const { return kLevelBody[k]; }
+  __device__ __forceinline__ int child_begin(int k) const { return kChildStart[k]; }
+  __device__ __forceinline__ int child(int k) const { return kChild[k]; }
 };
 
 __device__ __forceinline__ FixedTopo fixed_topo(const ModelView& mv) {
@@ -123,10 +129,55 @@ extern "C" __global__ void __launch_bounds__(256) FST_JIT_NAME(ModelView mv, int
 #endif
 
 #ifdef FST_JIT_EVAL
+// Roles in a.level_mask run level-parallel (32 environments per block, the
+// block's warps splitting each tree level); the others one environment per
+// thread. The grid's x extent covers the larger of the two; blocks past a
+// role's last environment leave at once (block-uniform, before any barrier).
 extern "C" __global__ void __launch_bounds__(256) FST_JIT_NAME(ModelView mv, int64_t B, EvalArgs a) {
-  FST_JIT_PROLOGUE;
-  if (!act) return;
+  extern __shared__ float4 smem[];
+  float* tile = reinterpret_cast<float*>(smem);
   const int role = a.roles[blockIdx.y];
+  const FixedTopo tp = fixed_topo(mv);
+  if ((a.level_mask >> role) & 1) {
+    if ((int64_t)blockIdx.x * kLaneEnvs >= B) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t e = (int64_t)blockIdx.x * kLaneEnvs + lane;
+    const bool act = e < B;
+    const int F = role == ROLE_ABA ? kAbaState : role == ROLE_CRBA ? kCrbaState : role == ROLE_RNEA ? kRneaState : kFkState;
+    const LaneState S{tile + (mv.nq + 2 * mv.nv) * kLaneEnvs, F};
+    stage_block_rows(tile, a.q, mv.nq, B, e);
+    if (role == ROLE_RNEA) {
+      stage_block_rows(tile + mv.nq * kLaneEnvs, a.qd, mv.nv, B, e);
+      stage_block_rows(tile + (mv.nq + mv.nv) * kLaneEnvs, a.qdd, mv.nv, B, e);
+    } else if (role == ROLE_ABA) {
+      stage_block_rows(tile + mv.nq * kLaneEnvs, a.qd, mv.nv, B, e);
+      stage_block_rows(tile + (mv.nq + mv.nv) * kLaneEnvs, a.tau, mv.nv, B, e);
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    const Col cq{tile + lane, kLaneEnvs};
+    const Col c1{tile + mv.nq * kLaneEnvs + lane, kLaneEnvs};
+    const Col c2{tile + (mv.nq + mv.nv) * kLaneEnvs + lane, kLaneEnvs};
+    switch (role) {
+      case ROLE_ABA:
+        aba_level(tp, world_accel(mv), cq, c1, c2, S, a.qdd_out, B, e, act);
+        break;
+      case ROLE_CRBA:
+        crba_level(tp, cq, mv.nv, S, a.M, B, e, act);
+        break;
+      case ROLE_RNEA:
+        rnea_level(tp, world_accel(mv), cq, c1, c2, S, a.tau_out, B, e, act);
+        break;
+      default:
+        fk_level(tp, cq, S, a.poses, B, e, act);
+        if (a.J) jac_columns(tp, mv.nv, a.links, S, a.J, B, e, act);
+        break;
+    }
+    return;
+  }
+  const int T = blockDim.x;
+  const int64_t e = (int64_t)blockIdx.x * T + threadIdx.x;
+  if (e >= B) return;
   const Col cq = stage_rows(tile, a.q, mv.nq, B, e);
   Col c1{}, c2{};
   if (role == ROLE_RNEA) {
@@ -137,7 +188,6 @@ extern "C" __global__ void __launch_bounds__(256) FST_JIT_NAME(ModelView mv, int
     c2 = stage_rows(tile + (mv.nq + mv.nv) * T, a.tau, mv.nv, B, e);
   }
   cp_async_wait_all();
-  const FixedTopo tp = fixed_topo(mv);
   switch (role) {
     case ROLE_ABA:
       aba_env<FST_N>(tp, world_accel(mv), cq, c1, c2, a.qdd_out, B, e);

@@ -128,7 +128,9 @@ __device__ __forceinline__ void fk_level(const TP& tp, const Col& q, const LaneS
   const int W = n_warps(), w = warp_id();
   FST_UNROLL
   for (int l = 0; l < tp.depth(); ++l) {
-    for (int k = tp.level_begin(l) + w; k < tp.level_begin(l + 1); k += W) {
+    FST_UNROLL
+    for (int k = tp.level_begin(l); k < tp.level_begin(l + 1); ++k) {
+      if ((k - tp.level_begin(l)) % W != w) continue;
       const int i = tp.level_body(k);
       const BodyI bi = tp.I(i);
       const Xf X = joint_X(tp.C(i), bi, q);
@@ -209,7 +211,9 @@ __device__ __forceinline__ void rnea_level(const TP& tp, SV a0, const Col& q, co
   enum { X_ = 0, V_ = 12, A_ = 18, F_ = 24 };
   FST_UNROLL
   for (int l = 0; l < tp.depth(); ++l) {
-    for (int k = tp.level_begin(l) + w; k < tp.level_begin(l + 1); k += W) {
+    FST_UNROLL
+    for (int k = tp.level_begin(l); k < tp.level_begin(l + 1); ++k) {
+      if ((k - tp.level_begin(l)) % W != w) continue;
       const int i = tp.level_body(k);
       const BodyC& c = tp.C(i);
       const BodyI bi = tp.I(i);
@@ -234,7 +238,9 @@ __device__ __forceinline__ void rnea_level(const TP& tp, SV a0, const Col& q, co
   }
   FST_UNROLL
   for (int l = tp.depth() - 1; l >= 0; --l) {
-    for (int k = tp.level_begin(l) + w; k < tp.level_begin(l + 1); k += W) {
+    FST_UNROLL
+    for (int k = tp.level_begin(l); k < tp.level_begin(l + 1); ++k) {
+      if ((k - tp.level_begin(l)) % W != w) continue;
       const int i = tp.level_body(k);
       const BodyI bi = tp.I(i);
       SV F = S.sv(i, F_);
@@ -254,7 +260,9 @@ __device__ __forceinline__ void crba_level(const TP& tp, const Col& q, int nv, c
   enum { X_ = 0, IC_ = 12, CT_ = 22 };
   FST_UNROLL
   for (int l = tp.depth() - 1; l >= 0; --l) {
-    for (int k = tp.level_begin(l) + w; k < tp.level_begin(l + 1); k += W) {
+    FST_UNROLL
+    for (int k = tp.level_begin(l); k < tp.level_begin(l + 1); ++k) {
+      if ((k - tp.level_begin(l)) % W != w) continue;
       const int i = tp.level_body(k);
       const BodyI bi = tp.I(i);
       const Xf X = joint_X(tp.C(i), bi, q);
@@ -336,7 +344,9 @@ __device__ __forceinline__ void aba_level(const TP& tp, SV a0, const Col& q, con
   // 1. root to leaf: velocities, bias accelerations, rigid inertias
   FST_UNROLL
   for (int l = 0; l < tp.depth(); ++l) {
-    for (int k = tp.level_begin(l) + w; k < tp.level_begin(l + 1); k += W) {
+    FST_UNROLL
+    for (int k = tp.level_begin(l); k < tp.level_begin(l + 1); ++k) {
+      if ((k - tp.level_begin(l)) % W != w) continue;
       const int i = tp.level_body(k);
       const BodyC& c = tp.C(i);
       const BodyI bi = tp.I(i);
@@ -363,7 +373,9 @@ __device__ __forceinline__ void aba_level(const TP& tp, SV a0, const Col& q, con
   //    X^T p^a for its parent in its own IA/PA slots
   FST_UNROLL
   for (int l = tp.depth() - 1; l >= 0; --l) {
-    for (int k = tp.level_begin(l) + w; k < tp.level_begin(l + 1); k += W) {
+    FST_UNROLL
+    for (int k = tp.level_begin(l); k < tp.level_begin(l + 1); ++k) {
+      if ((k - tp.level_begin(l)) % W != w) continue;
       const int i = tp.level_body(k);
       const BodyI bi = tp.I(i);
       Sym6 IA = S.sym(i, IA_);
@@ -403,7 +415,9 @@ __device__ __forceinline__ void aba_level(const TP& tp, SV a0, const Col& q, con
   // 3. root to leaf: accelerations
   FST_UNROLL
   for (int l = 0; l < tp.depth(); ++l) {
-    for (int k = tp.level_begin(l) + w; k < tp.level_begin(l + 1); k += W) {
+    FST_UNROLL
+    for (int k = tp.level_begin(l); k < tp.level_begin(l + 1); ++k) {
+      if ((k - tp.level_begin(l)) % W != w) continue;
       const int i = tp.level_body(k);
       const BodyI bi = tp.I(i);
       const SV ap = bi.parent < 0 ? a0 : S.sv(bi.parent, VA_);

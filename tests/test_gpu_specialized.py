@@ -94,3 +94,28 @@ def test_specialized_theta_override(torch_cuda):
     assert env_err(from_soa(api.rnea(m, q, qd, qdd, theta=tht)),
                    rbd.rnea(tree, s["q"], s["qd"], s["qdd"], theta=th)).max() <= TOL["tau"]
     assert env_err(from_soa(api.crba(m, q, theta=tht)), rbd.crba(tree, s["q"], theta=th)).max() <= TOL["M"]
+
+
+@pytest.mark.parametrize("name", ["quadruped11", "humanoid29", "general8"])
+@pytest.mark.parametrize("level_kinds", [("aba",), ("aba", "crba", "rnea", "jacobian")])
+def test_specialized_eval_with_level_parallel_roles(torch_cuda, name, level_kinds):
+    """The specialised fused kernel runs roles whose operator is tuned
+    level-parallel that way (32 environments per block, warps splitting
+    levels) and the others one environment per thread, in one launch."""
+    torch = torch_cuda
+    from paper_2605_31481_gb300 import api
+    tree = TREES[name]()
+    B = 1000
+    s = w.random_state(tree, B, seed=14)
+    m = api.Model(tree, specialize=["eval"])
+    m.set_launch(list(level_kinds), 128, "level")
+    m.set_launch(["eval"], 64, "specialized")
+    q, qd, qdd, tau = (to_soa_cuda(s[k], torch) for k in ("q", "qd", "qdd", "tau"))
+    ee = list(tree.ee)
+    ev = api.eval(m, q, qd, qdd, tau, fk=True, links=ee, rnea=True, crba=True, aba=True)
+    torch.cuda.synchronize()
+    ref = {"poses": oracle_poses(tree, s["q"]), "J": np.stack([rbd.jacobian(tree, s["q"], e) for e in ee], 1),
+           "tau": rbd.rnea(tree, s["q"], s["qd"], s["qdd"]), "M": rbd.crba(tree, s["q"]),
+           "qdd": rbd.aba(tree, s["q"], s["qd"], s["tau"])}
+    for k, tol in TOL.items():
+        assert env_err(from_soa(ev[k]), ref[k]).max() <= tol, k
