@@ -163,6 +163,10 @@ FST_API fst_status fst_model_specialize(fst_model* model, uint32_t kinds);
 #define FST_VARIANT_GENERIC 1
 #define FST_VARIANT_SPECIALIZED 2
 #define FST_VARIANT_LEVEL 3
+/* eval only: the specialised fused kernel, with each role (ABA, CRBA, RNEA,
+ * FK/Jacobian) level-parallel where that operator's own kind is set to LEVEL
+ * and one environment per thread otherwise. */
+#define FST_VARIANT_MIXED 4
 FST_API fst_status fst_model_set_launch(fst_model* model, uint32_t kinds, int32_t block, int32_t variant);
 
 /* Bit mask of the specialised kinds currently in use for this model. */

@@ -99,7 +99,7 @@ class Model:
         """Launch configuration (fst_model_set_launch) of the given kernel
         kinds (names from _ffi.SPEC_KINDS, None = all): threads per block
         (0 = built-in heuristic) and variant ("auto", "generic",
-        "specialized", "level")."""
+        "specialized", "level", "mixed" (eval only))."""
         mask = 0 if kinds is None else sum(1 << _ffi.SPEC_KINDS.index(k) for k in kinds)
         check(_ffi.lib().fst_model_set_launch(self._h, mask, int(block), _ffi.VARIANTS[variant]))
 

@@ -151,6 +151,8 @@ def tune(model, B, kinds=FORWARD_KINDS + ("eval",), links=None, use_cache=True, 
         fn = _op(model, kind, buf)
         cands = {}
         variants = ["generic"] + (["specialized"] if kind in spec else []) + (["level"] if kind in LEVEL_KINDS else [])
+        if kind == "eval" and kind in spec:
+            variants.append("mixed")       # specialised fused kernel, roles mapped as their operators
         for variant in variants:
             for block in CANDIDATE_BLOCKS:
                 model.set_launch([kind], block, variant)

@@ -60,7 +60,8 @@ fst_status need(const char* fn, const void* p, const char* name) {
 // Whether a call of this kind runs the specialised kernel: it must exist,
 // and the kind must not be pinned to another variant.
 bool use_jit(const fst_model* m, int kind) {
-  return (m->variant[kind] == FST_VARIANT_AUTO || m->variant[kind] == FST_VARIANT_SPECIALIZED) && jit_has(m, kind);
+  const int v = m->variant[kind];
+  return (v == FST_VARIANT_AUTO || v == FST_VARIANT_SPECIALIZED || v == FST_VARIANT_MIXED) && jit_has(m, kind);
 }
 
 // Whether a call of this kind runs the level-parallel kernel: selected, and
@@ -168,13 +169,15 @@ fst_status fst_model_set_launch(fst_model* m, uint32_t kinds, int32_t block, int
   if (!m) return set_error(FST_ERR_INVALID_ARG, "fst_model_set_launch: null model");
   if (block != 0 && block != 32 && block != 64 && block != 128 && block != 256)
     return set_error(FST_ERR_INVALID_ARG, "fst_model_set_launch: block must be 0, 32, 64, 128 or 256");
-  if (variant < FST_VARIANT_AUTO || variant > FST_VARIANT_LEVEL)
+  if (variant < FST_VARIANT_AUTO || variant > FST_VARIANT_MIXED)
     return set_error(FST_ERR_INVALID_ARG, "fst_model_set_launch: unknown variant");
   // "all kinds" with the level variant means every kind that has one
   if (kinds == 0) kinds = variant == FST_VARIANT_LEVEL ? (1u << (JK_EVAL + 1)) - 1u : FST_SPEC_ALL;
   if (kinds & ~(uint32_t)FST_SPEC_ALL) return set_error(FST_ERR_INVALID_ARG, "fst_model_set_launch: unknown kind bits");
   for (int k = 0; k < JK_COUNT; ++k) {
-    if (((kinds >> k) & 1u) && variant == FST_VARIANT_SPECIALIZED && !jit_has(m, k))
+    if (((kinds >> k) & 1u) && variant == FST_VARIANT_MIXED && k != JK_EVAL)
+      return set_error(FST_ERR_INVALID_ARG, "fst_model_set_launch: the mixed variant is for eval only");
+    if (((kinds >> k) & 1u) && (variant == FST_VARIANT_SPECIALIZED || variant == FST_VARIANT_MIXED) && !jit_has(m, k))
       return set_error(FST_ERR_INVALID_ARG, "fst_model_set_launch: a selected kind is not specialised yet");
     if (((kinds >> k) & 1u) && variant == FST_VARIANT_LEVEL && k > JK_EVAL)
       return set_error(FST_ERR_INVALID_ARG, "fst_model_set_launch: the level-parallel variant exists for FK, "
@@ -363,7 +366,8 @@ fst_status fst_eval(const fst_model* m, int64_t B, const fst_eval_io* io, const 
                                                                       : LEVEL_JAC;
       size_t need;
       int64_t blocks;
-      if (use_level(m, kind, lk)) {
+      if (m->variant[JK_EVAL] == FST_VARIANT_MIXED && m->variant[kind] == FST_VARIANT_LEVEL &&
+          level_smem_needed(mv, lk) <= kLevelSmemLimit) {
         a.level_mask |= 1 << role;
         need = level_smem_needed(mv, lk) - (size_t)m->n * (sizeof(BodyC) + sizeof(BodyI)) -
                (sizeof(TopoLists) + 15) / 16 * 16;  // no model copy in shared memory here

@@ -109,7 +109,7 @@ def test_specialized_eval_with_level_parallel_roles(torch_cuda, name, level_kind
     s = w.random_state(tree, B, seed=14)
     m = api.Model(tree, specialize=["eval"])
     m.set_launch(list(level_kinds), 128, "level")
-    m.set_launch(["eval"], 64, "specialized")
+    m.set_launch(["eval"], 64, "mixed")
     q, qd, qdd, tau = (to_soa_cuda(s[k], torch) for k in ("q", "qd", "qdd", "tau"))
     ee = list(tree.ee)
     ev = api.eval(m, q, qd, qdd, tau, fk=True, links=ee, rnea=True, crba=True, aba=True)
