@@ -125,7 +125,8 @@ FST_API fst_status fst_model_theta(const fst_model* model, float* theta);
 #define FST_SPEC_RNEA_VJP (1u << 7)
 #define FST_SPEC_ABA_VJP (1u << 8)
 #define FST_SPEC_LOSS_GRAD (1u << 9)
-#define FST_SPEC_ALL 0x3ffu
+#define FST_SPEC_EVAL_MIXED (1u << 10) /* the fused kernel of FST_VARIANT_MIXED */
+#define FST_SPEC_ALL 0x7ffu
 
 /* Compiles kernels specialised for this model's tree (run-time compilation
  * with NVRTC for the current GPU). The paper folds the fixed joint offsets

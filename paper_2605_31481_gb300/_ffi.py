@@ -19,7 +19,8 @@ STATUS_NAMES = {
 MAX_BODIES = 64
 MAX_LINKS = 16
 VARIANTS = {"auto": 0, "generic": 1, "specialized": 2, "level": 3, "mixed": 4}
-SPEC_KINDS = ("fk", "jacobian", "rnea", "crba", "aba", "eval", "fk_vjp", "rnea_vjp", "aba_vjp", "loss_grad")
+SPEC_KINDS = ("fk", "jacobian", "rnea", "crba", "aba", "eval", "fk_vjp", "rnea_vjp", "aba_vjp", "loss_grad",
+              "eval_mixed")
 
 c_int32, c_int64, c_double, c_void_p = ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_void_p
 c_float_p = ctypes.POINTER(ctypes.c_float)

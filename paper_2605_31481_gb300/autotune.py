@@ -151,7 +151,7 @@ def tune(model, B, kinds=FORWARD_KINDS + ("eval",), links=None, use_cache=True, 
         fn = _op(model, kind, buf)
         cands = {}
         variants = ["generic"] + (["specialized"] if kind in spec else []) + (["level"] if kind in LEVEL_KINDS else [])
-        if kind == "eval" and kind in spec:
+        if kind == "eval" and "eval_mixed" in spec:
             variants.append("mixed")       # specialised fused kernel, roles mapped as their operators
         for variant in variants:
             for block in CANDIDATE_BLOCKS:
@@ -231,4 +231,5 @@ class StepPlan:
 
     def describe(self):
         return {"mode": self.mode, "us": {k: round(v, 3) for k, v in self.times.items()},
-                "kinds": {k: f"{v['variant']}/{v['block']}" for k, v in self.tuned.items()}}
+                "kinds": {k: f"{v['variant']}/{v['block']}" for k, v in self.tuned.items()},
+                "eval_candidates_us": self.tuned["eval"]["candidates"]}

@@ -61,7 +61,7 @@ fst_status need(const char* fn, const void* p, const char* name) {
 // and the kind must not be pinned to another variant.
 bool use_jit(const fst_model* m, int kind) {
   const int v = m->variant[kind];
-  return (v == FST_VARIANT_AUTO || v == FST_VARIANT_SPECIALIZED || v == FST_VARIANT_MIXED) && jit_has(m, kind);
+  return (v == FST_VARIANT_AUTO || v == FST_VARIANT_SPECIALIZED) && jit_has(m, kind);
 }
 
 // Whether a call of this kind runs the level-parallel kernel: selected, and
@@ -177,7 +177,9 @@ fst_status fst_model_set_launch(fst_model* m, uint32_t kinds, int32_t block, int
   for (int k = 0; k < JK_COUNT; ++k) {
     if (((kinds >> k) & 1u) && variant == FST_VARIANT_MIXED && k != JK_EVAL)
       return set_error(FST_ERR_INVALID_ARG, "fst_model_set_launch: the mixed variant is for eval only");
-    if (((kinds >> k) & 1u) && (variant == FST_VARIANT_SPECIALIZED || variant == FST_VARIANT_MIXED) && !jit_has(m, k))
+    if (((kinds >> k) & 1u) && variant == FST_VARIANT_SPECIALIZED && !jit_has(m, k))
+      return set_error(FST_ERR_INVALID_ARG, "fst_model_set_launch: a selected kind is not specialised yet");
+    if (((kinds >> k) & 1u) && variant == FST_VARIANT_MIXED && !jit_has(m, JK_EVAL_MIXED))
       return set_error(FST_ERR_INVALID_ARG, "fst_model_set_launch: a selected kind is not specialised yet");
     if (((kinds >> k) & 1u) && variant == FST_VARIANT_LEVEL && k > JK_EVAL)
       return set_error(FST_ERR_INVALID_ARG, "fst_model_set_launch: the level-parallel variant exists for FK, "
@@ -352,7 +354,7 @@ fst_status fst_eval(const fst_model* m, int64_t B, const fst_eval_io* io, const 
   const ModelView mv = view_of(m, theta);
   if (use_level(m, JK_EVAL, LEVEL_EVAL))
     return finish(fn, launch_eval_level(mv, B, a, level_block(m, JK_EVAL), (cudaStream_t)stream));
-  if (use_jit(m, JK_EVAL)) {
+  if (m->variant[JK_EVAL] == FST_VARIANT_MIXED && jit_has(m, JK_EVAL_MIXED)) {
     // roles whose own operator is tuned level-parallel run that way here too
     const int T = block_of(m, JK_EVAL, B);
     const int rows = m->nq + 2 * m->nv;
@@ -380,9 +382,12 @@ fst_status fst_eval(const fst_model* m, int64_t B, const fst_eval_io* io, const 
       if (blocks > gx) gx = blocks;
     }
     void* argv[] = {(void*)&mv, (void*)&B, (void*)&a};
-    return finish(fn, jit_launch(m, JK_EVAL, dim3((unsigned)gx, (unsigned)a.n_roles), T, sh, (cudaStream_t)stream,
-                                 argv));
+    return finish(fn, jit_launch(m, JK_EVAL_MIXED, dim3((unsigned)gx, (unsigned)a.n_roles), T, sh,
+                                 (cudaStream_t)stream, argv));
   }
+  if (use_jit(m, JK_EVAL))
+    return finish(fn, jit_go(m, JK_EVAL, B, m->nq + 2 * m->nv, 0, (unsigned)a.n_roles, (cudaStream_t)stream, nullptr,
+                             mv, B, a));
   return finish(fn, launch_eval(mv, B, a, launch_of(m, JK_EVAL, B, stream)));
 }
 

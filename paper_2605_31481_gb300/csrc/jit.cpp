@@ -40,10 +40,10 @@ namespace {
 
 const char* const kKindName[JK_COUNT] = {"fst_jit_fk",      "fst_jit_jacobian", "fst_jit_rnea",     "fst_jit_crba",
                                          "fst_jit_aba",     "fst_jit_eval",     "fst_jit_fk_vjp",   "fst_jit_rnea_vjp",
-                                         "fst_jit_aba_vjp", "fst_jit_loss_grad"};
+                                         "fst_jit_aba_vjp", "fst_jit_loss_grad", "fst_jit_eval_mixed"};
 const char* const kKindMacro[JK_COUNT] = {"FST_JIT_FK",      "FST_JIT_JACOBIAN", "FST_JIT_RNEA",     "FST_JIT_CRBA",
                                           "FST_JIT_ABA",     "FST_JIT_EVAL",     "FST_JIT_FK_VJP",   "FST_JIT_RNEA_VJP",
-                                          "FST_JIT_ABA_VJP", "FST_JIT_LOSS_GRAD"};
+                                          "FST_JIT_ABA_VJP", "FST_JIT_LOSS_GRAD", "FST_JIT_EVAL_MIXED"};
 
 // ---- NVRTC, opened at run time ---------------------------------------------
 struct Nvrtc {
@@ -265,6 +265,7 @@ struct JitState {
   CUmodule mod[JK_COUNT] = {};
   CUfunction fn[JK_COUNT] = {};
   int smem_limit[JK_COUNT] = {};
+  int carveout_set[JK_COUNT] = {};
 };
 
 fst_status jit_specialize(fst_model* m, unsigned mask) {
@@ -330,6 +331,11 @@ cudaError_t jit_launch(const fst_model* m, int kind, dim3 grid, int block, size_
     if (D.set_attr(J->fn[kind], CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, (int)smem) != CUDA_SUCCESS)
       return cudaErrorInvalidValue;
     J->smem_limit[kind] = (int)smem;
+  }
+  if (!J->carveout_set[kind]) {
+    if (const char* env = std::getenv("FST_SMEM_CARVEOUT"))
+      D.set_attr(J->fn[kind], CU_FUNC_ATTRIBUTE_PREFERRED_SHARED_MEMORY_CARVEOUT, std::atoi(env));
+    J->carveout_set[kind] = 1;
   }
   const CUresult r = D.launch(J->fn[kind], grid.x, grid.y, grid.z, (unsigned)block, 1, 1, (unsigned)smem,
                               (CUstream)s, args, nullptr);

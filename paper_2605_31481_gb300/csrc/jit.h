@@ -20,6 +20,7 @@ enum JitKind {
   JK_RNEA_VJP,
   JK_ABA_VJP,
   JK_LOSS_GRAD,
+  JK_EVAL_MIXED,
   JK_COUNT
 };
 

@@ -118,6 +118,19 @@ __device__ __forceinline__ void stage_block_rows(float* tile, const float* __res
   }
 }
 
+// Loop over the bodies of level l that belong to this warp (every W-th one,
+// starting at the warp's index). With a run-time topology this is a strided
+// loop; with a compile-time one it is unrolled over the whole level with a
+// cheap round-robin ownership test, so each body's constants fold into its
+// code and each warp executes only its own bodies.
+#ifdef FST_FIXED_TOPOLOGY
+#define FST_FOR_MY_BODIES(tp, l, k)                                                          \
+  _Pragma("unroll") for (int k = (tp).level_begin(l), own_ = 0; k < (tp).level_begin((l) + 1); \
+                         ++k, own_ = (own_ + 1 == W ? 0 : own_ + 1)) if (own_ == w)
+#else
+#define FST_FOR_MY_BODIES(tp, l, k) for (int k = (tp).level_begin(l) + w; k < (tp).level_begin((l) + 1); k += W)
+#endif
+
 __device__ __forceinline__ int warp_id() { return threadIdx.x >> 5; }
 __device__ __forceinline__ int n_warps() { return blockDim.x >> 5; }
 
@@ -128,9 +141,7 @@ __device__ __forceinline__ void fk_level(const TP& tp, const Col& q, const LaneS
   const int W = n_warps(), w = warp_id();
   FST_UNROLL
   for (int l = 0; l < tp.depth(); ++l) {
-    FST_UNROLL
-    for (int k = tp.level_begin(l); k < tp.level_begin(l + 1); ++k) {
-      if ((k - tp.level_begin(l)) % W != w) continue;
+    FST_FOR_MY_BODIES(tp, l, k) {
       const int i = tp.level_body(k);
       const BodyI bi = tp.I(i);
       const Xf X = joint_X(tp.C(i), bi, q);
@@ -211,9 +222,7 @@ __device__ __forceinline__ void rnea_level(const TP& tp, SV a0, const Col& q, co
   enum { X_ = 0, V_ = 12, A_ = 18, F_ = 24 };
   FST_UNROLL
   for (int l = 0; l < tp.depth(); ++l) {
-    FST_UNROLL
-    for (int k = tp.level_begin(l); k < tp.level_begin(l + 1); ++k) {
-      if ((k - tp.level_begin(l)) % W != w) continue;
+    FST_FOR_MY_BODIES(tp, l, k) {
       const int i = tp.level_body(k);
       const BodyC& c = tp.C(i);
       const BodyI bi = tp.I(i);
@@ -238,9 +247,7 @@ __device__ __forceinline__ void rnea_level(const TP& tp, SV a0, const Col& q, co
   }
   FST_UNROLL
   for (int l = tp.depth() - 1; l >= 0; --l) {
-    FST_UNROLL
-    for (int k = tp.level_begin(l); k < tp.level_begin(l + 1); ++k) {
-      if ((k - tp.level_begin(l)) % W != w) continue;
+    FST_FOR_MY_BODIES(tp, l, k) {
       const int i = tp.level_body(k);
       const BodyI bi = tp.I(i);
       SV F = S.sv(i, F_);
@@ -260,9 +267,7 @@ __device__ __forceinline__ void crba_level(const TP& tp, const Col& q, int nv, c
   enum { X_ = 0, IC_ = 12, CT_ = 22 };
   FST_UNROLL
   for (int l = tp.depth() - 1; l >= 0; --l) {
-    FST_UNROLL
-    for (int k = tp.level_begin(l); k < tp.level_begin(l + 1); ++k) {
-      if ((k - tp.level_begin(l)) % W != w) continue;
+    FST_FOR_MY_BODIES(tp, l, k) {
       const int i = tp.level_body(k);
       const BodyI bi = tp.I(i);
       const Xf X = joint_X(tp.C(i), bi, q);
@@ -344,9 +349,7 @@ __device__ __forceinline__ void aba_level(const TP& tp, SV a0, const Col& q, con
   // 1. root to leaf: velocities, bias accelerations, rigid inertias
   FST_UNROLL
   for (int l = 0; l < tp.depth(); ++l) {
-    FST_UNROLL
-    for (int k = tp.level_begin(l); k < tp.level_begin(l + 1); ++k) {
-      if ((k - tp.level_begin(l)) % W != w) continue;
+    FST_FOR_MY_BODIES(tp, l, k) {
       const int i = tp.level_body(k);
       const BodyC& c = tp.C(i);
       const BodyI bi = tp.I(i);
@@ -373,9 +376,7 @@ __device__ __forceinline__ void aba_level(const TP& tp, SV a0, const Col& q, con
   //    X^T p^a for its parent in its own IA/PA slots
   FST_UNROLL
   for (int l = tp.depth() - 1; l >= 0; --l) {
-    FST_UNROLL
-    for (int k = tp.level_begin(l); k < tp.level_begin(l + 1); ++k) {
-      if ((k - tp.level_begin(l)) % W != w) continue;
+    FST_FOR_MY_BODIES(tp, l, k) {
       const int i = tp.level_body(k);
       const BodyI bi = tp.I(i);
       Sym6 IA = S.sym(i, IA_);
@@ -415,9 +416,7 @@ __device__ __forceinline__ void aba_level(const TP& tp, SV a0, const Col& q, con
   // 3. root to leaf: accelerations
   FST_UNROLL
   for (int l = 0; l < tp.depth(); ++l) {
-    FST_UNROLL
-    for (int k = tp.level_begin(l); k < tp.level_begin(l + 1); ++k) {
-      if ((k - tp.level_begin(l)) % W != w) continue;
+    FST_FOR_MY_BODIES(tp, l, k) {
       const int i = tp.level_body(k);
       const BodyI bi = tp.I(i);
       const SV ap = bi.parent < 0 ? a0 : S.sv(bi.parent, VA_);

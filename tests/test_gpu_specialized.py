@@ -107,7 +107,7 @@ def test_specialized_eval_with_level_parallel_roles(torch_cuda, name, level_kind
     tree = TREES[name]()
     B = 1000
     s = w.random_state(tree, B, seed=14)
-    m = api.Model(tree, specialize=["eval"])
+    m = api.Model(tree, specialize=["eval_mixed"])
     m.set_launch(list(level_kinds), 128, "level")
     m.set_launch(["eval"], 64, "mixed")
     q, qd, qdd, tau = (to_soa_cuda(s[k], torch) for k in ("q", "qd", "qdd", "tau"))
