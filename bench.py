@@ -279,8 +279,10 @@ def run_fst(args):
     bound = "alu" if fl / (p_alu * 1e12) > by / (pk["hbm_gbs"] * 1e9) else "hbm"
     desc = plan.describe()
     kname = {"fused": f"fused eval kernel ({desc['kinds']['eval']})",
+             "hybrid": f"ABA kernel ({desc['kinds']['aba']}) on a parallel graph branch beside the fused kernel of "
+                       f"the other four ({desc['kinds']['eval']}), carveout {plan.carveout}",
              "concurrent": "5 per-operator kernels on parallel graph branches (" +
-                           ", ".join(f"{k} {desc['kinds'][k]}" for k in OPS) + ")",
+                           ", ".join(f"{k} {desc['kinds'][k]}" for k in OPS) + f"), carveout {plan.carveout}",
              "sequential": "5 per-operator kernels in sequence"}[plan.mode]
     common = {"kernel": kname, "traffic": args.traffic,
               "algorithmic_bytes_per_launch": by * B, "algorithmic_flops_per_launch": fl * B,
@@ -320,7 +322,7 @@ def run_fst(args):
             "roofline": roof,
             "e2e": {"value": round(e2e_value, 1), "unit": "env-evals/s", "h2d_bytes_per_step": e2e["h2d"],
                     "d2h_bytes_per_step": e2e["d2h"]},
-            "gpu_launches": K * (1 if plan.fused else len(OPS)),
+            "gpu_launches": K * {"fused": 1, "hybrid": 2}.get(plan.mode, len(OPS)),
             "kernels": kernels,
             "plan": desc,
             "clocks": clocks,

@@ -170,6 +170,14 @@ FST_API fst_status fst_model_specialize(fst_model* model, uint32_t kinds);
 #define FST_VARIANT_MIXED 4
 FST_API fst_status fst_model_set_launch(fst_model* model, uint32_t kinds, int32_t block, int32_t variant);
 
+/* Shared-memory carveout (percent of the unified L1/shared storage given to
+ * shared memory) requested for every kernel launched from now on; -1 (the
+ * default) lets each kernel ask for what suits it alone. Kernels only share
+ * an SM when they ask for the same carveout, so overlapping different
+ * kernels on parallel streams (the step plan's concurrent modes) wants one
+ * common value. Process-wide. */
+FST_API fst_status fst_set_smem_carveout(int32_t percent);
+
 /* Bit mask of the specialised kinds currently in use for this model. */
 FST_API fst_status fst_model_specialized(const fst_model* model, uint32_t* kinds);
 

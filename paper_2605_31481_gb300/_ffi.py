@@ -70,6 +70,7 @@ _SIGS = {
     "fst_model_specialize": (c_int32, [c_void_p, ctypes.c_uint32]),
     "fst_model_specialized": (c_int32, [c_void_p, ctypes.POINTER(ctypes.c_uint32)]),
     "fst_model_set_launch": (c_int32, [c_void_p, ctypes.c_uint32, c_int32, c_int32]),
+    "fst_set_smem_carveout": (c_int32, [c_int32]),
     "fst_model_theta": (c_int32, [c_void_p, ctypes.POINTER(ctypes.c_float)]),
     "fst_fk": (c_int32, [c_void_p, c_int64, c_void_p, c_void_p, c_void_p]),
     "fst_jacobian": (c_int32, [c_void_p, c_int64, c_void_p, ctypes.POINTER(c_int32), c_int32, c_void_p, c_void_p]),

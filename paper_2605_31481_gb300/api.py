@@ -128,6 +128,11 @@ class Model:
         return f"Model({self.name}: n_b={self.n_bodies}, nq={self.nq}, nv={self.nv}, depth={self.depth})"
 
 
+def set_smem_carveout(percent: int):
+    """fst_set_smem_carveout: -1 = per kernel, else one percentage for all."""
+    check(_ffi.lib().fst_set_smem_carveout(int(percent)))
+
+
 def _check_in(x, rows, name, model):
     if not isinstance(x, torch.Tensor):
         raise TypeError(f"{name} must be a torch.Tensor")

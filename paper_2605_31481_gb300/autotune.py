@@ -176,29 +176,39 @@ class StepPlan:
     configuration):
       fused       one launch (fst_eval), operators side by side in one kernel
                   with one variant for all of them;
-      concurrent  each operator's own kernel (each at its best variant) on its
-                  own stream, forked from and joined back into the caller's
-                  stream, so they overlap on the GPU; captured into a CUDA
-                  graph these become parallel branches;
-      sequential  the per-operator kernels one after another."""
+      hybrid      ABA's own kernel (at its best variant) on a side stream,
+                  overlapping one fused launch of the four other operators;
+      concurrent  each operator's own kernel on its own stream;
+      sequential  the per-operator kernels one after another.
+    Side streams are forked from and joined back into the caller's stream,
+    so in a captured CUDA graph they become parallel branches. Kernels only
+    share an SM when they request the same shared-memory carveout, so the
+    overlapping modes are also tried with one common carveout (100 %); the
+    chosen carveout is applied with fst_set_smem_carveout."""
 
-    MODES = ("fused", "concurrent", "sequential")
+    MODES = ("fused", "hybrid", "concurrent", "sequential")
 
     def __init__(self, model, B, links=None, use_cache=True, verbose=False, modes=MODES):
         self.model = model
         self.links = list(links if links is not None else model.ee)
+        api.set_smem_carveout(-1)
         self.tuned = tune(model, B, FORWARD_KINDS + ("eval",), links=self.links, use_cache=use_cache,
                           verbose=verbose)
         self.streams = [torch.cuda.Stream(device=model.device) for _ in FORWARD_KINDS]
         buf = Buffers(model, B, self.links)
         times = {}
-        for mode in modes:
-            self.mode = mode
-            times[mode] = graph_time_us(lambda: self(buf.q, buf.qd, buf.qdd, buf.tau, buf.out))
+        for carveout in (-1, 100):
+            api.set_smem_carveout(carveout)
+            for mode in modes:
+                if carveout >= 0 and mode in ("fused", "sequential"):
+                    continue
+                self.mode = mode
+                times[(mode, carveout)] = graph_time_us(lambda: self(buf.q, buf.qd, buf.qdd, buf.tau, buf.out))
         self.times = times
-        self.mode = min(times, key=times.get)
+        self.mode, self.carveout = min(times, key=times.get)
+        api.set_smem_carveout(self.carveout)
         self.fused = self.mode == "fused"
-        self.expected_us = times[self.mode]
+        self.expected_us = times[(self.mode, self.carveout)]
 
     def _ops(self, q, qd, qdd, tau, out):
         m = self.model
@@ -208,6 +218,15 @@ class StepPlan:
                 lambda: api.crba(m, q, out=out["M"]),
                 lambda: api.aba(m, q, qd, tau, out=out["qdd"]))
 
+    def _fork(self, fns):
+        cur = torch.cuda.current_stream(self.model.device)
+        for st, fn in zip(self.streams, fns):
+            st.wait_stream(cur)
+            with torch.cuda.stream(st):
+                fn()
+        for st in self.streams[:len(fns)]:
+            cur.wait_stream(st)
+
     def __call__(self, q, qd, qdd, tau, out):
         m = self.model
         if self.mode == "fused":
@@ -216,20 +235,17 @@ class StepPlan:
         if self.mode == "sequential":
             for op in ops:
                 op()
-            return out
-        cur = torch.cuda.current_stream(m.device)
-        # longest first, so its blocks are dispatched first
-        order = sorted(range(len(ops)), key=lambda k: -self.tuned[FORWARD_KINDS[k]]["us"])
-        for k in order:
-            st = self.streams[k]
-            st.wait_stream(cur)
-            with torch.cuda.stream(st):
-                ops[k]()
-        for st in self.streams:
-            cur.wait_stream(st)
+        elif self.mode == "hybrid":
+            self._fork([ops[4], lambda: api.eval(m, q, qd, qdd, tau, fk=True, links=self.links, rnea=True, crba=True,
+                                                 aba=False, out=out)])
+        else:
+            # longest first, so its blocks are dispatched first
+            order = sorted(range(len(ops)), key=lambda k: -self.tuned[FORWARD_KINDS[k]]["us"])
+            self._fork([ops[k] for k in order])
         return out
 
     def describe(self):
-        return {"mode": self.mode, "us": {k: round(v, 3) for k, v in self.times.items()},
+        return {"mode": self.mode, "carveout": self.carveout,
+                "us": {f"{k[0]}{'' if k[1] < 0 else f'@{k[1]}%'}": round(v, 3) for k, v in self.times.items()},
                 "kinds": {k: f"{v['variant']}/{v['block']}" for k, v in self.tuned.items()},
                 "eval_candidates_us": self.tuned["eval"]["candidates"]}

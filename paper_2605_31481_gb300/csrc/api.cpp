@@ -1,6 +1,7 @@
 // C ABI of libfst.so: argument validation, device checks, launches.
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstring>
 #include <new>
 #include <sstream>
@@ -15,7 +16,12 @@ namespace fst {
 
 namespace {
 thread_local std::string g_last_error;
-}
+std::atomic<int> g_carveout{-1};
+std::atomic<int> g_carveout_gen{0};
+}  // namespace
+
+int carveout_override() { return g_carveout.load(); }
+int carveout_generation() { return g_carveout_gen.load(); }
 
 fst_status set_error(fst_status s, const std::string& msg) {
   g_last_error = msg;
@@ -155,6 +161,14 @@ fst_status fst_model_destroy(fst_model* m) {
   if (m->di) cudaFree(m->di);
   if (m->dt) cudaFree(m->dt);
   delete m;
+  return FST_OK;
+}
+
+fst_status fst_set_smem_carveout(int32_t percent) {
+  if (percent < -1 || percent > 100)
+    return set_error(FST_ERR_INVALID_ARG, "fst_set_smem_carveout: percent must be in [-1, 100]");
+  g_carveout.store(percent);
+  g_carveout_gen.fetch_add(1);
   return FST_OK;
 }
 

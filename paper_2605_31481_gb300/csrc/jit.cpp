@@ -28,6 +28,7 @@
 
 #include "fst_internal.h"
 #include "jit.h"
+#include "launch.h"
 
 namespace fst {
 
@@ -332,10 +333,13 @@ cudaError_t jit_launch(const fst_model* m, int kind, dim3 grid, int block, size_
       return cudaErrorInvalidValue;
     J->smem_limit[kind] = (int)smem;
   }
-  if (!J->carveout_set[kind]) {
-    if (const char* env = std::getenv("FST_SMEM_CARVEOUT"))
-      D.set_attr(J->fn[kind], CU_FUNC_ATTRIBUTE_PREFERRED_SHARED_MEMORY_CARVEOUT, std::atoi(env));
-    J->carveout_set[kind] = 1;
+  const int gen = carveout_generation() + 1;
+  if (J->carveout_set[kind] != gen) {
+    int pct = -1;
+    if (const char* env = std::getenv("FST_SMEM_CARVEOUT")) pct = std::atoi(env);
+    if (carveout_override() >= 0) pct = carveout_override();
+    if (pct >= 0) D.set_attr(J->fn[kind], CU_FUNC_ATTRIBUTE_PREFERRED_SHARED_MEMORY_CARVEOUT, pct > 100 ? 100 : pct);
+    J->carveout_set[kind] = gen;
   }
   const CUresult r = D.launch(J->fn[kind], grid.x, grid.y, grid.z, (unsigned)block, 1, 1, (unsigned)smem,
                               (CUstream)s, args, nullptr);

@@ -48,19 +48,32 @@ inline unsigned grid_for(int64_t B, int block) { return (unsigned)((B + block - 
 //  * the shared-memory carveout: just enough shared memory for ~4 resident
 //    blocks, leaving the rest of the 256 KB unified L1 for the per-thread
 //    sweep state (local memory). FST_SMEM_CARVEOUT=<percent> overrides it.
+// Library-wide carveout override (fst_set_smem_carveout): -1 = per kernel,
+// else the percentage for every kernel; `generation` changes on every set so
+// kernels pick the new value up at their next launch.
+int carveout_override();
+int carveout_generation();
+
 template <typename K>
 inline void prepare(K* kernel, size_t smem) {
+  struct Done {
+    size_t smem;
+    int gen;
+  };
   static std::mutex mu;
-  static std::unordered_map<const void*, size_t> done;
+  static std::unordered_map<const void*, Done> done;
+  const int gen = carveout_generation();
   std::lock_guard<std::mutex> lock(mu);
   auto it = done.find((const void*)kernel);
-  if (it != done.end() && it->second >= smem) return;
+  if (it != done.end() && it->second.smem >= smem && it->second.gen == gen) return;
   if (smem > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int pct = (int)((4 * smem * 100 + 228 * 1024 - 1) / (228 * 1024));
   if (const char* env = std::getenv("FST_SMEM_CARVEOUT")) pct = std::atoi(env);
+  if (carveout_override() >= 0) pct = carveout_override();
   pct = pct < 0 ? 0 : (pct > 100 ? 100 : pct);
   cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
-  done[(const void*)kernel] = smem;
+  const size_t keep = (it != done.end() && it->second.smem > smem) ? it->second.smem : smem;
+  done[(const void*)kernel] = Done{keep, gen};
 }
 
 // Kernel launchers (return the cudaGetLastError() after the launch).
