@@ -195,6 +195,15 @@ class StepPlan:
         self.tuned = tune(model, B, FORWARD_KINDS + ("eval",), links=self.links, use_cache=use_cache,
                           verbose=verbose)
         self.streams = [torch.cuda.Stream(device=model.device) for _ in FORWARD_KINDS]
+        key = _key(model, "plan", B)
+        hit = _load_cache().get(key) if use_cache else None
+        if hit:
+            self.times = {(k, c): v for k, c, v in hit["times"]}
+            self.mode, self.carveout = hit["mode"], hit["carveout"]
+            api.set_smem_carveout(self.carveout)
+            self.fused = self.mode == "fused"
+            self.expected_us = self.times[(self.mode, self.carveout)]
+            return
         buf = Buffers(model, B, self.links)
         times = {}
         for carveout in (-1, 100):
@@ -209,6 +218,9 @@ class StepPlan:
         api.set_smem_carveout(self.carveout)
         self.fused = self.mode == "fused"
         self.expected_us = times[(self.mode, self.carveout)]
+        if use_cache:
+            _store_cache({key: {"mode": self.mode, "carveout": self.carveout,
+                                "times": [[k, c, round(v, 3)] for (k, c), v in times.items()]}})
 
     def _ops(self, q, qd, qdd, tau, out):
         m = self.model
