@@ -335,10 +335,11 @@ cudaError_t jit_launch(const fst_model* m, int kind, dim3 grid, int block, size_
   }
   const int gen = carveout_generation() + 1;
   if (J->carveout_set[kind] != gen) {
-    int pct = -1;
+    int pct = -1;  // the driver's default preference (CU_SHAREDMEM_CARVEOUT_DEFAULT)
     if (const char* env = std::getenv("FST_SMEM_CARVEOUT")) pct = std::atoi(env);
     if (carveout_override() >= 0) pct = carveout_override();
-    if (pct >= 0) D.set_attr(J->fn[kind], CU_FUNC_ATTRIBUTE_PREFERRED_SHARED_MEMORY_CARVEOUT, pct > 100 ? 100 : pct);
+    pct = pct < -1 ? -1 : (pct > 100 ? 100 : pct);
+    if (pct >= 0 || J->carveout_set[kind] != 0) D.set_attr(J->fn[kind], CU_FUNC_ATTRIBUTE_PREFERRED_SHARED_MEMORY_CARVEOUT, pct);
     J->carveout_set[kind] = gen;
   }
   const CUresult r = D.launch(J->fn[kind], grid.x, grid.y, grid.z, (unsigned)block, 1, 1, (unsigned)smem,

@@ -66,13 +66,15 @@ inline void prepare(K* kernel, size_t smem) {
   std::lock_guard<std::mutex> lock(mu);
   auto it = done.find((const void*)kernel);
   if (it != done.end() && it->second.smem >= smem && it->second.gen == gen) return;
-  if (smem > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  int pct = (int)((4 * smem * 100 + 228 * 1024 - 1) / (228 * 1024));
+  // The attribute only ever grows: a launch of another model with less
+  // shared memory must not shrink the limit a larger one already relies on.
+  const size_t keep = (it != done.end() && it->second.smem > smem) ? it->second.smem : smem;
+  if (keep > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)keep);
+  int pct = (int)((4 * keep * 100 + 228 * 1024 - 1) / (228 * 1024));
   if (const char* env = std::getenv("FST_SMEM_CARVEOUT")) pct = std::atoi(env);
   if (carveout_override() >= 0) pct = carveout_override();
   pct = pct < 0 ? 0 : (pct > 100 ? 100 : pct);
   cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
-  const size_t keep = (it != done.end() && it->second.smem > smem) ? it->second.smem : smem;
   done[(const void*)kernel] = Done{keep, gen};
 }
 

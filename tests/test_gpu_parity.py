@@ -201,3 +201,28 @@ def test_level_parallel_variant_matches_oracle(torch_cuda, name, block):
     _assert_close({k: from_soa(v) for k, v in out.items()}, ref, f"level/{name}/{block}")
     for k in out:
         assert torch.equal(ev[k], out[k]), k
+
+
+def test_carveout_change_keeps_shared_memory_limit(torch_cuda):
+    """A change of the shared-memory carveout re-prepares each kernel; a
+    smaller model prepared after it must not shrink the dynamic shared-memory
+    limit that a larger model's launch of the same kernel needs."""
+    import torch
+    from paper_2605_31481_gb300 import api
+    big, small = TREES["humanoid29"](), TREES["quadruped11"]()
+    models = {}
+    for name, tree in (("big", big), ("small", small)):
+        m = api.Model(tree)
+        m.set_launch(None, 32, "level")
+        s = w.random_state(tree, 64, seed=3)
+        models[name] = (m, [to_soa_cuda(s[k], torch) for k in ("q", "qd", "qdd", "tau")], list(tree.ee))
+    try:
+        for carveout, order in ((100, ("big",)), (-1, ("small", "big")), (50, ("small", "big", "small"))):
+            api.set_smem_carveout(carveout)
+            for name in order:
+                m, (q, qd, qdd, tau), ee = models[name]
+                api.eval(m, q, qd, qdd, tau, fk=True, links=ee, rnea=True, crba=True, aba=True)
+                api.aba(m, q, qd, tau)
+        torch.cuda.synchronize()
+    finally:
+        api.set_smem_carveout(-1)
