@@ -44,6 +44,27 @@ FP32_LANES_PER_SM, N_SM = 128, 152
 OPS = ("fk", "jacobian", "rnea", "crba", "aba")
 
 
+# DRAM bytes (read + write) per step of the timed kernels, from one ncu
+# capture of each (profiles/step_quadruped11_B4096.md), keyed by the step
+# plan and a hash of the kernel sources at capture time: a source change
+# since the capture makes the entry stale and the reported traffic null.
+NCU_TRAFFIC = {
+    ("hybrid", "level/256", "specialized/128", "32977bc62627"): 781824 + 585728,
+}
+
+
+def kernel_source_hash():
+    import hashlib
+    h = hashlib.sha1()
+    d = os.path.join(ROOT, "paper_2605_31481_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh", ".h", ".cpp")):
+            h.update(f.encode())
+            with open(os.path.join(d, f), "rb") as fh:
+                h.update(fh.read())
+    return h.hexdigest()[:12]
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -284,7 +305,10 @@ def run_fst(args):
              "concurrent": "5 per-operator kernels on parallel graph branches (" +
                            ", ".join(f"{k} {desc['kinds'][k]}" for k in OPS) + f"), carveout {plan.carveout}",
              "sequential": "5 per-operator kernels in sequence"}[plan.mode]
-    common = {"kernel": kname, "traffic": args.traffic,
+    traffic = args.traffic
+    if traffic is None:
+        traffic = NCU_TRAFFIC.get((plan.mode, desc["kinds"]["aba"], desc["kinds"]["eval"], kernel_source_hash()))
+    common = {"kernel": kname, "traffic": traffic,
               "algorithmic_bytes_per_launch": by * B, "algorithmic_flops_per_launch": fl * B,
               "kernel_ms": round(kernel_ms, 5),
               "alu_frac": round(fl * B / t_k / 1e12 / p_alu, 5),
