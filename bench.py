@@ -45,7 +45,7 @@ OPS = ("fk", "jacobian", "rnea", "crba", "aba")
 
 
 # DRAM bytes (read + write) per step of the timed kernels, from one ncu
-# capture of each (profiles/step_quadruped11_B4096.md), keyed by the step
+# capture of each (the step's summary under profiles/), keyed by the step
 # plan and a hash of the kernel sources at capture time: a source change
 # since the capture makes the entry stale and the reported traffic null.
 NCU_TRAFFIC = {
@@ -368,19 +368,22 @@ def rnea_fwd_bwd(torch, fst, w):
     """RNEA forward + backward on the 7-DOF chain, B = 8192: the sysid loss
     sum (RNEA - tau_meas)^2 and its gradient in one fused kernel, against the
     plain sequence (RNEA kernel, the residual as a torch op, the RNEA adjoint
-    kernel). Both graph-replayed."""
+    kernel, which recomputes the forward sweep) and against the store
+    variant of that sequence (the RNEA kernel writes its forward state to a
+    tape that the adjoint kernel reads). All graph-replayed."""
     tree = w.chain(7, seed=0)
     B = 8192
     m = fst.Model(tree)
     try:
-        m.specialize(["rnea", "rnea_vjp", "loss_grad"])
+        m.specialize(["rnea", "rnea_vjp", "loss_grad", "rnea_store", "rnea_vjp_stored"])
     except Exception:
         pass
     s = w.random_state(tree, B, seed=1)
     cu = lambda x: torch.from_numpy(np.ascontiguousarray(x.T.astype(np.float32))).cuda()
     q, qd, qdd, tm = cu(s["q"]), cu(s["qd"]), cu(s["qdd"]), cu(s["tau"])
     from paper_2605_31481_gb300 import autotune
-    autotune.tune(m, B, kinds=("rnea", "rnea_vjp", "loss_grad"), use_cache=False)
+    autotune.tune(m, B, kinds=("rnea", "rnea_vjp", "loss_grad", "rnea_store", "rnea_vjp_stored"), use_cache=False)
+    tape = fst.api.rnea_tape(m, B)
     scratch = fst.api.adjoint_scratch(m, B)
     tau = torch.empty_like(tm)
     buf = torch.empty(tree.n_bodies * 10 + 1, device="cuda")
@@ -393,11 +396,18 @@ def rnea_fwd_bwd(torch, fst, w):
         tb = 2.0 * (tau - tm)
         fst.api.rnea_vjp(m, q, qd, qdd, tb, q_bar=False, qd_bar=False, qdd_bar=False, scratch=scratch)
 
-    tf, tp = _graph_us(torch, fused), _graph_us(torch, plain)
+    def stored():
+        fst.api.rnea_store(m, q, qd, qdd, tape=tape, out=tau)
+        tb = 2.0 * (tau - tm)
+        fst.api.rnea_vjp_stored(m, q, qd, tape, tb, q_bar=False, qd_bar=False, qdd_bar=False, scratch=scratch)
+
+    tf, tp, ts = _graph_us(torch, fused), _graph_us(torch, plain), _graph_us(torch, stored)
     return {"workload": "chain7, B=8192, loss sum (RNEA - tau_meas)^2 and d/dtheta",
-            "fused_us": round(tf, 3), "plain_us": round(tp, 3),
+            "fused_us": round(tf, 3), "plain_us": round(tp, 3), "plain_store_us": round(ts, 3),
             "fused_per_s": round(B / tf * 1e6, 1), "plain_per_s": round(B / tp * 1e6, 1),
-            "speedup": round(tp / tf, 3), "unit": "RNEA fwd+bwd env-evals/s"}
+            "plain_store_per_s": round(B / ts * 1e6, 1),
+            "speedup": round(tp / tf, 3), "store_vs_recompute": round(tp / ts, 3),
+            "tape_bytes": tape.numel() * 4, "unit": "RNEA fwd+bwd env-evals/s"}
 
 
 def rl_step(torch, fst, w, steps=1000):

@@ -126,7 +126,9 @@ FST_API fst_status fst_model_theta(const fst_model* model, float* theta);
 #define FST_SPEC_ABA_VJP (1u << 8)
 #define FST_SPEC_LOSS_GRAD (1u << 9)
 #define FST_SPEC_EVAL_MIXED (1u << 10) /* the fused kernel of FST_VARIANT_MIXED */
-#define FST_SPEC_ALL 0x7ffu
+#define FST_SPEC_RNEA_STORE (1u << 11)
+#define FST_SPEC_RNEA_VJP_STORED (1u << 12)
+#define FST_SPEC_ALL 0x1fffu
 
 /* Compiles kernels specialised for this model's tree (run-time compilation
  * with NVRTC for the current GPU). The paper folds the fixed joint offsets
@@ -271,6 +273,31 @@ FST_API fst_status fst_rnea_vjp(const fst_model* model, int64_t B, const float* 
                                 const float* tau_bar, float* q_bar, float* qd_bar,
                                 float* qdd_bar, float* theta_bar, void* scratch,
                                 size_t scratch_bytes, void* stream);
+
+/* Store variant of the RNEA adjoint. The paper differentiates through an
+ * autograd tape that keeps every intermediate (Sec. 3.5); fst_rnea_vjp
+ * instead recomputes the forward sweep inside the adjoint kernel. These
+ * three calls keep the choice open: fst_rnea_store runs RNEA (tau optional,
+ * may be NULL) and writes the forward state the reverse sweeps read, per
+ * body and environment 30 floats: the joint transform (R row-major 9, t 3),
+ * the spatial velocity and acceleration ([w; v] each) and the accumulated
+ * force ([n; f]), as tape [n_b][30][B] in caller-owned device memory of
+ * fst_rnea_tape_bytes() bytes (tape_bytes smaller returns
+ * FST_ERR_INVALID_ARG). fst_rnea_vjp_stored then gives the same cotangents
+ * as fst_rnea_vjp (within FP32 rounding)
+ * without the forward sweep, reading q (free-joint quaternion only), qd and
+ * the tape; theta must be the one the tape was written with. The tape costs
+ * 120 n_b bytes per environment of HBM traffic each way; recomputation costs
+ * the forward sweep's arithmetic. */
+FST_API fst_status fst_rnea_tape_bytes(const fst_model* model, int64_t B, size_t* bytes);
+FST_API fst_status fst_rnea_store(const fst_model* model, int64_t B, const float* q,
+                                  const float* qd, const float* qdd, const float* theta,
+                                  float* tau, float* tape, size_t tape_bytes, void* stream);
+FST_API fst_status fst_rnea_vjp_stored(const fst_model* model, int64_t B, const float* q,
+                                       const float* qd, const float* theta, const float* tape,
+                                       size_t tape_bytes, const float* tau_bar, float* q_bar,
+                                       float* qd_bar, float* qdd_bar, float* theta_bar,
+                                       void* scratch, size_t scratch_bytes, void* stream);
 
 /* ABA: cotangents of qdd = ABA(q, qd, tau; theta) for qdd_bar [nv][B].
  * qdd [nv][B] must be the forward result for the same inputs. Uses

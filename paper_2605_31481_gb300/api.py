@@ -307,6 +307,50 @@ def rnea_vjp(model: Model, q, qd, qdd, tau_bar, theta=None, *, q_bar=True, qd_ba
     return res
 
 
+def rnea_tape(model: Model, B: int):
+    """Device buffer for the store variant's forward tape ([n_b][30][B])."""
+    n = ctypes.c_size_t()
+    check(_ffi.lib().fst_rnea_tape_bytes(model.handle, B, ctypes.byref(n)))
+    import torch
+    return torch.empty(max(n.value // 4, 1), dtype=torch.float32, device=model.device)
+
+
+def rnea_store(model: Model, q, qd, qdd, theta=None, tape=None, out=None, tau=True):
+    """RNEA that also writes the forward tape for rnea_vjp_stored.
+    Returns (tau or None, tape)."""
+    B = _check_in(q, model.nq, "q", model)
+    for x, nm in ((qd, "qd"), (qdd, "qdd")):
+        if _check_in(x, model.nv, nm, model) != B:
+            raise ValueError(f"{nm} batch size differs from q")
+    tape = rnea_tape(model, B) if tape is None else tape
+    out = _out(out, (model.nv, B), model) if tau else None
+    check(_ffi.lib().fst_rnea_store(model.handle, B, _ptr(q), _ptr(qd), _ptr(qdd), _ptr(_theta(theta, model)),
+                                    _ptr(out), _ptr(tape), tape.numel() * 4, _stream()))
+    return out, tape
+
+
+def rnea_vjp_stored(model: Model, q, qd, tape, tau_bar, theta=None, *, q_bar=True, qd_bar=True, qdd_bar=True,
+                    theta_bar=True, scratch=None):
+    """rnea_vjp() from a tape written by rnea_store() (no forward sweep)."""
+    B = _check_in(q, model.nq, "q", model)
+    for x, nm in ((qd, "qd"), (tau_bar, "tau_bar")):
+        _check_in(x, model.nv, nm, model)
+    res = {}
+    if q_bar:
+        res["q"] = _out(None, (model.nq, B), model)
+    if qd_bar:
+        res["qd"] = _out(None, (model.nv, B), model)
+    if qdd_bar:
+        res["qdd"] = _out(None, (model.nv, B), model)
+    if theta_bar:
+        res["theta"] = _out(None, (model.n_bodies, 10), model)
+    sp, sb = _scratch(model, B, scratch) if theta_bar else (None, 0)
+    check(_ffi.lib().fst_rnea_vjp_stored(model.handle, B, _ptr(q), _ptr(qd), _ptr(_theta(theta, model)), _ptr(tape),
+                                         tape.numel() * 4, _ptr(tau_bar), _ptr(res.get("q")), _ptr(res.get("qd")),
+                                         _ptr(res.get("qdd")), _ptr(res.get("theta")), sp, sb, _stream()))
+    return res
+
+
 def aba_vjp(model: Model, q, qd, qdd, qdd_bar, theta=None, *, q_bar=True, qd_bar=True, tau_bar=True,
             theta_bar=True, scratch=None):
     """Cotangents of aba() for qdd_bar (nv, B); qdd is aba()'s result.

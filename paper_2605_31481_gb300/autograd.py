@@ -25,6 +25,28 @@ class RNEAFunction(torch.autograd.Function):
         return None, r.get("q"), r.get("qd"), r.get("qdd"), r.get("theta")
 
 
+class RNEAStoredFunction(torch.autograd.Function):
+    """RNEA whose forward keeps the sweep state on a tape (fst_rnea_store)
+    and whose backward reads it (fst_rnea_vjp_stored) instead of recomputing
+    the forward sweep: 120 bytes per body and environment of memory and
+    traffic traded for the forward sweep's arithmetic."""
+
+    @staticmethod
+    def forward(ctx, model, q, qd, qdd, theta):
+        ctx.model = model
+        tau, tape = api.rnea_store(model, q, qd, qdd, theta=theta)
+        ctx.save_for_backward(q, qd, theta, tape)
+        return tau
+
+    @staticmethod
+    def backward(ctx, tau_bar):
+        q, qd, theta, tape = ctx.saved_tensors
+        need = ctx.needs_input_grad
+        r = api.rnea_vjp_stored(ctx.model, q, qd, tape, tau_bar.contiguous(), theta=theta, q_bar=need[1],
+                                qd_bar=need[2], qdd_bar=need[3], theta_bar=theta is not None and need[4])
+        return None, r.get("q"), r.get("qd"), r.get("qdd"), r.get("theta")
+
+
 class ABAFunction(torch.autograd.Function):
     @staticmethod
     def forward(ctx, model, q, qd, tau, theta):
@@ -55,8 +77,12 @@ class FKFunction(torch.autograd.Function):
         return None, api.fk_vjp(ctx.model, q, poses_bar.contiguous())
 
 
-def rnea(model, q, qd, qdd, theta=None):
-    """Differentiable inverse dynamics tau (nv, B)."""
+def rnea(model, q, qd, qdd, theta=None, store=False):
+    """Differentiable inverse dynamics tau (nv, B). store=True keeps the
+    forward sweep's state for the backward (store variant) instead of
+    recomputing it there."""
+    if store:
+        return RNEAStoredFunction.apply(model, q, qd, qdd, theta)
     return RNEAFunction.apply(model, q, qd, qdd, theta)
 
 

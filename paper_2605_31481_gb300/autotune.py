@@ -97,6 +97,7 @@ class Buffers:
         self.pbar = r(model.n_bodies, 12, B)
         self.scratch = api.adjoint_scratch(model, B)
         self.qdd_fwd = torch.empty(model.nv, B, device=dev)
+        self.tape = api.rnea_tape(model, B)
 
 
 def _op(model, kind, buf):
@@ -116,6 +117,10 @@ def _op(model, kind, buf):
                                 out=b.out)
     if kind == "rnea_vjp":
         return lambda: api.rnea_vjp(m, b.q, b.qd, b.qdd, b.tbar, scratch=b.scratch)
+    if kind == "rnea_store":
+        return lambda: api.rnea_store(m, b.q, b.qd, b.qdd, tape=b.tape, out=b.out["tau"])
+    if kind == "rnea_vjp_stored":
+        return lambda: api.rnea_vjp_stored(m, b.q, b.qd, b.tape, b.tbar, scratch=b.scratch)
     if kind == "fk_vjp":
         return lambda: api.fk_vjp(m, b.q, b.pbar)
     if kind == "aba_vjp":
@@ -148,6 +153,8 @@ def tune(model, B, kinds=FORWARD_KINDS + ("eval",), links=None, use_cache=True, 
             buf = Buffers(model, B, links)
             if "aba_vjp" in kinds:
                 api.aba(model, buf.q, buf.qd, buf.tau, out=buf.qdd_fwd)
+            if "rnea_vjp_stored" in kinds:
+                api.rnea_store(model, buf.q, buf.qd, buf.qdd, tape=buf.tape, tau=False)
         fn = _op(model, kind, buf)
         cands = {}
         variants = ["generic"] + (["specialized"] if kind in spec else []) + (["level"] if kind in LEVEL_KINDS else [])

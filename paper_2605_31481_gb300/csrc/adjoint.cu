@@ -10,6 +10,7 @@
 #include "launch.h"
 
 namespace fst {
+static_assert(kTapeFloats == kTapeFloatsPerBody, "tape layout");
 namespace {
 
 // shared memory: model | staged rows (rows x T floats) | per-warp theta slots
@@ -68,6 +69,57 @@ __global__ void __launch_bounds__(256) rnea_vjp_kernel(ModelView mv, int64_t B, 
   cp_async_wait_all();
   VjpOut o{qbar, qdbar, qddbar, slots ? slots + (threadIdx.x / 32) * P : nullptr, 1.f, act};
   rnea_vjp_env<NB>(sm, world_accel(mv), cq, cqd, cqdd, ctb, o, B, e);
+  if (partial) {
+    __syncthreads();
+    write_partial(slots, P, partial);
+  }
+}
+
+// Store variant, forward: tau (optional) and the tape.
+template <int NB>
+__global__ void __launch_bounds__(256) rnea_store_kernel(ModelView mv, int64_t B, const float* __restrict__ q,
+                                                         const float* __restrict__ qd, const float* __restrict__ qdd,
+                                                         float* __restrict__ tau, float* __restrict__ tape) {
+  extern __shared__ float4 smem[];
+  const int T = blockDim.x;
+  float* tile = smem_tile(smem, mv.n);
+  const int64_t e = (int64_t)blockIdx.x * T + threadIdx.x;
+  const bool act = e < B;
+  Col cq{}, cqd{}, cqdd{};
+  if (act) {
+    cq = stage_rows(tile, q, mv.nq, B, e);
+    cqd = stage_rows(tile + mv.nq * T, qd, mv.nv, B, e);
+    cqdd = stage_rows(tile + (mv.nq + mv.nv) * T, qdd, mv.nv, B, e);
+  }
+  const SmemModel sm = stage_model(mv, smem);
+  if (!act) return;
+  cp_async_wait_all();
+  rnea_store_env<NB>(sm, world_accel(mv), cq, cqd, cqdd, tau, tape, B, e);
+}
+
+// Store variant, adjoint: the reverse sweeps read the tape (no forward sweep).
+template <int NB>
+__global__ void __launch_bounds__(256) rnea_vjp_stored_kernel(ModelView mv, int64_t B, const float* __restrict__ q,
+                                                              const float* __restrict__ qd,
+                                                              const float* __restrict__ tape,
+                                                              const float* __restrict__ tbar, float* qbar,
+                                                              float* qdbar, float* qddbar, float* partial) {
+  extern __shared__ float4 smem[];
+  const int T = blockDim.x;
+  const int rows = mv.nq + 2 * mv.nv;
+  float* tile = smem_tile(smem, mv.n);
+  const int64_t e = (int64_t)blockIdx.x * T + threadIdx.x;
+  const bool act = e < B;
+  const Col cq = stage_or_zero(tile, q, mv.nq, B, e, act);
+  const Col cqd = stage_or_zero(tile + mv.nq * T, qd, mv.nv, B, e, act);
+  const Col ctb = stage_or_zero(tile + (mv.nq + mv.nv) * T, tbar, mv.nv, B, e, act);
+  float* slots = partial ? theta_slots(smem, mv.n, rows) : nullptr;
+  const int P = mv.n * 10;
+  if (slots) zero_slots(slots, (T / 32) * P);
+  const SmemModel sm = stage_model(mv, smem);
+  cp_async_wait_all();
+  VjpOut o{qbar, qdbar, qddbar, slots ? slots + (threadIdx.x / 32) * P : nullptr, 1.f, act};
+  rnea_vjp_stored_env<NB>(sm, world_accel(mv), cq, cqd, tape, ctb, o, B, e);
   if (partial) {
     __syncthreads();
     write_partial(slots, P, partial);
@@ -230,6 +282,29 @@ cudaError_t launch_rnea_vjp(const ModelView& mv, int64_t B, const float* q, cons
   float* partial = thbar ? scratch : nullptr;
   FST_NB_DISPATCH(mv.n, prepare(rnea_vjp_kernel<NB>, sh);
                   rnea_vjp_kernel<NB><<<grid_for(B, T), T, sh, s>>>(mv, B, q, qd, qdd, tbar, qbar, qdbar, qddbar, partial));
+  cudaError_t err = cudaGetLastError();
+  if (err == cudaSuccess && thbar) err = reduce(partial, (int)grid_for(B, T), mv.n * 10, thbar, s);
+  return err;
+}
+
+cudaError_t launch_rnea_store(const ModelView& mv, int64_t B, const float* q, const float* qd, const float* qdd,
+                              float* tau, float* tape, const Launch& L) {
+  const size_t sh = smem_bytes(mv.n, mv.nq + 2 * mv.nv, L.block);
+  FST_NB_DISPATCH(mv.n, prepare(rnea_store_kernel<NB>, sh);
+                  rnea_store_kernel<NB><<<grid_for(B, L.block), L.block, sh, L.stream>>>(mv, B, q, qd, qdd, tau, tape));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rnea_vjp_stored(const ModelView& mv, int64_t B, const float* q, const float* qd, const float* tape,
+                                   const float* tbar, float* qbar, float* qdbar, float* qddbar, float* thbar,
+                                   float* scratch, cudaStream_t s) {
+  const int rows = mv.nq + 2 * mv.nv;
+  const int T = fit_block(B, mv.n, rows, thbar != nullptr);
+  const size_t sh = vjp_smem(mv.n, rows, T, thbar != nullptr);
+  float* partial = thbar ? scratch : nullptr;
+  FST_NB_DISPATCH(mv.n, prepare(rnea_vjp_stored_kernel<NB>, sh);
+                  rnea_vjp_stored_kernel<NB><<<grid_for(B, T), T, sh, s>>>(mv, B, q, qd, tape, tbar, qbar, qdbar,
+                                                                           qddbar, partial));
   cudaError_t err = cudaGetLastError();
   if (err == cudaSuccess && thbar) err = reduce(partial, (int)grid_for(B, T), mv.n * 10, thbar, s);
   return err;

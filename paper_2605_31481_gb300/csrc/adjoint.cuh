@@ -197,6 +197,73 @@ __device__ __forceinline__ void rnea_vjp_env(const TP& tp, SV a0, const Col& q, 
   rnea_vjp_reverse<NB>(tp, a0, q, qd, X, v, a, F, tbar, o, B, e);
 }
 
+// ---- store variant: the forward state on a tape -----------------------------
+// Instead of recomputing the forward sweep inside the adjoint kernel, the
+// forward kernel can leave, per body, the quantities the reverse sweeps read:
+// the joint transform X (R row-major 9, t 3), velocity v and acceleration a
+// ([w; v] each) and the accumulated force F ([n; f]). Tape layout
+// [n][kTapeFloats][B], environment index fastest (coalesced).
+constexpr int kTapeFloats = 30;
+
+template <int NB, class TP>
+__device__ __forceinline__ void tape_store(const TP& tp, const Xf (&X)[NB], const SV (&v)[NB], const SV (&a)[NB],
+                                           const SV (&F)[NB], float* __restrict__ tape, int64_t B, int64_t e) {
+  FST_UNROLL
+  for (int i = 0; i < tp.n(); ++i) {
+    float* p = tape + (int64_t)i * kTapeFloats * B + e;
+    const float r[kTapeFloats] = {X[i].R[0], X[i].R[1], X[i].R[2], X[i].R[3], X[i].R[4], X[i].R[5], X[i].R[6],
+                                  X[i].R[7], X[i].R[8], X[i].t[0], X[i].t[1], X[i].t[2], v[i].w.x, v[i].w.y,
+                                  v[i].w.z,  v[i].v.x,  v[i].v.y,  v[i].v.z,  a[i].w.x,  a[i].w.y,  a[i].w.z,
+                                  a[i].v.x,  a[i].v.y,  a[i].v.z,  F[i].w.x,  F[i].w.y,  F[i].w.z,  F[i].v.x,
+                                  F[i].v.y,  F[i].v.z};
+#pragma unroll
+    for (int k = 0; k < kTapeFloats; ++k) p[(int64_t)k * B] = r[k];
+  }
+}
+
+// Reads one environment's forward state back (zeros for a padding thread).
+template <int NB, class TP>
+__device__ __forceinline__ void tape_load(const TP& tp, const float* __restrict__ tape, int64_t B, int64_t e, bool act,
+                                          Xf (&X)[NB], SV (&v)[NB], SV (&a)[NB], SV (&F)[NB]) {
+  FST_UNROLL
+  for (int i = 0; i < tp.n(); ++i) {
+    float r[kTapeFloats];
+    const float* p = tape + (int64_t)i * kTapeFloats * B + e;
+#pragma unroll
+    for (int k = 0; k < kTapeFloats; ++k) r[k] = act ? __ldg(p + (int64_t)k * B) : 0.f;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) X[i].R[k] = r[k];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) X[i].t[k] = r[9 + k];
+    v[i] = SV{f3{r[12], r[13], r[14]}, f3{r[15], r[16], r[17]}};
+    a[i] = SV{f3{r[18], r[19], r[20]}, f3{r[21], r[22], r[23]}};
+    F[i] = SV{f3{r[24], r[25], r[26]}, f3{r[27], r[28], r[29]}};
+  }
+}
+
+// RNEA forward that also writes the tape (tau optional).
+template <int NB, class TP>
+__device__ __forceinline__ void rnea_store_env(const TP& tp, SV a0, const Col& q, const Col& qd, const Col& qdd,
+                                               float* __restrict__ tau, float* __restrict__ tape, int64_t B,
+                                               int64_t e) {
+  Xf X[NB];
+  SV v[NB], a[NB], F[NB];
+  rnea_forward<NB>(tp, a0, q, qd, qdd, X, v, a, F);
+  rnea_backward<NB>(tp, X, F, tau, B, e);
+  tape_store<NB>(tp, X, v, a, F, tape, B, e);
+}
+
+// RNEA vector-Jacobian product from a tape written by rnea_store_env.
+template <int NB, class TP>
+__device__ __forceinline__ void rnea_vjp_stored_env(const TP& tp, SV a0, const Col& q, const Col& qd,
+                                                    const float* __restrict__ tape, const Col& tbar,
+                                                    const VjpOut& o, int64_t B, int64_t e) {
+  Xf X[NB];
+  SV v[NB], a[NB], F[NB];
+  tape_load<NB>(tp, tape, B, e, o.active, X, v, a, F);
+  rnea_vjp_reverse<NB>(tp, a0, q, qd, X, v, a, F, tbar, o, B, e);
+}
+
 // S_i^T f into a staged column (tau of one environment).
 template <class TP>
 __device__ __forceinline__ void ST_col(const TP& tp, int i, SV f, float* col, int ld) {

@@ -464,6 +464,66 @@ fst_status fst_rnea_vjp(const fst_model* m, int64_t B, const float* q, const flo
                                     (float*)scratch, (cudaStream_t)stream));
 }
 
+fst_status fst_rnea_tape_bytes(const fst_model* m, int64_t B, size_t* bytes) {
+  if (!m || !bytes) return set_error(FST_ERR_INVALID_ARG, "fst_rnea_tape_bytes: null argument");
+  if (B < 0) return set_error(FST_ERR_INVALID_ARG, "fst_rnea_tape_bytes: B must be >= 0");
+  *bytes = sizeof(float) * (size_t)kTapeFloatsPerBody * (size_t)m->n * (size_t)B;
+  return FST_OK;
+}
+
+fst_status fst_rnea_store(const fst_model* m, int64_t B, const float* q, const float* qd, const float* qdd,
+                          const float* theta, float* tau, float* tape, size_t tape_bytes, void* stream) {
+  static const char* fn = "fst_rnea_store";
+  bool skip;
+  FST_CHECK(check_call(fn, m, B, &skip));
+  if (skip) return FST_OK;
+  FST_CHECK(need(fn, tape, "tape"));
+  if (tape_bytes < sizeof(float) * (size_t)kTapeFloatsPerBody * (size_t)m->n * (size_t)B)
+    return set_error(FST_ERR_INVALID_ARG, "fst_rnea_store: tape smaller than fst_rnea_tape_bytes()");
+  FST_CHECK(need(fn, q, "q"));
+  if (m->nv) {
+    FST_CHECK(need(fn, qd, "qd"));
+    FST_CHECK(need(fn, qdd, "qdd"));
+  }
+  const ModelView mv = view_of(m, theta);
+  if (use_jit(m, JK_RNEA_STORE))
+    return finish(fn, jit_go(m, JK_RNEA_STORE, B, m->nq + 2 * m->nv, 0, 1, (cudaStream_t)stream, nullptr, mv, B, q,
+                             qd, qdd, tau, tape));
+  return finish(fn, launch_rnea_store(mv, B, q, qd, qdd, tau, tape, launch_of(m, JK_RNEA_STORE, B, stream)));
+}
+
+fst_status fst_rnea_vjp_stored(const fst_model* m, int64_t B, const float* q, const float* qd, const float* theta,
+                               const float* tape, size_t tape_bytes, const float* tau_bar, float* q_bar,
+                               float* qd_bar, float* qdd_bar, float* theta_bar, void* scratch, size_t scratch_bytes,
+                               void* stream) {
+  static const char* fn = "fst_rnea_vjp_stored";
+  bool skip;
+  FST_CHECK(check_call(fn, m, B, &skip));
+  if (theta_bar) FST_CHECK(need_scratch(fn, m, B, scratch, scratch_bytes));
+  if (skip || m->nv == 0) {
+    if (theta_bar && m->n) cudaMemsetAsync(theta_bar, 0, sizeof(float) * m->n * 10, (cudaStream_t)stream);
+    return FST_OK;
+  }
+  FST_CHECK(need(fn, q, "q"));
+  FST_CHECK(need(fn, qd, "qd"));
+  FST_CHECK(need(fn, tape, "tape"));
+  FST_CHECK(need(fn, tau_bar, "tau_bar"));
+  if (tape_bytes < sizeof(float) * (size_t)kTapeFloatsPerBody * (size_t)m->n * (size_t)B)
+    return set_error(FST_ERR_INVALID_ARG, "fst_rnea_vjp_stored: tape smaller than fst_rnea_tape_bytes()");
+  const ModelView mv = view_of(m, theta);
+  if (use_jit(m, JK_RNEA_VJP_STORED)) {
+    unsigned nblk = 0;
+    float* partial = theta_bar ? (float*)scratch : nullptr;
+    const int P = theta_bar ? m->n * 10 : 0;
+    cudaError_t err = jit_go(m, JK_RNEA_VJP_STORED, B, m->nq + 2 * m->nv, P, 1, (cudaStream_t)stream, &nblk, mv, B, q,
+                             qd, tape, tau_bar, q_bar, qd_bar, qdd_bar, partial);
+    if (err == cudaSuccess && theta_bar) err = launch_partial_reduce(partial, (int)nblk, P, theta_bar, (cudaStream_t)stream);
+    return finish(fn, err);
+  }
+  return finish(fn, launch_rnea_vjp_stored(mv, B, q, qd, tape, tau_bar, q_bar, qd_bar, qdd_bar, theta_bar,
+                                           (float*)scratch, (cudaStream_t)stream));
+}
+
 fst_status fst_aba_vjp(const fst_model* m, int64_t B, const float* q, const float* qd, const float* qdd,
                        const float* theta, const float* qdd_bar, float* q_bar, float* qd_bar, float* tau_bar,
                        float* theta_bar, void* scratch, size_t scratch_bytes, void* stream) {

@@ -21,6 +21,8 @@ enum JitKind {
   JK_ABA_VJP,
   JK_LOSS_GRAD,
   JK_EVAL_MIXED,
+  JK_RNEA_STORE,
+  JK_RNEA_VJP_STORED,
   JK_COUNT
 };
 

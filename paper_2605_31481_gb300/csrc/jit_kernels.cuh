@@ -284,6 +284,47 @@ extern "C" __global__ void __launch_bounds__(256) FST_JIT_NAME(ModelView mv, int
 }
 #endif
 
+#ifdef FST_JIT_RNEA_STORE
+extern "C" __global__ void __launch_bounds__(256) FST_JIT_NAME(ModelView mv, int64_t B, const float* __restrict__ q,
+                                                                 const float* __restrict__ qd,
+                                                                 const float* __restrict__ qdd, float* __restrict__ tau,
+                                                                 float* __restrict__ tape) {
+  FST_JIT_PROLOGUE;
+  if (!act) return;
+  const Col cq = stage_rows(tile, q, mv.nq, B, e);
+  const Col cqd = stage_rows(tile + mv.nq * T, qd, mv.nv, B, e);
+  const Col cqdd = stage_rows(tile + (mv.nq + mv.nv) * T, qdd, mv.nv, B, e);
+  cp_async_wait_all();
+  rnea_store_env<FST_N>(fixed_topo(mv), world_accel(mv), cq, cqd, cqdd, tau, tape, B, e);
+}
+#endif
+
+#ifdef FST_JIT_RNEA_VJP_STORED
+extern "C" __global__ void __launch_bounds__(256) FST_JIT_NAME(ModelView mv, int64_t B, const float* __restrict__ q,
+                                                                 const float* __restrict__ qd,
+                                                                 const float* __restrict__ tape,
+                                                                 const float* __restrict__ tbar, float* qbar,
+                                                                 float* qdbar, float* qddbar, float* partial) {
+  FST_JIT_PROLOGUE;
+  const int rows = mv.nq + 2 * mv.nv;
+  const Col cq = jit_stage_or_zero(tile, q, mv.nq, B, e, act);
+  const Col cqd = jit_stage_or_zero(tile + mv.nq * T, qd, mv.nv, B, e, act);
+  const Col ctb = jit_stage_or_zero(tile + (mv.nq + mv.nv) * T, tbar, mv.nv, B, e, act);
+  const int P = FST_N * 10;
+  float* slots = partial ? tile + rows * T : nullptr;
+  if (slots)
+    for (int k = threadIdx.x; k < (T / 32) * P; k += T) slots[k] = 0.f;
+  cp_async_wait_all();
+  __syncthreads();
+  VjpOut o{qbar, qdbar, qddbar, slots ? slots + (threadIdx.x / 32) * P : nullptr, 1.f, act};
+  rnea_vjp_stored_env<FST_N>(fixed_topo(mv), world_accel(mv), cq, cqd, tape, ctb, o, B, e);
+  if (partial) {
+    __syncthreads();
+    jit_write_partial(slots, P, partial);
+  }
+}
+#endif
+
 #ifdef FST_JIT_ABA_VJP
 extern "C" __global__ void __launch_bounds__(256) FST_JIT_NAME(ModelView mv, int64_t B, const float* __restrict__ q,
                                                                  const float* __restrict__ qd,

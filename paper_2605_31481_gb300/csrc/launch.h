@@ -94,6 +94,9 @@ cudaError_t launch_aba(const ModelView& mv, int64_t B, const float* q, const flo
 // warps splitting each tree level's bodies; per-body state in shared memory.
 enum LevelKind { LEVEL_FK = 0, LEVEL_JAC, LEVEL_RNEA, LEVEL_CRBA, LEVEL_ABA, LEVEL_EVAL };
 constexpr size_t kLevelSmemLimit = 227 * 1024;
+
+// Floats per body and environment on the store-variant RNEA tape (X 12, v 6, a 6, F 6).
+constexpr int kTapeFloatsPerBody = 30;
 size_t level_smem_needed(const ModelView& mv, int kind);
 cudaError_t launch_fk_level(const ModelView& mv, int64_t B, const float* q, float* poses, int block, cudaStream_t s);
 cudaError_t launch_jac_level(const ModelView& mv, int64_t B, const float* q, const LinkList& links, float* J,
@@ -115,6 +118,11 @@ cudaError_t launch_fk_vjp(const ModelView& mv, int64_t B, const float* q, const 
 cudaError_t launch_rnea_vjp(const ModelView& mv, int64_t B, const float* q, const float* qd, const float* qdd,
                             const float* tbar, float* qbar, float* qdbar, float* qddbar, float* thbar, float* scratch,
                             cudaStream_t s);
+cudaError_t launch_rnea_store(const ModelView& mv, int64_t B, const float* q, const float* qd, const float* qdd,
+                              float* tau, float* tape, const Launch& L);
+cudaError_t launch_rnea_vjp_stored(const ModelView& mv, int64_t B, const float* q, const float* qd, const float* tape,
+                                   const float* tbar, float* qbar, float* qdbar, float* qddbar, float* thbar,
+                                   float* scratch, cudaStream_t s);
 cudaError_t launch_aba_vjp(const ModelView& mv, int64_t B, const float* q, const float* qd, const float* qdd,
                            const float* qddbar, float* qbar, float* qdbar, float* taubar, float* thbar, float* scratch,
                            cudaStream_t s);

@@ -160,3 +160,75 @@ def test_autograd_wrappers(torch_cuda):
     M = rbd.crba(tree, s["q"])
     lam = np.linalg.solve(M, np.moveaxis(gq.cpu().numpy().astype(np.float64), -1, 0)[..., None])[..., 0]
     assert env_err(from_soa(tau2.grad), lam).max() <= 10 * GTOL
+
+
+@pytest.mark.parametrize("specialize", [False, True])
+@pytest.mark.parametrize("name", ["chain7", "quadruped11", "humanoid29", "general8"])
+def test_rnea_store_variant_matches_oracle_and_recompute(torch_cuda, name, specialize):
+    """Store variant: fst_rnea_store writes the forward tape, and
+    fst_rnea_vjp_stored gives the oracle's cotangents (and the recompute
+    variant's within FP32 rounding) without re-running the forward sweep."""
+    torch = torch_cuda
+    from paper_2605_31481_gb300 import api
+    tree = TREES[name]()
+    B = 161
+    s = w.random_state(tree, B, seed=13)
+    rng = np.random.default_rng(11)
+    tb = rng.standard_normal((B, tree.nv))
+    m = api.Model(tree, specialize=["rnea_store", "rnea_vjp_stored", "rnea_vjp"] if specialize else None)
+    th = rbd.Model(tree).theta() * (1 + rng.uniform(-0.2, 0.2, (tree.n_bodies, 10)))
+    tht = torch.from_numpy(th.astype(np.float32)).cuda()
+    q, qd, qdd, tbar = (to_soa_cuda(x, torch) for x in (s["q"], s["qd"], s["qdd"], tb))
+    tau, tape = api.rnea_store(m, q, qd, qdd, theta=tht)
+    assert tape.numel() == 30 * tree.n_bodies * B
+    tau_plain = api.rnea(m, q, qd, qdd, theta=tht)
+    res = api.rnea_vjp_stored(m, q, qd, tape, tbar, theta=tht)
+    rec = api.rnea_vjp(m, q, qd, qdd, tbar, theta=tht)
+    torch.cuda.synchronize()
+    assert env_err(from_soa(tau), rbd.rnea(tree, s["q"], s["qd"], s["qdd"], theta=th)).max() <= 1e-4
+    assert env_err(from_soa(tau), from_soa(tau_plain)).max() <= 1e-6
+    rq, rqd, rqdd, rth = derivs.rnea_vjp(tree, s["q"], s["qd"], s["qdd"], tb, theta=th)
+    for k, ref in (("q", rq), ("qd", rqd), ("qdd", rqdd)):
+        err = env_err(from_soa(res[k]), ref)
+        assert err.max() <= GTOL, f"{name} {k}: {err.max():.3e}"
+        assert env_err(from_soa(res[k]), from_soa(rec[k])).max() <= 1e-5, k
+    assert _th_err(res["theta"].cpu().numpy(), rth) <= THTOL
+    assert _th_err(res["theta"].cpu().numpy(), rec["theta"].cpu().numpy().astype(np.float64)) <= 1e-5
+    # the tape of the first environment holds X, v, a and the accumulated force of body 0
+    X0 = tape.view(tree.n_bodies, 30, B)[0, :, 0].cpu().numpy()
+    R = X0[:9].reshape(3, 3)
+    assert np.abs(R @ R.T - np.eye(3)).max() < 1e-5
+
+
+def test_rnea_store_rejects_small_tape(torch_cuda):
+    torch = torch_cuda
+    from paper_2605_31481_gb300 import api, _ffi
+    tree = TREES["chain7"]()
+    m = api.Model(tree)
+    B = 64
+    s = w.random_state(tree, B, seed=1)
+    q, qd, qdd = (to_soa_cuda(s[k], torch) for k in ("q", "qd", "qdd"))
+    small = torch.empty(30 * tree.n_bodies * B - 1, device="cuda")
+    with pytest.raises(_ffi.FstError):
+        api.rnea_store(m, q, qd, qdd, tape=small)
+    with pytest.raises(_ffi.FstError):
+        api.rnea_vjp_stored(m, q, qd, small, qd)
+
+
+def test_autograd_store_variant(torch_cuda):
+    torch = torch_cuda
+    from paper_2605_31481_gb300 import api, autograd
+    tree = TREES["quadruped11"]()
+    B = 100
+    s = w.random_state(tree, B, seed=21)
+    m = api.Model(tree)
+    th0 = torch.from_numpy(rbd.Model(tree).theta().astype(np.float32)).cuda()
+    grads = []
+    for store in (False, True):
+        q, qd, qdd = (to_soa_cuda(s[k], torch).requires_grad_() for k in ("q", "qd", "qdd"))
+        th = th0.clone().requires_grad_()
+        tau = autograd.rnea(m, q, qd, qdd, theta=th, store=store)
+        (tau * tau).sum().backward()
+        grads.append([x.grad for x in (q, qd, qdd, th)])
+    for a, b in zip(*grads):
+        assert torch.allclose(a, b, rtol=1e-5, atol=1e-5 * float(b.abs().max()))
