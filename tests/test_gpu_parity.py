@@ -2,12 +2,14 @@
 element, on seeded inputs: several tiles plus a ragged tail, the full
 workload sizes on sampled environments, and the edge cases (B = 0, B = 1,
 inertia override, NaN isolation, every joint type)."""
+import os
+
 import numpy as np
 import pytest
 from scipy.spatial.transform import Rotation
 
 from oracle import rbd
-from paper_2605_31481_gb300 import workloads as w
+from paper_2605_31481_gb300 import urdf, workloads as w
 from tests._helpers import TOL, env_err, from_soa, oracle_poses, to_soa_cuda
 
 pytestmark = pytest.mark.gpu
@@ -42,6 +44,7 @@ TREES = {
     "humanoid29": lambda: w.humanoid(seed=0),
     "general8": _general_tree,
     "legged18": lambda: w.legged(6, seed=3),
+    "urdf_arm6_tool": lambda: urdf.load_urdf(os.path.join(os.path.dirname(__file__), "data", "arm6_tool.urdf")),
 }
 
 
