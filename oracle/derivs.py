@@ -17,6 +17,7 @@ not depend on any adjoint derivation, so it uses:
 import numpy as np
 
 from . import rbd
+from . import spatial as sp
 
 H_CS = 1e-30
 
@@ -105,3 +106,74 @@ def fk_vjp(tree, q, poses_bar):
         return np.concatenate([T[..., :3, :3].reshape(T.shape[:2] + (9,)), T[..., :3, 3]], axis=-1)
     J = jac_cs(f, (q,), 0)                                # (B, n_b, 12, nq)
     return np.einsum("bnk,bnkj->bj", poses_bar, J)
+
+
+# ---------------------------------------------------------------------------
+# dense derivatives along the configuration's tangent space
+# ---------------------------------------------------------------------------
+
+def integrate(tree, q, dv):
+    """q (+) dv: the configuration moved along a tangent vector dv (B, nv).
+
+    Revolute and prismatic coordinates add. A free joint moves its frame by
+    the displacement dv = [dp; dw] expressed in that moving frame: the
+    position gains R(quat) dp and the quaternion is multiplied on the right
+    by (dw / 2, 1), the rotation about the body-frame axis dw to first order.
+    The map is exact to first order at dv = 0, the only place the
+    derivatives below evaluate it. Analytic, so complex steps pass through."""
+    m = rbd.Model(tree)
+    q = np.asarray(q)
+    dv = np.asarray(dv)
+    dt = np.result_type(q.dtype, dv.dtype)
+    out = np.array(q, dtype=dt, copy=True)
+    for i, t in enumerate(m.jtype):
+        a, b = m.qi[i], m.vi[i]
+        if t in (rbd.REVOLUTE, rbd.PRISMATIC):
+            out[:, a] = q[:, a] + dv[:, b]
+        elif t == rbd.FREE:
+            quat = q[:, a + 3:a + 7]
+            R = sp.quat_to_R(quat)
+            out[:, a:a + 3] = q[:, a:a + 3] + np.einsum("bij,bj->bi", R, dv[:, b:b + 3])
+            x1, y1, z1, w1 = np.moveaxis(quat, -1, 0)
+            x2, y2, z2 = np.moveaxis(dv[:, b + 3:b + 6] / 2, -1, 0)
+            # Hamilton product (x1, y1, z1, w1) (x) (x2, y2, z2, 1)
+            out[:, a + 3] = w1 * x2 + x1 + y1 * z2 - z1 * y2
+            out[:, a + 4] = w1 * y2 + y1 + z1 * x2 - x1 * z2
+            out[:, a + 5] = w1 * z2 + z1 + x1 * y2 - y1 * x2
+            out[:, a + 6] = w1 - (x1 * x2 + y1 * y2 + z1 * z2)
+    return out
+
+
+def tangent_jac_cs(f, tree, q, nv):
+    """d f(q (+) dv) / d dv at dv = 0, per environment: (B, out..., nv)."""
+    B = np.asarray(q).shape[0]
+    cols = []
+    for j in range(nv):
+        dv = np.zeros((B, nv), dtype=np.complex128)
+        dv[:, j] = 1j * H_CS
+        cols.append(np.imag(f(integrate(tree, np.asarray(q, np.complex128), dv))) / H_CS)
+    return np.stack(cols, axis=-1)
+
+
+def rnea_derivatives(tree, q, qd, qdd, theta=None):
+    """Dense derivatives of inverse dynamics: d tau / d q along the tangent
+    directions of `integrate` and d tau / d qd, each (B, nv, nv) with row =
+    tau component, column = direction. (d tau / d qdd is the mass matrix.)"""
+    m = rbd.Model(tree)
+    th = m.theta() if theta is None else np.asarray(theta, dtype=np.float64)
+    qdc, qddc = np.asarray(qd, np.complex128), np.asarray(qdd, np.complex128)
+    dq = tangent_jac_cs(lambda q_: rbd.rnea(tree, q_, qdc, qddc, theta=th), tree, q, m.nv)
+    dqd = jac_cs(lambda q_, qd_, qdd_: rbd.rnea(tree, q_, qd_, qdd_, theta=th), (q, qd, qdd), 1)
+    return dq, dqd
+
+
+def aba_derivatives(tree, q, qd, tau, theta=None):
+    """Dense derivatives of forward dynamics qdd = ABA(q, qd, tau): d qdd / d q
+    (tangent directions), d qdd / d qd and d qdd / d tau (= M^-1), each
+    (B, nv, nv), by complex steps of the oracle's ABA."""
+    m = rbd.Model(tree)
+    th = m.theta() if theta is None else np.asarray(theta, dtype=np.float64)
+    qdc, tauc = np.asarray(qd, np.complex128), np.asarray(tau, np.complex128)
+    dq = tangent_jac_cs(lambda q_: rbd.aba(tree, q_, qdc, tauc, theta=th), tree, q, m.nv)
+    f = lambda q_, qd_, tau_: rbd.aba(tree, q_, qd_, tau_, theta=th)
+    return dq, jac_cs(f, (q, qd, tau), 1), jac_cs(f, (q, qd, tau), 2)

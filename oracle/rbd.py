@@ -102,8 +102,9 @@ class Model:
         return sp.pose_to_X(self.local_pose(i, q))
 
     def a0(self, B, dtype, gravity=None):
-        g = self.gravity if gravity is None else np.asarray(gravity, dtype=np.float64)
-        a = np.zeros((B, 6), dtype=dtype)
+        # a complex gravity passes through, so complex steps can differentiate in it
+        g = self.gravity if gravity is None else np.asarray(gravity)
+        a = np.zeros((B, 6), dtype=np.result_type(dtype, g.dtype, np.float64))
         a[:, 3:6] = -g
         return a
 
@@ -157,7 +158,8 @@ def rnea(tree, q, qd, qdd, theta=None, gravity=None):
     Backward sweep: tau_i = S_i^T f_i, f_p += X_i^T f_i."""
     m = Model(tree)
     q, qd, qdd = np.asarray(q), np.asarray(qd), np.asarray(qdd)
-    dt = np.result_type(q, qd, qdd, np.float64 if theta is None else np.asarray(theta))
+    dt = np.result_type(q, qd, qdd, np.float64 if theta is None else np.asarray(theta),
+                        np.float64 if gravity is None else np.asarray(gravity))
     B = q.shape[0]
     I = m.inertias(theta)
     a0 = m.a0(B, dt, gravity)
@@ -224,7 +226,8 @@ def aba(tree, q, qd, tau, theta=None, gravity=None):
     accelerations root to leaf)."""
     m = Model(tree)
     q, qd, tau = np.asarray(q), np.asarray(qd), np.asarray(tau)
-    dt = np.result_type(q, qd, tau, np.float64 if theta is None else np.asarray(theta))
+    dt = np.result_type(q, qd, tau, np.float64 if theta is None else np.asarray(theta),
+                        np.float64 if gravity is None else np.asarray(gravity))
     B = q.shape[0]
     I = m.inertias(theta)
     a0 = m.a0(B, dt, gravity)
