@@ -128,7 +128,9 @@ FST_API fst_status fst_model_theta(const fst_model* model, float* theta);
 #define FST_SPEC_EVAL_MIXED (1u << 10) /* the fused kernel of FST_VARIANT_MIXED */
 #define FST_SPEC_RNEA_STORE (1u << 11)
 #define FST_SPEC_RNEA_VJP_STORED (1u << 12)
-#define FST_SPEC_ALL 0x1fffu
+#define FST_SPEC_RNEA_DERIVATIVES (1u << 13)
+#define FST_SPEC_ABA_DERIVATIVES (1u << 14)
+#define FST_SPEC_ALL 0x7fffu
 
 /* Compiles kernels specialised for this model's tree (run-time compilation
  * with NVRTC for the current GPU). The paper folds the fixed joint offsets
@@ -307,6 +309,36 @@ FST_API fst_status fst_aba_vjp(const fst_model* model, int64_t B, const float* q
                                const float* qdd_bar, float* q_bar, float* qd_bar,
                                float* tau_bar, float* theta_bar, void* scratch,
                                size_t scratch_bytes, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Dense derivatives of the dynamics (the analytical derivatives the paper
+ * names as the step after its autograd gradients, Sec. 3.5). Matrices are
+ * [nv][nv][B] device arrays, element (row r, column c) of environment e at
+ * (r * nv + c) * B + e; row = output component, column = direction.
+ * Derivatives with respect to q are taken along the configuration's tangent
+ * space (nv directions): a revolute or prismatic coordinate directly; a free
+ * joint's 6 directions displace its moving frame by [dp; dw] expressed in
+ * that frame (position += R dp, R := R exp(dw)), in the order of its
+ * velocity [v; w]. Computed by forward-mode sweeps through RNEA, one per
+ * degree of freedom.
+ * ------------------------------------------------------------------------- */
+
+/* d tau / d q and d tau / d qd of tau = RNEA(q, qd, qdd; theta); either
+ * output may be NULL (not computed). d tau / d qdd is M (fst_crba). */
+FST_API fst_status fst_rnea_derivatives(const fst_model* model, int64_t B, const float* q,
+                                        const float* qd, const float* qdd, const float* theta,
+                                        float* dtau_dq, float* dtau_dqd, void* stream);
+
+/* Derivatives of qdd = ABA(q, qd, tau; theta): d qdd / d q, d qdd / d qd
+ * (either may be NULL) and Minv = d qdd / d tau = M^-1 (required: it also
+ * serves as the per-environment Cholesky workspace). qdd [nv][B] optionally
+ * receives the forward-dynamics result itself. An environment whose M is
+ * not positive definite (for example a massless body on a moving joint)
+ * gets non-finite values. */
+FST_API fst_status fst_aba_derivatives(const fst_model* model, int64_t B, const float* q,
+                                       const float* qd, const float* tau, const float* theta,
+                                       float* qdd, float* dqdd_dq, float* dqdd_dqd, float* Minv,
+                                       void* stream);
 
 /* System-identification loss L = sum_env sum_i (tau_i - tau_meas_i)^2,
  * tau = RNEA(q, qd, qdd; theta) (paper Sec. 4.3), and its gradient, in one

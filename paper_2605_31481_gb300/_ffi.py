@@ -20,7 +20,7 @@ MAX_BODIES = 64
 MAX_LINKS = 16
 VARIANTS = {"auto": 0, "generic": 1, "specialized": 2, "level": 3, "mixed": 4}
 SPEC_KINDS = ("fk", "jacobian", "rnea", "crba", "aba", "eval", "fk_vjp", "rnea_vjp", "aba_vjp", "loss_grad",
-              "eval_mixed", "rnea_store", "rnea_vjp_stored")
+              "eval_mixed", "rnea_store", "rnea_vjp_stored", "rnea_derivatives", "aba_derivatives")
 
 c_int32, c_int64, c_double, c_void_p = ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_void_p
 c_float_p = ctypes.POINTER(ctypes.c_float)
@@ -88,6 +88,10 @@ _SIGS = {
     "fst_rnea_vjp_stored": (c_int32, [c_void_p, c_int64, c_void_p, c_void_p, c_void_p, c_void_p, ctypes.c_size_t,
                                       c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, ctypes.c_size_t,
                                       c_void_p]),
+    "fst_rnea_derivatives": (c_int32, [c_void_p, c_int64, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                       c_void_p, c_void_p]),
+    "fst_aba_derivatives": (c_int32, [c_void_p, c_int64, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                      c_void_p, c_void_p, c_void_p, c_void_p]),
     "fst_aba_vjp": (c_int32, [c_void_p, c_int64, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                               c_void_p, c_void_p, c_void_p, c_void_p, ctypes.c_size_t, c_void_p]),
     "fst_rnea_loss_grad": (c_int32, [c_void_p, c_int64, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,

@@ -351,6 +351,46 @@ def rnea_vjp_stored(model: Model, q, qd, tape, tau_bar, theta=None, *, q_bar=Tru
     return res
 
 
+def rnea_derivatives(model: Model, q, qd, qdd, theta=None, *, dq=True, dqd=True):
+    """Dense d tau / d q (tangent directions) and d tau / d qd, (nv, nv, B)
+    each (row = tau component, column = direction). Returns a dict with the
+    requested keys "q", "qd"."""
+    B = _check_in(q, model.nq, "q", model)
+    for x, nm in ((qd, "qd"), (qdd, "qdd")):
+        if _check_in(x, model.nv, nm, model) != B:
+            raise ValueError(f"{nm} batch size differs from q")
+    res = {}
+    if dq:
+        res["q"] = _out(None, (model.nv, model.nv, B), model)
+    if dqd:
+        res["qd"] = _out(None, (model.nv, model.nv, B), model)
+    check(_ffi.lib().fst_rnea_derivatives(model.handle, B, _ptr(q), _ptr(qd), _ptr(qdd), _ptr(_theta(theta, model)),
+                                          _ptr(res.get("q")), _ptr(res.get("qd")), _stream()))
+    return res
+
+
+def aba_derivatives(model: Model, q, qd, tau, theta=None, *, dq=True, dqd=True, qdd=False):
+    """Dense d qdd / d q (tangent directions), d qdd / d qd and
+    d qdd / d tau = M^-1, (nv, nv, B) each, at qdd = ABA(q, qd, tau).
+    Returns a dict with keys "q", "qd" (as requested), "tau" (M^-1) and,
+    with qdd=True, "qdd" (nv, B)."""
+    B = _check_in(q, model.nq, "q", model)
+    for x, nm in ((qd, "qd"), (tau, "tau")):
+        if _check_in(x, model.nv, nm, model) != B:
+            raise ValueError(f"{nm} batch size differs from q")
+    res = {"tau": _out(None, (model.nv, model.nv, B), model)}
+    if dq:
+        res["q"] = _out(None, (model.nv, model.nv, B), model)
+    if dqd:
+        res["qd"] = _out(None, (model.nv, model.nv, B), model)
+    if qdd:
+        res["qdd"] = _out(None, (model.nv, B), model)
+    check(_ffi.lib().fst_aba_derivatives(model.handle, B, _ptr(q), _ptr(qd), _ptr(tau), _ptr(_theta(theta, model)),
+                                         _ptr(res.get("qdd")), _ptr(res.get("q")), _ptr(res.get("qd")),
+                                         _ptr(res["tau"]), _stream()))
+    return res
+
+
 def aba_vjp(model: Model, q, qd, qdd, qdd_bar, theta=None, *, q_bar=True, qd_bar=True, tau_bar=True,
             theta_bar=True, scratch=None):
     """Cotangents of aba() for qdd_bar (nv, B); qdd is aba()'s result.

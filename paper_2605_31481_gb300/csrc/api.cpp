@@ -524,6 +524,41 @@ fst_status fst_rnea_vjp_stored(const fst_model* m, int64_t B, const float* q, co
                                            (float*)scratch, (cudaStream_t)stream));
 }
 
+fst_status fst_rnea_derivatives(const fst_model* m, int64_t B, const float* q, const float* qd, const float* qdd,
+                                const float* theta, float* dtau_dq, float* dtau_dqd, void* stream) {
+  static const char* fn = "fst_rnea_derivatives";
+  bool skip;
+  FST_CHECK(check_call(fn, m, B, &skip));
+  if (skip || m->nv == 0 || (!dtau_dq && !dtau_dqd)) return FST_OK;
+  FST_CHECK(need(fn, q, "q"));
+  FST_CHECK(need(fn, qd, "qd"));
+  FST_CHECK(need(fn, qdd, "qdd"));
+  const ModelView mv = view_of(m, theta);
+  if (use_jit(m, JK_RNEA_DERIVS))
+    return finish(fn, jit_go(m, JK_RNEA_DERIVS, B, m->nq + 2 * m->nv, 0, 1, (cudaStream_t)stream, nullptr, mv, B, q,
+                             qd, qdd, dtau_dq, dtau_dqd));
+  return finish(fn, launch_rnea_derivs(mv, B, q, qd, qdd, dtau_dq, dtau_dqd, launch_of(m, JK_RNEA_DERIVS, B, stream)));
+}
+
+fst_status fst_aba_derivatives(const fst_model* m, int64_t B, const float* q, const float* qd, const float* tau,
+                               const float* theta, float* qdd, float* dqdd_dq, float* dqdd_dqd, float* Minv,
+                               void* stream) {
+  static const char* fn = "fst_aba_derivatives";
+  bool skip;
+  FST_CHECK(check_call(fn, m, B, &skip));
+  if (skip || m->nv == 0) return FST_OK;
+  FST_CHECK(need(fn, q, "q"));
+  FST_CHECK(need(fn, qd, "qd"));
+  FST_CHECK(need(fn, tau, "tau"));
+  FST_CHECK(need(fn, Minv, "Minv"));
+  const ModelView mv = view_of(m, theta);
+  if (use_jit(m, JK_ABA_DERIVS))
+    return finish(fn, jit_go(m, JK_ABA_DERIVS, B, m->nq + 3 * m->nv, 0, 1, (cudaStream_t)stream, nullptr, mv, B, q,
+                             qd, tau, qdd, dqdd_dq, dqdd_dqd, Minv));
+  return finish(fn, launch_aba_derivs(mv, B, q, qd, tau, qdd, dqdd_dq, dqdd_dqd, Minv,
+                                      launch_of(m, JK_ABA_DERIVS, B, stream)));
+}
+
 fst_status fst_aba_vjp(const fst_model* m, int64_t B, const float* q, const float* qd, const float* qdd,
                        const float* theta, const float* qdd_bar, float* q_bar, float* qd_bar, float* tau_bar,
                        float* theta_bar, void* scratch, size_t scratch_bytes, void* stream) {

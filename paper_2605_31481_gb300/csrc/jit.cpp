@@ -42,11 +42,11 @@ namespace {
 const char* const kKindName[JK_COUNT] = {"fst_jit_fk",      "fst_jit_jacobian", "fst_jit_rnea",     "fst_jit_crba",
                                          "fst_jit_aba",     "fst_jit_eval",     "fst_jit_fk_vjp",   "fst_jit_rnea_vjp",
                                          "fst_jit_aba_vjp", "fst_jit_loss_grad", "fst_jit_eval_mixed", "fst_jit_rnea_store",
-                                         "fst_jit_rnea_vjp_stored"};
+                                         "fst_jit_rnea_vjp_stored", "fst_jit_rnea_derivs", "fst_jit_aba_derivs"};
 const char* const kKindMacro[JK_COUNT] = {"FST_JIT_FK",      "FST_JIT_JACOBIAN", "FST_JIT_RNEA",     "FST_JIT_CRBA",
                                           "FST_JIT_ABA",     "FST_JIT_EVAL",     "FST_JIT_FK_VJP",   "FST_JIT_RNEA_VJP",
                                           "FST_JIT_ABA_VJP", "FST_JIT_LOSS_GRAD", "FST_JIT_EVAL_MIXED", "FST_JIT_RNEA_STORE",
-                                          "FST_JIT_RNEA_VJP_STORED"};
+                                          "FST_JIT_RNEA_VJP_STORED", "FST_JIT_RNEA_DERIVS", "FST_JIT_ABA_DERIVS"};
 
 // ---- NVRTC, opened at run time ---------------------------------------------
 struct Nvrtc {

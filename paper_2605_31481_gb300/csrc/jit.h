@@ -23,6 +23,8 @@ enum JitKind {
   JK_EVAL_MIXED,
   JK_RNEA_STORE,
   JK_RNEA_VJP_STORED,
+  JK_RNEA_DERIVS,
+  JK_ABA_DERIVS,
   JK_COUNT
 };
 

@@ -12,6 +12,7 @@
 #pragma once
 
 #include "adjoint.cuh"
+#include "derivs.cuh"
 #include "level.cuh"
 
 namespace fst {
@@ -322,6 +323,40 @@ extern "C" __global__ void __launch_bounds__(256) FST_JIT_NAME(ModelView mv, int
     __syncthreads();
     jit_write_partial(slots, P, partial);
   }
+}
+#endif
+
+#ifdef FST_JIT_RNEA_DERIVS
+extern "C" __global__ void __launch_bounds__(256) FST_JIT_NAME(ModelView mv, int64_t B, const float* __restrict__ q,
+                                                                 const float* __restrict__ qd,
+                                                                 const float* __restrict__ qdd, float* __restrict__ dq,
+                                                                 float* __restrict__ dqd) {
+  FST_JIT_PROLOGUE;
+  if (!act) return;
+  const Col cq = stage_rows(tile, q, mv.nq, B, e);
+  const Col cqd = stage_rows(tile + mv.nq * T, qd, mv.nv, B, e);
+  const Col cqdd = stage_rows(tile + (mv.nq + mv.nv) * T, qdd, mv.nv, B, e);
+  cp_async_wait_all();
+  rnea_derivs_env<FST_N>(fixed_topo(mv), world_accel(mv), cq, cqd, cqdd, mv.nv, dq, dqd, B, e);
+}
+#endif
+
+#ifdef FST_JIT_ABA_DERIVS
+extern "C" __global__ void __launch_bounds__(256) FST_JIT_NAME(ModelView mv, int64_t B, const float* __restrict__ q,
+                                                                 const float* __restrict__ qd,
+                                                                 const float* __restrict__ tau, float* __restrict__ qdd,
+                                                                 float* __restrict__ dq, float* __restrict__ dqd,
+                                                                 float* __restrict__ Minv) {
+  FST_JIT_PROLOGUE;
+  if (!act) return;
+  const Col cq = stage_rows(tile, q, mv.nq, B, e);
+  const Col cqd = stage_rows(tile + mv.nq * T, qd, mv.nv, B, e);
+  const Col ctau = stage_rows(tile + (mv.nq + mv.nv) * T, tau, mv.nv, B, e);
+  float* col = tile + (mv.nq + 2 * mv.nv) * T + threadIdx.x;
+  cp_async_wait_all();
+  aba_derivs_env<FST_N>(fixed_topo(mv), world_accel(mv), cq, cqd, ctau, mv.nv, col, T, dq, dqd, Minv, B, e);
+  if (qdd)
+    for (int k = 0; k < mv.nv; ++k) qdd[(int64_t)k * B + e] = col[k * T];
 }
 #endif
 

@@ -123,6 +123,10 @@ cudaError_t launch_rnea_store(const ModelView& mv, int64_t B, const float* q, co
 cudaError_t launch_rnea_vjp_stored(const ModelView& mv, int64_t B, const float* q, const float* qd, const float* tape,
                                    const float* tbar, float* qbar, float* qdbar, float* qddbar, float* thbar,
                                    float* scratch, cudaStream_t s);
+cudaError_t launch_rnea_derivs(const ModelView& mv, int64_t B, const float* q, const float* qd, const float* qdd,
+                               float* dq, float* dqd, const Launch& L);
+cudaError_t launch_aba_derivs(const ModelView& mv, int64_t B, const float* q, const float* qd, const float* tau,
+                              float* qdd, float* dq, float* dqd, float* Minv, const Launch& L);
 cudaError_t launch_aba_vjp(const ModelView& mv, int64_t B, const float* q, const float* qd, const float* qdd,
                            const float* qddbar, float* qbar, float* qdbar, float* taubar, float* thbar, float* scratch,
                            cudaStream_t s);
