@@ -177,3 +177,34 @@ def aba_derivatives(tree, q, qd, tau, theta=None):
     dq = tangent_jac_cs(lambda q_: rbd.aba(tree, q_, qdc, tauc, theta=th), tree, q, m.nv)
     f = lambda q_, qd_, tau_: rbd.aba(tree, q_, qd_, tau_, theta=th)
     return dq, jac_cs(f, (q, qd, tau), 1), jac_cs(f, (q, qd, tau), 2)
+
+
+# ---------------------------------------------------------------------------
+# adjoints of the Jacobian and of the mass matrix
+# ---------------------------------------------------------------------------
+
+def jacobian_vjp(tree, q, links, J_bar):
+    """q_bar (B, nq) for the cotangent J_bar (B, n_links, 6, nv) of the
+    Jacobians of `links` (rows [v; w], the layout of rbd.jacobian)."""
+    def f(q_):
+        return np.stack([rbd.jacobian(tree, q_, l) for l in links], axis=1)
+    J = jac_cs(f, (q,), 0)                                # (B, L, 6, nv, nq)
+    return np.einsum("blrc,blrcj->bj", J_bar, J)
+
+
+def crba_vjp(tree, q, M_bar, theta=None):
+    """Cotangents of M = CRBA(q; theta) for M_bar (B, nv, nv): q_bar (B, nq)
+    by complex steps, and theta_bar (n_b, 10) summed over environments, exact
+    because M is linear in theta (M = sum theta_bk CRBA(q; unit theta_bk))."""
+    m = rbd.Model(tree)
+    th = m.theta() if theta is None else np.asarray(theta, dtype=np.float64)
+    J = jac_cs(lambda q_: rbd.crba(tree, q_, theta=th), (q,), 0)   # (B, nv, nv, nq)
+    q_bar = np.einsum("brc,brcj->bj", M_bar, J)
+    n = th.shape[0]
+    th_bar = np.zeros((n, 10))
+    for b in range(n):
+        for k in range(10):
+            u = np.zeros((n, 10))
+            u[b, k] = 1.0
+            th_bar[b, k] = np.sum(M_bar * rbd.crba(tree, q, theta=u))
+    return q_bar, th_bar
