@@ -276,6 +276,21 @@ FST_API fst_status fst_rnea_vjp(const fst_model* model, int64_t B, const float* 
                                 float* qdd_bar, float* theta_bar, void* scratch,
                                 size_t scratch_bytes, void* stream);
 
+/* Jacobian: q_bar [nq][B] = sum (d J / d q)^T J_bar for J_bar
+ * [n_links][6][nv][B] in the layout of fst_jacobian (the same links).
+ * q_bar is required. */
+FST_API fst_status fst_jacobian_vjp(const fst_model* model, int64_t B, const float* q,
+                                    const int32_t* links, int32_t n_links, const float* J_bar,
+                                    float* q_bar, void* stream);
+
+/* Mass matrix: cotangents of M = CRBA(q; theta) for M_bar [nv][nv][B]:
+ * q_bar [nq][B] (may be NULL) and theta_bar (may be NULL; needs scratch as
+ * for fst_rnea_vjp). Uses M e_k = RNEA(q, 0, e_k) without gravity: the sum
+ * over columns k of RNEA adjoints with tau_bar = M_bar[:, k]. */
+FST_API fst_status fst_crba_vjp(const fst_model* model, int64_t B, const float* q, const float* theta,
+                                const float* M_bar, float* q_bar, float* theta_bar, void* scratch,
+                                size_t scratch_bytes, void* stream);
+
 /* Store variant of the RNEA adjoint. The paper differentiates through an
  * autograd tape that keeps every intermediate (Sec. 3.5); fst_rnea_vjp
  * instead recomputes the forward sweep inside the adjoint kernel. These

@@ -88,6 +88,10 @@ _SIGS = {
     "fst_rnea_vjp_stored": (c_int32, [c_void_p, c_int64, c_void_p, c_void_p, c_void_p, c_void_p, ctypes.c_size_t,
                                       c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, ctypes.c_size_t,
                                       c_void_p]),
+    "fst_jacobian_vjp": (c_int32, [c_void_p, c_int64, c_void_p, ctypes.POINTER(c_int32), c_int32, c_void_p, c_void_p,
+                                   c_void_p]),
+    "fst_crba_vjp": (c_int32, [c_void_p, c_int64, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                               ctypes.c_size_t, c_void_p]),
     "fst_rnea_derivatives": (c_int32, [c_void_p, c_int64, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                        c_void_p, c_void_p]),
     "fst_aba_derivatives": (c_int32, [c_void_p, c_int64, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,

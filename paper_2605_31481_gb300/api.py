@@ -143,6 +143,14 @@ def _check_in(x, rows, name, model):
     return x.shape[1]
 
 
+def _check_shape(x, shape, name, model):
+    if not isinstance(x, torch.Tensor):
+        raise TypeError(f"{name} must be a torch.Tensor")
+    if (tuple(x.shape) != tuple(shape) or x.dtype != torch.float32 or x.device != model.device
+            or not x.is_contiguous()):
+        raise ValueError(f"{name} must be a contiguous float32 {tuple(shape)} tensor on {model.device}")
+
+
 def _out(out, shape, model):
     if out is None:
         return torch.empty(shape, dtype=torch.float32, device=model.device)
@@ -348,6 +356,33 @@ def rnea_vjp_stored(model: Model, q, qd, tape, tau_bar, theta=None, *, q_bar=Tru
     check(_ffi.lib().fst_rnea_vjp_stored(model.handle, B, _ptr(q), _ptr(qd), _ptr(_theta(theta, model)), _ptr(tape),
                                          tape.numel() * 4, _ptr(tau_bar), _ptr(res.get("q")), _ptr(res.get("qd")),
                                          _ptr(res.get("qdd")), _ptr(res.get("theta")), sp, sb, _stream()))
+    return res
+
+
+def jacobian_vjp(model: Model, q, links, J_bar):
+    """q_bar (nq, B) for the cotangent J_bar (n_links, 6, nv, B) of jacobian()."""
+    B = _check_in(q, model.nq, "q", model)
+    links = [int(l) for l in links]
+    _check_shape(J_bar, (len(links), 6, model.nv, B), "J_bar", model)
+    arr = (ctypes.c_int32 * len(links))(*links)
+    q_bar = _out(None, (model.nq, B), model)
+    check(_ffi.lib().fst_jacobian_vjp(model.handle, B, _ptr(q), arr, len(links), _ptr(J_bar), _ptr(q_bar), _stream()))
+    return q_bar
+
+
+def crba_vjp(model: Model, q, M_bar, theta=None, *, q_bar=True, theta_bar=True, scratch=None):
+    """Cotangents of crba() for M_bar (nv, nv, B): a dict with keys among
+    "q" (nq, B) and "theta" (n_b, 10, summed over environments)."""
+    B = _check_in(q, model.nq, "q", model)
+    _check_shape(M_bar, (model.nv, model.nv, B), "M_bar", model)
+    res = {}
+    if q_bar:
+        res["q"] = _out(None, (model.nq, B), model)
+    if theta_bar:
+        res["theta"] = _out(None, (model.n_bodies, 10), model)
+    sp, sb = _scratch(model, B, scratch) if theta_bar else (None, 0)
+    check(_ffi.lib().fst_crba_vjp(model.handle, B, _ptr(q), _ptr(_theta(theta, model)), _ptr(M_bar),
+                                  _ptr(res.get("q")), _ptr(res.get("theta")), sp, sb, _stream()))
     return res
 
 

@@ -243,6 +243,64 @@ __global__ void __launch_bounds__(256) fk_vjp_kernel(ModelView mv, int64_t B, co
   fk_vjp_env<NB>(sm, cq, cpb, qbar, B, e);
 }
 
+// Jacobian adjoint: Jbar [n_links][6][nv][B] -> q_bar.
+template <int NB>
+__global__ void __launch_bounds__(256) jac_vjp_kernel(ModelView mv, int64_t B, const float* __restrict__ q,
+                                                      LinkList links, const float* __restrict__ Jbar,
+                                                      float* __restrict__ qbar) {
+  extern __shared__ float4 smem[];
+  const int T = blockDim.x;
+  float* tile = smem_tile(smem, mv.n);
+  const int64_t e = (int64_t)blockIdx.x * T + threadIdx.x;
+  const bool act = e < B;
+  Col cq{};
+  if (act) cq = stage_rows(tile, q, mv.nq, B, e);
+  const SmemModel sm = stage_model(mv, smem);
+  if (!act) return;
+  cp_async_wait_all();
+  jac_vjp_env<NB>(sm, cq, mv.nv, links, Jbar, qbar, B, e);
+}
+
+// Mass-matrix adjoint. M e_k = RNEA(q, 0, e_k) without gravity, so for
+// L = sum_rc Mbar_rc M_rc the cotangents are the sum over columns k of the
+// RNEA adjoint at (q, qd = 0, qdd = e_k, no gravity) with taubar = Mbar[:, k];
+// q_bar accumulates in place, thetabar in the per-warp slots.
+template <int NB>
+__global__ void __launch_bounds__(256) crba_vjp_kernel(ModelView mv, int64_t B, const float* __restrict__ q,
+                                                       const float* __restrict__ Mbar, float* qbar, float* partial) {
+  extern __shared__ float4 smem[];
+  const int T = blockDim.x;
+  const int rows = mv.nq + 3 * mv.nv;
+  const int nv = mv.nv;
+  float* tile = smem_tile(smem, mv.n);
+  const int64_t e = (int64_t)blockIdx.x * T + threadIdx.x;
+  const bool act = e < B;
+  const Col cq = stage_or_zero(tile, q, mv.nq, B, e, act);
+  float* zc = tile + mv.nq * T + threadIdx.x;  // qd = 0
+  float* uc = zc + nv * T;                      // qdd = e_k
+  float* tc = uc + nv * T;                      // taubar = Mbar[:, k]
+  for (int k = 0; k < nv; ++k) {
+    zc[k * T] = 0.f;
+    uc[k * T] = 0.f;
+  }
+  float* slots = partial ? theta_slots(smem, mv.n, rows) : nullptr;
+  const int P = mv.n * 10;
+  if (slots) zero_slots(slots, (T / 32) * P);
+  const SmemModel sm = stage_model(mv, smem);
+  cp_async_wait_all();
+  for (int k = 0; k < nv; ++k) {
+    uc[k * T] = 1.f;
+    if (k > 0) uc[(k - 1) * T] = 0.f;
+    for (int i = 0; i < nv; ++i) tc[i * T] = act ? __ldg(Mbar + ((int64_t)i * nv + k) * B + e) : 0.f;
+    VjpOut o{qbar, nullptr, nullptr, slots ? slots + (threadIdx.x / 32) * P : nullptr, 1.f, act, k > 0};
+    rnea_vjp_env<NB>(sm, sv_zero(), cq, Col{zc, T}, Col{uc, T}, Col{tc, T}, o, B, e);
+  }
+  if (partial) {
+    __syncthreads();
+    write_partial(slots, P, partial);
+  }
+}
+
 // out[p] = sum over blocks b (in order) of partial[b * P + p]
 __global__ void partial_reduce_kernel(const float* __restrict__ partial, int nblk, int P, float* __restrict__ out) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
@@ -337,6 +395,28 @@ cudaError_t launch_rnea_loss_grad(const ModelView& mv, int64_t B, const float* q
   cudaError_t err = cudaGetLastError();
   // loss_theta: [n*10] theta gradient followed by the loss
   if (err == cudaSuccess) err = reduce(scratch, (int)grid_for(B, T), mv.n * 10 + 1, loss_theta, s);
+  return err;
+}
+
+cudaError_t launch_jac_vjp(const ModelView& mv, int64_t B, const float* q, const LinkList& links, const float* Jbar,
+                           float* qbar, cudaStream_t s) {
+  const int T = fit_block(B, mv.n, mv.nq, false);
+  const size_t sh = smem_bytes(mv.n, mv.nq, T);
+  FST_NB_DISPATCH(mv.n, prepare(jac_vjp_kernel<NB>, sh);
+                  jac_vjp_kernel<NB><<<grid_for(B, T), T, sh, s>>>(mv, B, q, links, Jbar, qbar));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_crba_vjp(const ModelView& mv, int64_t B, const float* q, const float* Mbar, float* qbar,
+                            float* thbar, float* scratch, cudaStream_t s) {
+  const int rows = mv.nq + 3 * mv.nv;
+  const int T = fit_block(B, mv.n, rows, thbar != nullptr);
+  const size_t sh = vjp_smem(mv.n, rows, T, thbar != nullptr);
+  float* partial = thbar ? scratch : nullptr;
+  FST_NB_DISPATCH(mv.n, prepare(crba_vjp_kernel<NB>, sh);
+                  crba_vjp_kernel<NB><<<grid_for(B, T), T, sh, s>>>(mv, B, q, Mbar, qbar, partial));
+  cudaError_t err = cudaGetLastError();
+  if (err == cudaSuccess && thbar) err = reduce(partial, (int)grid_for(B, T), mv.n * 10, thbar, s);
   return err;
 }
 

@@ -83,10 +83,15 @@ struct VjpOut {
   float* th_warp;    // shared memory [n][10] slot of this warp, or null (no thetabar)
   float sign;        // +1 for RNEA, -1 for the ABA adjoint
   bool active;       // false for padding threads past B: they add nothing
+  bool accumulate = false;  // add to q/qd/qdd bar instead of overwriting them
 };
 
-__device__ __forceinline__ void store_if(float* base, int row, int64_t B, int64_t e, float val, bool active) {
-  if (base && active) base[(int64_t)row * B + e] = val;
+__device__ __forceinline__ void store_if(float* base, int row, int64_t B, int64_t e, float val, bool active,
+                                         bool acc = false) {
+  if (base && active) {
+    float* p = base + (int64_t)row * B + e;
+    *p = acc ? *p + val : val;
+  }
 }
 
 // Reverse sweeps of the RNEA vector-Jacobian product, given the forward
@@ -161,9 +166,9 @@ __device__ __forceinline__ void rnea_vjp_reverse(const TP& tp, SV a0, const Col&
     }
     if (one) {
       qdbi += dot(S, vb[i]);
-      store_if(o.qbar, bi.qi, B, e, o.sign * qbi, o.active);
-      store_if(o.qdbar, bi.vi, B, e, o.sign * qdbi, o.active);
-      store_if(o.qddbar, bi.vi, B, e, o.sign * dot(S, ab[i]), o.active);
+      store_if(o.qbar, bi.qi, B, e, o.sign * qbi, o.active, o.accumulate);
+      store_if(o.qdbar, bi.vi, B, e, o.sign * qdbi, o.active, o.accumulate);
+      store_if(o.qddbar, bi.vi, B, e, o.sign * dot(S, ab[i]), o.active, o.accumulate);
     } else if (bi.type == FST_JOINT_FREE) {
       // a = X a0 + S qdd, v = S qd (no parent): only gravity moves with q
       const f3 g1 = RTmul(c.R0, a0.v);  // R_joint^T a0
@@ -176,11 +181,11 @@ __device__ __forceinline__ void rnea_vjp_reverse(const TP& tp, SV a0, const Col&
       const float vo[6] = {vb[i].v.x, vb[i].v.y, vb[i].v.z, vb[i].w.x, vb[i].w.y, vb[i].w.z};
       const float ao[6] = {ab[i].v.x, ab[i].v.y, ab[i].v.z, ab[i].w.x, ab[i].w.y, ab[i].w.z};
 #pragma unroll
-      for (int r = 0; r < 7; ++r) store_if(o.qbar, bi.qi + r, B, e, o.sign * qo[r], o.active);
+      for (int r = 0; r < 7; ++r) store_if(o.qbar, bi.qi + r, B, e, o.sign * qo[r], o.active, o.accumulate);
 #pragma unroll
       for (int r = 0; r < 6; ++r) {
-        store_if(o.qdbar, bi.vi + r, B, e, o.sign * vo[r], o.active);
-        store_if(o.qddbar, bi.vi + r, B, e, o.sign * ao[r], o.active);
+        store_if(o.qdbar, bi.vi + r, B, e, o.sign * vo[r], o.active, o.accumulate);
+        store_if(o.qddbar, bi.vi + r, B, e, o.sign * ao[r], o.active, o.accumulate);
       }
     }
   }
@@ -277,13 +282,10 @@ __device__ __forceinline__ void ST_col(const TP& tp, int i, SV f, float* col, in
   }
 }
 
-// FK vector-Jacobian product: poses_bar (staged [n][12] column) -> q_bar.
+// World poses of every body (R row-major, p) and the joint transforms.
 template <int NB, class TP>
-__device__ __forceinline__ void fk_vjp_env(const TP& tp, const Col& q, const Col& pbar, float* __restrict__ qbar,
-                                           int64_t B, int64_t e) {
-  float Rw[NB][9];
-  float pw[NB][3];
-  Xf X[NB];
+__device__ __forceinline__ void fk_world(const TP& tp, const Col& q, Xf (&X)[NB], float (&Rw)[NB][9],
+                                         float (&pw)[NB][3]) {
   FST_UNROLL
   for (int i = 0; i < tp.n(); ++i) {
     const BodyI bi = tp.I(i);
@@ -297,15 +299,13 @@ __device__ __forceinline__ void fk_vjp_env(const TP& tp, const Col& q, const Col
       compose(Rw[bi.parent], pw[bi.parent], X[i], Rw[i], pw[i]);
     }
   }
-  float Rb[NB][9];
-  float pb[NB][3];
-  FST_UNROLL
-  for (int i = 0; i < tp.n(); ++i) {
-#pragma unroll
-    for (int k = 0; k < 9; ++k) Rb[i][k] = pbar[12 * i + k];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) pb[i][k] = pbar[12 * i + 9 + k];
-  }
+}
+
+// Reverse of fk_world: world-pose cotangents (Rb, pb; consumed) -> q_bar.
+template <int NB, class TP>
+__device__ __forceinline__ void fk_vjp_core(const TP& tp, const Col& q, const Xf (&X)[NB], const float (&Rw)[NB][9],
+                                            float (&Rb)[NB][9], float (&pb)[NB][3], float* __restrict__ qbar,
+                                            int64_t B, int64_t e) {
   FST_UNROLL
   for (int i = tp.n() - 1; i >= 0; --i) {
     const BodyC& c = tp.C(i);
@@ -364,6 +364,102 @@ __device__ __forceinline__ void fk_vjp_env(const TP& tp, const Col& q, const Col
       for (int r = 0; r < 7; ++r) qbar[(int64_t)(bi.qi + r) * B + e] = out[r];
     }
   }
+}
+
+
+// FK vector-Jacobian product: poses_bar (staged [n][12] column) -> q_bar.
+template <int NB, class TP>
+__device__ __forceinline__ void fk_vjp_env(const TP& tp, const Col& q, const Col& pbar, float* __restrict__ qbar,
+                                           int64_t B, int64_t e) {
+  float Rw[NB][9];
+  float pw[NB][3];
+  Xf X[NB];
+  fk_world<NB>(tp, q, X, Rw, pw);
+  float Rb[NB][9];
+  float pb[NB][3];
+  FST_UNROLL
+  for (int i = 0; i < tp.n(); ++i) {
+#pragma unroll
+    for (int k = 0; k < 9; ++k) Rb[i][k] = pbar[12 * i + k];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) pb[i][k] = pbar[12 * i + 9 + k];
+  }
+  fk_vjp_core<NB>(tp, q, X, Rw, Rb, pb, qbar, B, e);
+}
+
+// Jacobian vector-Jacobian product: Jbar [n_links][6][nv][B] (rows [v; w])
+// -> q_bar. Each column of link l's Jacobian is the world twist of a motion
+// subspace column on l's support path, w = R s_w, v = R s_v + p x w (a free
+// joint: R e_j, and p x R e_a with R e_a); its cotangents (vbar, wbar) give
+// world-pose cotangents wbar' = wbar + vbar x p, pbar += w x vbar,
+// Rbar += vbar s_v^T + wbar' s_w^T, which the FK reverse sweep takes to q.
+template <int NB, class TP>
+__device__ __forceinline__ void jac_vjp_env(const TP& tp, const Col& q, int nv, const LinkList& links,
+                                            const float* __restrict__ Jbar, float* __restrict__ qbar, int64_t B,
+                                            int64_t e) {
+  float Rw[NB][9];
+  float pw[NB][3];
+  Xf X[NB];
+  fk_world<NB>(tp, q, X, Rw, pw);
+  float Rb[NB][9];
+  float pb[NB][3];
+  FST_UNROLL
+  for (int i = 0; i < tp.n(); ++i) {
+#pragma unroll
+    for (int k = 0; k < 9; ++k) Rb[i][k] = 0.f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) pb[i][k] = 0.f;
+  }
+  for (int l = 0; l < links.n; ++l) {
+    const unsigned long long anc = tp.C(links.idx[l]).anc;
+    const float* Jl = Jbar + (int64_t)l * 6 * nv * B + e;
+    FST_UNROLL
+    for (int k = 0; k < tp.n(); ++k) {
+      if (!((anc >> k) & 1ull)) continue;
+      const BodyI bk = tp.I(k);
+      const int nvk = nv_of(bk.type);
+      const f3 p = f3{pw[k][0], pw[k][1], pw[k][2]};
+      for (int j = 0; j < nvk; ++j) {
+        const int c = bk.vi + j;
+        const f3 vb = f3{__ldg(Jl + ((int64_t)0 * nv + c) * B), __ldg(Jl + ((int64_t)1 * nv + c) * B),
+                         __ldg(Jl + ((int64_t)2 * nv + c) * B)};
+        const f3 wb = f3{__ldg(Jl + ((int64_t)3 * nv + c) * B), __ldg(Jl + ((int64_t)4 * nv + c) * B),
+                         __ldg(Jl + ((int64_t)5 * nv + c) * B)};
+        f3 sw, sv;
+        if (bk.type == FST_JOINT_FREE) {
+          sw = f3{0.f, 0.f, 0.f};
+          sv = sw;
+          if (j < 3) {
+            (j == 0 ? sv.x : j == 1 ? sv.y : sv.z) = 1.f;
+          } else {
+            (j == 3 ? sw.x : j == 4 ? sw.y : sw.z) = 1.f;
+          }
+        } else {
+          const SV s = S_of(tp.C(k));
+          sw = s.w;
+          sv = s.v;
+        }
+        const f3 w = f3{fmaf(Rw[k][0], sw.x, fmaf(Rw[k][1], sw.y, Rw[k][2] * sw.z)),
+                        fmaf(Rw[k][3], sw.x, fmaf(Rw[k][4], sw.y, Rw[k][5] * sw.z)),
+                        fmaf(Rw[k][6], sw.x, fmaf(Rw[k][7], sw.y, Rw[k][8] * sw.z))};
+        const bool free_lin = bk.type == FST_JOINT_FREE && j < 3;
+        const f3 wb2 = free_lin ? wb : wb + cross(vb, p);
+        if (!free_lin) {
+          const f3 dp = cross(w, vb);
+          pb[k][0] += dp.x;
+          pb[k][1] += dp.y;
+          pb[k][2] += dp.z;
+        }
+        const float va[3] = {vb.x, vb.y, vb.z}, wa[3] = {wb2.x, wb2.y, wb2.z};
+        const float svb[3] = {sv.x, sv.y, sv.z}, swb[3] = {sw.x, sw.y, sw.z};
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+          for (int b = 0; b < 3; ++b) Rb[k][3 * a + b] += fmaf(va[a], svb[b], wa[a] * swb[b]);
+      }
+    }
+  }
+  fk_vjp_core<NB>(tp, q, X, Rw, Rb, pb, qbar, B, e);
 }
 
 }  // namespace fst

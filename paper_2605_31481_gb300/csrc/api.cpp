@@ -524,6 +524,46 @@ fst_status fst_rnea_vjp_stored(const fst_model* m, int64_t B, const float* q, co
                                            (float*)scratch, (cudaStream_t)stream));
 }
 
+fst_status fst_jacobian_vjp(const fst_model* m, int64_t B, const float* q, const int32_t* links, int32_t n_links,
+                            const float* J_bar, float* q_bar, void* stream) {
+  static const char* fn = "fst_jacobian_vjp";
+  if (!links && n_links) return set_error(FST_ERR_INVALID_ARG, "fst_jacobian_vjp: null links");
+  if (n_links < 1 || n_links > FST_MAX_LINKS)
+    return set_error(FST_ERR_INVALID_ARG, "fst_jacobian_vjp: n_links must be in [1, FST_MAX_LINKS]");
+  bool skip;
+  FST_CHECK(check_call(fn, m, B, &skip));
+  LinkList L{};
+  L.n = n_links;
+  for (int l = 0; l < n_links; ++l) {
+    if (links[l] < 0 || links[l] >= m->n)
+      return set_error(FST_ERR_INVALID_ARG, "fst_jacobian_vjp: link index out of range");
+    L.idx[l] = links[l];
+  }
+  if (skip) return FST_OK;
+  FST_CHECK(need(fn, q, "q"));
+  FST_CHECK(need(fn, q_bar, "q_bar"));
+  if (m->nv == 0) return finish(fn, cudaMemsetAsync(q_bar, 0, sizeof(float) * m->nq * (size_t)B, (cudaStream_t)stream));
+  FST_CHECK(need(fn, J_bar, "J_bar"));
+  return finish(fn, launch_jac_vjp(view_of(m, nullptr), B, q, L, J_bar, q_bar, (cudaStream_t)stream));
+}
+
+fst_status fst_crba_vjp(const fst_model* m, int64_t B, const float* q, const float* theta, const float* M_bar,
+                        float* q_bar, float* theta_bar, void* scratch, size_t scratch_bytes, void* stream) {
+  static const char* fn = "fst_crba_vjp";
+  bool skip;
+  FST_CHECK(check_call(fn, m, B, &skip));
+  if (theta_bar) FST_CHECK(need_scratch(fn, m, B, scratch, scratch_bytes));
+  if (skip || m->nv == 0) {
+    if (theta_bar && m->n) cudaMemsetAsync(theta_bar, 0, sizeof(float) * m->n * 10, (cudaStream_t)stream);
+    if (q_bar && m->nq && B > 0) cudaMemsetAsync(q_bar, 0, sizeof(float) * m->nq * (size_t)B, (cudaStream_t)stream);
+    return FST_OK;
+  }
+  FST_CHECK(need(fn, q, "q"));
+  FST_CHECK(need(fn, M_bar, "M_bar"));
+  return finish(fn, launch_crba_vjp(view_of(m, theta), B, q, M_bar, q_bar, theta_bar, (float*)scratch,
+                                    (cudaStream_t)stream));
+}
+
 fst_status fst_rnea_derivatives(const fst_model* m, int64_t B, const float* q, const float* qd, const float* qdd,
                                 const float* theta, float* dtau_dq, float* dtau_dqd, void* stream) {
   static const char* fn = "fst_rnea_derivatives";

@@ -127,6 +127,10 @@ cudaError_t launch_rnea_derivs(const ModelView& mv, int64_t B, const float* q, c
                                float* dq, float* dqd, const Launch& L);
 cudaError_t launch_aba_derivs(const ModelView& mv, int64_t B, const float* q, const float* qd, const float* tau,
                               float* qdd, float* dq, float* dqd, float* Minv, const Launch& L);
+cudaError_t launch_jac_vjp(const ModelView& mv, int64_t B, const float* q, const LinkList& links, const float* Jbar,
+                           float* qbar, cudaStream_t s);
+cudaError_t launch_crba_vjp(const ModelView& mv, int64_t B, const float* q, const float* Mbar, float* qbar,
+                            float* thbar, float* scratch, cudaStream_t s);
 cudaError_t launch_aba_vjp(const ModelView& mv, int64_t B, const float* q, const float* qd, const float* qdd,
                            const float* qddbar, float* qbar, float* qdbar, float* taubar, float* thbar, float* scratch,
                            cudaStream_t s);
