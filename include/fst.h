@@ -172,6 +172,16 @@ FST_API fst_status fst_model_specialize(fst_model* model, uint32_t kinds);
  * FK/Jacobian) level-parallel where that operator's own kind is set to LEVEL
  * and one environment per thread otherwise. */
 #define FST_VARIANT_MIXED 4
+/* FK, Jacobian, RNEA, CRBA, ABA and eval of a specialised model: the
+ * path-parallel mapping. Every root-to-leaf path of the tree gets its own
+ * lane (G = the number of paths rounded up to a power of two, at most 8
+ * lanes per environment, 32 / G environments per warp); a lane sweeps its
+ * path with the sweep state in registers, bodies shared by several paths
+ * are computed by each of them, and the leaf-to-root sums over a body's
+ * children are warp shuffles. The serial chain per environment is the tree
+ * depth instead of the body count. Needs fst_model_specialize of the kind;
+ * trees with more than 8 leaves have no path-parallel kernels. */
+#define FST_VARIANT_PATH 5
 FST_API fst_status fst_model_set_launch(fst_model* model, uint32_t kinds, int32_t block, int32_t variant);
 
 /* Shared-memory carveout (percent of the unified L1/shared storage given to

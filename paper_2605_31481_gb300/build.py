@@ -36,7 +36,7 @@ def nvcc_path() -> str:
 
 # Device headers embedded into the library for run-time specialisation
 # (NVRTC compiles them again for one fixed tree; see csrc/jit.cpp).
-JIT_HEADERS = ["fst_layout.h", "fst_device.cuh", "ops.cuh", "adjoint.cuh", "derivs.cuh", "level.cuh", "jit_kernels.cuh"]
+JIT_HEADERS = ["fst_layout.h", "fst_device.cuh", "ops.cuh", "adjoint.cuh", "derivs.cuh", "level.cuh", "pathpar.cuh", "jit_kernels.cuh"]
 EMBED = "jit_embed.cpp"
 
 

@@ -76,6 +76,24 @@ bool use_level(const fst_model* m, int kind, int level_kind) {
   return m->variant[kind] == FST_VARIANT_LEVEL && level_smem_needed(view_of(m, nullptr), level_kind) <= kLevelSmemLimit;
 }
 
+// Whether a call of this kind runs the path-parallel kernel.
+bool use_path(const fst_model* m, int kind) {
+  return m->variant[kind] == FST_VARIANT_PATH && jit_has_path(m, kind);
+}
+
+// Launches a path-parallel kernel: G lanes per environment, so a block of T
+// threads serves (T / 32) * (32 / G) environments; `rows` staged input rows
+// per environment; gy = blockIdx.y extent.
+template <typename... A>
+cudaError_t path_go(const fst_model* m, int kind, int64_t B, int rows, unsigned gy, cudaStream_t s, A... args) {
+  const int T = m->block[kind] ? m->block[kind] : 128;
+  const int G = jit_path_lanes(m);
+  const int EPB = (T / 32) * (32 / G);
+  const dim3 grid((unsigned)((B + EPB - 1) / EPB), gy);
+  void* argv[] = {(void*)&args...};
+  return jit_launch_path(m, kind, grid, T, (size_t)rows * EPB * sizeof(float), s, argv);
+}
+
 // Threads per block of a level-parallel launch: a multiple of 32 (one warp
 // per share of a level), 32 environments per block.
 int level_block(const fst_model* m, int kind) { return m->block[kind] ? m->block[kind] : 128; }
@@ -183,10 +201,11 @@ fst_status fst_model_set_launch(fst_model* m, uint32_t kinds, int32_t block, int
   if (!m) return set_error(FST_ERR_INVALID_ARG, "fst_model_set_launch: null model");
   if (block != 0 && block != 32 && block != 64 && block != 128 && block != 256)
     return set_error(FST_ERR_INVALID_ARG, "fst_model_set_launch: block must be 0, 32, 64, 128 or 256");
-  if (variant < FST_VARIANT_AUTO || variant > FST_VARIANT_MIXED)
+  if (variant < FST_VARIANT_AUTO || variant > FST_VARIANT_PATH)
     return set_error(FST_ERR_INVALID_ARG, "fst_model_set_launch: unknown variant");
-  // "all kinds" with the level variant means every kind that has one
-  if (kinds == 0) kinds = variant == FST_VARIANT_LEVEL ? (1u << (JK_EVAL + 1)) - 1u : FST_SPEC_ALL;
+  // "all kinds" with the level or path variant means every kind that has one
+  if (kinds == 0)
+    kinds = (variant == FST_VARIANT_LEVEL || variant == FST_VARIANT_PATH) ? (1u << (JK_EVAL + 1)) - 1u : FST_SPEC_ALL;
   if (kinds & ~(uint32_t)FST_SPEC_ALL) return set_error(FST_ERR_INVALID_ARG, "fst_model_set_launch: unknown kind bits");
   for (int k = 0; k < JK_COUNT; ++k) {
     if (((kinds >> k) & 1u) && variant == FST_VARIANT_MIXED && k != JK_EVAL)
@@ -195,6 +214,10 @@ fst_status fst_model_set_launch(fst_model* m, uint32_t kinds, int32_t block, int
       return set_error(FST_ERR_INVALID_ARG, "fst_model_set_launch: a selected kind is not specialised yet");
     if (((kinds >> k) & 1u) && variant == FST_VARIANT_MIXED && !jit_has(m, JK_EVAL_MIXED))
       return set_error(FST_ERR_INVALID_ARG, "fst_model_set_launch: a selected kind is not specialised yet");
+    if (((kinds >> k) & 1u) && variant == FST_VARIANT_PATH && !jit_has_path(m, k))
+      return set_error(FST_ERR_INVALID_ARG, "fst_model_set_launch: no path-parallel kernel for a selected kind "
+                                            "(specialise FK, Jacobian, RNEA, CRBA, ABA or eval first; trees with "
+                                            "more than 8 leaves have none)");
     if (((kinds >> k) & 1u) && variant == FST_VARIANT_LEVEL && k > JK_EVAL)
       return set_error(FST_ERR_INVALID_ARG, "fst_model_set_launch: the level-parallel variant exists for FK, "
                                             "Jacobian, RNEA, CRBA, ABA and eval only");
@@ -239,6 +262,8 @@ fst_status fst_fk(const fst_model* m, int64_t B, const float* q, float* poses, v
   const ModelView mv = view_of(m, nullptr);
   if (use_level(m, JK_FK, LEVEL_FK))
     return finish(fn, launch_fk_level(mv, B, q, poses, level_block(m, JK_FK), (cudaStream_t)stream));
+  if (use_path(m, JK_FK))
+    return finish(fn, path_go(m, JK_FK, B, m->nq, 1, (cudaStream_t)stream, mv, B, q, poses));
   if (use_jit(m, JK_FK))
     return finish(fn, jit_go(m, JK_FK, B, m->nq, 0, 1, (cudaStream_t)stream, nullptr, mv, B, q, poses));
   return finish(fn, launch_fk(mv, B, q, poses, launch_of(m, JK_FK, B, stream)));
@@ -264,6 +289,8 @@ fst_status fst_jacobian(const fst_model* m, int64_t B, const float* q, const int
   const ModelView mv = view_of(m, nullptr);
   if (use_level(m, JK_JACOBIAN, LEVEL_JAC))
     return finish(fn, launch_jac_level(mv, B, q, L, J, level_block(m, JK_JACOBIAN), (cudaStream_t)stream));
+  if (use_path(m, JK_JACOBIAN))
+    return finish(fn, path_go(m, JK_JACOBIAN, B, m->nq, 1, (cudaStream_t)stream, mv, B, q, L, J));
   if (use_jit(m, JK_JACOBIAN))
     return finish(fn, jit_go(m, JK_JACOBIAN, B, m->nq, 0, 1, (cudaStream_t)stream, nullptr, mv, B, q, L, J));
   return finish(fn, launch_jacobian(mv, B, q, L, J, launch_of(m, JK_JACOBIAN, B, stream)));
@@ -282,6 +309,8 @@ fst_status fst_rnea(const fst_model* m, int64_t B, const float* q, const float* 
   const ModelView mv = view_of(m, theta);
   if (use_level(m, JK_RNEA, LEVEL_RNEA))
     return finish(fn, launch_rnea_level(mv, B, q, qd, qdd, tau, level_block(m, JK_RNEA), (cudaStream_t)stream));
+  if (use_path(m, JK_RNEA))
+    return finish(fn, path_go(m, JK_RNEA, B, m->nq + 2 * m->nv, 1, (cudaStream_t)stream, mv, B, q, qd, qdd, tau));
   if (use_jit(m, JK_RNEA))
     return finish(fn, jit_go(m, JK_RNEA, B, m->nq + 2 * m->nv, 0, 1, (cudaStream_t)stream, nullptr, mv, B, q, qd,
                              qdd, tau));
@@ -298,6 +327,8 @@ fst_status fst_crba(const fst_model* m, int64_t B, const float* q, const float* 
   const ModelView mv = view_of(m, theta);
   if (use_level(m, JK_CRBA, LEVEL_CRBA))
     return finish(fn, launch_crba_level(mv, B, q, M, level_block(m, JK_CRBA), (cudaStream_t)stream));
+  if (use_path(m, JK_CRBA))
+    return finish(fn, path_go(m, JK_CRBA, B, m->nq, 1, (cudaStream_t)stream, mv, B, q, M));
   if (use_jit(m, JK_CRBA))
     return finish(fn, jit_go(m, JK_CRBA, B, m->nq, 0, 1, (cudaStream_t)stream, nullptr, mv, B, q, M));
   return finish(fn, launch_crba(mv, B, q, M, launch_of(m, JK_CRBA, B, stream)));
@@ -316,6 +347,8 @@ fst_status fst_aba(const fst_model* m, int64_t B, const float* q, const float* q
   const ModelView mv = view_of(m, theta);
   if (use_level(m, JK_ABA, LEVEL_ABA))
     return finish(fn, launch_aba_level(mv, B, q, qd, tau, qdd, level_block(m, JK_ABA), (cudaStream_t)stream));
+  if (use_path(m, JK_ABA))
+    return finish(fn, path_go(m, JK_ABA, B, m->nq + 2 * m->nv, 1, (cudaStream_t)stream, mv, B, q, qd, tau, qdd));
   if (use_jit(m, JK_ABA))
     return finish(fn, jit_go(m, JK_ABA, B, m->nq + 2 * m->nv, 0, 1, (cudaStream_t)stream, nullptr, mv, B, q, qd,
                              tau, qdd));
@@ -399,6 +432,8 @@ fst_status fst_eval(const fst_model* m, int64_t B, const fst_eval_io* io, const 
     return finish(fn, jit_launch(m, JK_EVAL_MIXED, dim3((unsigned)gx, (unsigned)a.n_roles), T, sh,
                                  (cudaStream_t)stream, argv));
   }
+  if (use_path(m, JK_EVAL))
+    return finish(fn, path_go(m, JK_EVAL, B, m->nq + 2 * m->nv, (unsigned)a.n_roles, (cudaStream_t)stream, mv, B, a));
   if (use_jit(m, JK_EVAL))
     return finish(fn, jit_go(m, JK_EVAL, B, m->nq + 2 * m->nv, 0, (unsigned)a.n_roles, (cudaStream_t)stream, nullptr,
                              mv, B, a));

@@ -134,10 +134,88 @@ void put_floats(std::ostringstream& os, const float* p, int n) {
   os << "}";
 }
 
+// Root-to-leaf paths of the tree in depth-first order (so the paths through
+// any body are adjacent), for the path-parallel kernels. Returns the lane
+// count G (the number of paths rounded up to a power of two), or 0 when the
+// tree has more than 8 leaves.
+struct PathTables {
+  int G = 0;
+  std::vector<int> path;   // [G][depth], -1 past a path's end
+  std::vector<int> seg;    // [G][depth], lo | hi << 8
+  std::vector<unsigned> lead;  // [G], bit t: first lane holding that body
+  std::vector<int> red;    // [depth]
+  std::vector<int> owner;  // [n]
+  std::vector<int> depth_of;  // [n]
+};
+
+PathTables path_tables(const fst_model* m) {
+  PathTables P;
+  const TopoLists& T = m->ht;
+  const int D = m->depth;
+  std::vector<std::vector<int>> paths;
+  std::vector<int> cur;
+  // iterative depth-first walk from every root, children in list order
+  std::vector<std::pair<int, int>> stack;  // (body, next child position)
+  for (int r = 0; r < m->n; ++r) {
+    if (m->hi[r].parent >= 0) continue;
+    stack.push_back({r, T.child_start[r]});
+    cur.push_back(r);
+    while (!stack.empty()) {
+      auto& top = stack.back();
+      const int b = top.first;
+      if (T.child_start[b] == T.child_start[b + 1] && top.second == T.child_start[b]) {
+        paths.push_back(cur);
+        top.second = -1;  // mark done
+      }
+      if (top.second >= 0 && top.second < T.child_start[b + 1]) {
+        const int c = T.child[top.second++];
+        stack.push_back({c, T.child_start[c]});
+        cur.push_back(c);
+        continue;
+      }
+      stack.pop_back();
+      cur.pop_back();
+    }
+  }
+  const int n_paths = (int)paths.size();
+  if (n_paths == 0 || n_paths > 8) return P;
+  int G = 1;
+  while (G < n_paths) G *= 2;
+  P.G = G;
+  P.path.assign((size_t)G * D, -1);
+  for (int g = 0; g < n_paths; ++g)
+    for (int t = 0; t < (int)paths[g].size(); ++t) P.path[(size_t)g * D + t] = paths[g][t];
+  P.seg.assign((size_t)G * D, 0);
+  P.lead.assign(G, 0u);
+  P.red.assign(D, 0);
+  P.owner.assign(m->n, 0);
+  P.depth_of.assign(m->n, 0);
+  for (int g = 0; g < G; ++g)
+    for (int t = 0; t < D; ++t) {
+      const int b = P.path[(size_t)g * D + t];
+      int lo = g, hi = g + 1;
+      if (b >= 0) {
+        while (lo > 0 && P.path[(size_t)(lo - 1) * D + t] == b) --lo;
+        while (hi < G && P.path[(size_t)hi * D + t] == b) ++hi;
+        if (lo == g) {
+          P.lead[g] |= 1u << t;
+          P.owner[b] = g;
+          P.depth_of[b] = t;
+        }
+      }
+      P.seg[(size_t)g * D + t] = lo | (hi << 8);
+    }
+  for (int b = 0; b < m->n; ++b) {
+    const int nc = T.child_start[b + 1] - T.child_start[b];
+    if (nc > 1) P.red[P.depth_of[b]] = 1;
+  }
+  return P;
+}
+
 std::string make_source(const fst_model* m, int kind) {
   std::ostringstream os;
   os << "#define FST_FIXED_TOPOLOGY 1\n#define FST_N " << m->n << "\n#define " << kKindMacro[kind] << " 1\n"
-     << "#define FST_JIT_NAME " << kKindName[kind] << "\n"
+     << "#define FST_JIT_NAME " << kKindName[kind] << "\n#define FST_JIT_PATH_NAME " << kKindName[kind] << "_path\n"
      << "#include \"fst_layout.h\"\nnamespace fst {\nstatic __device__ const BodyC kC[" << m->n << "] = {\n";
   for (int i = 0; i < m->n; ++i) {
     const BodyC& c = m->hc[i];
@@ -176,7 +254,19 @@ std::string make_source(const fst_model* m, int kind) {
   ints("kLevelBody", T.level_body, m->n);
   ints("kChildStart", T.child_start, m->n + 1);
   ints("kChild", T.child, T.child_start[m->n]);
-  os << "}  // namespace fst\n#define FST_DEPTH " << m->depth << "\n#include \"jit_kernels.cuh\"\n";
+  const PathTables P = path_tables(m);
+  if (P.G > 0) {
+    ints("kPath", P.path.data(), (int)P.path.size());
+    ints("kSeg", P.seg.data(), (int)P.seg.size());
+    os << "static __device__ const unsigned kLead[" << P.G << "] = {";
+    for (int g = 0; g < P.G; ++g) os << (g ? "," : "") << P.lead[g] << "u";
+    os << "};\n";
+    ints("kRed", P.red.data(), (int)P.red.size());
+    ints("kOwner", P.owner.data(), m->n);
+    ints("kDepthOf", P.depth_of.data(), m->n);
+  }
+  os << "}  // namespace fst\n#define FST_DEPTH " << m->depth << "\n#define FST_PATH_G " << P.G
+     << "\n#include \"jit_kernels.cuh\"\n";
   return os.str();
 }
 
@@ -267,8 +357,11 @@ void compile_one(CompileJob& job, const std::string& arch_opt) {
 struct JitState {
   CUmodule mod[JK_COUNT] = {};
   CUfunction fn[JK_COUNT] = {};
+  CUfunction fn_path[JK_COUNT] = {};  // path-parallel kernel of the same module, if any
   int smem_limit[JK_COUNT] = {};
   int carveout_set[JK_COUNT] = {};
+  int path_carveout_set[JK_COUNT] = {};
+  int path_G = 0;
 };
 
 fst_status jit_specialize(fst_model* m, unsigned mask) {
@@ -304,7 +397,11 @@ fst_status jit_specialize(fst_model* m, unsigned mask) {
     }
     m->jit->mod[j.kind] = mod;
     m->jit->fn[j.kind] = fn;
+    CUfunction fp;
+    const std::string pname = std::string(kKindName[j.kind]) + "_path";
+    if (D.get(&fp, mod, pname.c_str()) == CUDA_SUCCESS) m->jit->fn_path[j.kind] = fp;
   }
+  m->jit->path_G = path_tables(m).G;
   return FST_OK;
 }
 
@@ -326,6 +423,30 @@ unsigned jit_mask(const fst_model* m) {
 }
 
 bool jit_has(const fst_model* m, int kind) { return m->jit && m->jit->fn[kind]; }
+
+bool jit_has_path(const fst_model* m, int kind) { return m->jit && m->jit->fn_path[kind]; }
+
+int jit_path_lanes(const fst_model* m) { return m->jit ? m->jit->path_G : 0; }
+
+cudaError_t jit_launch_path(const fst_model* m, int kind, dim3 grid, int block, size_t smem, cudaStream_t s,
+                            void** args) {
+  const Driver& D = driver();
+  JitState* J = m->jit;
+  if (smem > 48 * 1024) return cudaErrorInvalidValue;  // the staged tile is a few KB
+  const int gen = carveout_generation() + 1;
+  if (J->path_carveout_set[kind] != gen) {
+    int pct = -1;
+    if (const char* env = std::getenv("FST_SMEM_CARVEOUT")) pct = std::atoi(env);
+    if (carveout_override() >= 0) pct = carveout_override();
+    pct = pct < -1 ? -1 : (pct > 100 ? 100 : pct);
+    if (pct >= 0 || J->path_carveout_set[kind] != 0)
+      D.set_attr(J->fn_path[kind], CU_FUNC_ATTRIBUTE_PREFERRED_SHARED_MEMORY_CARVEOUT, pct);
+    J->path_carveout_set[kind] = gen;
+  }
+  const CUresult r = D.launch(J->fn_path[kind], grid.x, grid.y, grid.z, (unsigned)block, 1, 1, (unsigned)smem,
+                              (CUstream)s, args, nullptr);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorLaunchFailure;
+}
 
 cudaError_t jit_launch(const fst_model* m, int kind, dim3 grid, int block, size_t smem, cudaStream_t s, void** args) {
   const Driver& D = driver();

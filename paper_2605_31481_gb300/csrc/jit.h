@@ -27,11 +27,17 @@ enum JitKind {
   JK_ABA_DERIVS,
   JK_COUNT
 };
+static_assert(JK_COUNT <= 16, "fst_model keeps 16 launch slots");
 
 fst_status jit_specialize(fst_model* m, unsigned mask);
 void jit_release(fst_model* m);
 unsigned jit_mask(const fst_model* m);
 bool jit_has(const fst_model* m, int kind);
+// Path-parallel kernels: present for a kind, and the lanes per environment.
+bool jit_has_path(const fst_model* m, int kind);
+int jit_path_lanes(const fst_model* m);
+cudaError_t jit_launch_path(const fst_model* m, int kind, dim3 grid, int block, size_t smem, cudaStream_t s,
+                            void** args);
 cudaError_t jit_launch(const fst_model* m, int kind, dim3 grid, int block, size_t smem, cudaStream_t s, void** args);
 
 }  // namespace fst

@@ -14,6 +14,7 @@
 #include "adjoint.cuh"
 #include "derivs.cuh"
 #include "level.cuh"
+#include "pathpar.cuh"
 
 namespace fst {
 
@@ -29,6 +30,15 @@ struct FixedTopo {
   __device__ __forceinline__ int level_body(int k) const { return kLevelBody[k]; }
   __device__ __forceinline__ int child_begin(int k) const { return kChildStart[k]; }
   __device__ __forceinline__ int child(int k) const { return kChild[k]; }
+#if FST_PATH_G > 0
+  // root-to-leaf paths, one per lane (path-parallel variant)
+  __device__ __forceinline__ int path(int g, int t) const { return kPath[g * FST_DEPTH + t]; }
+  __device__ __forceinline__ int seg(int g, int t) const { return kSeg[g * FST_DEPTH + t]; }
+  __device__ __forceinline__ unsigned lead_mask(int g) const { return kLead[g]; }
+  __device__ __forceinline__ bool red(int t) const { return kRed[t] != 0; }
+  __device__ __forceinline__ int owner(int i) const { return kOwner[i]; }
+  __device__ __forceinline__ int depth_of(int i) const { return kDepthOf[i]; }
+#endif
 };
 
 __device__ __forceinline__ FixedTopo fixed_topo(const ModelView& mv) {
@@ -449,3 +459,129 @@ extern "C" __global__ void __launch_bounds__(256) FST_JIT_NAME(ModelView mv, int
   jit_write_partial(slots, P, partial);
 }
 #endif
+
+// ---- path-parallel kernels (FST_VARIANT_PATH), one per operator module ------
+#if FST_PATH_G > 0
+#define FST_PATH_PROLOGUE                                                  \
+  extern __shared__ float4 smem[];                                        \
+  float* tile = reinterpret_cast<float*>(smem);                           \
+  constexpr int G = FST_PATH_G;                                           \
+  constexpr int D = FST_DEPTH;                                            \
+  const PathLane<G> L;                                                    \
+  const int EPB = (int)(blockDim.x >> 5) * PathLane<G>::E;                \
+  const int eb = (int)(threadIdx.x >> 5) * PathLane<G>::E + L.es;         \
+  const int64_t e0 = (int64_t)blockIdx.x * EPB;                           \
+  const int64_t e = e0 + eb;                                              \
+  const bool act = e < B;                                                 \
+  const FixedTopo tp = fixed_topo(mv);                                    \
+  const LanePath<D> lp = lane_path<G, D>(tp, L.g)
+
+#define FST_PATH_READY \
+  cp_async_wait_all(); \
+  __syncthreads()
+
+#define FST_PATH_COL(r) (Col{tile + (r)*EPB + eb, EPB})
+
+#ifdef FST_JIT_FK
+extern "C" __global__ void __launch_bounds__(256) FST_JIT_PATH_NAME(ModelView mv, int64_t B,
+                                                                      const float* __restrict__ q,
+                                                                      float* __restrict__ poses) {
+  FST_PATH_PROLOGUE;
+  path_stage(tile, q, mv.nq, B, e0, EPB);
+  FST_PATH_READY;
+  Xf P[D];
+  fk_path<G, D>(tp, lp, FST_PATH_COL(0), P, poses, B, e, act);
+}
+#endif
+
+#ifdef FST_JIT_JACOBIAN
+extern "C" __global__ void __launch_bounds__(256) FST_JIT_PATH_NAME(ModelView mv, int64_t B,
+                                                                      const float* __restrict__ q, LinkList links,
+                                                                      float* __restrict__ J) {
+  FST_PATH_PROLOGUE;
+  path_stage(tile, q, mv.nq, B, e0, EPB);
+  FST_PATH_READY;
+  Xf P[D];
+  fk_path<G, D>(tp, lp, FST_PATH_COL(0), P, nullptr, B, e, act);
+  jac_path<G, D>(tp, L, P, mv.nv, links, J, B, e, act);
+}
+#endif
+
+#ifdef FST_JIT_RNEA
+extern "C" __global__ void __launch_bounds__(256) FST_JIT_PATH_NAME(ModelView mv, int64_t B,
+                                                                      const float* __restrict__ q,
+                                                                      const float* __restrict__ qd,
+                                                                      const float* __restrict__ qdd,
+                                                                      float* __restrict__ tau) {
+  FST_PATH_PROLOGUE;
+  path_stage(tile, q, mv.nq, B, e0, EPB);
+  path_stage(tile + mv.nq * EPB, qd, mv.nv, B, e0, EPB);
+  path_stage(tile + (mv.nq + mv.nv) * EPB, qdd, mv.nv, B, e0, EPB);
+  FST_PATH_READY;
+  rnea_path<G, D>(tp, L, lp, world_accel(mv), FST_PATH_COL(0), FST_PATH_COL(mv.nq), FST_PATH_COL(mv.nq + mv.nv),
+                  tau, B, e, act);
+}
+#endif
+
+#ifdef FST_JIT_CRBA
+extern "C" __global__ void __launch_bounds__(256) FST_JIT_PATH_NAME(ModelView mv, int64_t B,
+                                                                      const float* __restrict__ q,
+                                                                      float* __restrict__ M) {
+  FST_PATH_PROLOGUE;
+  path_stage(tile, q, mv.nq, B, e0, EPB);
+  FST_PATH_READY;
+  crba_path<G, D>(tp, L, lp, FST_PATH_COL(0), mv.nv, M, B, e, act);
+}
+#endif
+
+#ifdef FST_JIT_ABA
+extern "C" __global__ void __launch_bounds__(256) FST_JIT_PATH_NAME(ModelView mv, int64_t B,
+                                                                      const float* __restrict__ q,
+                                                                      const float* __restrict__ qd,
+                                                                      const float* __restrict__ tau,
+                                                                      float* __restrict__ qdd) {
+  FST_PATH_PROLOGUE;
+  path_stage(tile, q, mv.nq, B, e0, EPB);
+  path_stage(tile + mv.nq * EPB, qd, mv.nv, B, e0, EPB);
+  path_stage(tile + (mv.nq + mv.nv) * EPB, tau, mv.nv, B, e0, EPB);
+  FST_PATH_READY;
+  aba_path<G, D>(tp, L, lp, world_accel(mv), FST_PATH_COL(0), FST_PATH_COL(mv.nq), FST_PATH_COL(mv.nq + mv.nv), qdd,
+                 B, e, act);
+}
+#endif
+
+#ifdef FST_JIT_EVAL
+// Roles on blockIdx.y, each path-parallel.
+extern "C" __global__ void __launch_bounds__(256) FST_JIT_PATH_NAME(ModelView mv, int64_t B, EvalArgs a) {
+  FST_PATH_PROLOGUE;
+  const int role = a.roles[blockIdx.y];
+  path_stage(tile, a.q, mv.nq, B, e0, EPB);
+  if (role == ROLE_RNEA) {
+    path_stage(tile + mv.nq * EPB, a.qd, mv.nv, B, e0, EPB);
+    path_stage(tile + (mv.nq + mv.nv) * EPB, a.qdd, mv.nv, B, e0, EPB);
+  } else if (role == ROLE_ABA) {
+    path_stage(tile + mv.nq * EPB, a.qd, mv.nv, B, e0, EPB);
+    path_stage(tile + (mv.nq + mv.nv) * EPB, a.tau, mv.nv, B, e0, EPB);
+  }
+  FST_PATH_READY;
+  const Col cq = FST_PATH_COL(0), c1 = FST_PATH_COL(mv.nq), c2 = FST_PATH_COL(mv.nq + mv.nv);
+  switch (role) {
+    case ROLE_ABA:
+      aba_path<G, D>(tp, L, lp, world_accel(mv), cq, c1, c2, a.qdd_out, B, e, act);
+      break;
+    case ROLE_CRBA:
+      crba_path<G, D>(tp, L, lp, cq, mv.nv, a.M, B, e, act);
+      break;
+    case ROLE_RNEA:
+      rnea_path<G, D>(tp, L, lp, world_accel(mv), cq, c1, c2, a.tau_out, B, e, act);
+      break;
+    default: {
+      Xf P[D];
+      fk_path<G, D>(tp, lp, cq, P, a.poses, B, e, act);
+      if (a.J) jac_path<G, D>(tp, L, P, mv.nv, a.links, a.J, B, e, act);
+      break;
+    }
+  }
+}
+#endif
+#endif  // FST_PATH_G > 0
