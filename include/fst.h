@@ -182,6 +182,12 @@ FST_API fst_status fst_model_specialize(fst_model* model, uint32_t kinds);
  * depth instead of the body count. Needs fst_model_specialize of the kind;
  * trees with more than 8 leaves have no path-parallel kernels. */
 #define FST_VARIANT_PATH 5
+/* The same sweeps with a warp per path: blocks of 32 environments (one per
+ * lane) and one warp per root-to-leaf path, each warp running code compiled
+ * for its own path; the paths meet through shared memory, with one block
+ * barrier per depth where paths join. The block size is fixed by the tree
+ * (32 x number of paths); the block argument is ignored. */
+#define FST_VARIANT_PATH_WARP 6
 FST_API fst_status fst_model_set_launch(fst_model* model, uint32_t kinds, int32_t block, int32_t variant);
 
 /* Shared-memory carveout (percent of the unified L1/shared storage given to

@@ -76,22 +76,35 @@ bool use_level(const fst_model* m, int kind, int level_kind) {
   return m->variant[kind] == FST_VARIANT_LEVEL && level_smem_needed(view_of(m, nullptr), level_kind) <= kLevelSmemLimit;
 }
 
-// Whether a call of this kind runs the path-parallel kernel.
-bool use_path(const fst_model* m, int kind) {
-  return m->variant[kind] == FST_VARIANT_PATH && jit_has_path(m, kind);
+// The path-parallel kernel slot a call of this kind runs (0: none): 1 for
+// FST_VARIANT_PATH (a lane per path), 2 for FST_VARIANT_PATH_WARP (a warp
+// per path).
+int path_slot(const fst_model* m, int kind) {
+  const int v = m->variant[kind];
+  const int slot = v == FST_VARIANT_PATH ? 1 : v == FST_VARIANT_PATH_WARP ? 2 : 0;
+  return slot && jit_has_slot(m, kind, slot) ? slot : 0;
 }
+bool use_path(const fst_model* m, int kind) { return path_slot(m, kind) != 0; }
 
-// Launches a path-parallel kernel: G lanes per environment, so a block of T
-// threads serves (T / 32) * (32 / G) environments; `rows` staged input rows
-// per environment; gy = blockIdx.y extent.
+// Launches a path-parallel kernel with `rows` staged input rows per
+// environment and gy = blockIdx.y extent. A lane per path: G lanes per
+// environment, so a block of T threads serves (T / 32) * (32 / G)
+// environments. A warp per path: blocks of 32 environments and one warp per
+// path, plus two merge buffers of 27 floats per warp and lane.
 template <typename... A>
 cudaError_t path_go(const fst_model* m, int kind, int64_t B, int rows, unsigned gy, cudaStream_t s, A... args) {
+  void* argv[] = {(void*)&args...};
+  const int slot = path_slot(m, kind);
+  if (slot == 2) {
+    const int np = jit_path_count(m);
+    const size_t sh = ((size_t)rows * 32 + (size_t)2 * np * 27 * 32) * sizeof(float);
+    return jit_launch_slot(m, kind, 2, dim3((unsigned)((B + 31) / 32), gy), 32 * np, sh, s, argv);
+  }
   const int T = m->block[kind] ? m->block[kind] : 128;
   const int G = jit_path_lanes(m);
   const int EPB = (T / 32) * (32 / G);
   const dim3 grid((unsigned)((B + EPB - 1) / EPB), gy);
-  void* argv[] = {(void*)&args...};
-  return jit_launch_path(m, kind, grid, T, (size_t)rows * EPB * sizeof(float), s, argv);
+  return jit_launch_slot(m, kind, 1, grid, T, (size_t)rows * EPB * sizeof(float), s, argv);
 }
 
 // Threads per block of a level-parallel launch: a multiple of 32 (one warp
@@ -201,11 +214,13 @@ fst_status fst_model_set_launch(fst_model* m, uint32_t kinds, int32_t block, int
   if (!m) return set_error(FST_ERR_INVALID_ARG, "fst_model_set_launch: null model");
   if (block != 0 && block != 32 && block != 64 && block != 128 && block != 256)
     return set_error(FST_ERR_INVALID_ARG, "fst_model_set_launch: block must be 0, 32, 64, 128 or 256");
-  if (variant < FST_VARIANT_AUTO || variant > FST_VARIANT_PATH)
+  if (variant < FST_VARIANT_AUTO || variant > FST_VARIANT_PATH_WARP)
     return set_error(FST_ERR_INVALID_ARG, "fst_model_set_launch: unknown variant");
   // "all kinds" with the level or path variant means every kind that has one
   if (kinds == 0)
-    kinds = (variant == FST_VARIANT_LEVEL || variant == FST_VARIANT_PATH) ? (1u << (JK_EVAL + 1)) - 1u : FST_SPEC_ALL;
+    kinds = (variant == FST_VARIANT_LEVEL || variant == FST_VARIANT_PATH || variant == FST_VARIANT_PATH_WARP)
+                ? (1u << (JK_EVAL + 1)) - 1u
+                : FST_SPEC_ALL;
   if (kinds & ~(uint32_t)FST_SPEC_ALL) return set_error(FST_ERR_INVALID_ARG, "fst_model_set_launch: unknown kind bits");
   for (int k = 0; k < JK_COUNT; ++k) {
     if (((kinds >> k) & 1u) && variant == FST_VARIANT_MIXED && k != JK_EVAL)
@@ -214,7 +229,8 @@ fst_status fst_model_set_launch(fst_model* m, uint32_t kinds, int32_t block, int
       return set_error(FST_ERR_INVALID_ARG, "fst_model_set_launch: a selected kind is not specialised yet");
     if (((kinds >> k) & 1u) && variant == FST_VARIANT_MIXED && !jit_has(m, JK_EVAL_MIXED))
       return set_error(FST_ERR_INVALID_ARG, "fst_model_set_launch: a selected kind is not specialised yet");
-    if (((kinds >> k) & 1u) && variant == FST_VARIANT_PATH && !jit_has_path(m, k))
+    if (((kinds >> k) & 1u) && (variant == FST_VARIANT_PATH || variant == FST_VARIANT_PATH_WARP) &&
+        !jit_has_slot(m, k, variant == FST_VARIANT_PATH ? 1 : 2))
       return set_error(FST_ERR_INVALID_ARG, "fst_model_set_launch: no path-parallel kernel for a selected kind "
                                             "(specialise FK, Jacobian, RNEA, CRBA, ABA or eval first; trees with "
                                             "more than 8 leaves have none)");

@@ -140,6 +140,7 @@ void put_floats(std::ostringstream& os, const float* p, int n) {
 // tree has more than 8 leaves.
 struct PathTables {
   int G = 0;
+  int np = 0;              // number of paths
   std::vector<int> path;   // [G][depth], -1 past a path's end
   std::vector<int> seg;    // [G][depth], lo | hi << 8
   std::vector<unsigned> lead;  // [G], bit t: first lane holding that body
@@ -182,6 +183,7 @@ PathTables path_tables(const fst_model* m) {
   int G = 1;
   while (G < n_paths) G *= 2;
   P.G = G;
+  P.np = n_paths;
   P.path.assign((size_t)G * D, -1);
   for (int g = 0; g < n_paths; ++g)
     for (int t = 0; t < (int)paths[g].size(); ++t) P.path[(size_t)g * D + t] = paths[g][t];
@@ -216,6 +218,7 @@ std::string make_source(const fst_model* m, int kind) {
   std::ostringstream os;
   os << "#define FST_FIXED_TOPOLOGY 1\n#define FST_N " << m->n << "\n#define " << kKindMacro[kind] << " 1\n"
      << "#define FST_JIT_NAME " << kKindName[kind] << "\n#define FST_JIT_PATH_NAME " << kKindName[kind] << "_path\n"
+     << "#define FST_JIT_WARP_NAME " << kKindName[kind] << "_pathw\n"
      << "#include \"fst_layout.h\"\nnamespace fst {\nstatic __device__ const BodyC kC[" << m->n << "] = {\n";
   for (int i = 0; i < m->n; ++i) {
     const BodyC& c = m->hc[i];
@@ -265,7 +268,8 @@ std::string make_source(const fst_model* m, int kind) {
     ints("kOwner", P.owner.data(), m->n);
     ints("kDepthOf", P.depth_of.data(), m->n);
   }
-  os << "}  // namespace fst\n#define FST_DEPTH " << m->depth << "\n#define FST_PATH_G " << P.G
+  os << "}  // namespace fst\n#define FST_DEPTH " << m->depth << "\n#define FST_PATH_NP " << P.np
+     << "\n#define FST_PATH_G " << P.G
      << "\n#include \"jit_kernels.cuh\"\n";
   return os.str();
 }
@@ -354,14 +358,15 @@ void compile_one(CompileJob& job, const std::string& arch_opt) {
 
 }  // namespace
 
+// Per kind, up to three kernels of one module: the one-environment-per-thread
+// kernel (slot 0) and, for trees with at most 8 leaves, the path-parallel
+// kernels with a lane per path (slot 1) or a warp per path (slot 2).
 struct JitState {
   CUmodule mod[JK_COUNT] = {};
-  CUfunction fn[JK_COUNT] = {};
-  CUfunction fn_path[JK_COUNT] = {};  // path-parallel kernel of the same module, if any
-  int smem_limit[JK_COUNT] = {};
-  int carveout_set[JK_COUNT] = {};
-  int path_carveout_set[JK_COUNT] = {};
-  int path_G = 0;
+  CUfunction fn[JK_SLOTS][JK_COUNT] = {};
+  int smem_limit[JK_SLOTS][JK_COUNT] = {};
+  int carveout_set[JK_SLOTS][JK_COUNT] = {};
+  int path_G = 0, path_np = 0;
 };
 
 fst_status jit_specialize(fst_model* m, unsigned mask) {
@@ -380,7 +385,7 @@ fst_status jit_specialize(fst_model* m, unsigned mask) {
   if (!m->jit) m->jit = new JitState();
   std::vector<CompileJob> jobs;
   for (int k = 0; k < JK_COUNT; ++k)
-    if (((mask >> k) & 1u) && !m->jit->fn[k]) jobs.push_back(CompileJob{k, make_source(m, k), {}, {}});
+    if (((mask >> k) & 1u) && !m->jit->fn[0][k]) jobs.push_back(CompileJob{k, make_source(m, k), {}, {}});
   std::vector<std::thread> threads;
   for (auto& j : jobs) threads.emplace_back([&j, &arch] { compile_one(j, arch); });
   for (auto& t : threads) t.join();
@@ -396,12 +401,17 @@ fst_status jit_specialize(fst_model* m, unsigned mask) {
       return set_error(FST_ERR_CUDA, "fst_model_specialize: kernel not found in the compiled module");
     }
     m->jit->mod[j.kind] = mod;
-    m->jit->fn[j.kind] = fn;
-    CUfunction fp;
-    const std::string pname = std::string(kKindName[j.kind]) + "_path";
-    if (D.get(&fp, mod, pname.c_str()) == CUDA_SUCCESS) m->jit->fn_path[j.kind] = fp;
+    m->jit->fn[0][j.kind] = fn;
+    const char* suffix[JK_SLOTS] = {"", "_path", "_pathw"};
+    for (int v = 1; v < JK_SLOTS; ++v) {
+      CUfunction fp;
+      const std::string pname = std::string(kKindName[j.kind]) + suffix[v];
+      if (D.get(&fp, mod, pname.c_str()) == CUDA_SUCCESS) m->jit->fn[v][j.kind] = fp;
+    }
   }
-  m->jit->path_G = path_tables(m).G;
+  const PathTables P = path_tables(m);
+  m->jit->path_G = P.G;
+  m->jit->path_np = P.np;
   return FST_OK;
 }
 
@@ -418,56 +428,45 @@ unsigned jit_mask(const fst_model* m) {
   unsigned mask = 0;
   if (m->jit)
     for (int k = 0; k < JK_COUNT; ++k)
-      if (m->jit->fn[k]) mask |= 1u << k;
+      if (m->jit->fn[0][k]) mask |= 1u << k;
   return mask;
 }
 
-bool jit_has(const fst_model* m, int kind) { return m->jit && m->jit->fn[kind]; }
+bool jit_has(const fst_model* m, int kind) { return m->jit && m->jit->fn[0][kind]; }
 
-bool jit_has_path(const fst_model* m, int kind) { return m->jit && m->jit->fn_path[kind]; }
+bool jit_has_slot(const fst_model* m, int kind, int slot) { return m->jit && m->jit->fn[slot][kind]; }
 
 int jit_path_lanes(const fst_model* m) { return m->jit ? m->jit->path_G : 0; }
 
-cudaError_t jit_launch_path(const fst_model* m, int kind, dim3 grid, int block, size_t smem, cudaStream_t s,
-                            void** args) {
-  const Driver& D = driver();
-  JitState* J = m->jit;
-  if (smem > 48 * 1024) return cudaErrorInvalidValue;  // the staged tile is a few KB
-  const int gen = carveout_generation() + 1;
-  if (J->path_carveout_set[kind] != gen) {
-    int pct = -1;
-    if (const char* env = std::getenv("FST_SMEM_CARVEOUT")) pct = std::atoi(env);
-    if (carveout_override() >= 0) pct = carveout_override();
-    pct = pct < -1 ? -1 : (pct > 100 ? 100 : pct);
-    if (pct >= 0 || J->path_carveout_set[kind] != 0)
-      D.set_attr(J->fn_path[kind], CU_FUNC_ATTRIBUTE_PREFERRED_SHARED_MEMORY_CARVEOUT, pct);
-    J->path_carveout_set[kind] = gen;
-  }
-  const CUresult r = D.launch(J->fn_path[kind], grid.x, grid.y, grid.z, (unsigned)block, 1, 1, (unsigned)smem,
-                              (CUstream)s, args, nullptr);
-  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorLaunchFailure;
-}
+int jit_path_count(const fst_model* m) { return m->jit ? m->jit->path_np : 0; }
 
-cudaError_t jit_launch(const fst_model* m, int kind, dim3 grid, int block, size_t smem, cudaStream_t s, void** args) {
+cudaError_t jit_launch_slot(const fst_model* m, int kind, int slot, dim3 grid, int block, size_t smem,
+                            cudaStream_t s, void** args) {
   const Driver& D = driver();
   JitState* J = m->jit;
-  if (smem > 48 * 1024 && (int)smem > J->smem_limit[kind]) {
-    if (D.set_attr(J->fn[kind], CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, (int)smem) != CUDA_SUCCESS)
+  CUfunction f = J->fn[slot][kind];
+  if (smem > 48 * 1024 && (int)smem > J->smem_limit[slot][kind]) {
+    if (D.set_attr(f, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, (int)smem) != CUDA_SUCCESS)
       return cudaErrorInvalidValue;
-    J->smem_limit[kind] = (int)smem;
+    J->smem_limit[slot][kind] = (int)smem;
   }
   const int gen = carveout_generation() + 1;
-  if (J->carveout_set[kind] != gen) {
+  if (J->carveout_set[slot][kind] != gen) {
     int pct = -1;  // the driver's default preference (CU_SHAREDMEM_CARVEOUT_DEFAULT)
     if (const char* env = std::getenv("FST_SMEM_CARVEOUT")) pct = std::atoi(env);
     if (carveout_override() >= 0) pct = carveout_override();
     pct = pct < -1 ? -1 : (pct > 100 ? 100 : pct);
-    if (pct >= 0 || J->carveout_set[kind] != 0) D.set_attr(J->fn[kind], CU_FUNC_ATTRIBUTE_PREFERRED_SHARED_MEMORY_CARVEOUT, pct);
-    J->carveout_set[kind] = gen;
+    if (pct >= 0 || J->carveout_set[slot][kind] != 0)
+      D.set_attr(f, CU_FUNC_ATTRIBUTE_PREFERRED_SHARED_MEMORY_CARVEOUT, pct);
+    J->carveout_set[slot][kind] = gen;
   }
-  const CUresult r = D.launch(J->fn[kind], grid.x, grid.y, grid.z, (unsigned)block, 1, 1, (unsigned)smem,
-                              (CUstream)s, args, nullptr);
+  const CUresult r = D.launch(f, grid.x, grid.y, grid.z, (unsigned)block, 1, 1, (unsigned)smem, (CUstream)s, args,
+                              nullptr);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorLaunchFailure;
+}
+
+cudaError_t jit_launch(const fst_model* m, int kind, dim3 grid, int block, size_t smem, cudaStream_t s, void** args) {
+  return jit_launch_slot(m, kind, 0, grid, block, smem, s, args);
 }
 
 }  // namespace fst

@@ -33,11 +33,14 @@ fst_status jit_specialize(fst_model* m, unsigned mask);
 void jit_release(fst_model* m);
 unsigned jit_mask(const fst_model* m);
 bool jit_has(const fst_model* m, int kind);
-// Path-parallel kernels: present for a kind, and the lanes per environment.
-bool jit_has_path(const fst_model* m, int kind);
-int jit_path_lanes(const fst_model* m);
-cudaError_t jit_launch_path(const fst_model* m, int kind, dim3 grid, int block, size_t smem, cudaStream_t s,
-                            void** args);
+// Kernel slots of a kind: 0 one environment per thread, 1 path-parallel with
+// a lane per path, 2 path-parallel with a warp per path.
+constexpr int JK_SLOTS = 3;
+bool jit_has_slot(const fst_model* m, int kind, int slot);
+int jit_path_lanes(const fst_model* m);   // lanes per environment of slot 1
+int jit_path_count(const fst_model* m);   // warps per block of slot 2
+cudaError_t jit_launch_slot(const fst_model* m, int kind, int slot, dim3 grid, int block, size_t smem,
+                            cudaStream_t s, void** args);
 cudaError_t jit_launch(const fst_model* m, int kind, dim3 grid, int block, size_t smem, cudaStream_t s, void** args);
 
 }  // namespace fst

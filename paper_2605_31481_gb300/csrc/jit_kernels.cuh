@@ -467,7 +467,7 @@ extern "C" __global__ void __launch_bounds__(256) FST_JIT_NAME(ModelView mv, int
   float* tile = reinterpret_cast<float*>(smem);                           \
   constexpr int G = FST_PATH_G;                                           \
   constexpr int D = FST_DEPTH;                                            \
-  const PathLane<G> L;                                                    \
+  PathLane<G> L;                                                          \
   const int EPB = (int)(blockDim.x >> 5) * PathLane<G>::E;                \
   const int eb = (int)(threadIdx.x >> 5) * PathLane<G>::E + L.es;         \
   const int64_t e0 = (int64_t)blockIdx.x * EPB;                           \
@@ -490,7 +490,7 @@ extern "C" __global__ void __launch_bounds__(256) FST_JIT_PATH_NAME(ModelView mv
   path_stage(tile, q, mv.nq, B, e0, EPB);
   FST_PATH_READY;
   Xf P[D];
-  fk_path<G, D>(tp, lp, FST_PATH_COL(0), P, poses, B, e, act);
+  fk_path<D>(tp, lp, FST_PATH_COL(0), P, poses, B, e, act);
 }
 #endif
 
@@ -502,8 +502,8 @@ extern "C" __global__ void __launch_bounds__(256) FST_JIT_PATH_NAME(ModelView mv
   path_stage(tile, q, mv.nq, B, e0, EPB);
   FST_PATH_READY;
   Xf P[D];
-  fk_path<G, D>(tp, lp, FST_PATH_COL(0), P, nullptr, B, e, act);
-  jac_path<G, D>(tp, L, P, mv.nv, links, J, B, e, act);
+  fk_path<D>(tp, lp, FST_PATH_COL(0), P, nullptr, B, e, act);
+  jac_path<D>(tp, lp, P, mv.nv, links, J, B, e, act);
 }
 #endif
 
@@ -518,7 +518,7 @@ extern "C" __global__ void __launch_bounds__(256) FST_JIT_PATH_NAME(ModelView mv
   path_stage(tile + mv.nq * EPB, qd, mv.nv, B, e0, EPB);
   path_stage(tile + (mv.nq + mv.nv) * EPB, qdd, mv.nv, B, e0, EPB);
   FST_PATH_READY;
-  rnea_path<G, D>(tp, L, lp, world_accel(mv), FST_PATH_COL(0), FST_PATH_COL(mv.nq), FST_PATH_COL(mv.nq + mv.nv),
+  rnea_path<D>(tp, L, lp, world_accel(mv), FST_PATH_COL(0), FST_PATH_COL(mv.nq), FST_PATH_COL(mv.nq + mv.nv),
                   tau, B, e, act);
 }
 #endif
@@ -530,7 +530,7 @@ extern "C" __global__ void __launch_bounds__(256) FST_JIT_PATH_NAME(ModelView mv
   FST_PATH_PROLOGUE;
   path_stage(tile, q, mv.nq, B, e0, EPB);
   FST_PATH_READY;
-  crba_path<G, D>(tp, L, lp, FST_PATH_COL(0), mv.nv, M, B, e, act);
+  crba_path<D>(tp, L, lp, FST_PATH_COL(0), mv.nv, M, B, e, act);
 }
 #endif
 
@@ -545,7 +545,7 @@ extern "C" __global__ void __launch_bounds__(256) FST_JIT_PATH_NAME(ModelView mv
   path_stage(tile + mv.nq * EPB, qd, mv.nv, B, e0, EPB);
   path_stage(tile + (mv.nq + mv.nv) * EPB, tau, mv.nv, B, e0, EPB);
   FST_PATH_READY;
-  aba_path<G, D>(tp, L, lp, world_accel(mv), FST_PATH_COL(0), FST_PATH_COL(mv.nq), FST_PATH_COL(mv.nq + mv.nv), qdd,
+  aba_path<D>(tp, L, lp, world_accel(mv), FST_PATH_COL(0), FST_PATH_COL(mv.nq), FST_PATH_COL(mv.nq + mv.nv), qdd,
                  B, e, act);
 }
 #endif
@@ -567,21 +567,194 @@ extern "C" __global__ void __launch_bounds__(256) FST_JIT_PATH_NAME(ModelView mv
   const Col cq = FST_PATH_COL(0), c1 = FST_PATH_COL(mv.nq), c2 = FST_PATH_COL(mv.nq + mv.nv);
   switch (role) {
     case ROLE_ABA:
-      aba_path<G, D>(tp, L, lp, world_accel(mv), cq, c1, c2, a.qdd_out, B, e, act);
+      aba_path<D>(tp, L, lp, world_accel(mv), cq, c1, c2, a.qdd_out, B, e, act);
       break;
     case ROLE_CRBA:
-      crba_path<G, D>(tp, L, lp, cq, mv.nv, a.M, B, e, act);
+      crba_path<D>(tp, L, lp, cq, mv.nv, a.M, B, e, act);
       break;
     case ROLE_RNEA:
-      rnea_path<G, D>(tp, L, lp, world_accel(mv), cq, c1, c2, a.tau_out, B, e, act);
+      rnea_path<D>(tp, L, lp, world_accel(mv), cq, c1, c2, a.tau_out, B, e, act);
       break;
     default: {
       Xf P[D];
-      fk_path<G, D>(tp, lp, cq, P, a.poses, B, e, act);
-      if (a.J) jac_path<G, D>(tp, L, P, mv.nv, a.links, a.J, B, e, act);
+      fk_path<D>(tp, lp, cq, P, a.poses, B, e, act);
+      if (a.J) jac_path<D>(tp, lp, P, mv.nv, a.links, a.J, B, e, act);
       break;
     }
   }
+}
+#endif
+#endif  // FST_PATH_G > 0
+
+// ---- path-per-warp kernels (FST_VARIANT_PATH_WARP) ----------------------------
+// A block of FST_PATH_NP warps serves 32 environments (one per lane); warp g
+// sweeps path g with code compiled for that path (every body constant folds),
+// and the paths meet through the shared-memory merge of SmemMerge.
+#if FST_PATH_G > 0
+template <int g>
+struct WarpPath {
+  __device__ __forceinline__ int body(int t) const { return kPath[g * FST_DEPTH + t]; }
+  __device__ __forceinline__ bool leads(int t) const { return (kLead[g] >> t) & 1u; }
+  __device__ __forceinline__ int lo(int t) const { return kSeg[g * FST_DEPTH + t] & 0xff; }
+  __device__ __forceinline__ int hi(int t) const { return kSeg[g * FST_DEPTH + t] >> 8; }
+  __device__ __forceinline__ int index() const { return g; }
+};
+
+template <int K>
+struct IC {
+  static constexpr int value = K;
+};
+
+// Calls f(IC<w>) with this warp's index as a compile-time constant.
+template <int K, int NP, class F>
+__device__ __forceinline__ void for_warp(int w, F& f) {
+  if constexpr (K < NP) {
+    if (w == K)
+      f(IC<K>{});
+    else
+      for_warp<K + 1, NP>(w, f);
+  }
+}
+
+constexpr int kWarpXch = 27;  // floats per lane and warp in one merge (Sym6 + force)
+
+#define FST_WARP_PROLOGUE(rows)                                  \
+  extern __shared__ float4 smem[];                              \
+  float* tile = reinterpret_cast<float*>(smem);                 \
+  constexpr int D = FST_DEPTH;                                  \
+  constexpr int NP = FST_PATH_NP;                               \
+  const int lane = (int)(threadIdx.x & 31);                     \
+  const int warp = (int)(threadIdx.x >> 5);                     \
+  const int64_t e = (int64_t)blockIdx.x * 32 + lane;            \
+  const bool act = e < B;                                       \
+  const FixedTopo tp = fixed_topo(mv);                          \
+  SmemMerge<NP, kWarpXch> mg{tile + (rows) * 32, warp, lane, 0}
+
+#define FST_WARP_READY \
+  cp_async_wait_all(); \
+  __syncthreads()
+
+#define FST_WARP_COL(r) (Col{tile + (r)*32 + lane, 32})
+
+#ifdef FST_JIT_FK
+extern "C" __global__ void __launch_bounds__(256) FST_JIT_WARP_NAME(ModelView mv, int64_t B,
+                                                                      const float* __restrict__ q,
+                                                                      float* __restrict__ poses) {
+  FST_WARP_PROLOGUE(mv.nq);
+  stage_block_rows(tile, q, mv.nq, B, e);
+  FST_WARP_READY;
+  auto f = [&](auto kc) {
+    Xf P[D];
+    fk_path<D>(tp, WarpPath<decltype(kc)::value>{}, FST_WARP_COL(0), P, poses, B, e, act);
+  };
+  for_warp<0, NP>(warp, f);
+}
+#endif
+
+#ifdef FST_JIT_JACOBIAN
+extern "C" __global__ void __launch_bounds__(256) FST_JIT_WARP_NAME(ModelView mv, int64_t B,
+                                                                      const float* __restrict__ q, LinkList links,
+                                                                      float* __restrict__ J) {
+  FST_WARP_PROLOGUE(mv.nq);
+  stage_block_rows(tile, q, mv.nq, B, e);
+  FST_WARP_READY;
+  auto f = [&](auto kc) {
+    const WarpPath<decltype(kc)::value> lp{};
+    Xf P[D];
+    fk_path<D>(tp, lp, FST_WARP_COL(0), P, nullptr, B, e, act);
+    jac_path<D>(tp, lp, P, mv.nv, links, J, B, e, act);
+  };
+  for_warp<0, NP>(warp, f);
+}
+#endif
+
+#ifdef FST_JIT_RNEA
+extern "C" __global__ void __launch_bounds__(256) FST_JIT_WARP_NAME(ModelView mv, int64_t B,
+                                                                      const float* __restrict__ q,
+                                                                      const float* __restrict__ qd,
+                                                                      const float* __restrict__ qdd,
+                                                                      float* __restrict__ tau) {
+  FST_WARP_PROLOGUE(mv.nq + 2 * mv.nv);
+  stage_block_rows(tile, q, mv.nq, B, e);
+  stage_block_rows(tile + mv.nq * 32, qd, mv.nv, B, e);
+  stage_block_rows(tile + (mv.nq + mv.nv) * 32, qdd, mv.nv, B, e);
+  FST_WARP_READY;
+  auto f = [&](auto kc) {
+    rnea_path<D>(tp, mg, WarpPath<decltype(kc)::value>{}, world_accel(mv), FST_WARP_COL(0), FST_WARP_COL(mv.nq),
+                 FST_WARP_COL(mv.nq + mv.nv), tau, B, e, act);
+  };
+  for_warp<0, NP>(warp, f);
+}
+#endif
+
+#ifdef FST_JIT_CRBA
+extern "C" __global__ void __launch_bounds__(256) FST_JIT_WARP_NAME(ModelView mv, int64_t B,
+                                                                      const float* __restrict__ q,
+                                                                      float* __restrict__ M) {
+  FST_WARP_PROLOGUE(mv.nq);
+  stage_block_rows(tile, q, mv.nq, B, e);
+  FST_WARP_READY;
+  auto f = [&](auto kc) {
+    crba_path<D>(tp, mg, WarpPath<decltype(kc)::value>{}, FST_WARP_COL(0), mv.nv, M, B, e, act);
+  };
+  for_warp<0, NP>(warp, f);
+}
+#endif
+
+#ifdef FST_JIT_ABA
+extern "C" __global__ void __launch_bounds__(256) FST_JIT_WARP_NAME(ModelView mv, int64_t B,
+                                                                      const float* __restrict__ q,
+                                                                      const float* __restrict__ qd,
+                                                                      const float* __restrict__ tau,
+                                                                      float* __restrict__ qdd) {
+  FST_WARP_PROLOGUE(mv.nq + 2 * mv.nv);
+  stage_block_rows(tile, q, mv.nq, B, e);
+  stage_block_rows(tile + mv.nq * 32, qd, mv.nv, B, e);
+  stage_block_rows(tile + (mv.nq + mv.nv) * 32, tau, mv.nv, B, e);
+  FST_WARP_READY;
+  auto f = [&](auto kc) {
+    aba_path<D>(tp, mg, WarpPath<decltype(kc)::value>{}, world_accel(mv), FST_WARP_COL(0), FST_WARP_COL(mv.nq),
+                FST_WARP_COL(mv.nq + mv.nv), qdd, B, e, act);
+  };
+  for_warp<0, NP>(warp, f);
+}
+#endif
+
+#ifdef FST_JIT_EVAL
+extern "C" __global__ void __launch_bounds__(256) FST_JIT_WARP_NAME(ModelView mv, int64_t B, EvalArgs a) {
+  FST_WARP_PROLOGUE(mv.nq + 2 * mv.nv);
+  const int role = a.roles[blockIdx.y];
+  stage_block_rows(tile, a.q, mv.nq, B, e);
+  if (role == ROLE_RNEA) {
+    stage_block_rows(tile + mv.nq * 32, a.qd, mv.nv, B, e);
+    stage_block_rows(tile + (mv.nq + mv.nv) * 32, a.qdd, mv.nv, B, e);
+  } else if (role == ROLE_ABA) {
+    stage_block_rows(tile + mv.nq * 32, a.qd, mv.nv, B, e);
+    stage_block_rows(tile + (mv.nq + mv.nv) * 32, a.tau, mv.nv, B, e);
+  }
+  FST_WARP_READY;
+  const Col cq = FST_WARP_COL(0), c1 = FST_WARP_COL(mv.nq), c2 = FST_WARP_COL(mv.nq + mv.nv);
+  auto f = [&](auto kc) {
+    const WarpPath<decltype(kc)::value> lp{};
+    switch (role) {
+      case ROLE_ABA:
+        aba_path<D>(tp, mg, lp, world_accel(mv), cq, c1, c2, a.qdd_out, B, e, act);
+        break;
+      case ROLE_CRBA:
+        crba_path<D>(tp, mg, lp, cq, mv.nv, a.M, B, e, act);
+        break;
+      case ROLE_RNEA:
+        rnea_path<D>(tp, mg, lp, world_accel(mv), cq, c1, c2, a.tau_out, B, e, act);
+        break;
+      default: {
+        Xf P[D];
+        fk_path<D>(tp, lp, cq, P, a.poses, B, e, act);
+        if (a.J) jac_path<D>(tp, lp, P, mv.nv, a.links, a.J, B, e, act);
+        break;
+      }
+    }
+  };
+  for_warp<0, NP>(warp, f);
 }
 #endif
 #endif  // FST_PATH_G > 0

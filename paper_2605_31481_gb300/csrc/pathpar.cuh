@@ -71,15 +71,25 @@ struct PathLane {
     for (int k = 0; k < 6; ++k) s.I[k] = sum(x.I[k], lo, hi);
     return s;
   }
+  __device__ __forceinline__ void sum2(const Sym6& x, SV y, int lo, int hi, Sym6& xo, SV& yo) const {
+    xo = sum(x, lo, hi);
+    yo = sum(y, lo, hi);
+  }
 };
 
-// This lane's path: bodies per depth, leader bits, sharing segments.
+// A lane's path with run-time tables (lane-group mapping): bodies per depth,
+// leader bits, sharing segments.
 template <int D>
 struct LanePath {
-  int body[D];
-  int lo[D], hi[D];
+  int b[D];
+  int l[D], h[D];
   unsigned lead;
+  int g;
+  __device__ __forceinline__ int body(int t) const { return b[t]; }
   __device__ __forceinline__ bool leads(int t) const { return (lead >> t) & 1u; }
+  __device__ __forceinline__ int lo(int t) const { return l[t]; }
+  __device__ __forceinline__ int hi(int t) const { return h[t]; }
+  __device__ __forceinline__ int index() const { return g; }
 };
 
 template <int G, int D, class TP>
@@ -87,14 +97,78 @@ __device__ __forceinline__ LanePath<D> lane_path(const TP& tp, int g) {
   LanePath<D> p;
 #pragma unroll
   for (int t = 0; t < D; ++t) {
-    p.body[t] = tp.path(g, t);
+    p.b[t] = tp.path(g, t);
     const int s = tp.seg(g, t);
-    p.lo[t] = s & 0xff;
-    p.hi[t] = s >> 8;
+    p.l[t] = s & 0xff;
+    p.h[t] = s >> 8;
   }
   p.lead = tp.lead_mask(g);
+  p.g = g;
   return p;
 }
+
+// Merge across the shared-memory exchange of a path-per-warp block: warp g
+// holds path g of the block's 32 environments (one per lane). A merge
+// writes each warp's contribution to buf[phase parity][warp][field][lane],
+// waits at one block barrier and sums the segment's slots in warp order.
+// Two alternating buffers make one barrier per merge enough: a warp can
+// only overwrite a buffer after the next merge's barrier, which every warp
+// reaches after finishing its reads of that buffer.
+template <int NP, int NF>
+struct SmemMerge {
+  float* buf;  // 2 * NP * NF * 32 floats
+  int g, lane, phase;
+  template <int N>
+  __device__ __forceinline__ void sum_arr(const float (&x)[N], float (&out)[N], int lo, int hi) {
+    static_assert(N <= NF, "exchange slot too small");
+    float* b = buf + (phase & 1) * NP * NF * 32;
+#pragma unroll
+    for (int f = 0; f < N; ++f) b[(g * NF + f) * 32 + lane] = x[f];
+    // The warps run different (per-path) code, so this is the non-aligned
+    // form of the block barrier, on its own barrier id; every warp passes
+    // the same number of merges.
+    asm volatile("barrier.sync 1, %0;" ::"r"(NP * 32) : "memory");
+#pragma unroll
+    for (int f = 0; f < N; ++f) {
+      float s = 0.f;
+#pragma unroll
+      for (int k = 0; k < NP; ++k)
+        if (k >= lo && k < hi) s += b[(k * NF + f) * 32 + lane];
+      out[f] = s;
+    }
+    ++phase;
+  }
+  __device__ __forceinline__ SV sum(SV x, int lo, int hi) {
+    const float a[6] = {x.w.x, x.w.y, x.w.z, x.v.x, x.v.y, x.v.z};
+    float o[6];
+    sum_arr(a, o, lo, hi);
+    return SV{f3{o[0], o[1], o[2]}, f3{o[3], o[4], o[5]}};
+  }
+  __device__ __forceinline__ In10 sum(const In10& x, int lo, int hi) {
+    const float a[10] = {x.m, x.h.x, x.h.y, x.h.z, x.I[0], x.I[1], x.I[2], x.I[3], x.I[4], x.I[5]};
+    float o[10];
+    sum_arr(a, o, lo, hi);
+    return in_load(o);
+  }
+  __device__ __forceinline__ void sum2(const Sym6& x, SV y, int lo, int hi, Sym6& xo, SV& yo) {
+    float a[27], o[27];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) a[k] = x.A[k];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) a[6 + k] = x.Bk[k];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) a[15 + k] = x.C[k];
+    a[21] = y.w.x; a[22] = y.w.y; a[23] = y.w.z; a[24] = y.v.x; a[25] = y.v.y; a[26] = y.v.z;
+    sum_arr(a, o, lo, hi);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) xo.A[k] = o[k];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) xo.Bk[k] = o[6 + k];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) xo.C[k] = o[15 + k];
+    yo = SV{f3{o[21], o[22], o[23]}, f3{o[24], o[25], o[26]}};
+  }
+};
 
 __device__ __forceinline__ Sym6 sym6_zero() {
   Sym6 s;
@@ -117,12 +191,12 @@ __device__ __forceinline__ In10 in_zero() {
 }
 
 // ---- FK: world poses along the path ------------------------------------------
-template <int G, int D, class TP>
-__device__ __forceinline__ void fk_path(const TP& tp, const LanePath<D>& lp, const Col& q, Xf (&P)[D],
+template <int D, class TP, class LP>
+__device__ __forceinline__ void fk_path(const TP& tp, const LP& lp, const Col& q, Xf (&P)[D],
                                         float* __restrict__ poses, int64_t B, int64_t e, bool act) {
 #pragma unroll
   for (int t = 0; t < D; ++t) {
-    const int i = lp.body[t];
+    const int i = lp.body(t);
     if (i < 0) continue;
     const Xf X = joint_X(tp.C(i), tp.I(i), q);
     if (t == 0)
@@ -140,14 +214,14 @@ __device__ __forceinline__ void fk_path(const TP& tp, const LanePath<D>& lp, con
 }
 
 // ---- Jacobians: each lane takes the links whose leader it is -------------------
-template <int G, int D, class TP>
-__device__ __forceinline__ void jac_path(const TP& tp, const PathLane<G>& L, const Xf (&P)[D], int nv,
+template <int D, class TP, class LP>
+__device__ __forceinline__ void jac_path(const TP& tp, const LP& lp, const Xf (&P)[D], int nv,
                                          const LinkList& links, float* __restrict__ J, int64_t B, int64_t e,
                                          bool act) {
   for (int r = 0; r < links.n; ++r) {
     int l = -1;
     for (int k = 0, cnt = 0; k < links.n; ++k)
-      if (tp.owner(links.idx[k]) == L.g) {
+      if (tp.owner(links.idx[k]) == lp.index()) {
         if (cnt == r) l = k;
         ++cnt;
       }
@@ -198,8 +272,8 @@ __device__ __forceinline__ void jac_path(const TP& tp, const PathLane<G>& L, con
 }
 
 // ---- RNEA -------------------------------------------------------------------------
-template <int G, int D, class TP>
-__device__ __forceinline__ void rnea_path(const TP& tp, const PathLane<G>& L, const LanePath<D>& lp, SV a0,
+template <int D, class TP, class LP, class MG>
+__device__ __forceinline__ void rnea_path(const TP& tp, MG& L, const LP& lp, SV a0,
                                           const Col& q, const Col& qd, const Col& qdd, float* __restrict__ tau,
                                           int64_t B, int64_t e, bool act) {
   Xf X[D];
@@ -207,7 +281,7 @@ __device__ __forceinline__ void rnea_path(const TP& tp, const PathLane<G>& L, co
   SV vp = sv_zero(), ap = a0;
 #pragma unroll
   for (int t = 0; t < D; ++t) {
-    const int i = lp.body[t];
+    const int i = lp.body(t);
     if (i < 0) continue;
     const BodyC& c = tp.C(i);
     const BodyI bi = tp.I(i);
@@ -230,9 +304,9 @@ __device__ __forceinline__ void rnea_path(const TP& tp, const PathLane<G>& L, co
   SV cc = sv_zero();  // X_c^T F_c of the child on this lane's path
 #pragma unroll
   for (int t = D - 1; t >= 0; --t) {
-    const int i = lp.body[t];
+    const int i = lp.body(t);
     SV s = cc;
-    if (t + 1 < D && tp.red(t)) s = L.sum(lp.leads(t + 1) ? cc : sv_zero(), lp.lo[t], lp.hi[t]);
+    if (t + 1 < D && tp.red(t)) s = L.sum(lp.leads(t + 1) ? cc : sv_zero(), lp.lo(t), lp.hi(t));
     if (i < 0) {
       cc = sv_zero();
       continue;
@@ -244,22 +318,22 @@ __device__ __forceinline__ void rnea_path(const TP& tp, const PathLane<G>& L, co
 }
 
 // ---- CRBA -------------------------------------------------------------------------
-template <int G, int D, class TP>
-__device__ __forceinline__ void crba_path(const TP& tp, const PathLane<G>& L, const LanePath<D>& lp, const Col& q,
+template <int D, class TP, class LP, class MG>
+__device__ __forceinline__ void crba_path(const TP& tp, MG& L, const LP& lp, const Col& q,
                                           int nv, float* __restrict__ M, int64_t B, int64_t e, bool act) {
   Xf X[D];
   In10 Ic[D];
 #pragma unroll
   for (int t = 0; t < D; ++t) {
-    const int i = lp.body[t];
+    const int i = lp.body(t);
     if (i >= 0) X[t] = joint_X(tp.C(i), tp.I(i), q);
   }
   In10 cc = in_zero();
 #pragma unroll
   for (int t = D - 1; t >= 0; --t) {
-    const int i = lp.body[t];
+    const int i = lp.body(t);
     In10 s = cc;
-    if (t + 1 < D && tp.red(t)) s = L.sum(lp.leads(t + 1) ? cc : in_zero(), lp.lo[t], lp.hi[t]);
+    if (t + 1 < D && tp.red(t)) s = L.sum(lp.leads(t + 1) ? cc : in_zero(), lp.lo(t), lp.hi(t));
     if (i < 0) {
       cc = in_zero();
       continue;
@@ -273,7 +347,7 @@ __device__ __forceinline__ void crba_path(const TP& tp, const PathLane<G>& L, co
   float* Me = M + e;
 #pragma unroll
   for (int t = 0; t < D; ++t) {
-    const int i = lp.body[t];
+    const int i = lp.body(t);
     if (i < 0 || !lp.leads(t)) continue;
     const BodyI bi = tp.I(i);
     if (bi.type == FST_JOINT_REVOLUTE || bi.type == FST_JOINT_PRISMATIC) {
@@ -283,7 +357,7 @@ __device__ __forceinline__ void crba_path(const TP& tp, const PathLane<G>& L, co
 #pragma unroll
       for (int u = t - 1; u >= 0; --u) {
         F = XT_force(X[u + 1], F);
-        const int j = lp.body[u];
+        const int j = lp.body(u);
         const BodyI bj = tp.I(j);
         if (bj.type == FST_JOINT_REVOLUTE || bj.type == FST_JOINT_PRISMATIC) {
           const float mij = dot(S_of(tp.C(j)), F);
@@ -331,8 +405,8 @@ __device__ __forceinline__ void crba_path(const TP& tp, const PathLane<G>& L, co
 }
 
 // ---- ABA --------------------------------------------------------------------------
-template <int G, int D, class TP>
-__device__ __forceinline__ void aba_path(const TP& tp, const PathLane<G>& L, const LanePath<D>& lp, SV a0,
+template <int D, class TP, class LP, class MG>
+__device__ __forceinline__ void aba_path(const TP& tp, MG& L, const LP& lp, SV a0,
                                          const Col& q, const Col& qd, const Col& tau, float* __restrict__ qdd,
                                          int64_t B, int64_t e, bool act) {
   Xf X[D];
@@ -342,7 +416,7 @@ __device__ __forceinline__ void aba_path(const TP& tp, const PathLane<G>& L, con
   SV vp = sv_zero();
 #pragma unroll
   for (int t = 0; t < D; ++t) {
-    const int i = lp.body[t];
+    const int i = lp.body(t);
     if (i < 0) continue;
     const BodyC& c = tp.C(i);
     const BodyI bi = tp.I(i);
@@ -366,13 +440,12 @@ __device__ __forceinline__ void aba_path(const TP& tp, const PathLane<G>& L, con
   SV cp = sv_zero(), pAr = sv_zero();
 #pragma unroll
   for (int t = D - 1; t >= 0; --t) {
-    const int i = lp.body[t];
+    const int i = lp.body(t);
     Sym6 sI = cI;
     SV sp = cp;
     if (t + 1 < D && tp.red(t)) {
       const bool mine = lp.leads(t + 1);
-      sI = L.sum(mine ? cI : sym6_zero(), lp.lo[t], lp.hi[t]);
-      sp = L.sum(mine ? cp : sv_zero(), lp.lo[t], lp.hi[t]);
+      L.sum2(mine ? cI : sym6_zero(), mine ? cp : sv_zero(), lp.lo(t), lp.hi(t), sI, sp);
     }
     cI = sym6_zero();
     cp = sv_zero();
@@ -410,7 +483,7 @@ __device__ __forceinline__ void aba_path(const TP& tp, const PathLane<G>& L, con
   SV ap = a0;
 #pragma unroll
   for (int t = 0; t < D; ++t) {
-    const int i = lp.body[t];
+    const int i = lp.body(t);
     if (i < 0) continue;
     const BodyI bi = tp.I(i);
     SV ai = X_motion(X[t], ap) + cb[t];

@@ -31,13 +31,13 @@ def models(torch_cuda):
 
 
 @pytest.mark.parametrize("name", list(TREES))
-@pytest.mark.parametrize("block", [32, 128, 256])
-def test_path_parallel_matches_oracle(torch_cuda, models, name, block):
+@pytest.mark.parametrize("variant,block", [("path", 32), ("path", 128), ("path", 256), ("pathwarp", 0)])
+def test_path_parallel_matches_oracle(torch_cuda, models, name, variant, block):
     torch = torch_cuda
     from paper_2605_31481_gb300 import api
     tree = TREES[name]()
     m = models[name]
-    m.set_launch(None, block, "path")
+    m.set_launch(None, block, variant)
     B = 333                                    # ragged against every block's environment count
     s = w.random_state(tree, B, seed=8)
     q, qd, qdd, tau = (to_soa_cuda(s[k], torch) for k in ("q", "qd", "qdd", "tau"))
@@ -47,18 +47,19 @@ def test_path_parallel_matches_oracle(torch_cuda, models, name, block):
     ev = api.eval(m, q, qd, qdd, tau, fk=True, links=ee, rnea=True, crba=True, aba=True)
     torch.cuda.synchronize()
     ref = _oracle_all(tree, s, ee)
-    _assert_close({k: from_soa(v) for k, v in out.items()}, ref, f"path/{name}/{block}")
+    _assert_close({k: from_soa(v) for k, v in out.items()}, ref, f"{variant}/{name}/{block}")
     for k in out:
         assert torch.equal(ev[k], out[k]), k
 
 
-def test_path_parallel_theta_override_and_small_batches(torch_cuda, models):
+@pytest.mark.parametrize("variant", ["path", "pathwarp"])
+def test_path_parallel_theta_override_and_small_batches(torch_cuda, models, variant):
     torch = torch_cuda
     from oracle import rbd
     from paper_2605_31481_gb300 import api
     tree = TREES["humanoid29"]()
     m = models["humanoid29"]
-    m.set_launch(None, 64, "path")
+    m.set_launch(None, 64, variant)
     rng = np.random.default_rng(3)
     th = rbd.Model(tree).theta() * (1 + rng.uniform(-0.2, 0.2, (tree.n_bodies, 10)))
     tht = torch.from_numpy(th.astype(np.float32)).cuda()
@@ -80,6 +81,7 @@ def test_path_variant_needs_the_kernels(torch_cuda):
     with pytest.raises(_ffi.FstError):
         m.set_launch(["aba"], 64, "path")                       # not specialised
     wide = api.Model(w.legged(9, seed=1), specialize=["aba"])   # 9 leaves: no path-parallel kernel
-    with pytest.raises(_ffi.FstError):
-        wide.set_launch(["aba"], 64, "path")
+    for v in ("path", "pathwarp"):
+        with pytest.raises(_ffi.FstError):
+            wide.set_launch(["aba"], 64, v)
     wide.set_launch(["aba"], 64, "specialized")
