@@ -160,9 +160,14 @@ def tune(model, B, kinds=FORWARD_KINDS + ("eval",), links=None, use_cache=True, 
         variants = ["generic"] + (["specialized"] if kind in spec else []) + (["level"] if kind in LEVEL_KINDS else [])
         if kind == "eval" and "eval_mixed" in spec:
             variants.append("mixed")       # specialised fused kernel, roles mapped as their operators
+        if kind in spec and kind in LEVEL_KINDS:
+            variants += ["path", "pathwarp"]   # path-parallel, where the tree has at most 8 leaves
         for variant in variants:
-            for block in CANDIDATE_BLOCKS:
-                model.set_launch([kind], block, variant)
+            for block in ((0,) if variant == "pathwarp" else CANDIDATE_BLOCKS):
+                try:
+                    model.set_launch([kind], block, variant)
+                except _ffi.FstError:
+                    break                      # no such kernel for this tree
                 cands[f"{variant}/{block}"] = graph_time_us(fn)
         best = min(cands, key=cands.get)
         variant, block = best.split("/")
