@@ -302,9 +302,11 @@ def run_fst(args):
     desc = plan.describe()
     kname = {"fused": f"fused eval kernel ({desc['kinds']['eval']})",
              "hybrid": f"ABA kernel ({desc['kinds']['aba']}) on a parallel graph branch beside the fused kernel of "
-                       f"the other four ({desc['kinds']['eval']}), carveout {plan.carveout}",
+                       f"the other four ({desc['kinds']['eval']}), carveout {plan.carveout}" +
+                       (", ABA branch on a high-priority stream" if plan.prio else ""),
              "concurrent": "5 per-operator kernels on parallel graph branches (" +
-                           ", ".join(f"{k} {desc['kinds'][k]}" for k in OPS) + f"), carveout {plan.carveout}",
+                           ", ".join(f"{k} {desc['kinds'][k]}" for k in OPS) + f"), carveout {plan.carveout}" +
+                           (", stream priorities graded longest first" if plan.prio else ""),
              "sequential": "5 per-operator kernels in sequence"}[plan.mode]
     traffic = args.traffic
     if traffic is None:
