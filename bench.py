@@ -306,7 +306,7 @@ def run_fst(args):
                        (", ABA branch on a high-priority stream" if plan.prio else ""),
              "concurrent": "5 per-operator kernels on parallel graph branches (" +
                            ", ".join(f"{k} {desc['kinds'][k]}" for k in OPS) + f"), carveout {plan.carveout}" +
-                           (", stream priorities graded longest first" if plan.prio else ""),
+                           (", ABA branch on a high-priority stream" if plan.prio else ""),
              "sequential": "5 per-operator kernels in sequence"}[plan.mode]
     traffic = args.traffic
     if traffic is None:

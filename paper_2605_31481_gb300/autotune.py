@@ -201,9 +201,9 @@ class StepPlan:
     share an SM when they request the same shared-memory carveout, so the
     overlapping modes are also tried with one common carveout (100 %); the
     chosen carveout is applied with fst_set_smem_carveout. They are also
-    tried with graded stream priorities (the operator measured slowest on
-    the highest-priority stream): the block scheduler then dispatches the
-    longest chain's blocks first and fills the other SMs with the rest."""
+    tried with the operator measured slowest on a high-priority stream: the
+    block scheduler then dispatches the longest chain's blocks first and
+    fills the other SMs with the rest."""
 
     MODES = ("fused", "hybrid", "concurrent", "sequential")
 
@@ -214,10 +214,11 @@ class StepPlan:
         self.tuned = tune(model, B, FORWARD_KINDS + ("eval",), links=self.links, use_cache=use_cache,
                           verbose=verbose)
         self._plain = [torch.cuda.Stream(device=model.device) for _ in FORWARD_KINDS]
-        # graded priorities: the first stream forked (the longest operator) highest
-        self._ranked = [torch.cuda.Stream(device=model.device, priority=-(len(FORWARD_KINDS) - k))
+        # the first stream forked (the longest operator) at the device's highest
+        # priority (out-of-range values clamp to it), the others at the default
+        self._ranked = [torch.cuda.Stream(device=model.device, priority=-1000 if k == 0 else 0)
                         for k in range(len(FORWARD_KINDS))]
-        key = _key(model, "plan2", B)
+        key = _key(model, "plan3", B)
         hit = _load_cache().get(key) if use_cache else None
         if hit:
             self.times = {(k, c, p): v for k, c, p, v in hit["times"]}
