@@ -218,35 +218,53 @@ class StepPlan:
         # priority (out-of-range values clamp to it), the others at the default
         self._ranked = [torch.cuda.Stream(device=model.device, priority=-1000 if k == 0 else 0)
                         for k in range(len(FORWARD_KINDS))]
-        key = _key(model, "plan3", B)
+        key = _key(model, "plan4", B)
         hit = _load_cache().get(key) if use_cache else None
         if hit:
-            self.times = {(k, c, p): v for k, c, p, v in hit["times"]}
-            self._apply(hit["mode"], hit["carveout"], hit["prio"])
+            self.times = {(k, c, p, ev): v for k, c, p, ev, v in hit["times"]}
+            self._apply(hit["mode"], hit["carveout"], hit["prio"], hit["eval"])
             return
         buf = Buffers(model, B, self.links)
+        # the hybrid's fused kernel carries three roles, not the four the
+        # eval tuning measured: try the best few fused configurations there
+        ranked = sorted(self.tuned["eval"]["candidates"].items(), key=lambda kv: kv[1])
+        best_eval = f"{self.tuned['eval']['variant']}/{self.tuned['eval']['block']}"
+        hybrid_evals = []
+        for name, _ in ranked:
+            if name.split("/")[0] not in {c.split("/")[0] for c in hybrid_evals}:
+                hybrid_evals.append(name)
+            if len(hybrid_evals) == 3:
+                break
         times = {}
         for carveout in (-1, 100):
             api.set_smem_carveout(carveout)
             for mode in modes:
-                for prio in (False, True):
-                    if (carveout >= 0 or prio) and mode in ("fused", "sequential"):
-                        continue
-                    self.mode, self.streams = mode, self._ranked if prio else self._plain
-                    times[(mode, carveout, prio)] = graph_time_us(
-                        lambda: self(buf.q, buf.qd, buf.qdd, buf.tau, buf.out))
+                for ev in (hybrid_evals if mode == "hybrid" else [best_eval]):
+                    self._set_eval(ev)
+                    for prio in (False, True):
+                        if (carveout >= 0 or prio) and mode in ("fused", "sequential"):
+                            continue
+                        self.mode, self.streams = mode, self._ranked if prio else self._plain
+                        times[(mode, carveout, prio, ev)] = graph_time_us(
+                            lambda: self(buf.q, buf.qd, buf.qdd, buf.tau, buf.out))
         self.times = times
         self._apply(*min(times, key=times.get))
         if use_cache:
             _store_cache({key: {"mode": self.mode, "carveout": self.carveout, "prio": self.prio,
-                                "times": [[k, c, p, round(v, 3)] for (k, c, p), v in times.items()]}})
+                                "eval": self.eval_config,
+                                "times": [[k, c, p, ev, round(v, 3)] for (k, c, p, ev), v in times.items()]}})
 
-    def _apply(self, mode, carveout, prio):
-        self.mode, self.carveout, self.prio = mode, carveout, bool(prio)
+    def _set_eval(self, config):
+        variant, block = config.split("/")
+        self.model.set_launch(["eval"], int(block), variant)
+
+    def _apply(self, mode, carveout, prio, eval_config):
+        self.mode, self.carveout, self.prio, self.eval_config = mode, carveout, bool(prio), eval_config
         self.streams = self._ranked if self.prio else self._plain
+        self._set_eval(eval_config)
         api.set_smem_carveout(carveout)
         self.fused = mode == "fused"
-        self.expected_us = self.times[(mode, carveout, self.prio)]
+        self.expected_us = self.times[(mode, carveout, self.prio, eval_config)]
 
     def _ops(self, q, qd, qdd, tau, out):
         m = self.model
@@ -283,8 +301,10 @@ class StepPlan:
         return out
 
     def describe(self):
+        kinds = {k: f"{v['variant']}/{v['block']}" for k, v in self.tuned.items()}
+        kinds["eval"] = self.eval_config
         return {"mode": self.mode, "carveout": self.carveout, "priorities": self.prio,
-                "us": {f"{k[0]}{'' if k[1] < 0 else f'@{k[1]}%'}{'+prio' if k[2] else ''}": round(v, 3)
-                       for k, v in self.times.items()},
-                "kinds": {k: f"{v['variant']}/{v['block']}" for k, v in self.tuned.items()},
+                "us": {f"{k[0]}{'[' + k[3] + ']' if k[0] == 'hybrid' else ''}{'' if k[1] < 0 else f'@{k[1]}%'}"
+                       f"{'+prio' if k[2] else ''}": round(v, 3) for k, v in self.times.items()},
+                "kinds": kinds,
                 "eval_candidates_us": self.tuned["eval"]["candidates"]}

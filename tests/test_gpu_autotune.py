@@ -85,7 +85,7 @@ def test_step_plan_matches_per_operator_calls(torch_cuda, tmp_path, monkeypatch)
                "M": api.crba(m, q), "qdd": api.aba(m, q, qd, tau)}
         for k, tol in TOL.items():
             assert env_err(from_soa(out[k]), from_soa(ref[k])).max() <= tol, (mode, k)
-    assert set(plan.MODES) <= set(plan.describe()["us"])
+    assert set(plan.MODES) <= {k.split("[")[0].split("@")[0].split("+")[0] for k in plan.describe()["us"]}
     from paper_2605_31481_gb300 import api as _api
     _api.set_smem_carveout(-1)
     ref = {"poses": api.fk(m, q), "J": api.jacobian(m, q, tree.ee), "tau": api.rnea(m, q, qd, qdd),
