@@ -286,12 +286,13 @@ def run_fst(args):
     value = world * B * K / (ms / 1e3)
 
     # end to end through the public binding, host buffers in and out
-    e2e = run_e2e(torch, fst, model, tree, B, links, st, dev, K, args.warmup)
+    e2e = run_e2e(torch, fst, model, tree, B, links, st, dev, min(K, 5000), args.warmup, plan=plan,
+                  slots=args.e2e_slots)
     if world > 1:
         tt = torch.tensor([e2e["ms"]], device=dev)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         e2e["ms"] = float(tt.item())
-    e2e_value = world * B * K / (e2e["ms"] / 1e3)
+    e2e_value = world * B * e2e["steps"] / (e2e["ms"] / 1e3)
 
     pk = peaks()
     p_alu = fp32_peak_tflops(pk["sm_max_mhz"])
@@ -350,7 +351,8 @@ def run_fst(args):
             "per_op_env_evals_per_s": {k: round(B / (v / 1e3), 1) for k, v in per_op_ms.items()},
             "roofline": roof,
             "e2e": {"value": round(e2e_value, 1), "unit": "env-evals/s", "h2d_bytes_per_step": e2e["h2d"],
-                    "d2h_bytes_per_step": e2e["d2h"]},
+                    "d2h_bytes_per_step": e2e["d2h"], "steps": e2e["steps"],
+                    "pipelined_slots": e2e["slots"]},
             "gpu_launches": K * {"fused": 1, "hybrid": 2}.get(plan.mode, len(OPS)),
             "kernels": kernels,
             "plan": desc,
@@ -595,38 +597,55 @@ def ctypes_ptr(t):
     return ctypes.c_void_p(t.data_ptr())
 
 
-def run_e2e(torch, fst, model, tree, B, links, st, dev, K, warmup):
-    """Same step through the public binding, with the inputs copied from
-    pinned host memory and every output read back to pinned host memory."""
+def run_e2e(torch, fst, model, tree, B, links, st, dev, K, warmup, plan=None, slots=2):
+    """The same step through the public binding, end to end: every step copies
+    its inputs from pinned host memory, runs the step (the tuned step plan),
+    and reads every output back into pinned host memory. Steps are pipelined
+    over `slots` streams, each with its own device and host buffers, so one
+    step's read-back overlaps the next step's upload and compute; the timed
+    region ends when the last step's outputs are on the host."""
     nq, nv, nb, nl = tree.nq, tree.nv, tree.n_bodies, len(links)
-    host_in = {k: torch.from_numpy(np.ascontiguousarray(st[k][:B].T.astype(np.float32))).pin_memory()
-               for k in ("q", "qd", "qdd", "tau")}
-    dev_in = {k: torch.empty_like(v, device=dev) for k, v in host_in.items()}
     shapes = {"poses": (nb, 12, B), "J": (nl, 6, nv, B), "tau": (nv, B), "M": (nv, nv, B), "qdd": (nv, B)}
-    dev_out = {k: torch.empty(s, device=dev) for k, s in shapes.items()}
-    host_out = {k: torch.empty(s).pin_memory() for k, s in shapes.items()}
+    src = {k: np.ascontiguousarray(st[k][:B].T.astype(np.float32)) for k in ("q", "qd", "qdd", "tau")}
+    S = []
+    for _ in range(slots):
+        host_in = {k: torch.from_numpy(v.copy()).pin_memory() for k, v in src.items()}
+        S.append({"stream": torch.cuda.Stream(device=dev), "host_in": host_in,
+                  "dev_in": {k: torch.empty_like(v, device=dev) for k, v in host_in.items()},
+                  "dev_out": {k: torch.empty(sh, device=dev) for k, sh in shapes.items()},
+                  "host_out": {k: torch.empty(sh).pin_memory() for k, sh in shapes.items()}})
 
-    def step():
-        for k in dev_in:
-            dev_in[k].copy_(host_in[k], non_blocking=True)
-        fst.eval(model, dev_in["q"], dev_in["qd"], dev_in["qdd"], dev_in["tau"], fk=True, links=links, rnea=True,
-                 crba=True, aba=True, out=dev_out)
-        for k in dev_out:
-            host_out[k].copy_(dev_out[k], non_blocking=True)
+    def step(k):
+        sl = S[k % slots]
+        with torch.cuda.stream(sl["stream"]):
+            for n in sl["dev_in"]:
+                sl["dev_in"][n].copy_(sl["host_in"][n], non_blocking=True)
+            i = sl["dev_in"]
+            if plan is not None:
+                plan(i["q"], i["qd"], i["qdd"], i["tau"], sl["dev_out"])
+            else:
+                fst.eval(model, i["q"], i["qd"], i["qdd"], i["tau"], fk=True, links=links, rnea=True, crba=True,
+                         aba=True, out=sl["dev_out"])
+            for n in sl["dev_out"]:
+                sl["host_out"][n].copy_(sl["dev_out"][n], non_blocking=True)
 
-    for _ in range(max(3, warmup // 10)):
-        step()
+    for k in range(max(3, warmup // 10)):
+        step(k)
     torch.cuda.synchronize()
-    s = torch.cuda.current_stream()
+    cur = torch.cuda.current_stream()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a.record(s)
-    for _ in range(K):
-        step()
-    b.record(s)
+    a.record(cur)
+    for sl in S:
+        sl["stream"].wait_stream(cur)
+    for k in range(K):
+        step(k)
+    for sl in S:
+        cur.wait_stream(sl["stream"])
+    b.record(cur)
     torch.cuda.synchronize()
-    h2d = sum(v.numel() * 4 for v in host_in.values())
-    d2h = sum(v.numel() * 4 for v in host_out.values())
-    return {"ms": a.elapsed_time(b), "h2d": h2d, "d2h": d2h}
+    h2d = sum(v.numel() * 4 for v in S[0]["host_in"].values())
+    d2h = sum(v.numel() * 4 for v in S[0]["host_out"].values())
+    return {"ms": a.elapsed_time(b), "h2d": h2d, "d2h": d2h, "slots": slots, "steps": K}
 
 
 # ---------------------------------------------------------------------------
@@ -753,6 +772,8 @@ def main():
     ap.add_argument("--impl", choices=("fst", "reference"), default="fst")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the secondary legs (fwd+bwd, RL-step graph, humanoid sweep) after the timed step")
+    ap.add_argument("--e2e-slots", type=int, default=2,
+                    help="end-to-end leg: steps in flight (streams with their own buffers)")
     ap.add_argument("--traffic", type=float, default=None,
                     help="dram bytes per launch of the dominant kernel from an ncu capture (else null)")
     args = ap.parse_args()
