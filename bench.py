@@ -598,39 +598,65 @@ def ctypes_ptr(t):
 
 
 def run_e2e(torch, fst, model, tree, B, links, st, dev, K, warmup, plan=None, slots=2):
-    """The same step through the public binding, end to end: every step copies
-    its inputs from pinned host memory, runs the step (the tuned step plan),
-    and reads every output back into pinned host memory. Steps are pipelined
-    over `slots` streams, each with its own device and host buffers, so one
-    step's read-back overlaps the next step's upload and compute; the timed
+    """The same step through the public binding, end to end: every step
+    uploads its inputs from pinned host memory, runs the step (the tuned step
+    plan) and reads every output back into pinned host memory. Inputs and
+    outputs each live in one contiguous block (one copy per direction), and
+    the whole step is captured once as a CUDA graph and replayed, as a
+    training loop with a fixed step shape would. With slots > 1, that many
+    such step graphs (each with its own buffers and stream) alternate, so one
+    step's read-back overlaps the next step's upload and compute. The timed
     region ends when the last step's outputs are on the host."""
     nq, nv, nb, nl = tree.nq, tree.nv, tree.n_bodies, len(links)
-    shapes = {"poses": (nb, 12, B), "J": (nl, 6, nv, B), "tau": (nv, B), "M": (nv, nv, B), "qdd": (nv, B)}
-    src = {k: np.ascontiguousarray(st[k][:B].T.astype(np.float32)) for k in ("q", "qd", "qdd", "tau")}
+    in_rows = {"q": nq, "qd": nv, "qdd": nv, "tau": nv}
+    out_shapes = {"poses": (nb, 12, B), "J": (nl, 6, nv, B), "tau": (nv, B), "M": (nv, nv, B), "qdd": (nv, B)}
+    n_in = sum(in_rows.values()) * B
+    n_out = sum(int(np.prod(sh)) for sh in out_shapes.values())
+    packed = np.concatenate([np.ascontiguousarray(st[k][:B].T.astype(np.float32)).ravel() for k in in_rows])
+
+    def views(flat, layout):
+        out, off = {}, 0
+        for k, sh in layout.items():
+            sh = (sh, B) if isinstance(sh, int) else sh
+            n = int(np.prod(sh))
+            out[k] = flat[off:off + n].view(*sh)
+            off += n
+        return out
+
     S = []
     for _ in range(slots):
-        host_in = {k: torch.from_numpy(v.copy()).pin_memory() for k, v in src.items()}
-        S.append({"stream": torch.cuda.Stream(device=dev), "host_in": host_in,
-                  "dev_in": {k: torch.empty_like(v, device=dev) for k, v in host_in.items()},
-                  "dev_out": {k: torch.empty(sh, device=dev) for k, sh in shapes.items()},
-                  "host_out": {k: torch.empty(sh).pin_memory() for k, sh in shapes.items()}})
+        sl = {"stream": torch.cuda.Stream(device=dev),
+              "host_in": torch.from_numpy(packed.copy()).pin_memory(),
+              "dev_in": torch.empty(n_in, device=dev), "dev_out": torch.empty(n_out, device=dev),
+              "host_out": torch.empty(n_out).pin_memory()}
+        sl["in"], sl["out"] = views(sl["dev_in"], in_rows), views(sl["dev_out"], out_shapes)
+        S.append(sl)
 
-    def step(k):
+    def step(sl):
+        sl["dev_in"].copy_(sl["host_in"], non_blocking=True)
+        i = sl["in"]
+        if plan is not None:
+            plan(i["q"], i["qd"], i["qdd"], i["tau"], sl["out"])
+        else:
+            fst.eval(model, i["q"], i["qd"], i["qdd"], i["tau"], fk=True, links=links, rnea=True, crba=True, aba=True,
+                     out=sl["out"])
+        sl["host_out"].copy_(sl["dev_out"], non_blocking=True)
+
+    for sl in S:
+        with torch.cuda.stream(sl["stream"]):
+            for _ in range(3):
+                step(sl)
+        torch.cuda.synchronize()
+        sl["graph"] = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(sl["graph"], stream=sl["stream"]):
+            step(sl)
+    def replay(k):
         sl = S[k % slots]
         with torch.cuda.stream(sl["stream"]):
-            for n in sl["dev_in"]:
-                sl["dev_in"][n].copy_(sl["host_in"][n], non_blocking=True)
-            i = sl["dev_in"]
-            if plan is not None:
-                plan(i["q"], i["qd"], i["qdd"], i["tau"], sl["dev_out"])
-            else:
-                fst.eval(model, i["q"], i["qd"], i["qdd"], i["tau"], fk=True, links=links, rnea=True, crba=True,
-                         aba=True, out=sl["dev_out"])
-            for n in sl["dev_out"]:
-                sl["host_out"][n].copy_(sl["dev_out"][n], non_blocking=True)
+            sl["graph"].replay()
 
     for k in range(max(3, warmup // 10)):
-        step(k)
+        replay(k)
     torch.cuda.synchronize()
     cur = torch.cuda.current_stream()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -638,14 +664,12 @@ def run_e2e(torch, fst, model, tree, B, links, st, dev, K, warmup, plan=None, sl
     for sl in S:
         sl["stream"].wait_stream(cur)
     for k in range(K):
-        step(k)
+        replay(k)
     for sl in S:
         cur.wait_stream(sl["stream"])
     b.record(cur)
     torch.cuda.synchronize()
-    h2d = sum(v.numel() * 4 for v in S[0]["host_in"].values())
-    d2h = sum(v.numel() * 4 for v in S[0]["host_out"].values())
-    return {"ms": a.elapsed_time(b), "h2d": h2d, "d2h": d2h, "slots": slots, "steps": K}
+    return {"ms": a.elapsed_time(b), "h2d": n_in * 4, "d2h": n_out * 4, "slots": slots, "steps": K}
 
 
 # ---------------------------------------------------------------------------
