@@ -597,7 +597,7 @@ def ctypes_ptr(t):
     return ctypes.c_void_p(t.data_ptr())
 
 
-def run_e2e(torch, fst, model, tree, B, links, st, dev, K, warmup, plan=None, slots=2):
+def run_e2e(torch, fst, model, tree, B, links, st, dev, K, warmup, plan=None, slots=3):
     """The same step through the public binding, end to end: every step
     uploads its inputs from pinned host memory, runs the step (the tuned step
     plan) and reads every output back into pinned host memory. Inputs and
@@ -796,7 +796,7 @@ def main():
     ap.add_argument("--impl", choices=("fst", "reference"), default="fst")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the secondary legs (fwd+bwd, RL-step graph, humanoid sweep) after the timed step")
-    ap.add_argument("--e2e-slots", type=int, default=2,
+    ap.add_argument("--e2e-slots", type=int, default=3,
                     help="end-to-end leg: steps in flight (streams with their own buffers)")
     ap.add_argument("--traffic", type=float, default=None,
                     help="dram bytes per launch of the dominant kernel from an ncu capture (else null)")
