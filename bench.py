@@ -534,7 +534,8 @@ def sysid(torch, fst, w, steps=500):
     setting on a synthetic arm): B = 8192 samples, measured torques = true
     RNEA x (1 + 0.05 N(0,1)), all 70 parameters start perturbed by
     U(-30%, +30%), Adam (lr 1e-2) for `steps` steps, each step one fused
-    loss-and-gradient kernel."""
+    loss-and-gradient kernel; and the exact least-squares minimiser from
+    71 + 1 calls of the same kernel."""
     from paper_2605_31481_gb300 import sysid as sid
     tree = w.chain(7, seed=0)
     B = 8192
@@ -559,11 +560,21 @@ def sysid(torch, fst, w, steps=500):
     dt = time.perf_counter() - t0
     err = sid.mass_errors(theta, true.cpu().numpy())
     err0 = sid.mass_errors(theta0, true.cpu().numpy())
-    return {"workload": "chain7, B=8192, 70 parameters, 5% torque noise, +-30% initial error, Adam 500 steps",
-            "steps": steps, "seconds": round(dt, 3), "steps_per_s": round(steps / dt, 1),
-            "mass_error_pct_initial_mean": round(100 * float(err0.mean()), 2),
-            "mass_error_pct_mean": round(100 * float(err.mean()), 2),
-            "mass_error_pct_per_link": [round(100 * float(x), 2) for x in err]}
+    sid.identify_least_squares(m, q, qd, qdd, tau_meas, theta0)    # warm
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    theta_ls, _ = sid.identify_least_squares(m, q, qd, qdd, tau_meas, theta0)
+    torch.cuda.synchronize()
+    dt_ls = time.perf_counter() - t0
+    err_ls = sid.mass_errors(theta_ls, true.cpu().numpy())
+    return {"workload": "chain7, B=8192, 70 parameters, 5% torque noise, +-30% initial error",
+            "adam": {"steps": steps, "seconds": round(dt, 3), "steps_per_s": round(steps / dt, 1),
+                     "mass_error_pct_mean": round(100 * float(err.mean()), 2),
+                     "mass_error_pct_per_link": [round(100 * float(x), 2) for x in err]},
+            "least_squares": {"kernel_calls": int(true.numel()) + 2, "seconds": round(dt_ls, 4),
+                              "mass_error_pct_mean": round(100 * float(err_ls.mean()), 2),
+                              "mass_error_pct_per_link": [round(100 * float(x), 2) for x in err_ls]},
+            "mass_error_pct_initial_mean": round(100 * float(err0.mean()), 2)}
 
 
 def per_op_times(torch, launch, sets, R, stream, K_op, hot=False):

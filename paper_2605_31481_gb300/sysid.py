@@ -6,7 +6,8 @@ through autograd with L-BFGS. Here every iteration is one fused kernel
 (fst_rnea_loss_grad: the loss and its gradient with respect to all 10
 inertial parameters of every link, deterministic) followed by an Adam step on
 the normalised parameters s = theta / theta_init, as plain torch ops on 10*n
-numbers. With world_size > 1 (torch.distributed initialised), each rank holds
+numbers; or, since the loss is quadratic in theta, its exact minimiser from
+10*n + 2 kernel calls (identify_least_squares). With world_size > 1 (torch.distributed initialised), each rank holds
 a contiguous shard of the environments and the gradients and losses are
 summed with one all-reduce per step.
 """
@@ -62,6 +63,48 @@ def identify(model, q, qd, qdd, tau_meas, theta_init, steps=500, lr=1e-2, betas=
         vh = v / (1 - b2 ** t)
         s.sub_(lr * mh / (vh.sqrt() + eps))
     return (s * scale).contiguous(), losses
+
+
+def identify_least_squares(model, q, qd, qdd, tau_meas, theta_init, rcond=1e-5):
+    """Exact minimiser of the same loss, which is quadratic in theta (tau is
+    linear in the inertial parameters): with s = theta / theta_init,
+    L(s) = |Y D s - tau_meas|^2, D = diag(theta_init). Its Hessian
+    H = 2 D Y^T Y D is built column by column from the fused loss-gradient
+    kernel with zero measured torques (then grad = H s exactly, so column k
+    is the gradient at s = e_k: 10 n_b kernel calls), the gradient g at the
+    initial guess from one more call, and the step s = 1 - H^+ g is solved in
+    FP64 with a pseudo-inverse that drops eigenvalues below rcond times the
+    largest. Parameter combinations the data cannot determine (H's null
+    space) keep their initial values. With torch.distributed initialised each
+    rank passes its shard and every gradient is summed across ranks.
+    Returns (theta, loss at theta) with the loss evaluated by the kernel."""
+    n = theta_init.numel()
+    scale = theta_init.reshape(-1).double()
+    scratch = api.adjoint_scratch(model, q.shape[1])
+    buf = torch.empty(n + 1, device=theta_init.device)
+    zero_tau = torch.zeros_like(tau_meas)
+
+    def grad(s_vec, tau):
+        theta = (s_vec * scale).float().view_as(theta_init).contiguous()
+        api.rnea_loss_grad(model, q, qd, qdd, tau, theta=theta, scratch=scratch, out=buf)
+        allreduce_sum(buf)
+        return buf[:-1].double() * scale, float(buf[-1])
+
+    H = torch.empty(n, n, dtype=torch.float64, device=theta_init.device)
+    for k in range(n):
+        e = torch.zeros(n, dtype=torch.float64, device=theta_init.device)
+        e[k] = 1.0
+        H[:, k] = grad(e, zero_tau)[0]
+    H = 0.5 * (H + H.T)
+    ones = torch.ones(n, dtype=torch.float64, device=theta_init.device)
+    g, _ = grad(ones, tau_meas)
+    lam, V = torch.linalg.eigh(H)
+    keep = lam > rcond * lam.abs().max()
+    inv = torch.where(keep, 1.0 / torch.where(keep, lam, torch.ones_like(lam)), torch.zeros_like(lam))
+    s_vec = ones - V @ (inv * (V.T @ g))
+    theta = (s_vec * scale).float().view_as(theta_init).contiguous()
+    _, loss = grad(s_vec, tau_meas)
+    return theta, loss
 
 
 def mass_errors(theta, true_theta):
