@@ -107,6 +107,50 @@ def identify_least_squares(model, q, qd, qdd, tau_meas, theta_init, rcond=1e-5):
     return theta, loss
 
 
+def mass_directions(theta_known):
+    """(n_b, 10) rows d theta / d m per link with the centre of mass and the
+    rotational inertia about it held fixed: [1, c, S(c)], S(c) the
+    parallel-axis term (xx, xy, yy, xz, yz, zz) of a unit mass at c."""
+    th = theta_known.double()
+    c = th[:, 1:4] / th[:, 0:1]
+    x, y, z = c[:, 0], c[:, 1], c[:, 2]
+    S = torch.stack([y * y + z * z, -x * y, x * x + z * z, -x * z, -y * z, x * x + y * y], dim=1)
+    return torch.cat([torch.ones_like(x)[:, None], c, S], dim=1)
+
+
+def identify_masses(model, q, qd, qdd, tau_meas, theta_known):
+    """The paper's identification setting (Sec. 4.3): only the link masses
+    are unknown, each link's centre of mass and rotational inertia about it
+    are known (taken from theta_known). theta(m) is affine in the masses, so
+    the least-squares masses solve a n_b x n_b system whose matrix and
+    right-hand side come from n_b + 1 calls of the fused loss-gradient
+    kernel (zero torques give the columns, the measured ones the gradient at
+    the known parameters). Returns (masses (n_b,), theta at those masses)."""
+    nb = theta_known.shape[0]
+    phi = mass_directions(theta_known)                       # (n_b, 10)
+    scratch = api.adjoint_scratch(model, q.shape[1])
+    buf = torch.empty(nb * 10 + 1, device=theta_known.device)
+    zero_tau = torch.zeros_like(tau_meas)
+
+    def grad(theta64, tau):
+        api.rnea_loss_grad(model, q, qd, qdd, tau, theta=theta64.float().contiguous(), scratch=scratch, out=buf)
+        allreduce_sum(buf)
+        return buf[:-1].double().view(nb, 10)
+
+    H = torch.empty(nb, nb, dtype=torch.float64, device=theta_known.device)
+    for k in range(nb):
+        d = torch.zeros(nb, 10, dtype=torch.float64, device=theta_known.device)
+        d[k] = phi[k]
+        H[:, k] = (grad(d, zero_tau) * phi).sum(dim=1)        # Phi^T (2 Y^T Y) Phi e_k
+    H = 0.5 * (H + H.T)
+    base = theta_known.double()
+    g = (grad(base, tau_meas) * phi).sum(dim=1)              # gradient in the masses at theta_known
+    dm = torch.linalg.solve(H, -g)
+    m = base[:, 0] + dm
+    theta = base + dm[:, None] * phi
+    return m.float(), theta.float().contiguous()
+
+
 def mass_errors(theta, true_theta):
     """Per-link relative mass error |m_hat - m| / m (numpy)."""
     th = np.asarray(theta.detach().cpu() if isinstance(theta, torch.Tensor) else theta, dtype=np.float64)
