@@ -218,7 +218,7 @@ class StepPlan:
         # priority (out-of-range values clamp to it), the others at the default
         self._ranked = [torch.cuda.Stream(device=model.device, priority=-1000 if k == 0 else 0)
                         for k in range(len(FORWARD_KINDS))]
-        key = _key(model, "plan4", B)
+        key = _key(model, "plan5", B)
         hit = _load_cache().get(key) if use_cache else None
         if hit:
             self.times = {(k, c, p, ev): v for k, c, p, ev, v in hit["times"]}
@@ -229,12 +229,7 @@ class StepPlan:
         # eval tuning measured: try the best few fused configurations there
         ranked = sorted(self.tuned["eval"]["candidates"].items(), key=lambda kv: kv[1])
         best_eval = f"{self.tuned['eval']['variant']}/{self.tuned['eval']['block']}"
-        hybrid_evals = []
-        for name, _ in ranked:
-            if name.split("/")[0] not in {c.split("/")[0] for c in hybrid_evals}:
-                hybrid_evals.append(name)
-            if len(hybrid_evals) == 3:
-                break
+        hybrid_evals = [name for name, _ in ranked[:5]]
         times = {}
         for carveout in (-1, 100):
             api.set_smem_carveout(carveout)
