@@ -218,7 +218,7 @@ class StepPlan:
         # priority (out-of-range values clamp to it), the others at the default
         self._ranked = [torch.cuda.Stream(device=model.device, priority=-1000 if k == 0 else 0)
                         for k in range(len(FORWARD_KINDS))]
-        key = _key(model, "plan5", B)
+        key = _key(model, "plan6", B)
         hit = _load_cache().get(key) if use_cache else None
         if hit:
             self.times = {(k, c, p, ev): v for k, c, p, ev, v in hit["times"]}
@@ -230,6 +230,10 @@ class StepPlan:
         ranked = sorted(self.tuned["eval"]["candidates"].items(), key=lambda kv: kv[1])
         best_eval = f"{self.tuned['eval']['variant']}/{self.tuned['eval']['block']}"
         hybrid_evals = [name for name, _ in ranked[:5]]
+        # beside the ABA branch, fewer and larger fused blocks can win: every
+        # block size of the specialised fused kernel is tried as well
+        hybrid_evals += [n for n in (f"specialized/{b}" for b in CANDIDATE_BLOCKS)
+                         if n in self.tuned["eval"]["candidates"] and n not in hybrid_evals]
         times = {}
         for carveout in (-1, 100):
             api.set_smem_carveout(carveout)
