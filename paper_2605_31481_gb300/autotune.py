@@ -218,7 +218,7 @@ class StepPlan:
         # priority (out-of-range values clamp to it), the others at the default
         self._ranked = [torch.cuda.Stream(device=model.device, priority=-1000 if k == 0 else 0)
                         for k in range(len(FORWARD_KINDS))]
-        key = _key(model, "plan6", B)
+        key = _key(model, "plan7", B)
         hit = _load_cache().get(key) if use_cache else None
         if hit:
             self.times = {(k, c, p, ev): v for k, c, p, ev, v in hit["times"]}
@@ -234,11 +234,15 @@ class StepPlan:
         # block size of the specialised fused kernel is tried as well
         hybrid_evals += [n for n in (f"specialized/{b}" for b in CANDIDATE_BLOCKS)
                          if n in self.tuned["eval"]["candidates"] and n not in hybrid_evals]
+        # and the ABA branch at its three best configurations
+        best_aba = f"{self.tuned['aba']['variant']}/{self.tuned['aba']['block']}"
+        abas = [n for n, _ in sorted(self.tuned["aba"]["candidates"].items(), key=lambda kv: kv[1])[:3]]
+        hybrid_cfgs = [f"{ev}|{ab}" for ev in hybrid_evals for ab in abas]
         times = {}
         for carveout in (-1, 100):
             api.set_smem_carveout(carveout)
             for mode in modes:
-                for ev in (hybrid_evals if mode == "hybrid" else [best_eval]):
+                for ev in (hybrid_cfgs if mode == "hybrid" else [f"{best_eval}|{best_aba}"]):
                     self._set_eval(ev)
                     for prio in (False, True):
                         if (carveout >= 0 or prio) and mode in ("fused", "sequential"):
@@ -254,8 +258,10 @@ class StepPlan:
                                 "times": [[k, c, p, ev, round(v, 3)] for (k, c, p, ev), v in times.items()]}})
 
     def _set_eval(self, config):
-        variant, block = config.split("/")
-        self.model.set_launch(["eval"], int(block), variant)
+        """config: "<eval variant>/<block>|<aba variant>/<block>"."""
+        for kind, part in zip(("eval", "aba"), config.split("|")):
+            variant, block = part.split("/")
+            self.model.set_launch([kind], int(block), variant)
 
     def _apply(self, mode, carveout, prio, eval_config):
         self.mode, self.carveout, self.prio, self.eval_config = mode, carveout, bool(prio), eval_config
@@ -301,7 +307,7 @@ class StepPlan:
 
     def describe(self):
         kinds = {k: f"{v['variant']}/{v['block']}" for k, v in self.tuned.items()}
-        kinds["eval"] = self.eval_config
+        kinds["eval"], kinds["aba"] = self.eval_config.split("|")
         return {"mode": self.mode, "carveout": self.carveout, "priorities": self.prio,
                 "us": {f"{k[0]}{'[' + k[3] + ']' if k[0] == 'hybrid' else ''}{'' if k[1] < 0 else f'@{k[1]}%'}"
                        f"{'+prio' if k[2] else ''}": round(v, 3) for k, v in self.times.items()},
