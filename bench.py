@@ -49,7 +49,7 @@ OPS = ("fk", "jacobian", "rnea", "crba", "aba")
 # plan and a hash of the kernel sources at capture time: a source change
 # since the capture makes the entry stale and the reported traffic null.
 NCU_TRAFFIC = {
-    ("hybrid", "level/256", "specialized/128", "32977bc62627"): 781824 + 585728,
+    ("hybrid", "level/256", "specialized/256", "0f2e525d4ebd"): 782080 + 585472,
 }
 
 
