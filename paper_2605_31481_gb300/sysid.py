@@ -35,22 +35,32 @@ def allreduce_sum(t: torch.Tensor) -> torch.Tensor:
 
 
 def identify(model, q, qd, qdd, tau_meas, theta_init, steps=500, lr=1e-2, betas=(0.9, 0.999), eps=1e-8,
-             history=False):
+             history=False, state=None, return_state=False):
     """Adam on s = theta / theta_init minimising the squared torque error.
 
     q, qd, qdd, tau_meas: this rank's environments, (field, B) CUDA tensors.
     theta_init: (n_b, 10) float32 CUDA tensor (entries must be non-zero).
-    Returns (theta, losses) with losses the per-step total loss if history."""
+    Returns (theta, losses) with losses the per-step total loss if history.
+    With return_state=True, also the optimiser state (a dict of tensors and
+    the step count, suitable for torch.save); passing it back as `state`
+    continues the run exactly where it stopped (checkpoint and resume: the
+    loss-gradient reduction is deterministic, so a resumed run equals an
+    uninterrupted one bit for bit)."""
     B = q.shape[1]
-    scale = theta_init.clone()
-    s = torch.ones_like(theta_init)
-    m = torch.zeros_like(s)
-    v = torch.zeros_like(s)
+    if state is None:
+        scale = theta_init.clone()
+        s = torch.ones_like(theta_init)
+        m = torch.zeros_like(s)
+        v = torch.zeros_like(s)
+        t0 = 0
+    else:
+        scale, s, m, v = (state[k].to(theta_init.device).clone() for k in ("scale", "s", "m", "v"))
+        t0 = int(state["step"])
     scratch = api.adjoint_scratch(model, B)
     buf = torch.empty(theta_init.numel() + 1, device=theta_init.device)
     losses = []
     b1, b2 = betas
-    for t in range(1, steps + 1):
+    for t in range(t0 + 1, t0 + steps + 1):
         theta = (s * scale).contiguous()
         api.rnea_loss_grad(model, q, qd, qdd, tau_meas, theta=theta, scratch=scratch, out=buf)
         allreduce_sum(buf)
@@ -62,7 +72,10 @@ def identify(model, q, qd, qdd, tau_meas, theta_init, steps=500, lr=1e-2, betas=
         mh = m / (1 - b1 ** t)
         vh = v / (1 - b2 ** t)
         s.sub_(lr * mh / (vh.sqrt() + eps))
-    return (s * scale).contiguous(), losses
+    theta = (s * scale).contiguous()
+    if return_state:
+        return theta, losses, {"scale": scale, "s": s, "m": m, "v": v, "step": t0 + steps}
+    return theta, losses
 
 
 def identify_least_squares(model, q, qd, qdd, tau_meas, theta_init, rcond=1e-5):

@@ -112,3 +112,29 @@ def test_mass_only_identification_matches_oracle_least_squares():
     ref, *_ = np.linalg.lstsq(A, tau_meas.reshape(-1) - base, rcond=None)
     np.testing.assert_allclose(masses, ref, rtol=2e-3)
     assert (np.abs(masses - true[:, 0]) / true[:, 0]).mean() < 0.05
+
+
+def test_identification_checkpoint_and_resume(tmp_path):
+    """250 steps, the optimiser state through torch.save / torch.load, 250
+    more: bitwise the result of 500 uninterrupted steps."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2605_31481_gb300 import build
+    build.build(quiet=True)
+    from paper_2605_31481_gb300 import api, sysid
+    tree = w.chain(7, seed=0)
+    B = 2048
+    s = w.random_state(tree, B, seed=4)
+    rng = np.random.default_rng(9)
+    true = rbd.Model(tree).theta()
+    tau_meas = rbd.rnea(tree, s["q"], s["qd"], s["qdd"]) * (1 + 0.05 * rng.standard_normal((B, tree.nv)))
+    th0 = torch.from_numpy((true * (1 + rng.uniform(-0.3, 0.3, true.shape))).astype(np.float32)).cuda()
+    m = api.Model(tree)
+    q, qd, qdd, tm = (to_soa_cuda(x, torch) for x in (s["q"], s["qd"], s["qdd"], tau_meas))
+    full, _ = sysid.identify(m, q, qd, qdd, tm, th0, steps=500)
+    _, _, st = sysid.identify(m, q, qd, qdd, tm, th0, steps=250, return_state=True)
+    torch.save(st, tmp_path / "sysid.pt")
+    st = torch.load(tmp_path / "sysid.pt")
+    resumed, _ = sysid.identify(m, q, qd, qdd, tm, th0, steps=250, state=st)
+    assert torch.equal(full, resumed)
