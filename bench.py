@@ -287,7 +287,7 @@ def run_fst(args):
 
     # end to end through the public binding, host buffers in and out
     e2e = run_e2e(torch, fst, model, tree, B, links, st, dev, min(K, 5000), args.warmup, plan=plan,
-                  slots=args.e2e_slots)
+                  slots=args.e2e_slots, split=args.e2e_split)
     if world > 1:
         tt = torch.tensor([e2e["ms"]], device=dev)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
@@ -352,7 +352,7 @@ def run_fst(args):
             "roofline": roof,
             "e2e": {"value": round(e2e_value, 1), "unit": "env-evals/s", "h2d_bytes_per_step": e2e["h2d"],
                     "d2h_bytes_per_step": e2e["d2h"], "steps": e2e["steps"],
-                    "pipelined_slots": e2e["slots"]},
+                    "pipelined_slots": e2e["slots"], "readback_chunks": e2e["readback_chunks"]},
             "gpu_launches": K * {"fused": 1, "hybrid": 2}.get(plan.mode, len(OPS)),
             "kernels": kernels,
             "plan": desc,
@@ -619,7 +619,7 @@ def ctypes_ptr(t):
     return ctypes.c_void_p(t.data_ptr())
 
 
-def run_e2e(torch, fst, model, tree, B, links, st, dev, K, warmup, plan=None, slots=3):
+def run_e2e(torch, fst, model, tree, B, links, st, dev, K, warmup, plan=None, slots=3, split=1):
     """The same step through the public binding, end to end: every step
     uploads its inputs from pinned host memory, runs the step (the tuned step
     plan) and reads every output back into pinned host memory. Inputs and
@@ -650,9 +650,11 @@ def run_e2e(torch, fst, model, tree, B, links, st, dev, K, warmup, plan=None, sl
         sl = {"stream": torch.cuda.Stream(device=dev),
               "host_in": torch.from_numpy(packed.copy()).pin_memory(),
               "dev_in": torch.empty(n_in, device=dev), "dev_out": torch.empty(n_out, device=dev),
-              "host_out": torch.empty(n_out).pin_memory()}
+              "host_out": torch.empty(n_out).pin_memory(),
+              "copy_streams": [torch.cuda.Stream(device=dev) for _ in range(split)]}
         sl["in"], sl["out"] = views(sl["dev_in"], in_rows), views(sl["dev_out"], out_shapes)
         S.append(sl)
+    bounds = [n_out * k // split for k in range(split + 1)]
 
     def step(sl):
         sl["dev_in"].copy_(sl["host_in"], non_blocking=True)
@@ -662,7 +664,17 @@ def run_e2e(torch, fst, model, tree, B, links, st, dev, K, warmup, plan=None, sl
         else:
             fst.eval(model, i["q"], i["qd"], i["qdd"], i["tau"], fk=True, links=links, rnea=True, crba=True, aba=True,
                      out=sl["out"])
-        sl["host_out"].copy_(sl["dev_out"], non_blocking=True)
+        if split == 1:
+            sl["host_out"].copy_(sl["dev_out"], non_blocking=True)
+            return
+        # the read-back in `split` chunks on parallel branches (several copy engines)
+        cur = torch.cuda.current_stream()
+        for k, cs in enumerate(sl["copy_streams"]):
+            cs.wait_stream(cur)
+            with torch.cuda.stream(cs):
+                sl["host_out"][bounds[k]:bounds[k + 1]].copy_(sl["dev_out"][bounds[k]:bounds[k + 1]], non_blocking=True)
+        for cs in sl["copy_streams"]:
+            cur.wait_stream(cs)
 
     for sl in S:
         with torch.cuda.stream(sl["stream"]):
@@ -691,7 +703,8 @@ def run_e2e(torch, fst, model, tree, B, links, st, dev, K, warmup, plan=None, sl
         cur.wait_stream(sl["stream"])
     b.record(cur)
     torch.cuda.synchronize()
-    return {"ms": a.elapsed_time(b), "h2d": n_in * 4, "d2h": n_out * 4, "slots": slots, "steps": K}
+    return {"ms": a.elapsed_time(b), "h2d": n_in * 4, "d2h": n_out * 4, "slots": slots, "steps": K,
+            "readback_chunks": split}
 
 
 # ---------------------------------------------------------------------------
@@ -820,6 +833,8 @@ def main():
                     help="skip the secondary legs (fwd+bwd, RL-step graph, humanoid sweep) after the timed step")
     ap.add_argument("--e2e-slots", type=int, default=3,
                     help="end-to-end leg: steps in flight (streams with their own buffers)")
+    ap.add_argument("--e2e-split", type=int, default=1,
+                    help="end-to-end leg: read-back chunks copied on parallel graph branches")
     ap.add_argument("--traffic", type=float, default=None,
                     help="dram bytes per launch of the dominant kernel from an ncu capture (else null)")
     args = ap.parse_args()
