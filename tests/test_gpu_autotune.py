@@ -92,3 +92,38 @@ def test_step_plan_matches_per_operator_calls(torch_cuda, tmp_path, monkeypatch)
            "M": api.crba(m, q), "qdd": api.aba(m, q, qd, tau)}
     for k, tol in TOL.items():
         assert env_err(from_soa(out[k]), from_soa(ref[k])).max() <= tol, k
+
+
+def test_bench_step_at_full_size_matches_oracle(torch_cuda, tmp_path, monkeypatch):
+    """The timed step exactly as bench.py runs it (the 11-DOF tree, B = 4096,
+    specialised model, tuned step plan, replayed from a CUDA graph) against
+    the oracle on sampled environments, element by element."""
+    torch = torch_cuda
+    from paper_2605_31481_gb300 import api, autotune
+    monkeypatch.setenv("FST_TUNE_CACHE", str(tmp_path / "tune.json"))
+    tree = w.spined_quadruped(seed=0)
+    B = 4096
+    s = w.random_state(tree, B, seed=1)
+    q, qd, qdd, tau = (to_soa_cuda(s[k], torch) for k in ("q", "qd", "qdd", "tau"))
+    m = api.Model(tree, specialize=True)
+    plan = autotune.StepPlan(m, B, links=list(tree.ee))
+    out = {"poses": torch.empty(tree.n_bodies, 12, B, device="cuda"),
+           "J": torch.empty(4, 6, tree.nv, B, device="cuda"), "tau": torch.empty(tree.nv, B, device="cuda"),
+           "M": torch.empty(tree.nv, tree.nv, B, device="cuda"), "qdd": torch.empty(tree.nv, B, device="cuda")}
+    g = torch.cuda.CUDAGraph()
+    plan(q, qd, qdd, tau, out)
+    torch.cuda.synchronize()
+    with torch.cuda.graph(g):
+        plan(q, qd, qdd, tau, out)
+    for v in out.values():
+        v.fill_(float("nan"))
+    g.replay()
+    torch.cuda.synchronize()
+    idx = np.unique(np.r_[np.random.default_rng(2).choice(B, 256, replace=False), 0, 31, 32, B - 1])
+    ref = {"poses": oracle_poses(tree, s["q"][idx]),
+           "J": np.stack([rbd.jacobian(tree, s["q"][idx], e) for e in tree.ee], 1),
+           "tau": rbd.rnea(tree, s["q"][idx], s["qd"][idx], s["qdd"][idx]), "M": rbd.crba(tree, s["q"][idx]),
+           "qdd": rbd.aba(tree, s["q"][idx], s["qd"][idx], s["tau"][idx])}
+    for k, tol in TOL.items():
+        err = env_err(from_soa(out[k])[idx], ref[k])
+        assert np.all(np.isfinite(err)) and err.max() <= tol, (plan.describe()["mode"], k, err.max())
