@@ -3,9 +3,11 @@
 
 #include <atomic>
 #include <cstring>
+#include <initializer_list>
 #include <new>
 #include <sstream>
 #include <string>
+#include <utility>
 
 #include "fst_internal.h"
 #include "jit.h"
@@ -115,6 +117,17 @@ int block_of(const fst_model* m, int kind, int64_t B) { return m->block[kind] ? 
 
 Launch launch_of(const fst_model* m, int kind, int64_t B, void* stream) {
   return Launch{block_of(m, kind, B), (cudaStream_t)stream};
+}
+
+// Zeroes the outputs of a call with nothing to compute (B = 0 or no degrees
+// of freedom); null pointers and empty sizes are skipped.
+cudaError_t zero_outputs(cudaStream_t s, std::initializer_list<std::pair<void*, size_t>> outs) {
+  for (const auto& o : outs)
+    if (o.first && o.second) {
+      const cudaError_t err = cudaMemsetAsync(o.first, 0, o.second, s);
+      if (err != cudaSuccess) return err;
+    }
+  return cudaSuccess;
 }
 
 fst_status finish(const char* fn, cudaError_t err) {
@@ -494,8 +507,7 @@ fst_status fst_rnea_vjp(const fst_model* m, int64_t B, const float* q, const flo
   FST_CHECK(check_call(fn, m, B, &skip));
   if (theta_bar) FST_CHECK(need_scratch(fn, m, B, scratch, scratch_bytes));
   if (skip || m->nv == 0) {
-    if (theta_bar && m->n) cudaMemsetAsync(theta_bar, 0, sizeof(float) * m->n * 10, (cudaStream_t)stream);
-    return FST_OK;
+    return finish(fn, zero_outputs((cudaStream_t)stream, {{theta_bar, sizeof(float) * m->n * 10}}));
   }
   FST_CHECK(need(fn, q, "q"));
   FST_CHECK(need(fn, qd, "qd"));
@@ -552,8 +564,7 @@ fst_status fst_rnea_vjp_stored(const fst_model* m, int64_t B, const float* q, co
   FST_CHECK(check_call(fn, m, B, &skip));
   if (theta_bar) FST_CHECK(need_scratch(fn, m, B, scratch, scratch_bytes));
   if (skip || m->nv == 0) {
-    if (theta_bar && m->n) cudaMemsetAsync(theta_bar, 0, sizeof(float) * m->n * 10, (cudaStream_t)stream);
-    return FST_OK;
+    return finish(fn, zero_outputs((cudaStream_t)stream, {{theta_bar, sizeof(float) * m->n * 10}}));
   }
   FST_CHECK(need(fn, q, "q"));
   FST_CHECK(need(fn, qd, "qd"));
@@ -605,9 +616,8 @@ fst_status fst_crba_vjp(const fst_model* m, int64_t B, const float* q, const flo
   FST_CHECK(check_call(fn, m, B, &skip));
   if (theta_bar) FST_CHECK(need_scratch(fn, m, B, scratch, scratch_bytes));
   if (skip || m->nv == 0) {
-    if (theta_bar && m->n) cudaMemsetAsync(theta_bar, 0, sizeof(float) * m->n * 10, (cudaStream_t)stream);
-    if (q_bar && m->nq && B > 0) cudaMemsetAsync(q_bar, 0, sizeof(float) * m->nq * (size_t)B, (cudaStream_t)stream);
-    return FST_OK;
+    return finish(fn, zero_outputs((cudaStream_t)stream, {{theta_bar, sizeof(float) * m->n * 10},
+                                                          {q_bar, sizeof(float) * m->nq * (size_t)B}}));
   }
   FST_CHECK(need(fn, q, "q"));
   FST_CHECK(need(fn, M_bar, "M_bar"));
@@ -658,8 +668,7 @@ fst_status fst_aba_vjp(const fst_model* m, int64_t B, const float* q, const floa
   FST_CHECK(check_call(fn, m, B, &skip));
   if (theta_bar) FST_CHECK(need_scratch(fn, m, B, scratch, scratch_bytes));
   if (skip || m->nv == 0) {
-    if (theta_bar && m->n) cudaMemsetAsync(theta_bar, 0, sizeof(float) * m->n * 10, (cudaStream_t)stream);
-    return FST_OK;
+    return finish(fn, zero_outputs((cudaStream_t)stream, {{theta_bar, sizeof(float) * m->n * 10}}));
   }
   FST_CHECK(need(fn, q, "q"));
   FST_CHECK(need(fn, qd, "qd"));
@@ -688,8 +697,7 @@ fst_status fst_rnea_loss_grad(const fst_model* m, int64_t B, const float* q, con
   FST_CHECK(need(fn, loss_theta_bar, "loss_theta_bar"));
   FST_CHECK(need_scratch(fn, m, B, scratch, scratch_bytes));
   if (skip || m->nv == 0) {
-    cudaMemsetAsync(loss_theta_bar, 0, sizeof(float) * (m->n * 10 + 1), (cudaStream_t)stream);
-    return FST_OK;
+    return finish(fn, zero_outputs((cudaStream_t)stream, {{loss_theta_bar, sizeof(float) * (m->n * 10 + 1)}}));
   }
   FST_CHECK(need(fn, q, "q"));
   FST_CHECK(need(fn, qd, "qd"));
