@@ -72,7 +72,14 @@ extern "C" fst_status fst_rnea_vjp_noalloc(const fst_model* m, int64_t B, const 
        << kStaticScratchFloats << " (use fst_rnea_vjp with a caller-provided scratch buffer)";
     return arg_error(os.str());
   }
-  if (B == 0 || m->nv == 0) return FST_OK;
+  if (B == 0 || m->nv == 0) {
+    // nothing to differentiate: theta_bar is still overwritten (with zeros), as fst_rnea_vjp does
+    if (theta_bar && m->n) {
+      const cudaError_t zerr = cudaMemsetAsync(theta_bar, 0, sizeof(float) * m->n * 10, (cudaStream_t)stream);
+      if (zerr != cudaSuccess) return fst::set_error(FST_ERR_CUDA, std::string(fn) + ": " + cudaGetErrorString(zerr));
+    }
+    return FST_OK;
+  }
   int dev = -1;
   cudaError_t err = cudaGetDevice(&dev);
   if (err != cudaSuccess) return fst::set_error(FST_ERR_CUDA, std::string(fn) + ": " + cudaGetErrorString(err));
