@@ -792,32 +792,58 @@ def cpu_baseline(tree, links, args, st=None, gpu_first=None, budget_s=12.0, Bs=5
     return cpu, parity
 
 
-def run_reference(args):
+def run_reference(args, budget_s=120.0):
+    """The FP64 oracle as the reference arm, on the host (rank 0 only). One
+    environment-evaluation is all five operators; each step runs one of
+    them in turn (FK, the 4 foot Jacobians, RNEA, CRBA, ABA) on a sample of
+    the workload's environments, sized from a short probe so that the whole
+    --steps K --warmup W run takes about budget_s seconds (at least one and
+    at most 256 environments per step)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
+    from oracle import rbd
     from paper_2605_31481_gb300 import workloads as w
     tree, B, links = workload()
-    Bs = 256
+    ops = (lambda s: rbd.fk(tree, s["q"]),
+           lambda s: [rbd.jacobian(tree, s["q"], l) for l in links],
+           lambda s: rbd.rnea(tree, s["q"], s["qd"], s["qdd"]),
+           lambda s: rbd.crba(tree, s["q"]),
+           lambda s: rbd.aba(tree, s["q"], s["qd"], s["tau"]))
+
+    def op_times(n):
+        s = w.random_state(tree, n, seed=1)
+        out = []
+        for f in ops:
+            f(s)
+            t0 = time.perf_counter()
+            f(s)
+            out.append(time.perf_counter() - t0)
+        return sum(out) / len(out)
+
+    t1, t64 = op_times(1), op_times(64)
+    per_env = max((t64 - t1) / 63, 1e-9)
+    target = budget_s / max(args.steps + args.warmup, 1)
+    Bs = int(max(1, min(256, (target - t1) / per_env)))
     s = w.random_state(tree, Bs, seed=1)
-    for _ in range(args.warmup):
-        oracle_step(tree, links, s)
-    t = []
-    for _ in range(args.steps):
-        t0 = time.perf_counter()
-        oracle_step(tree, links, s)
-        t.append(time.perf_counter() - t0)
-    tot = sum(t)
-    value = Bs * args.steps / tot
+    for k in range(args.warmup):
+        ops[k % len(ops)](s)
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        ops[k % len(ops)](s)
+    tot = time.perf_counter() - t0
+    value = Bs * args.steps / len(ops) / tot
+    sample = (f"{Bs} of the 4096 envs; each step one of the five operators in turn (FK, 4 Jacobians, RNEA, CRBA, "
+              f"ABA), FP64 numpy oracle, 1 thread")
     line = {
         "impl": "reference", "metric": METRIC, "value": round(value, 1), "unit": "env-evals/s",
         "n_gpus": int(os.environ.get("WORLD_SIZE", "1")), "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": round(1e3 * tot / args.steps, 3), "higher_is_better": True, "scaling": "weak",
+        "ms_per_step": round(1e3 * tot / max(args.steps, 1), 3), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": f"{tree.name}: 11 revolute DOF branched tree, depth 5, B=4096",
                    "B": B, "step": "+".join(OPS) + " (4 foot Jacobians)", "sample_envs_per_step": Bs},
         "cpu_baseline": {"value": round(value, 1), "unit": "env-evals/s", "cores": 1, "kind": "oracle",
-                         "sample": f"{Bs} of the 4096 envs per step, FP64 numpy oracle, 1 thread"},
+                         "sample": sample},
         "e2e": {"value": round(value, 1), "unit": "env-evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
