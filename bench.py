@@ -168,7 +168,14 @@ def run_fst(args):
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    __graft_entry__.build()
+        # one rank builds the in-tree library, the others wait for it
+        if rank == 0:
+            __graft_entry__.build()
+        dist.barrier()
+        if rank != 0:
+            __graft_entry__.build()          # up to date by now: only imports
+    else:
+        __graft_entry__.build()
     L = _ffi.lib()
 
     tree, B, links = workload()
