@@ -180,11 +180,15 @@ def run_fst(args):
 
     tree, B, links = workload()
     model = fst.Model(tree)
+    if world > 1 and rank != 0:
+        dist.barrier()                  # rank 0 compiles first and fills the on-disk cache
     try:
         model.specialize()
         kernels = "specialized available"
     except _ffi.FstError as exc:        # no NVRTC on this host: generic kernels only
         kernels = f"generic only ({exc})"
+    if world > 1 and rank == 0:
+        dist.barrier()
     from paper_2605_31481_gb300.autotune import StepPlan
     plan = StepPlan(model, B, links=links)
     nq, nv, nb, nl = tree.nq, tree.nv, tree.n_bodies, len(links)
