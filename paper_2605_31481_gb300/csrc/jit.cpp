@@ -323,9 +323,13 @@ void compile_one(CompileJob& job, const std::string& arch_opt) {
   const Nvrtc& N = nvrtc();
   int maj = 0, min = 0;
   N.version(&maj, &min);
-  const char* opts[] = {arch_opt.c_str(), "-std=c++17", "--device-as-default-execution-space"};
-  const int nopt = 3;
-  std::string key = job.src + arch_opt + std::to_string(maj) + "." + std::to_string(min);
+  // FST_JIT_MAXRREG=<n> caps the registers per thread of the specialised
+  // kernels (more resident warps per SM, at the risk of spills)
+  std::string maxrreg;
+  if (const char* r = std::getenv("FST_JIT_MAXRREG")) maxrreg = std::string("--maxrregcount=") + r;
+  const char* opts[] = {arch_opt.c_str(), "-std=c++17", "--device-as-default-execution-space", maxrreg.c_str()};
+  const int nopt = maxrreg.empty() ? 3 : 4;
+  std::string key = job.src + arch_opt + maxrreg + std::to_string(maj) + "." + std::to_string(min);
   for (int h = 0; h < kJitHeaderCount; ++h) key += kJitHeaderSources[h];
   char name[32];
   std::snprintf(name, sizeof(name), "%016llx", (unsigned long long)fnv1a(key));
