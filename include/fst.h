@@ -188,7 +188,31 @@ FST_API fst_status fst_model_specialize(fst_model* model, uint32_t kinds);
  * barrier per depth where paths join. The block size is fixed by the tree
  * (32 x number of paths); the block argument is ignored. */
 #define FST_VARIANT_PATH_WARP 6
+/* eval (specialised) and ABA (level-parallel): SM-pinned launches. Each SM
+ * serves the role the table of fst_model_set_sm_roles gives it, so an SM
+ * keeps running the same code from call to call (its instruction caches stay
+ * warm). Blocks pull tiles of environments from per-call counters; blocks on
+ * SMs without a matching role leave at once, and the block that finishes
+ * last completes whatever is left, so results never depend on where the
+ * hardware placed the blocks. Calls of one model with this variant must not
+ * overlap in time, except one eval beside one ABA (they count in separate
+ * regions). */
+#define FST_VARIANT_PINNED 7
 FST_API fst_status fst_model_set_launch(fst_model* model, uint32_t kinds, int32_t block, int32_t variant);
+
+/* Roles of the SMs for FST_VARIANT_PINNED launches: role_of_sm[i] is the
+ * role of SM id i (FST_ROLE_*, or FST_ROLE_NONE), for n <= 256 SM ids; ids
+ * past n get FST_ROLE_NONE. The roles are the operator groups of fst_eval:
+ * ABA, CRBA, RNEA and KIN (FK with the Jacobians). Synchronous (copies the
+ * table to the model's device memory): call it before capturing a stream.
+ * Until it is called every SM has no role, which is correct but slow (the
+ * last block does all the work). */
+#define FST_ROLE_NONE (-1)
+#define FST_ROLE_ABA 0
+#define FST_ROLE_CRBA 1
+#define FST_ROLE_RNEA 2
+#define FST_ROLE_KIN 3
+FST_API fst_status fst_model_set_sm_roles(fst_model* model, const int32_t* role_of_sm, int32_t n);
 
 /* Shared-memory carveout (percent of the unified L1/shared storage given to
  * shared memory) requested for every kernel launched from now on; -1 (the

@@ -18,7 +18,7 @@ STATUS_NAMES = {
 }
 MAX_BODIES = 64
 MAX_LINKS = 16
-VARIANTS = {"auto": 0, "generic": 1, "specialized": 2, "level": 3, "mixed": 4, "path": 5, "pathwarp": 6}
+VARIANTS = {"auto": 0, "generic": 1, "specialized": 2, "level": 3, "mixed": 4, "path": 5, "pathwarp": 6, "pinned": 7}
 SPEC_KINDS = ("fk", "jacobian", "rnea", "crba", "aba", "eval", "fk_vjp", "rnea_vjp", "aba_vjp", "loss_grad",
               "eval_mixed", "rnea_store", "rnea_vjp_stored", "rnea_derivatives", "aba_derivatives")
 
@@ -88,6 +88,7 @@ _SIGS = {
     "fst_rnea_vjp_stored": (c_int32, [c_void_p, c_int64, c_void_p, c_void_p, c_void_p, c_void_p, ctypes.c_size_t,
                                       c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, ctypes.c_size_t,
                                       c_void_p]),
+    "fst_model_set_sm_roles": (c_int32, [c_void_p, ctypes.POINTER(c_int32), c_int32]),
     "fst_jacobian_vjp": (c_int32, [c_void_p, c_int64, c_void_p, ctypes.POINTER(c_int32), c_int32, c_void_p, c_void_p,
                                    c_void_p]),
     "fst_crba_vjp": (c_int32, [c_void_p, c_int64, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,

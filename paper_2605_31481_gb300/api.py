@@ -103,6 +103,17 @@ class Model:
         mask = 0 if kinds is None else sum(1 << _ffi.SPEC_KINDS.index(k) for k in kinds)
         check(_ffi.lib().fst_model_set_launch(self._h, mask, int(block), _ffi.VARIANTS[variant]))
 
+    ROLES = {"none": -1, "aba": 0, "crba": 1, "rnea": 2, "kin": 3}
+
+    def set_sm_roles(self, roles):
+        """Role of every SM id for the "pinned" variant (fst_model_set_sm_roles):
+        a sequence of role names ("aba", "crba", "rnea", "kin", "none") or
+        codes, indexed by SM id."""
+        codes = [self.ROLES[r] if isinstance(r, str) else int(r) for r in roles]
+        arr = (ctypes.c_int32 * len(codes))(*codes)
+        with torch.cuda.device(self.device):
+            check(_ffi.lib().fst_model_set_sm_roles(self._h, arr, len(codes)))
+
     def specialized(self):
         """Names of the kernel kinds that run specialised for this model."""
         m = ctypes.c_uint32()

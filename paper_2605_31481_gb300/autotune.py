@@ -205,7 +205,8 @@ class StepPlan:
     block scheduler then dispatches the longest chain's blocks first and
     fills the other SMs with the rest."""
 
-    MODES = ("fused", "hybrid", "concurrent", "sequential")
+    MODES = ("fused", "hybrid", "pinned", "concurrent", "sequential")
+    PIN_SHARES = (0.45, 0.55, 0.65)   # fractions of the SMs pinned to ABA
 
     def __init__(self, model, B, links=None, use_cache=True, verbose=False, modes=MODES):
         self.model = model
@@ -218,7 +219,7 @@ class StepPlan:
         # priority (out-of-range values clamp to it), the others at the default
         self._ranked = [torch.cuda.Stream(device=model.device, priority=-1000 if k == 0 else 0)
                         for k in range(len(FORWARD_KINDS))]
-        key = _key(model, "plan7", B)
+        key = _key(model, "plan8", B)
         hit = _load_cache().get(key) if use_cache else None
         if hit:
             self.times = {(k, c, p, ev): v for k, c, p, ev, v in hit["times"]}
@@ -238,12 +239,21 @@ class StepPlan:
         best_aba = f"{self.tuned['aba']['variant']}/{self.tuned['aba']['block']}"
         abas = [n for n, _ in sorted(self.tuned["aba"]["candidates"].items(), key=lambda kv: kv[1])[:3]]
         hybrid_cfgs = [f"{ev}|{ab}" for ev in hybrid_evals for ab in abas]
+        # SM-pinned: the specialised fused kernel and the level-parallel ABA on
+        # disjoint SM sets, so each SM keeps running the same code
+        pinned_cfgs = []
+        if "specialized" in {c.split("/")[0] for c in self.tuned["eval"]["candidates"]}:
+            pinned_cfgs = [f"pinned/{b}|pinned/256@{sh}" for b in (64, 128) for sh in self.PIN_SHARES]
         times = {}
         for carveout in (-1, 100):
             api.set_smem_carveout(carveout)
             for mode in modes:
-                for ev in (hybrid_cfgs if mode == "hybrid" else [f"{best_eval}|{best_aba}"]):
-                    self._set_eval(ev)
+                cfgs = {"hybrid": hybrid_cfgs, "pinned": pinned_cfgs}.get(mode, [f"{best_eval}|{best_aba}"])
+                for ev in cfgs:
+                    try:
+                        self._set_eval(ev)
+                    except _ffi.FstError:
+                        continue                 # not available for this model
                     for prio in (False, True):
                         if (carveout >= 0 or prio) and mode in ("fused", "sequential"):
                             continue
@@ -258,10 +268,23 @@ class StepPlan:
                                 "times": [[k, c, p, ev, round(v, 3)] for (k, c, p, ev), v in times.items()]}})
 
     def _set_eval(self, config):
-        """config: "<eval variant>/<block>|<aba variant>/<block>"."""
+        """config: "<eval variant>/<block>|<aba variant>/<block>[@<ABA share of
+        the SMs>]"; a share sets the SM roles of the pinned variant."""
+        config, _, share = config.partition("@")
         for kind, part in zip(("eval", "aba"), config.split("|")):
             variant, block = part.split("/")
             self.model.set_launch([kind], int(block), variant)
+        if share:
+            self.model.set_sm_roles(self.pin_roles(float(share)))
+
+    @staticmethod
+    def pin_roles(aba_share, period=20):
+        """Role names for the 256 SM ids: of every `period` consecutive ids,
+        round(aba_share * period) serve ABA and the rest take KIN, RNEA and
+        CRBA in turn, so every role spreads over the whole chip."""
+        n_aba = int(round(aba_share * period))
+        other = ("kin", "rnea", "crba")
+        return ["aba" if i % period < n_aba else other[(i % period - n_aba) % 3] for i in range(256)]
 
     def _apply(self, mode, carveout, prio, eval_config):
         self.mode, self.carveout, self.prio, self.eval_config = mode, carveout, bool(prio), eval_config
@@ -296,7 +319,7 @@ class StepPlan:
         if self.mode == "sequential":
             for op in ops:
                 op()
-        elif self.mode == "hybrid":
+        elif self.mode in ("hybrid", "pinned"):
             self._fork([ops[4], lambda: api.eval(m, q, qd, qdd, tau, fk=True, links=self.links, rnea=True, crba=True,
                                                  aba=False, out=out)])
         else:
@@ -309,7 +332,7 @@ class StepPlan:
         kinds = {k: f"{v['variant']}/{v['block']}" for k, v in self.tuned.items()}
         kinds["eval"], kinds["aba"] = self.eval_config.split("|")
         return {"mode": self.mode, "carveout": self.carveout, "priorities": self.prio,
-                "us": {f"{k[0]}{'[' + k[3] + ']' if k[0] == 'hybrid' else ''}{'' if k[1] < 0 else f'@{k[1]}%'}"
+                "us": {f"{k[0]}{'[' + k[3] + ']' if k[0] in ('hybrid', 'pinned') else ''}{'' if k[1] < 0 else f'@{k[1]}%'}"
                        f"{'+prio' if k[2] else ''}": round(v, 3) for k, v in self.times.items()},
                 "kinds": kinds,
                 "eval_candidates_us": self.tuned["eval"]["candidates"]}

@@ -185,12 +185,15 @@ fst_status fst_model_create(const fst_body_desc* bodies, int32_t n_bodies, const
   if (err == cudaSuccess) err = cudaMemcpy(m->di, m->hi.data(), sizeof(BodyI) * m->n, cudaMemcpyHostToDevice);
   if (err == cudaSuccess) err = cudaMalloc((void**)&m->dt, sizeof(TopoLists));
   if (err == cudaSuccess) err = cudaMemcpy(m->dt, &m->ht, sizeof(TopoLists), cudaMemcpyHostToDevice);
+  if (err == cudaSuccess) err = cudaMalloc((void**)&m->dpin, sizeof(int) * (kPinTableSize + 2 * kPinRegion));
+  if (err == cudaSuccess) err = cudaMemset(m->dpin, 0xff, sizeof(int) * kPinTableSize);  // no roles: -1
   if (err != cudaSuccess) {
     fst_status st = (err == cudaErrorMemoryAllocation) ? set_error(FST_ERR_NO_MEMORY, "fst_model_create: cudaMalloc failed")
                                                        : cuda_error("fst_model_create", err);
     if (m->dc) cudaFree(m->dc);
     if (m->di) cudaFree(m->di);
     if (m->dt) cudaFree(m->dt);
+    if (m->dpin) cudaFree(m->dpin);
     delete m;
     return st;
   }
@@ -204,6 +207,7 @@ fst_status fst_model_destroy(fst_model* m) {
   if (m->dc) cudaFree(m->dc);
   if (m->di) cudaFree(m->di);
   if (m->dt) cudaFree(m->dt);
+  if (m->dpin) cudaFree(m->dpin);
   delete m;
   return FST_OK;
 }
@@ -227,13 +231,13 @@ fst_status fst_model_set_launch(fst_model* m, uint32_t kinds, int32_t block, int
   if (!m) return set_error(FST_ERR_INVALID_ARG, "fst_model_set_launch: null model");
   if (block != 0 && block != 32 && block != 64 && block != 128 && block != 256)
     return set_error(FST_ERR_INVALID_ARG, "fst_model_set_launch: block must be 0, 32, 64, 128 or 256");
-  if (variant < FST_VARIANT_AUTO || variant > FST_VARIANT_PATH_WARP)
+  if (variant < FST_VARIANT_AUTO || variant > FST_VARIANT_PINNED)
     return set_error(FST_ERR_INVALID_ARG, "fst_model_set_launch: unknown variant");
   // "all kinds" with the level or path variant means every kind that has one
   if (kinds == 0)
     kinds = (variant == FST_VARIANT_LEVEL || variant == FST_VARIANT_PATH || variant == FST_VARIANT_PATH_WARP)
                 ? (1u << (JK_EVAL + 1)) - 1u
-                : FST_SPEC_ALL;
+                : variant == FST_VARIANT_PINNED ? (1u << JK_EVAL) | (1u << JK_ABA) : FST_SPEC_ALL;
   if (kinds & ~(uint32_t)FST_SPEC_ALL) return set_error(FST_ERR_INVALID_ARG, "fst_model_set_launch: unknown kind bits");
   for (int k = 0; k < JK_COUNT; ++k) {
     if (((kinds >> k) & 1u) && variant == FST_VARIANT_MIXED && k != JK_EVAL)
@@ -247,6 +251,13 @@ fst_status fst_model_set_launch(fst_model* m, uint32_t kinds, int32_t block, int
       return set_error(FST_ERR_INVALID_ARG, "fst_model_set_launch: no path-parallel kernel for a selected kind "
                                             "(specialise FK, Jacobian, RNEA, CRBA, ABA or eval first; trees with "
                                             "more than 8 leaves have none)");
+    if (((kinds >> k) & 1u) && variant == FST_VARIANT_PINNED && k != JK_EVAL && k != JK_ABA)
+      return set_error(FST_ERR_INVALID_ARG, "fst_model_set_launch: the pinned variant is for eval and ABA only");
+    if (((kinds >> k) & 1u) && variant == FST_VARIANT_PINNED && k == JK_EVAL && !jit_has_slot(m, JK_EVAL, 3))
+      return set_error(FST_ERR_INVALID_ARG, "fst_model_set_launch: pinned eval needs the specialised eval kernel");
+    if (((kinds >> k) & 1u) && variant == FST_VARIANT_PINNED && k == JK_ABA &&
+        level_smem_needed(view_of(m, nullptr), LEVEL_ABA) > kLevelSmemLimit)
+      return set_error(FST_ERR_INVALID_ARG, "fst_model_set_launch: the tree is too large for pinned ABA");
     if (((kinds >> k) & 1u) && variant == FST_VARIANT_LEVEL && k > JK_EVAL)
       return set_error(FST_ERR_INVALID_ARG, "fst_model_set_launch: the level-parallel variant exists for FK, "
                                             "Jacobian, RNEA, CRBA, ABA and eval only");
@@ -257,6 +268,25 @@ fst_status fst_model_set_launch(fst_model* m, uint32_t kinds, int32_t block, int
       m->variant[k] = variant;
     }
   return FST_OK;
+}
+
+fst_status fst_model_set_sm_roles(fst_model* m, const int32_t* role_of_sm, int32_t n) {
+  if (!m || (!role_of_sm && n)) return set_error(FST_ERR_INVALID_ARG, "fst_model_set_sm_roles: null argument");
+  if (n < 0 || n > kPinTableSize)
+    return set_error(FST_ERR_INVALID_ARG, "fst_model_set_sm_roles: n must be in [0, 256]");
+  int table[kPinTableSize];
+  for (int i = 0; i < kPinTableSize; ++i) {
+    const int r = i < n ? role_of_sm[i] : FST_ROLE_NONE;
+    if (r < FST_ROLE_NONE || r > FST_ROLE_KIN)
+      return set_error(FST_ERR_INVALID_ARG, "fst_model_set_sm_roles: unknown role");
+    table[i] = r;
+  }
+  int dev = -1;
+  cudaError_t err = cudaGetDevice(&dev);
+  if (err == cudaSuccess && dev != m->device)
+    return set_error(FST_ERR_INVALID_ARG, "fst_model_set_sm_roles: the current device is not the model's device");
+  if (err == cudaSuccess) err = cudaMemcpy(m->dpin, table, sizeof(table), cudaMemcpyHostToDevice);
+  return err == cudaSuccess ? FST_OK : cuda_error("fst_model_set_sm_roles", err);
 }
 
 fst_status fst_model_specialized(const fst_model* m, uint32_t* kinds) {
@@ -376,6 +406,14 @@ fst_status fst_aba(const fst_model* m, int64_t B, const float* q, const float* q
   const ModelView mv = view_of(m, theta);
   if (use_level(m, JK_ABA, LEVEL_ABA))
     return finish(fn, launch_aba_level(mv, B, q, qd, tau, qdd, level_block(m, JK_ABA), (cudaStream_t)stream));
+  if (m->variant[JK_ABA] == FST_VARIANT_PINNED) {
+    int* counters = m->dpin + kPinTableSize + kPinAbaRegion * kPinRegion;
+    cudaError_t err = cudaMemsetAsync(counters, 0, sizeof(int) * kPinRegion, (cudaStream_t)stream);
+    if (err == cudaSuccess)
+      err = launch_aba_level_pinned(mv, B, q, qd, tau, qdd, m->block[JK_ABA] ? m->block[JK_ABA] : 256,
+                                    PinArgs{m->dpin, counters}, (cudaStream_t)stream);
+    return finish(fn, err);
+  }
   if (use_path(m, JK_ABA))
     return finish(fn, path_go(m, JK_ABA, B, m->nq + 2 * m->nv, 1, (cudaStream_t)stream, mv, B, q, qd, tau, qdd));
   if (use_jit(m, JK_ABA))
@@ -460,6 +498,20 @@ fst_status fst_eval(const fst_model* m, int64_t B, const fst_eval_io* io, const 
     void* argv[] = {(void*)&mv, (void*)&B, (void*)&a};
     return finish(fn, jit_launch(m, JK_EVAL_MIXED, dim3((unsigned)gx, (unsigned)a.n_roles), T, sh,
                                  (cudaStream_t)stream, argv));
+  }
+  if (m->variant[JK_EVAL] == FST_VARIANT_PINNED && jit_has_slot(m, JK_EVAL, 3)) {
+    int* counters = m->dpin + kPinTableSize + kPinEvalRegion * kPinRegion;
+    cudaError_t err = cudaMemsetAsync(counters, 0, sizeof(int) * kPinRegion, (cudaStream_t)stream);
+    if (err == cudaSuccess) {
+      int sms = 0;
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, m->device);
+      const int T = m->block[JK_EVAL] ? m->block[JK_EVAL] : 128;
+      const PinArgs p{m->dpin, counters};
+      void* argv[] = {(void*)&mv, (void*)&B, (void*)&a, (void*)&p};
+      err = jit_launch_slot(m, JK_EVAL, 3, dim3((unsigned)(2 * (sms > 0 ? sms : 1))), T,
+                            (size_t)(m->nq + 2 * m->nv) * T * sizeof(float), (cudaStream_t)stream, argv);
+    }
+    return finish(fn, err);
   }
   if (use_path(m, JK_EVAL))
     return finish(fn, path_go(m, JK_EVAL, B, m->nq + 2 * m->nv, (unsigned)a.n_roles, (cudaStream_t)stream, mv, B, a));

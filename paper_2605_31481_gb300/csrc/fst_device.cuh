@@ -382,6 +382,59 @@ __device__ __forceinline__ void cp_async4(float* smem_dst, const float* gmem_src
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
+// ---- SM-pinned tile loops ---------------------------------------------------
+// The straight-line specialised kernels run fast only while an SM keeps
+// executing the same code: their instructions then stay in the SM's
+// instruction caches from one step to the next. A pinned launch gives every
+// SM one role (a table indexed by the SM id): a block serves the role of the
+// SM it landed on, pulling tiles of environments from that role's counter,
+// and leaves when they run out; blocks on SMs without a role leave at once.
+// The block that finishes last then takes every tile still left in any slot
+// (a role none of whose SMs received a block), so the launch always does all
+// the work. No block ever waits for another.
+__device__ __forceinline__ int sm_id() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%smid;" : "=r"(r));
+  return (int)r;
+}
+
+__device__ __forceinline__ int pinned_role(const PinArgs& p) {
+  const int s = sm_id();
+  return s < kPinTableSize ? p.table[s] : -1;
+}
+
+// body(slot, tile) for the tiles of `my_slot` (or none if my_slot < 0), then
+// the clean-up described above. One call site of body, so its code is
+// emitted once. Every thread of the block must call it.
+template <class F>
+__device__ __forceinline__ void pinned_tiles(const PinArgs& p, int my_slot, int n_slots, int n_tiles, F& body) {
+  __shared__ int s_tile, s_last;
+  int slot = my_slot;
+  bool cleanup = false;
+  for (;;) {
+    if (slot >= 0) {
+      if (threadIdx.x == 0) s_tile = atomicAdd(&p.counters[slot], 1);
+      __syncthreads();
+      const int t = s_tile;
+      __syncthreads();
+      if (t < n_tiles) {
+        body(slot, t);
+        continue;
+      }
+    }
+    if (!cleanup) {  // own tiles done: count this block out; the last one cleans up
+      if (threadIdx.x == 0)
+        s_last = atomicAdd(&p.counters[kPinRegion - 1], 1) == (int)(gridDim.x * gridDim.y * gridDim.z) - 1;
+      __syncthreads();
+      if (!s_last) return;
+      cleanup = true;
+      slot = 0;
+      continue;
+    }
+    if (++slot >= n_slots) return;
+  }
+}
+
 // Stages rows [0, rows) of a [rows][B] array for this thread's environment
 // into tile[row * blockDim.x + threadIdx.x]. Only the calling thread reads
 // its own column afterwards, so the thread's own wait is enough.

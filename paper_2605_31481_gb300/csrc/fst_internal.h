@@ -25,6 +25,7 @@ struct fst_model {
   fst::BodyI* di = nullptr;
   fst::TopoLists ht{};               // level and child lists (host copy)
   fst::TopoLists* dt = nullptr;      // device copy
+  int* dpin = nullptr;               // SM-pinned launches: role table, then the counter regions
   fst::JitState* jit = nullptr;      // run-time specialised kernels, if any
   int block[16] = {0};               // threads per block per kernel kind (0 = built-in heuristic)
   int variant[16] = {0};             // per kind: 0 auto, 1 generic, 2 specialised (see fst_model_set_launch)

@@ -80,6 +80,19 @@ struct LinkList {
 // so the slowest role's blocks are dispatched first).
 enum Role { ROLE_ABA = 0, ROLE_CRBA = 1, ROLE_RNEA = 2, ROLE_KIN = 3 };
 
+// SM-pinned launches: the role each SM id serves (ROLE_*, -1 none), and the
+// per-launch tile counters (slots 0..6, then the count of finished blocks).
+// Two counter regions: one for the fused evaluation, one for ABA, so the two
+// can run side by side.
+constexpr int kPinTableSize = 256;
+constexpr int kPinRegion = 8;
+constexpr int kPinEvalRegion = 0;
+constexpr int kPinAbaRegion = 1;
+struct PinArgs {
+  const int* table;  // [kPinTableSize]
+  int* counters;     // [kPinRegion] of this launch
+};
+
 struct EvalArgs {
   const float* q;
   const float* qd;

@@ -219,6 +219,7 @@ std::string make_source(const fst_model* m, int kind) {
   os << "#define FST_FIXED_TOPOLOGY 1\n#define FST_N " << m->n << "\n#define " << kKindMacro[kind] << " 1\n"
      << "#define FST_JIT_NAME " << kKindName[kind] << "\n#define FST_JIT_PATH_NAME " << kKindName[kind] << "_path\n"
      << "#define FST_JIT_WARP_NAME " << kKindName[kind] << "_pathw\n"
+     << "#define FST_JIT_PIN_NAME " << kKindName[kind] << "_pin\n"
      << "#include \"fst_layout.h\"\nnamespace fst {\nstatic __device__ const BodyC kC[" << m->n << "] = {\n";
   for (int i = 0; i < m->n; ++i) {
     const BodyC& c = m->hc[i];
@@ -362,9 +363,10 @@ void compile_one(CompileJob& job, const std::string& arch_opt) {
 
 }  // namespace
 
-// Per kind, up to three kernels of one module: the one-environment-per-thread
-// kernel (slot 0) and, for trees with at most 8 leaves, the path-parallel
-// kernels with a lane per path (slot 1) or a warp per path (slot 2).
+// Per kind, up to four kernels of one module: the one-environment-per-thread
+// kernel (slot 0), for trees with at most 8 leaves the path-parallel kernels
+// with a lane per path (slot 1) or a warp per path (slot 2), and for eval the
+// SM-pinned kernel (slot 3).
 struct JitState {
   CUmodule mod[JK_COUNT] = {};
   CUfunction fn[JK_SLOTS][JK_COUNT] = {};
@@ -406,7 +408,7 @@ fst_status jit_specialize(fst_model* m, unsigned mask) {
     }
     m->jit->mod[j.kind] = mod;
     m->jit->fn[0][j.kind] = fn;
-    const char* suffix[JK_SLOTS] = {"", "_path", "_pathw"};
+    const char* suffix[JK_SLOTS] = {"", "_path", "_pathw", "_pin"};
     for (int v = 1; v < JK_SLOTS; ++v) {
       CUfunction fp;
       const std::string pname = std::string(kKindName[j.kind]) + suffix[v];

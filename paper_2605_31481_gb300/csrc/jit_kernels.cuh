@@ -175,6 +175,54 @@ extern "C" __global__ void __launch_bounds__(256) FST_JIT_NAME(ModelView mv, int
 }
 #endif
 
+#ifdef FST_JIT_EVAL
+// SM-pinned form (FST_VARIANT_PINNED): a block serves the role its SM is
+// pinned to, tile after tile of T environments (pinned_tiles).
+extern "C" __global__ void __launch_bounds__(256) FST_JIT_PIN_NAME(ModelView mv, int64_t B, EvalArgs a, PinArgs p) {
+  extern __shared__ float4 smem[];
+  float* tile = reinterpret_cast<float*>(smem);
+  const int T = blockDim.x;
+  const int code = pinned_role(p);
+  int my = -1;
+  for (int r = 0; r < a.n_roles; ++r)
+    if (a.roles[r] == code) my = r;
+  const FixedTopo tp = fixed_topo(mv);
+  auto body = [&](int slot, int t) {
+    const int role = a.roles[slot];
+    const int64_t e = (int64_t)t * T + threadIdx.x;
+    if (e >= B) return;
+    const Col cq = stage_rows(tile, a.q, mv.nq, B, e);
+    Col c1{}, c2{};
+    if (role == ROLE_RNEA) {
+      c1 = stage_rows(tile + mv.nq * T, a.qd, mv.nv, B, e);
+      c2 = stage_rows(tile + (mv.nq + mv.nv) * T, a.qdd, mv.nv, B, e);
+    } else if (role == ROLE_ABA) {
+      c1 = stage_rows(tile + mv.nq * T, a.qd, mv.nv, B, e);
+      c2 = stage_rows(tile + (mv.nq + mv.nv) * T, a.tau, mv.nv, B, e);
+    }
+    cp_async_wait_all();
+    switch (role) {
+      case ROLE_ABA:
+        aba_env<FST_N>(tp, world_accel(mv), cq, c1, c2, a.qdd_out, B, e);
+        break;
+      case ROLE_CRBA:
+        crba_env<FST_N>(tp, cq, mv.nv, a.M, B, e);
+        break;
+      case ROLE_RNEA:
+        rnea_env<FST_N>(tp, world_accel(mv), cq, c1, c2, a.tau_out, B, e);
+        break;
+      default:
+        if (a.J)
+          jac_env<FST_N>(tp, cq, mv.nv, a.links, a.poses, a.J, B, e);
+        else
+          fk_env<FST_N>(tp, cq, a.poses, B, e);
+        break;
+    }
+  };
+  pinned_tiles(p, my, a.n_roles, (int)((B + T - 1) / T), body);
+}
+#endif
+
 #ifdef FST_JIT_EVAL_MIXED
 // Roles in a.level_mask run level-parallel (32 environments per block, the
 // block's warps splitting each tree level); the others one environment per

@@ -131,6 +131,8 @@ cudaError_t launch_jac_vjp(const ModelView& mv, int64_t B, const float* q, const
                            float* qbar, cudaStream_t s);
 cudaError_t launch_crba_vjp(const ModelView& mv, int64_t B, const float* q, const float* Mbar, float* qbar,
                             float* thbar, float* scratch, cudaStream_t s);
+cudaError_t launch_aba_level_pinned(const ModelView& mv, int64_t B, const float* q, const float* qd,
+                                    const float* tau, float* qdd, int block, const PinArgs& p, cudaStream_t s);
 cudaError_t launch_aba_vjp(const ModelView& mv, int64_t B, const float* q, const float* qd, const float* qdd,
                            const float* qddbar, float* qbar, float* qdbar, float* taubar, float* thbar, float* scratch,
                            cudaStream_t s);

@@ -73,6 +73,39 @@ __global__ void __launch_bounds__(256) aba_level_kernel(ModelView mv, int64_t B,
             Col{tile + (mv.nq + mv.nv) * kLaneEnvs + lane, kLaneEnvs}, S, qdd, B, e, act);
 }
 
+// SM-pinned ABA (FST_VARIANT_PINNED): blocks on SMs pinned to ABA take
+// tiles of 32 environments until none is left (pinned_tiles). The model is
+// staged only by blocks that get work.
+__global__ void __launch_bounds__(256) aba_level_pin_kernel(ModelView mv, int64_t B, const float* __restrict__ q,
+                                                            const float* __restrict__ qd,
+                                                            const float* __restrict__ tau, float* __restrict__ qdd,
+                                                            PinArgs p) {
+  extern __shared__ float4 smem[];
+  float* tile = level_tile(smem, mv.n);
+  const LaneState S{tile + (mv.nq + 2 * mv.nv) * kLaneEnvs, kAbaState};
+  const int lane = threadIdx.x & 31;
+  const int my = pinned_role(p) == ROLE_ABA ? 0 : -1;
+  bool staged = false;
+  SmemModel sm{nullptr, nullptr, 0};
+  auto body = [&](int, int t) {
+    if (!staged) {
+      sm = stage_model(mv, smem);  // synchronises the block
+      staged = true;
+    }
+    const int64_t e = (int64_t)t * kLaneEnvs + lane;
+    const bool act = e < B;
+    stage_block_rows(tile, q, mv.nq, B, e);
+    stage_block_rows(tile + mv.nq * kLaneEnvs, qd, mv.nv, B, e);
+    stage_block_rows(tile + (mv.nq + mv.nv) * kLaneEnvs, tau, mv.nv, B, e);
+    cp_async_wait_all();
+    __syncthreads();
+    aba_level(sm, world_accel(mv), Col{tile + lane, kLaneEnvs}, Col{tile + mv.nq * kLaneEnvs + lane, kLaneEnvs},
+              Col{tile + (mv.nq + mv.nv) * kLaneEnvs + lane, kLaneEnvs}, S, qdd, B, e, act);
+    __syncthreads();  // the next tile reuses the staged rows and the state
+  };
+  pinned_tiles(p, my, 1, (int)((B + kLaneEnvs - 1) / kLaneEnvs), body);
+}
+
 // Fused evaluation with the level-parallel bodies: blockIdx.y is the role.
 __global__ void __launch_bounds__(256) eval_level_kernel(ModelView mv, int64_t B, EvalArgs a) {
   const int role = a.roles[blockIdx.y];
@@ -156,6 +189,18 @@ cudaError_t launch_aba_level(const ModelView& mv, int64_t B, const float* q, con
                              float* qdd, int block, cudaStream_t s) {
   return go(aba_level_kernel, mv, B, level_smem_needed(mv, LEVEL_ABA), block, 1, s, q, qd, tau, qdd);
 }
+cudaError_t launch_aba_level_pinned(const ModelView& mv, int64_t B, const float* q, const float* qd,
+                                    const float* tau, float* qdd, int block, const PinArgs& p, cudaStream_t s) {
+  const size_t sh = level_smem_needed(mv, LEVEL_ABA);
+  if (sh > kLevelSmemLimit) return cudaErrorInvalidConfiguration;
+  prepare(aba_level_pin_kernel, sh);
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  aba_level_pin_kernel<<<2 * (sms > 0 ? sms : 1), block, sh, s>>>(mv, B, q, qd, tau, qdd, p);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_eval_level(const ModelView& mv, int64_t B, const EvalArgs& a, int block, cudaStream_t s) {
   return go(eval_level_kernel, mv, B, level_smem_needed(mv, LEVEL_EVAL), block, (unsigned)a.n_roles, s, a);
 }
