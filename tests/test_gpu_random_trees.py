@@ -67,7 +67,7 @@ def test_random_tree_every_mapping_matches_oracle(torch_cuda, seed):
     ran = []
     for variant, block in configs:
         try:
-            m.set_launch(None if variant != "generic" else KINDS, block, variant)
+            m.set_launch(KINDS if variant in ("generic", "specialized") else None, block, variant)
         except _ffi.FstError:
             continue                       # no such kernel for this tree (too many leaves, too large)
         out = {"poses": api.fk(m, q), "J": api.jacobian(m, q, ee), "tau": api.rnea(m, q, qd, qdd),
