@@ -327,6 +327,9 @@ def run_fst(args):
              "concurrent": "5 per-operator kernels on parallel graph branches (" +
                            ", ".join(f"{k} {desc['kinds'][k]}" for k in OPS) + f"), carveout {plan.carveout}" +
                            (", ABA branch on a high-priority stream" if plan.prio else ""),
+             "split": f"ABA kernel ({desc['kinds']['aba']}) beside two launches of the fused kernel "
+                      f"({desc['kinds']['eval']}: FK with the Jacobians; RNEA with CRBA) on parallel graph branches, "
+                      f"carveout {plan.carveout}",
              "pinned": f"SM-pinned: ABA kernel ({desc['kinds']['aba']}) on its share of the SMs beside the fused "
                        f"kernel of the other four ({desc['kinds']['eval']}) on the rest, carveout {plan.carveout}",
              "sequential": "5 per-operator kernels in sequence"}[plan.mode]
@@ -374,7 +377,7 @@ def run_fst(args):
             "e2e": {"value": round(e2e_value, 1), "unit": "env-evals/s", "h2d_bytes_per_step": e2e["h2d"],
                     "d2h_bytes_per_step": e2e["d2h"], "steps": e2e["steps"],
                     "pipelined_slots": e2e["slots"], "readback_chunks": e2e["readback_chunks"]},
-            "gpu_launches": K * {"fused": 1, "hybrid": 2, "pinned": 2}.get(plan.mode, len(OPS)),
+            "gpu_launches": K * {"fused": 1, "hybrid": 2, "split": 3, "pinned": 2}.get(plan.mode, len(OPS)),
             "kernels": kernels,
             "plan": desc,
             "clocks": clocks,

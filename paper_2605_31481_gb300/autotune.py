@@ -194,6 +194,9 @@ class StepPlan:
                   with one variant for all of them;
       hybrid      ABA's own kernel (at its best variant) on a side stream,
                   overlapping one fused launch of the four other operators;
+      split       the same, with that fused launch split in two (FK with the
+                  Jacobians; RNEA with CRBA) on two more branches;
+      pinned      the hybrid pair as SM-pinned launches on disjoint SM sets;
       concurrent  each operator's own kernel on its own stream;
       sequential  the per-operator kernels one after another.
     Side streams are forked from and joined back into the caller's stream,
@@ -205,7 +208,7 @@ class StepPlan:
     block scheduler then dispatches the longest chain's blocks first and
     fills the other SMs with the rest."""
 
-    MODES = ("fused", "hybrid", "pinned", "concurrent", "sequential")
+    MODES = ("fused", "hybrid", "split", "pinned", "concurrent", "sequential")
     PIN_SHARES = (0.45, 0.55, 0.65)   # fractions of the SMs pinned to ABA
 
     def __init__(self, model, B, links=None, use_cache=True, verbose=False, modes=MODES):
@@ -219,7 +222,7 @@ class StepPlan:
         # priority (out-of-range values clamp to it), the others at the default
         self._ranked = [torch.cuda.Stream(device=model.device, priority=-1000 if k == 0 else 0)
                         for k in range(len(FORWARD_KINDS))]
-        key = _key(model, "plan8", B)
+        key = _key(model, "plan9", B)
         hit = _load_cache().get(key) if use_cache else None
         if hit:
             self.times = {(k, c, p, ev): v for k, c, p, ev, v in hit["times"]}
@@ -248,7 +251,8 @@ class StepPlan:
         for carveout in (-1, 100):
             api.set_smem_carveout(carveout)
             for mode in modes:
-                cfgs = {"hybrid": hybrid_cfgs, "pinned": pinned_cfgs}.get(mode, [f"{best_eval}|{best_aba}"])
+                cfgs = {"hybrid": hybrid_cfgs, "split": hybrid_cfgs, "pinned": pinned_cfgs}.get(
+                    mode, [f"{best_eval}|{best_aba}"])
                 for ev in cfgs:
                     try:
                         self._set_eval(ev)
@@ -322,6 +326,10 @@ class StepPlan:
         elif self.mode in ("hybrid", "pinned"):
             self._fork([ops[4], lambda: api.eval(m, q, qd, qdd, tau, fk=True, links=self.links, rnea=True, crba=True,
                                                  aba=False, out=out)])
+        elif self.mode == "split":
+            # ABA, then the fused kernel twice: kinematics alone, RNEA with CRBA
+            self._fork([ops[4], lambda: api.eval(m, q, qd, qdd, tau, fk=True, links=self.links, out=out),
+                        lambda: api.eval(m, q, qd, qdd, tau, fk=False, rnea=True, crba=True, out=out)])
         else:
             # longest first, so its blocks are dispatched first
             order = sorted(range(len(ops)), key=lambda k: -self.tuned[FORWARD_KINDS[k]]["us"])
@@ -332,7 +340,8 @@ class StepPlan:
         kinds = {k: f"{v['variant']}/{v['block']}" for k, v in self.tuned.items()}
         kinds["eval"], kinds["aba"] = self.eval_config.split("|")
         return {"mode": self.mode, "carveout": self.carveout, "priorities": self.prio,
-                "us": {f"{k[0]}{'[' + k[3] + ']' if k[0] in ('hybrid', 'pinned') else ''}{'' if k[1] < 0 else f'@{k[1]}%'}"
+                "us": {f"{k[0]}{'[' + k[3] + ']' if k[0] in ('hybrid', 'split', 'pinned') else ''}"
+                       f"{'' if k[1] < 0 else f'@{k[1]}%'}"
                        f"{'+prio' if k[2] else ''}": round(v, 3) for k, v in self.times.items()},
                 "kinds": kinds,
                 "eval_candidates_us": self.tuned["eval"]["candidates"]}
