@@ -323,10 +323,10 @@ def run_fst(args):
     kname = {"fused": f"fused eval kernel ({desc['kinds']['eval']})",
              "hybrid": f"ABA kernel ({desc['kinds']['aba']}) on a parallel graph branch beside the fused kernel of "
                        f"the other four ({desc['kinds']['eval']}), carveout {plan.carveout}" +
-                       (", ABA branch on a high-priority stream" if plan.prio else ""),
+                       (", fused kernel forked first" if plan.alt else ""),
              "concurrent": "5 per-operator kernels on parallel graph branches (" +
                            ", ".join(f"{k} {desc['kinds'][k]}" for k in OPS) + f"), carveout {plan.carveout}" +
-                           (", ABA branch on a high-priority stream" if plan.prio else ""),
+                           (", longest operator on a high-priority stream" if plan.prio else ""),
              "split": f"ABA kernel ({desc['kinds']['aba']}) beside two launches of the fused kernel "
                       f"({desc['kinds']['eval']}: FK with the Jacobians; RNEA with CRBA) on parallel graph branches, "
                       f"carveout {plan.carveout}",

@@ -204,9 +204,10 @@ class StepPlan:
     share an SM when they request the same shared-memory carveout, so the
     overlapping modes are also tried with one common carveout (100 %); the
     chosen carveout is applied with fst_set_smem_carveout. They are also
-    tried with the operator measured slowest on a high-priority stream: the
-    block scheduler then dispatches the longest chain's blocks first and
-    fills the other SMs with the rest."""
+    tried with the operator measured slowest on a high-priority stream
+    (concurrent mode) or with the fused launch forked before the ABA branch
+    (the block scheduler places the first-forked kernel's blocks first, and
+    on GB300 the order moves a hybrid step between 14.5 and 22 us)."""
 
     MODES = ("fused", "hybrid", "split", "pinned", "concurrent", "sequential")
     PIN_SHARES = (0.45, 0.55, 0.65)   # fractions of the SMs pinned to ABA
@@ -222,11 +223,11 @@ class StepPlan:
         # priority (out-of-range values clamp to it), the others at the default
         self._ranked = [torch.cuda.Stream(device=model.device, priority=-1000 if k == 0 else 0)
                         for k in range(len(FORWARD_KINDS))]
-        key = _key(model, "plan9", B)
+        key = _key(model, "plan10", B)
         hit = _load_cache().get(key) if use_cache else None
         if hit:
-            self.times = {(k, c, p, ev): v for k, c, p, ev, v in hit["times"]}
-            self._apply(hit["mode"], hit["carveout"], hit["prio"], hit["eval"])
+            self.times = {(k, c, a, ev): v for k, c, a, ev, v in hit["times"]}
+            self._apply(hit["mode"], hit["carveout"], hit["alt"], hit["eval"])
             return
         buf = Buffers(model, B, self.links)
         # the hybrid's fused kernel carries three roles, not the four the
@@ -258,16 +259,16 @@ class StepPlan:
                         self._set_eval(ev)
                     except _ffi.FstError:
                         continue                 # not available for this model
-                    for prio in (False, True):
-                        if (carveout >= 0 or prio) and mode in ("fused", "sequential"):
+                    for alt in (False, True):
+                        if (carveout >= 0 or alt) and mode in ("fused", "sequential"):
                             continue
-                        self.mode, self.streams = mode, self._ranked if prio else self._plain
-                        times[(mode, carveout, prio, ev)] = graph_time_us(
+                        self._set_alt(mode, alt)
+                        times[(mode, carveout, alt, ev)] = graph_time_us(
                             lambda: self(buf.q, buf.qd, buf.qdd, buf.tau, buf.out))
         self.times = times
         self._apply(*min(times, key=times.get))
         if use_cache:
-            _store_cache({key: {"mode": self.mode, "carveout": self.carveout, "prio": self.prio,
+            _store_cache({key: {"mode": self.mode, "carveout": self.carveout, "alt": self.alt,
                                 "eval": self.eval_config,
                                 "times": [[k, c, p, ev, round(v, 3)] for (k, c, p, ev), v in times.items()]}})
 
@@ -290,13 +291,22 @@ class StepPlan:
         other = ("kin", "rnea", "crba")
         return ["aba" if i % period < n_aba else other[(i % period - n_aba) % 3] for i in range(256)]
 
-    def _apply(self, mode, carveout, prio, eval_config):
-        self.mode, self.carveout, self.prio, self.eval_config = mode, carveout, bool(prio), eval_config
+    def _set_alt(self, mode, alt):
+        """The plan's binary option: for the concurrent mode, the longest
+        operator's stream at high priority; for the modes with an ABA branch,
+        the fused launch(es) forked before ABA instead of after it (the block
+        scheduler places the first-forked kernel's blocks first)."""
+        self.mode, self.alt = mode, bool(alt)
+        self.prio = self.alt and mode == "concurrent"
         self.streams = self._ranked if self.prio else self._plain
+
+    def _apply(self, mode, carveout, alt, eval_config):
+        self.carveout, self.eval_config = carveout, eval_config
+        self._set_alt(mode, alt)
         self._set_eval(eval_config)
         api.set_smem_carveout(carveout)
         self.fused = mode == "fused"
-        self.expected_us = self.times[(mode, carveout, self.prio, eval_config)]
+        self.expected_us = self.times[(mode, carveout, self.alt, eval_config)]
 
     def _ops(self, q, qd, qdd, tau, out):
         m = self.model
@@ -324,12 +334,14 @@ class StepPlan:
             for op in ops:
                 op()
         elif self.mode in ("hybrid", "pinned"):
-            self._fork([ops[4], lambda: api.eval(m, q, qd, qdd, tau, fk=True, links=self.links, rnea=True, crba=True,
-                                                 aba=False, out=out)])
+            fused = [lambda: api.eval(m, q, qd, qdd, tau, fk=True, links=self.links, rnea=True, crba=True, aba=False,
+                                      out=out)]
+            self._fork(fused + [ops[4]] if self.alt else [ops[4]] + fused)
         elif self.mode == "split":
-            # ABA, then the fused kernel twice: kinematics alone, RNEA with CRBA
-            self._fork([ops[4], lambda: api.eval(m, q, qd, qdd, tau, fk=True, links=self.links, out=out),
-                        lambda: api.eval(m, q, qd, qdd, tau, fk=False, rnea=True, crba=True, out=out)])
+            # ABA beside the fused kernel twice: kinematics alone, RNEA with CRBA
+            fused = [lambda: api.eval(m, q, qd, qdd, tau, fk=True, links=self.links, out=out),
+                     lambda: api.eval(m, q, qd, qdd, tau, fk=False, rnea=True, crba=True, out=out)]
+            self._fork(fused + [ops[4]] if self.alt else [ops[4]] + fused)
         else:
             # longest first, so its blocks are dispatched first
             order = sorted(range(len(ops)), key=lambda k: -self.tuned[FORWARD_KINDS[k]]["us"])
@@ -340,8 +352,10 @@ class StepPlan:
         kinds = {k: f"{v['variant']}/{v['block']}" for k, v in self.tuned.items()}
         kinds["eval"], kinds["aba"] = self.eval_config.split("|")
         return {"mode": self.mode, "carveout": self.carveout, "priorities": self.prio,
+                "fused_forked_first": self.alt and self.mode != "concurrent",
                 "us": {f"{k[0]}{'[' + k[3] + ']' if k[0] in ('hybrid', 'split', 'pinned') else ''}"
                        f"{'' if k[1] < 0 else f'@{k[1]}%'}"
-                       f"{'+prio' if k[2] else ''}": round(v, 3) for k, v in self.times.items()},
+                       f"{('+prio' if k[0] == 'concurrent' else '+fusedfirst') if k[2] else ''}": round(v, 3)
+                       for k, v in self.times.items()},
                 "kinds": kinds,
                 "eval_candidates_us": self.tuned["eval"]["candidates"]}
