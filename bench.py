@@ -592,6 +592,8 @@ def sysid(torch, fst, w, steps=500):
     torch.cuda.synchronize()
     dt_ls = time.perf_counter() - t0
     err_ls = sid.mass_errors(theta_ls, true.cpu().numpy())
+    sid.identify_masses(m, q, qd, qdd, tau_meas, true)                # warm (first use of the solver)
+    torch.cuda.synchronize()
     t0 = time.perf_counter()
     masses, _ = sid.identify_masses(m, q, qd, qdd, tau_meas, true)
     torch.cuda.synchronize()
