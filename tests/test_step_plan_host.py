@@ -1,0 +1,106 @@
+"""The step planner's selection and cache logic on the host, with the
+measurements, the tuner, the kernels and the CUDA streams replaced by fakes
+(no GPU): it keeps the fastest measured combination, applies its launch
+settings and carveout, and a second planner reads the same decision back
+from the cache without measuring."""
+import json
+
+import pytest
+
+from paper_2605_31481_gb300 import autotune
+
+
+class FakeModel:
+    device = "cpu"
+    ee = (1, 2)
+    fingerprint = "fake"
+    nq = nv = 3
+    n_bodies = 3
+
+    def __init__(self):
+        self.launch = {}
+        self.roles = None
+
+    def set_launch(self, kinds, block, variant):
+        for k in kinds:
+            self.launch[k] = (variant, block)
+
+    def set_sm_roles(self, roles):
+        self.roles = list(roles)
+
+
+@pytest.fixture
+def fakes(monkeypatch, tmp_path):
+    monkeypatch.setenv("FST_TUNE_CACHE", str(tmp_path / "tune.json"))
+    carve = []
+    monkeypatch.setattr(autotune.api, "set_smem_carveout", lambda c: carve.append(c))
+    cands = {"specialized/128": 17.0, "specialized/256": 21.0, "level/256": 17.1, "generic/64": 22.0}
+    aba = {"level/256": 10.2, "level/128": 10.4, "specialized/64": 14.3}
+    tuned = {k: {"variant": "specialized", "block": 64, "us": 5.0, "candidates": {"specialized/64": 5.0}}
+             for k in autotune.FORWARD_KINDS}
+    tuned["aba"] = {"variant": "level", "block": 256, "us": 10.2, "candidates": aba}
+    tuned["eval"] = {"variant": "specialized", "block": 128, "us": 17.0, "candidates": cands}
+    monkeypatch.setattr(autotune, "tune", lambda *a, **k: tuned)
+    monkeypatch.setattr(autotune.torch.cuda, "Stream", lambda *a, **k: object())
+    monkeypatch.setattr(autotune, "Buffers", lambda *a, **k: type("B", (), {"q": 0, "qd": 0, "qdd": 0, "tau": 0,
+                                                                            "out": {}})())
+    monkeypatch.setattr(autotune, "_key", lambda model, kind, B: f"{model.fingerprint}|{kind}|{B}")
+    calls = []
+
+    def fake_time(fn):
+        m = current["plan"]
+        t = {"fused": 17.0, "hybrid": 16.0, "split": 16.5, "pinned": 27.0, "concurrent": 25.0,
+             "sequential": 33.0}[m.mode]
+        ev = m.model.launch.get("eval")
+        if m.mode == "hybrid" and ev == ("specialized", 128) and m.alt and carve[-1] == 100:
+            t = 14.5                                   # the one combination that wins
+        calls.append((m.mode, carve[-1], m.alt, ev))
+        return t
+
+    current = {}
+    monkeypatch.setattr(autotune, "graph_time_us", fake_time)
+    monkeypatch.setattr(autotune.StepPlan, "__call__", lambda self, *a: None)
+    return {"current": current, "calls": calls, "carve": carve, "tmp": tmp_path}
+
+
+def test_plan_keeps_the_fastest_combination_and_caches_it(fakes):
+    model = FakeModel()
+    orig_init = autotune.StepPlan.__init__
+
+    def init(self, *a, **k):
+        fakes["current"]["plan"] = self
+        orig_init(self, *a, **k)
+
+    autotune.StepPlan.__init__ = init
+    try:
+        plan = autotune.StepPlan(model, 4096)
+        assert (plan.mode, plan.carveout, plan.alt) == ("hybrid", 100, True)
+        assert plan.eval_config.startswith("specialized/128|") and plan.expected_us == 14.5
+        assert model.launch["eval"] == ("specialized", 128) and fakes["carve"][-1] == 100
+        d = plan.describe()
+        assert d["fused_forked_first"] is True and d["priorities"] is False
+        assert min(d["us"].values()) == 14.5
+        n_measured = len(fakes["calls"])
+        assert n_measured > 20
+        cache = json.load(open(fakes["tmp"] / "tune.json"))
+        assert any(k.endswith("|plan10|4096") for k in cache)
+        # a second planner reads the decision back without measuring
+        model2 = FakeModel()
+        plan2 = autotune.StepPlan(model2, 4096)
+        assert len(fakes["calls"]) == n_measured
+        assert (plan2.mode, plan2.carveout, plan2.alt, plan2.eval_config) == \
+               (plan.mode, plan.carveout, plan.alt, plan.eval_config)
+        assert model2.launch["eval"] == ("specialized", 128)
+    finally:
+        autotune.StepPlan.__init__ = orig_init
+
+
+def test_fork_order_and_priority_options(fakes):
+    plan = autotune.StepPlan.__new__(autotune.StepPlan)
+    plan._plain, plan._ranked = ["p"], ["r"]
+    plan._set_alt("concurrent", True)
+    assert plan.prio and plan.streams == ["r"]
+    plan._set_alt("hybrid", True)
+    assert plan.alt and not plan.prio and plan.streams == ["p"]
+    plan._set_alt("fused", False)
+    assert not plan.alt and not plan.prio
