@@ -159,7 +159,10 @@ FST_API fst_status fst_model_specialize(fst_model* model, uint32_t kinds);
  *               RNEA, CRBA, ABA and eval only (a 0 mask then selects those
  *               six), and only while that state fits
  *               in shared memory (about 28 bodies for ABA); otherwise the
- *               generic kernel runs.
+ *               generic kernel runs;
+ *   MIXED, PATH, PATH_WARP, PINNED: see each below. A 0 mask with PATH or
+ *               PATH_WARP selects the six kinds above; with PINNED, eval
+ *               and ABA.
  * Results agree within FP32 rounding; only speed changes. SPECIALIZED for a
  * kind that fst_model_specialize has not compiled returns
  * FST_ERR_INVALID_ARG. The autotuner in the Python package measures the
