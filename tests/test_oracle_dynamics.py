@@ -152,6 +152,29 @@ def test_power_balance(tree):
     assert np.abs(dE - power).max() < 1e-6 * max(1, np.abs(power).max())
 
 
+@pytest.mark.parametrize("tree", [w.humanoid(), w.spined_quadruped(), w.legged(6)], ids=lambda t: t.name)
+def test_kinetic_energy_from_body_twists(tree):
+    """1/2 qd^T M qd equals the sum over bodies of 1/2 m |v_com|^2 +
+    1/2 w^T (R Ic R^T) w, each body's world twist [v_O; w] = J_i qd taken
+    from the Jacobian and its pose from FK. This pins CRBA on full-size trees,
+    the free base included (where qd is not dq/dt)."""
+    s = w.random_state(tree, 16, seed=5)
+    q, qd = s["q"], s["qd"]
+    T = rbd.fk(tree, q)
+    ke = np.zeros(len(q))
+    for i in range(tree.n_bodies):
+        tw = np.einsum("bij,bj->bi", rbd.jacobian(tree, q, i), qd)
+        vO, om = tw[:, 0:3], tw[:, 3:6]
+        R, p = T[:, i, :3, :3], T[:, i, :3, 3]
+        pc = p + R @ np.asarray(tree.com[i], dtype=np.float64)
+        vc = vO + np.cross(om, pc)
+        Iw = R @ sp.sym6_to_3x3(np.asarray(tree.I_com[i], dtype=np.float64)) @ np.swapaxes(R, 1, 2)
+        ke += 0.5 * tree.mass[i] * np.einsum("bi,bi->b", vc, vc) + 0.5 * np.einsum("bi,bij,bj->b", om, Iw, om)
+    M = rbd.crba(tree, q)
+    ref = 0.5 * np.einsum("bi,bij,bj->b", qd, M, qd)
+    np.testing.assert_allclose(ke, ref, rtol=1e-12)
+
+
 def _free_body(seed):
     t = w.random_tree([-1], [w.FREE], seed)
     return t
