@@ -1,4 +1,5 @@
-// Host-only checks of the model builder and of the path tables of the
+// Host-only checks of the model builder (its per-joint constants against the
+// plain product of the joint poses) and of the path tables of the
 // specialised kernels, compiled with -fsanitize=address,undefined by
 // tests/test_host_sanitize.py. Exits non-zero (with a message) on the first
 // violated property; a sanitizer report also fails the run.
@@ -7,6 +8,7 @@
 // (path_tables, make_source); nothing here calls NVRTC, the driver or a GPU.
 #include "jit.cpp"
 
+#include <array>
 #include <cmath>
 #include <cstdio>
 #include <random>
@@ -102,6 +104,102 @@ int check_paths(const fst_model& m, const fst::PathTables& P, int seed) {
   return 0;
 }
 
+// Rotation of a unit quaternion (w, x, y, z), in row-major order.
+void quat_R(double w, double x, double y, double z, double* R) {
+  const double n = std::sqrt(w * w + x * x + y * y + z * z);
+  w /= n, x /= n, y /= n, z /= n;
+  const double r[9] = {1 - 2 * (y * y + z * z), 2 * (x * y - w * z),     2 * (x * z + w * y),
+                       2 * (x * y + w * z),     1 - 2 * (x * x + z * z), 2 * (y * z - w * x),
+                       2 * (x * z - w * y),     2 * (y * z + w * x),     1 - 2 * (x * x + y * y)};
+  std::memcpy(R, r, sizeof(r));
+}
+
+void random_pose(std::mt19937& rng, double* T) {
+  std::normal_distribution<double> N(0.0, 1.0);
+  quat_R(N(rng), N(rng), N(rng), N(rng), T);
+  for (int k = 9; k < 12; ++k) T[k] = 0.3 * N(rng);
+}
+
+// C = A B for 3x4 poses (R row-major, then t).
+void pose_mul(const double* A, const double* B, double* C) {
+  double out[12];
+  for (int r = 0; r < 3; ++r) {
+    for (int c = 0; c < 3; ++c)
+      out[3 * r + c] = A[3 * r] * B[c] + A[3 * r + 1] * B[3 + c] + A[3 * r + 2] * B[6 + c];
+    out[9 + r] = A[3 * r] * B[9] + A[3 * r + 1] * B[10] + A[3 * r + 2] * B[11] + A[9 + r];
+  }
+  std::memcpy(C, out, sizeof(out));
+}
+
+// Parent-to-child pose T_joint * J(q) * T_link as a plain product, with the
+// joint motion J(q) a rotation by q about the axis (built from the
+// quaternion (cos q/2, sin q/2 axis)) or a translation by q along it.
+void product_pose(const fst_body_desc& d, double q, double* T) {
+  double J[12] = {1, 0, 0, 0, 1, 0, 0, 0, 1, 0, 0, 0};
+  const double na = std::sqrt(d.axis[0] * d.axis[0] + d.axis[1] * d.axis[1] + d.axis[2] * d.axis[2]);
+  const double u[3] = {d.axis[0] / na, d.axis[1] / na, d.axis[2] / na};
+  if (d.type == FST_JOINT_REVOLUTE)
+    quat_R(std::cos(0.5 * q), std::sin(0.5 * q) * u[0], std::sin(0.5 * q) * u[1], std::sin(0.5 * q) * u[2], J);
+  if (d.type == FST_JOINT_PRISMATIC)
+    for (int k = 0; k < 3; ++k) J[9 + k] = q * u[k];
+  pose_mul(d.T_joint, J, T);
+  pose_mul(T, d.T_link, T);
+}
+
+// The model builder's per-joint constants (paper Sec. 3.2, Eq. 2-5), FP32,
+// against the plain product of the joint's poses: the pose at random q, and
+// the motion subspace against central differences of the pose (the child
+// frame's twist in its own coordinates, [w; v]).
+int check_joint_constants(int seed) {
+  std::mt19937 rng(1000 + seed);
+  std::normal_distribution<double> N(0.0, 1.0);
+  const int n = 6;
+  auto b = random_tree(rng, n, false);
+  for (int i = 0; i < n; ++i) {
+    random_pose(rng, b[i].T_joint);
+    random_pose(rng, b[i].T_link);
+  }
+  fst_model m;
+  if (fst::build_model_host(b.data(), n, std::array<double, 3>{0, 0, -9.81}.data(), &m) != FST_OK)
+    return fail("a table with rotated joint and link frames is accepted", seed);
+  for (int i = 0; i < n; ++i) {
+    const fst_body_desc& d = b[i];
+    const fst::BodyC& c = m.hc[i];
+    for (int trial = 0; trial < 8; ++trial) {
+      const double q = d.type == FST_JOINT_FIXED ? 0.0 : 3.0 * N(rng);
+      double T[12], G[12];
+      product_pose(d, q, T);
+      const double s = std::sin(q), omc = 1.0 - std::cos(q);
+      for (int k = 0; k < 9; ++k)
+        G[k] = d.type == FST_JOINT_REVOLUTE ? c.R0[k] + s * c.A[k] + omc * c.Bm[k] : c.R0[k];
+      for (int k = 0; k < 3; ++k)
+        G[9 + k] = d.type == FST_JOINT_REVOLUTE   ? c.t0[k] + s * c.a[k] + omc * c.b[k]
+                   : d.type == FST_JOINT_PRISMATIC ? c.t0[k] + q * c.a[k]
+                                                   : c.t0[k];
+      for (int k = 0; k < 12; ++k)
+        if (std::fabs(G[k] - T[k]) > 2e-6 * (1.0 + std::fabs(q))) return fail("joint constants reproduce the pose product", seed);
+      if (d.type == FST_JOINT_FIXED) continue;
+      const double h = 1e-6;
+      double Tp[12], Tm[12];
+      product_pose(d, q + h, Tp);
+      product_pose(d, q - h, Tm);
+      double dR[9], dt[3];
+      for (int k = 0; k < 9; ++k) dR[k] = (Tp[k] - Tm[k]) / (2 * h);
+      for (int k = 0; k < 3; ++k) dt[k] = (Tp[9 + k] - Tm[9 + k]) / (2 * h);
+      double W[9];  // R^T dR, skew
+      for (int r = 0; r < 3; ++r)
+        for (int cc = 0; cc < 3; ++cc) W[3 * r + cc] = T[r] * dR[cc] + T[3 + r] * dR[3 + cc] + T[6 + r] * dR[6 + cc];
+      const double S[6] = {W[7], W[2], W[3],
+                           T[0] * dt[0] + T[3] * dt[1] + T[6] * dt[2],
+                           T[1] * dt[0] + T[4] * dt[1] + T[7] * dt[2],
+                           T[2] * dt[0] + T[5] * dt[1] + T[8] * dt[2]};
+      for (int k = 0; k < 6; ++k)
+        if (std::fabs(S[k] - c.S[k]) > 2e-6) return fail("motion subspace is the child frame's twist", seed);
+    }
+  }
+  return 0;
+}
+
 }  // namespace
 
 int main() {
@@ -120,6 +218,8 @@ int main() {
         if (fst::make_source(&m, k).find("jit_kernels.cuh") == std::string::npos) return fail("source generation", seed);
     ++checked;
   }
+  for (int seed = 0; seed < 50; ++seed)
+    if (check_joint_constants(seed)) return 1;
   // malformed tables are refused with an error status, never a crash
   std::mt19937 rng(1234);
   for (int c = 0; c < 8; ++c) {
