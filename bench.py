@@ -162,6 +162,20 @@ class ClockSampler:
 # GPU arm
 # ---------------------------------------------------------------------------
 
+def job_rate(ms, world, envs_per_rank, steps, device):
+    """Whole-job throughput of `world` replicas: the slowest rank's time (the
+    maximum over ranks of `ms`, in milliseconds, for `steps` steps of
+    `envs_per_rank` environments each) and the env-evals/s of all ranks
+    together over that time. Every rank must call it when world > 1."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        tt = torch.tensor([ms], dtype=torch.float64, device=device)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    return ms, world * envs_per_rank * steps / (ms / 1e3)
+
+
 def run_fst(args):
     import torch
     import torch.distributed as dist
@@ -299,20 +313,12 @@ def run_fst(args):
     per_op_ms = per_op_times(torch, launch, sets, R, stream, K_op=min(K, 3000))
     per_op_hot_ms = per_op_times(torch, launch, sets, R, stream, K_op=min(K, 3000), hot=True)
 
-    if world > 1:
-        tt = torch.tensor([ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
-    value = world * B * K / (ms / 1e3)
+    ms, value = job_rate(ms, world, B, K, dev)
 
     # end to end through the public binding, host buffers in and out
     e2e = run_e2e(torch, fst, model, tree, B, links, st, dev, min(K, 5000), args.warmup, plan=plan,
                   slots=args.e2e_slots, split=args.e2e_split)
-    if world > 1:
-        tt = torch.tensor([e2e["ms"]], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e["ms"] = float(tt.item())
-    e2e_value = world * B * e2e["steps"] / (e2e["ms"] / 1e3)
+    e2e["ms"], e2e_value = job_rate(e2e["ms"], world, B, e2e["steps"], dev)
 
     pk = peaks()
     p_alu = fp32_peak_tflops(pk["sm_max_mhz"])

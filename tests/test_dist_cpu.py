@@ -3,7 +3,8 @@ processes): each rank sums the inertial-parameter gradient over its own
 contiguous shard of environments, one all-reduce adds the shards, and the
 result equals the full-batch gradient. The per-shard gradients come from the
 oracle's regressor; this exercises the sharding and reduction the GPU path
-uses, without a GPU."""
+uses, without a GPU. The benchmark's whole-job rate (the slowest replica's
+time, all replicas' environments) is checked the same way."""
 import os
 import socket
 
@@ -73,3 +74,24 @@ def test_shards_cover_the_batch():
             assert ranges[0][0] == 0 and ranges[-1][1] == B
             assert all(a[1] == b[0] for a, b in zip(ranges, ranges[1:]))
             assert max(b - a for a, b in ranges) - min(b - a for a, b in ranges) <= 1
+
+
+def _rate_worker(rank, world, port, out_path):
+    import bench
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    ms, value = bench.job_rate(10.0 + 5.0 * rank, world, 4096, 100, "cpu")
+    if rank == 0:
+        np.save(out_path, np.array([ms, value]))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_bench_rate_takes_the_slowest_rank(tmp_path):
+    out = str(tmp_path / "r.npy")
+    mp.start_processes(_rate_worker, args=(2, _free_port(), out), nprocs=2, start_method="spawn", join=True)
+    ms, value = np.load(out)
+    assert ms == 15.0
+    assert value == pytest.approx(2 * 4096 * 100 / 0.015, rel=1e-12)
+    import bench
+    assert bench.job_rate(8.0, 1, 4096, 100, "cpu") == (8.0, 4096 * 100 / 0.008)
