@@ -213,7 +213,7 @@ def run_fst(args):
     if world > 1 and rank == 0:
         dist.barrier()
     from paper_2605_31481_gb300.autotune import StepPlan
-    plan = StepPlan(model, B, links=links)
+    plan = StepPlan(model, B, links=links, fixed=args.plan)
     nq, nv, nb, nl = tree.nq, tree.nv, tree.n_bodies, len(links)
     out_floats = nb * 12 + nl * 6 * nv + nv + nv * nv + nv
     in_floats = nq + 3 * nv
@@ -367,8 +367,11 @@ def run_fst(args):
         extras["multi_tree"] = multi_tree(torch, fst, w)
         extras["sysid"] = sysid(torch, fst, w)
     if rank == 0:
-        cpu1, parity = cpu_baseline(tree, links, args, st, first)
-        cpu = cpu_baseline_all_cores()
+        if args.no_cpu_baseline:
+            cpu1 = parity = cpu = None
+        else:
+            cpu1, parity = cpu_baseline(tree, links, args, st, first)
+            cpu = cpu_baseline_all_cores()
         line = {
             "metric": METRIC, "value": round(value, 1), "unit": "env-evals/s", "n_gpus": world, "steps": K,
             "warmup": args.warmup, "ms_per_step": round(ms / K, 5), "higher_is_better": True, "scaling": "weak",
@@ -896,9 +899,20 @@ def main():
                     help="end-to-end leg: read-back chunks copied on parallel graph branches")
     ap.add_argument("--traffic", type=float, default=None,
                     help="dram bytes per launch of the dominant kernel from an ncu capture (else null)")
+    ap.add_argument("--plan", default=None,
+                    help="run this step plan instead of tuning one, named as the keys of the line's plan.us, "
+                         "e.g. 'hybrid[specialized/128|level/128]@100%%+fusedfirst' (for profiling)")
+    ap.add_argument("--no-cpu-baseline", action="store_true",
+                    help="skip the host-oracle legs (cpu_baseline is then null; for profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    if args.plan is not None:
+        from paper_2605_31481_gb300.autotune import StepPlan
+        try:
+            StepPlan.parse_key(args.plan)
+        except ValueError as exc:
+            ap.error(str(exc))
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -21,6 +21,7 @@ from __future__ import annotations
 
 import json
 import os
+import re
 import threading
 
 import torch
@@ -212,17 +213,36 @@ class StepPlan:
     MODES = ("fused", "hybrid", "split", "pinned", "concurrent", "sequential")
     PIN_SHARES = (0.45, 0.55, 0.65)   # fractions of the SMs pinned to ABA
 
-    def __init__(self, model, B, links=None, use_cache=True, verbose=False, modes=MODES):
+    def __init__(self, model, B, links=None, use_cache=True, verbose=False, modes=MODES, fixed=None):
+        """fixed: run this one plan instead of searching, named as the keys of
+        describe()["us"] name plans (see parse_key); with the launch
+        configurations in brackets, nothing else is tuned either."""
         self.model = model
         self.links = list(links if links is not None else model.ee)
         api.set_smem_carveout(-1)
-        self.tuned = tune(model, B, FORWARD_KINDS + ("eval",), links=self.links, use_cache=use_cache,
-                          verbose=verbose)
+        fixed = self.parse_key(fixed) if fixed else None
+        if fixed and fixed[3] and fixed[0] not in ("concurrent", "sequential"):
+            self.tuned = {}                      # the plan names every launch it makes
+        else:
+            self.tuned = tune(model, B, FORWARD_KINDS + ("eval",), links=self.links, use_cache=use_cache,
+                              verbose=verbose)
         self._plain = [torch.cuda.Stream(device=model.device) for _ in FORWARD_KINDS]
         # the first stream forked (the longest operator) at the device's highest
         # priority (out-of-range values clamp to it), the others at the default
         self._ranked = [torch.cuda.Stream(device=model.device, priority=-1000 if k == 0 else 0)
                         for k in range(len(FORWARD_KINDS))]
+        if fixed:
+            mode, carveout, alt, ev = fixed
+            if ev is None:
+                ev = "|".join(f"{self.tuned[k]['variant']}/{self.tuned[k]['block']}" for k in ("eval", "aba"))
+            buf = Buffers(model, B, self.links)
+            api.set_smem_carveout(carveout)
+            self._set_eval(ev)
+            self._set_alt(mode, alt)
+            self.times = {(mode, carveout, alt, ev): graph_time_us(
+                lambda: self(buf.q, buf.qd, buf.qdd, buf.tau, buf.out))}
+            self._apply(mode, carveout, alt, ev)
+            return
         key = _key(model, "plan10", B)
         hit = _load_cache().get(key) if use_cache else None
         if hit:
@@ -271,6 +291,28 @@ class StepPlan:
             _store_cache({key: {"mode": self.mode, "carveout": self.carveout, "alt": self.alt,
                                 "eval": self.eval_config,
                                 "times": [[k, c, p, ev, round(v, 3)] for (k, c, p, ev), v in times.items()]}})
+
+    @classmethod
+    def parse_key(cls, key):
+        """A plan named as the keys of describe()["us"] name them:
+        "<mode>[<eval variant>/<block>|<aba variant>/<block>[@<ABA share>]]
+        [@<carveout>%][+fusedfirst | +prio]", the bracketed launch
+        configurations optional. Returns (mode, carveout or -1, the binary
+        option, the bracketed configuration or None)."""
+        m = re.fullmatch(r"([a-z]+)(?:\[([^\]]+)\])?(?:@(\d+)%)?(\+fusedfirst|\+prio)?", key)
+        if not m or m.group(1) not in cls.MODES:
+            raise ValueError(f"not a step plan: {key!r}")
+        mode, ev, carveout, opt = m.groups()
+        if opt and opt != ("+prio" if mode == "concurrent" else "+fusedfirst"):
+            raise ValueError(f"{opt} is not an option of the {mode} mode")
+        if opt and mode in ("fused", "sequential"):
+            raise ValueError(f"the {mode} mode has no option")
+        if ev is not None and (ev.count("|") != 1 or any(p.count("/") != 1 for p in ev.split("@")[0].split("|"))):
+            raise ValueError(f"launch configurations must read <variant>/<block>|<variant>/<block>: {ev!r}")
+        carveout = -1 if carveout is None else int(carveout)
+        if carveout > 100:
+            raise ValueError("carveout above 100 %")
+        return mode, carveout, opt is not None, ev
 
     def _set_eval(self, config):
         """config: "<eval variant>/<block>|<aba variant>/<block>[@<ABA share of
@@ -358,4 +400,4 @@ class StepPlan:
                        f"{('+prio' if k[0] == 'concurrent' else '+fusedfirst') if k[2] else ''}": round(v, 3)
                        for k, v in self.times.items()},
                 "kinds": kinds,
-                "eval_candidates_us": self.tuned["eval"]["candidates"]}
+                "eval_candidates_us": self.tuned.get("eval", {}).get("candidates", {})}

@@ -104,3 +104,58 @@ def test_fork_order_and_priority_options(fakes):
     assert plan.alt and not plan.prio and plan.streams == ["p"]
     plan._set_alt("fused", False)
     assert not plan.alt and not plan.prio
+
+
+def test_every_described_plan_parses_back_to_its_measurement(fakes):
+    model = FakeModel()
+    orig_init = autotune.StepPlan.__init__
+
+    def init(self, *a, **k):
+        fakes["current"]["plan"] = self
+        orig_init(self, *a, **k)
+
+    autotune.StepPlan.__init__ = init
+    try:
+        plan = autotune.StepPlan(model, 4096, use_cache=False)
+        names = plan.describe()["us"]
+        assert len(names) == len(plan.times)
+        for name, us in names.items():
+            mode, carveout, alt, ev = autotune.StepPlan.parse_key(name)
+            if ev is None:                       # modes whose launches the per-kind tuning sets
+                ev = next(e for (m, c, a, e) in plan.times if (m, c, a) == (mode, carveout, alt))
+            assert round(plan.times[(mode, carveout, alt, ev)], 3) == us
+    finally:
+        autotune.StepPlan.__init__ = orig_init
+
+
+def test_fixed_plan_runs_without_tuning_or_search(fakes, monkeypatch):
+    def no_tune(*a, **k):
+        raise AssertionError("a fixed plan with its launch configurations tunes nothing")
+
+    monkeypatch.setattr(autotune, "tune", no_tune)
+    model = FakeModel()
+    orig_init = autotune.StepPlan.__init__
+
+    def init(self, *a, **k):
+        fakes["current"]["plan"] = self
+        orig_init(self, *a, **k)
+
+    autotune.StepPlan.__init__ = init
+    try:
+        plan = autotune.StepPlan(model, 4096, fixed="hybrid[specialized/128|level/128]@100%+fusedfirst")
+        assert len(fakes["calls"]) == 1
+        assert (plan.mode, plan.carveout, plan.alt) == ("hybrid", 100, True)
+        assert model.launch == {"eval": ("specialized", 128), "aba": ("level", 128)}
+        assert fakes["carve"][-1] == 100 and plan.expected_us == 14.5
+        d = plan.describe()
+        assert d["kinds"] == {"eval": "specialized/128", "aba": "level/128"} and d["eval_candidates_us"] == {}
+        assert list(d["us"]) == ["hybrid[specialized/128|level/128]@100%+fusedfirst"]
+    finally:
+        autotune.StepPlan.__init__ = orig_init
+
+
+@pytest.mark.parametrize("bad", ["hybrid+prio", "fused+fusedfirst", "hybrid[specialized/128]", "warp",
+                                 "concurrent@101%"])
+def test_fixed_plan_names_are_checked(bad):
+    with pytest.raises(ValueError):
+        autotune.StepPlan.parse_key(bad)
