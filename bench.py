@@ -162,6 +162,29 @@ class ClockSampler:
 # GPU arm
 # ---------------------------------------------------------------------------
 
+def plan_kernel_name(mode, desc):
+    """What the timed step launches under a step plan, from the plan's
+    describe() (launch configurations of the kinds it sets)."""
+    kinds, carveout = desc["kinds"], desc["carveout"]
+    if mode == "fused":
+        return f"fused eval kernel ({kinds['eval']})"
+    if mode == "hybrid":
+        return (f"ABA kernel ({kinds['aba']}) on a parallel graph branch beside the fused kernel of the other four "
+                f"({kinds['eval']}), carveout {carveout}" + (", fused kernel forked first" if desc["fused_forked_first"] else ""))
+    if mode == "concurrent":
+        return ("5 per-operator kernels on parallel graph branches (" +
+                ", ".join(f"{k} {kinds.get(k, 'default')}" for k in OPS) + f"), carveout {carveout}" +
+                (", longest operator on a high-priority stream" if desc["priorities"] else ""))
+    if mode == "split":
+        return (f"ABA kernel ({kinds['aba']}) beside two launches of the fused kernel ({kinds['eval']}: FK with the "
+                f"Jacobians; RNEA with CRBA) on parallel graph branches, carveout {carveout}" +
+                (", fused kernels forked first" if desc["fused_forked_first"] else ""))
+    if mode == "pinned":
+        return (f"SM-pinned: ABA kernel ({kinds['aba']}) on its share of the SMs beside the fused kernel of the other "
+                f"four ({kinds['eval']}) on the rest, carveout {carveout}")
+    return "5 per-operator kernels in sequence"
+
+
 def job_rate(ms, world, envs_per_rank, steps, device):
     """Whole-job throughput of `world` replicas: the slowest rank's time (the
     maximum over ranks of `ms`, in milliseconds, for `steps` steps of
@@ -327,19 +350,7 @@ def run_fst(args):
     t_k = kernel_ms / 1e3
     bound = "alu" if fl / (p_alu * 1e12) > by / (pk["hbm_gbs"] * 1e9) else "hbm"
     desc = plan.describe()
-    kname = {"fused": f"fused eval kernel ({desc['kinds']['eval']})",
-             "hybrid": f"ABA kernel ({desc['kinds']['aba']}) on a parallel graph branch beside the fused kernel of "
-                       f"the other four ({desc['kinds']['eval']}), carveout {plan.carveout}" +
-                       (", fused kernel forked first" if plan.alt else ""),
-             "concurrent": "5 per-operator kernels on parallel graph branches (" +
-                           ", ".join(f"{k} {desc['kinds'][k]}" for k in OPS) + f"), carveout {plan.carveout}" +
-                           (", longest operator on a high-priority stream" if plan.prio else ""),
-             "split": f"ABA kernel ({desc['kinds']['aba']}) beside two launches of the fused kernel "
-                      f"({desc['kinds']['eval']}: FK with the Jacobians; RNEA with CRBA) on parallel graph branches, "
-                      f"carveout {plan.carveout}",
-             "pinned": f"SM-pinned: ABA kernel ({desc['kinds']['aba']}) on its share of the SMs beside the fused "
-                       f"kernel of the other four ({desc['kinds']['eval']}) on the rest, carveout {plan.carveout}",
-             "sequential": "5 per-operator kernels in sequence"}[plan.mode]
+    kname = plan_kernel_name(plan.mode, desc)
     traffic = args.traffic
     if traffic is None:
         traffic = NCU_TRAFFIC.get((plan.mode, desc["kinds"]["aba"], desc["kinds"]["eval"], kernel_source_hash()))

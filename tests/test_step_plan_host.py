@@ -159,3 +159,31 @@ def test_fixed_plan_runs_without_tuning_or_search(fakes, monkeypatch):
 def test_fixed_plan_names_are_checked(bad):
     with pytest.raises(ValueError):
         autotune.StepPlan.parse_key(bad)
+
+
+@pytest.mark.parametrize("name", ["hybrid[specialized/128|level/128]@100%+fusedfirst", "fused[specialized/128|level/256]",
+                                  "split[specialized/128|level/256]+fusedfirst", "concurrent@100%+prio", "sequential",
+                                  "pinned[pinned/128|pinned/256@0.45]@100%"])
+def test_bench_describes_a_fixed_plan(fakes, name):
+    """bench.py's report of the timed step works from a named plan's
+    describe(), with or without the per-kind tuning."""
+    import bench
+    model = FakeModel()
+    orig_init = autotune.StepPlan.__init__
+
+    def init(self, *a, **k):
+        fakes["current"]["plan"] = self
+        orig_init(self, *a, **k)
+
+    autotune.StepPlan.__init__ = init
+    try:
+        plan = autotune.StepPlan(model, 4096, fixed=name)
+        desc = plan.describe()
+        text = bench.plan_kernel_name(plan.mode, desc)
+        assert text and (plan.mode in ("concurrent", "sequential") or desc["kinds"]["eval"] in text)
+        assert plan.mode in ("fused", "concurrent", "sequential") or desc["kinds"]["aba"] in text
+        key = (plan.mode, desc["kinds"]["aba"], desc["kinds"]["eval"], bench.kernel_source_hash())
+        assert bench.NCU_TRAFFIC.get(key) is None or plan.mode == "hybrid"
+        json.dumps(desc)
+    finally:
+        autotune.StepPlan.__init__ = orig_init
