@@ -39,3 +39,23 @@ def test_pin_roles_proportions():
         assert abs(frac - share) <= 0.05
         others = [roles.count(r) for r in ("kin", "rnea", "crba")]
         assert max(others) - min(others) <= 256 // 20 + 1       # the three roles evenly
+
+
+def test_algorithmic_bytes_per_environment():
+    """FP32 inputs and outputs per environment of each operator: FK
+    4(nq + 12 n_b), Jacobian 4(nq + 6 nv k), RNEA and ABA 4(nq + 3 nv), CRBA
+    4(nq + nv^2), at the three benchmark trees (7-DOF chain with one
+    end-effector, 11-DOF quadruped with four feet, floating humanoid with
+    nq = 30, nv = 29 and 24 bodies)."""
+    from paper_2605_31481_gb300 import costs, workloads as w
+    chain, quad, hum = w.chain(7), w.spined_quadruped(), w.humanoid()
+    assert (hum.nq, hum.nv, hum.n_bodies) == (30, 29, 24)
+    expect = {"fk": (364, 572, 1272), "rnea": (112, 176, 468), "aba": (112, 176, 468), "crba": (224, 528, 3484)}
+    for op, values in expect.items():
+        assert tuple(costs.io_bytes(t, op) for t in (chain, quad, hum)) == values, op
+    assert costs.io_bytes(chain, "jacobian", 1) == 196 and costs.io_bytes(quad, "jacobian", 4) == 1100
+    # the timed step (FK + 4 foot Jacobians + RNEA + CRBA + ABA on the
+    # quadruped) reads q, qd, qdd and tau once: the operators' sum less the
+    # four extra reads of q and the second read of qd, 2332 B
+    ops = sum(costs.io_bytes(quad, op, 4) for op in ("fk", "jacobian", "rnea", "crba", "aba"))
+    assert ops - 4 * (4 * quad.nq + quad.nv) == 2332
