@@ -12,14 +12,15 @@ Per-primitive counts (f3 = 3-vector, SV = spatial 6-vector):
   X*m (motion to child) 42, X^T f (force to parent) 42, crm/crf 30,
   I*m (10-parameter inertia) 42, rigid inertia to parent 140,
   6x6 symmetric times SV 66, rank-1 downdate 48, symmetric 6x6 to parent 333,
+  6x6 Cholesky solve 169,
   revolute joint transform (paper Eq. 4-5) 53 + one sincos,
-  prismatic 6, free joint 111.
+  prismatic 6, free joint 114 (unit quaternion to R: 51).
 """
 from __future__ import annotations
 
 FIXED, REVOLUTE, PRISMATIC, FREE = 0, 1, 2, 3
 
-JX = {FIXED: 0, REVOLUTE: 53, PRISMATIC: 6, FREE: 111}
+JX = {FIXED: 0, REVOLUTE: 53, PRISMATIC: 6, FREE: 114}
 NV = {FIXED: 0, REVOLUTE: 1, PRISMATIC: 1, FREE: 6}
 
 
@@ -60,29 +61,36 @@ def flops(tree, op, links=()):
     if op == "rnea":
         for i in range(nb):
             dof = NV[jt[i]] > 0
-            total += JX[jt[i]] + (12 if dof else 0)
+            total += JX[jt[i]] + (12 if NV[jt[i]] == 1 else 0)   # S qd, S qdd (a free joint's is a copy)
             total += 42 + 6 if par[i] < 0 else 84 + 18 + 30
             total += 84 + 30 + 6
-            total += (11 if dof else 0) + (48 if par[i] >= 0 else 0)
+            total += (11 if NV[jt[i]] == 1 else 0) + (48 if par[i] >= 0 else 0)
         return total
     if op == "crba":
         for i in range(nb):
             total += JX[jt[i]] + (150 if par[i] >= 0 else 0)
             if NV[jt[i]] == 1:
-                total += 53 + 53 * (len(_path(tree, i)) - 1)
+                # F = I^c S and its projection, then one force transform per
+                # ancestor, projected where the ancestor has a 1-DOF joint
+                total += 53 + sum(42 + (11 if NV[jt[k]] == 1 else 0) for k in _path(tree, i)[1:])
         return total
     if op == "aba":
         for i in range(nb):
             root = par[i] < 0
             dof1 = NV[jt[i]] == 1
-            total += JX[jt[i]] + (6 if NV[jt[i]] else 0) + (0 if root else 42 + 6 + 30) + 72
+            # pass 1: velocity, bias acceleration, bias force
+            total += JX[jt[i]] + (6 if dof1 else 0) + (0 if root else 42 + 6 + 30) + 72
+            # pass 2: U, D, u, then the articulated inertia and bias force to the parent
             if dof1:
                 total += 90 + (0 if root else 48 + 85 + 333 + 21 + 48)
-                total += 73
             elif jt[i] == FIXED and not root:
                 total += 66 + 6 + 333 + 21 + 48
+            # pass 3: the acceleration, then qdd (1-DOF) or the 6x6 solve (free root)
+            total += 48
+            if dof1:
+                total += 25
             elif jt[i] == FREE:
-                total += 230 + 12
+                total += 169 + 12
         return total
     raise ValueError(op)
 
