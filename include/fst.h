@@ -7,8 +7,9 @@
  * Rigid Body Dynamics in PyTorch for GPU-Accelerated Robot Learning":
  * forward kinematics (Sec. 3.1 tier 3), the geometric Jacobian (Sec. 3.4,
  * Eq. 6), RNEA (Sec. 3.3, Eq. 7), CRBA and ABA (Sec. 3.5, Sec. 4.1), plus
- * hand-written adjoints of FK, RNEA and ABA (the paper differentiates by
- * autograd, Sec. 3.5 and Sec. 4.3).
+ * hand-written adjoints of FK, the Jacobian, RNEA, CRBA and ABA (the paper
+ * differentiates by autograd, Sec. 3.5 and Sec. 4.3), dense derivatives of
+ * inverse and forward dynamics, and a persistent launch over several trees.
  *
  * Conventions shared by every entry point
  * ---------------------------------------
@@ -60,7 +61,7 @@ typedef enum {
   FST_ERR_UNSUPPORTED = -4,  /* joint type or model size this build does not handle */
   FST_ERR_CUDA = -5,         /* a CUDA runtime call or kernel launch failed */
   FST_ERR_NO_MEMORY = -6,    /* device allocation at model creation failed */
-  FST_ERR_DEVICE_CHECK = -7  /* a device-side check recorded a failure */
+  FST_ERR_DEVICE_CHECK = -7  /* reserved: no entry point returns it (every check runs on the host) */
 } fst_status;
 
 enum {
