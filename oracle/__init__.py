@@ -1,8 +1,8 @@
 """FP64 CPU oracle for batched rigid-body dynamics.
 
 TEST INFRASTRUCTURE ONLY. Only the tests, the smoke check in
-`__graft_entry__.smoke()` and the CPU-baseline leg of `bench.py` may import
-this package. The product (the CUDA library and its Python binding) never
+`__graft_entry__.smoke()`, and the CPU-baseline leg and the reference arm
+(`--impl reference`) of `bench.py` may import this package. The product (the CUDA library and its Python binding) never
 calls it, and it shares no code with the product.
 
 What it computes, and where the definitions come from:
@@ -21,7 +21,10 @@ What it computes, and where the definitions come from:
                   Sec. 4.1; Featherstone 2008 Table 7.1).
 * `derivs`        exact derivatives by the complex-step method and the
                   inertial-parameter regressor (the paper differentiates with
-                  autograd, Sec. 3.5 and Sec. 4.3).
+                  autograd, Sec. 3.5 and Sec. 4.3); the dense derivatives
+                  d tau / d q, d tau / d qd, d qdd / d q, d qdd / d qd and
+                  M^-1 along the configuration's tangent space; the
+                  reference cotangents of the Jacobian and of CRBA.
 * `lagrange`      an independent route to M(q), C(q, qd) qd and g(q) from the
                   Lagrangian of the bodies, used only to pin the recursions.
 
