@@ -149,3 +149,26 @@ def test_integrate_first_order_matches_exact_motion():
     np.testing.assert_allclose(num[:, 3:7], (plus - minus) / (2 * h), atol=1e-7)
     np.testing.assert_allclose(num[:, 0:3], R.apply(dv[:, 0:3]), atol=1e-7)
     np.testing.assert_allclose(num[:, 7:], dv[:, 6:], atol=1e-7)
+
+
+@pytest.mark.parametrize("make", [lambda: w.spined_quadruped(seed=0), lambda: w.humanoid(seed=0)],
+                         ids=["quadruped11", "humanoid29"])
+def test_forward_dynamics_derivatives_match_central_differences(make):
+    """d qdd / d q along the tangent directions (a free base moved by scipy's
+    exact rotations), d qdd / d qd and d qdd / d tau against central
+    differences of ABA itself."""
+    tree = make()
+    s = w.random_state(tree, 4, seed=8)
+    dq, dqd, dtau = derivs.aba_derivatives(tree, s["q"], s["qd"], s["tau"])
+    f = lambda q_: rbd.aba(tree, q_, s["qd"], s["tau"])
+    for j in range(tree.nv):
+        fd = _fd_along(tree, f, s["q"], j)
+        assert np.abs(dq[..., j] - fd).max() <= 1e-6 * max(np.abs(fd).max(), 1.0), j
+    for name, got in (("qd", dqd), ("tau", dtau)):
+        for j in range(tree.nv):
+            e = np.zeros_like(s[name])
+            e[:, j] = 1e-6
+            lo, hi = dict(s), dict(s)
+            lo[name], hi[name] = s[name] - e, s[name] + e
+            fd = (rbd.aba(tree, hi["q"], hi["qd"], hi["tau"]) - rbd.aba(tree, lo["q"], lo["qd"], lo["tau"])) / 2e-6
+            assert np.abs(got[..., j] - fd).max() <= 1e-6 * max(np.abs(fd).max(), 1.0), (name, j)
