@@ -20,9 +20,9 @@
  * - `stream` is a cudaStream_t (NULL = the legacy default stream). Calls are
  *   asynchronous on it; none allocates, frees or synchronises, so every
  *   compute call can be captured into a CUDA graph.
- * - B = 0 is valid and does nothing. B < 0, null pointers with B > 0, or a
- *   call from a device other than the model's return FST_ERR_INVALID_ARG
- *   without launching anything.
+ * - B = 0 is valid and does nothing. B < 0, B > 2^31 - 1, null pointers
+ *   with B > 0, or a call from a device other than the model's return
+ *   FST_ERR_INVALID_ARG without launching anything.
  * - A failed kernel launch returns FST_ERR_CUDA. Nothing traps on the
  *   device. NaN/Inf inputs give NaN/Inf outputs for that environment only.
  * - On any status other than FST_OK, fst_last_error() gives a message

@@ -2,6 +2,7 @@
 #include <cuda_runtime.h>
 
 #include <atomic>
+#include <climits>
 #include <cstring>
 #include <initializer_list>
 #include <new>
@@ -48,7 +49,11 @@ fst_status check_call(const char* fn, const fst_model* m, int64_t B, bool* skip)
     *skip = true;
     return FST_OK;
   }
-  if (B > (int64_t)1 << 40) return set_error(FST_ERR_INVALID_ARG, std::string(fn) + ": B too large");
+  // grids are sized B / (environments per block) and must stay within the
+  // 2^31 - 1 limit of gridDim.x for every launch form (at least 4
+  // environments per block)
+  if (B > (int64_t)INT32_MAX)
+    return set_error(FST_ERR_INVALID_ARG, std::string(fn) + ": B must be at most 2^31 - 1 per call");
   int dev = -1;
   cudaError_t err = cudaGetDevice(&dev);
   if (err != cudaSuccess) return cuda_error(fn, err);
@@ -813,7 +818,8 @@ fst_status fst_multi_eval(fst_multi* g, const fst_multi_io* io, void* stream) {
   for (int k = 0; k < n; ++k) {
     const fst_model* m = g->models[k];
     const fst_multi_io& x = io[k];
-    if (x.B < 0) return set_error(FST_ERR_INVALID_ARG, std::string(fn) + ": B must be >= 0");
+    if (x.B < 0 || x.B > (int64_t)INT32_MAX)
+      return set_error(FST_ERR_INVALID_ARG, std::string(fn) + ": B must be in [0, 2^31 - 1]");
     if (x.B > 0 && m->nq && !x.q) return set_error(FST_ERR_INVALID_ARG, std::string(fn) + ": null q");
     if (x.B > 0 && x.tau_out && (!x.qd || !x.qdd)) return set_error(FST_ERR_INVALID_ARG, std::string(fn) + ": RNEA needs qd and qdd");
     if (x.B > 0 && x.qdd_out && (!x.qd || !x.tau)) return set_error(FST_ERR_INVALID_ARG, std::string(fn) + ": ABA needs qd and tau");
@@ -830,7 +836,11 @@ fst_status fst_multi_eval(fst_multi* g, const fst_multi_io* io, void* stream) {
   for (int i = 1; i < n; ++i)
     for (int j = i; j > 0 && g->models[order[j]]->n > g->models[order[j - 1]]->n; --j) std::swap(order[j], order[j - 1]);
   const int T = g->block;
-  int seg = 0, items = 0;
+  // every block of the persistent grid draws one item past the last, so the
+  // int work counter reaches n_items + grid: keep ample headroom below 2^31
+  const int64_t kMaxItems = (int64_t)INT32_MAX - (1 << 24);
+  int seg = 0;
+  int64_t items = 0;
   const int roles[4] = {ROLE_ABA, ROLE_CRBA, ROLE_RNEA, ROLE_KIN};
   for (int r : roles)
     for (int k : order) {
@@ -839,14 +849,16 @@ fst_status fst_multi_eval(fst_multi* g, const fst_multi_io* io, void* stream) {
                        : r == ROLE_CRBA ? (const void*)x.M
                        : r == ROLE_RNEA ? (const void*)x.tau_out : (const void*)x.poses;
       if (!outp || x.B == 0) continue;
-      a.seg_start[seg] = items;
+      a.seg_start[seg] = (int)items;  // within kMaxItems: checked below on every addition
       a.seg_model[seg] = (unsigned char)k;
       a.seg_op[seg] = (unsigned char)r;
-      items += (int)((x.B + T - 1) / T);
+      items += (x.B + T - 1) / T;
+      if (items > kMaxItems)
+        return set_error(FST_ERR_INVALID_ARG, std::string(fn) + ": too many work items (environments x operators)");
       ++seg;
     }
-  a.seg_start[seg] = items;
-  a.n_items = items;
+  a.seg_start[seg] = (int)items;
+  a.n_items = (int)items;
   a.model_bytes = (size_t)max_n * (sizeof(BodyC) + sizeof(BodyI)) + (sizeof(TopoLists) + 15) / 16 * 16;
   a.model_bytes = (a.model_bytes + 15) / 16 * 16;
   if (items == 0) return FST_OK;

@@ -113,3 +113,16 @@ def test_valid_table_without_gpu_reports_cuda_error(lib):
         pytest.skip("a GPU is present")
     st, msg = _create(lib, w.spined_quadruped())
     assert st == -5 and "fst_model_create" in msg
+
+
+def test_batch_size_bounds_are_checked_before_the_model_is_used(lib):
+    """B < 0 and B > 2^31 - 1 are refused and B = 0 does nothing, all before
+    the call reads the model, its device or any array (so an opaque stand-in
+    handle suffices here)."""
+    stand_in = ctypes.create_string_buffer(4096)
+    h = ctypes.cast(stand_in, ctypes.c_void_p)
+    for B in (-1, 2**31, 2**40):
+        assert lib.fst_fk(h, ctypes.c_int64(B), None, None, None) == -1
+        assert "B must" in lib.fst_last_error().decode()
+        assert lib.fst_rnea(h, ctypes.c_int64(B), None, None, None, None, None, None) == -1
+    assert lib.fst_fk(h, ctypes.c_int64(0), None, None, None) == 0
