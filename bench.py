@@ -390,7 +390,8 @@ def run_fst(args):
             "config": {"workload": f"{tree.name}: 11 revolute DOF branched tree, depth 5, B=4096 per GPU",
                        "B": B, "step": "+".join(OPS) + " (4 foot Jacobians)",
                        "l2": f"inputs/outputs rotate over {R} sets of {set_bytes / 2**20:.1f} MiB (> 2x L2)",
-                       "parallelism": f"replicas x{world}"},
+                       "parallelism": f"replicas x{world}",
+                       "seeds": {"model": 0, "inputs": "1 + 1000 x rank"}},
             "per_op_ms": {k: round(v, 5) for k, v in per_op_ms.items()},
             "per_op_hot_ms": {k: round(v, 5) for k, v in per_op_hot_ms.items()},
             "per_op_env_evals_per_s": {k: round(B / (v / 1e3), 1) for k, v in per_op_ms.items()},
