@@ -1,21 +1,28 @@
-"""Autotuner for the launch configuration of the kernels.
+"""Autotuner for the launch configuration of the kernels, and the step planner.
 
-For one model and batch size it measures, on the current GPU, every
-candidate configuration of each kernel kind — the environment-to-thread
-mapping and kernel variant (one environment per thread with the tree in
-shared memory, one environment per thread with a kernel specialised for the
-tree, or level-parallel: 32 environments per block with the block's warps
-splitting each tree level) and the block size (32 to 256 threads) — and keeps
-the fastest via fst_model_set_launch. For a multi-operator step it also
-decides between the fused launch (fst_eval, operators side by side) and the
-operators one after another: fusing pays at small B, where one operator
-leaves most SMs idle, and costs at large B, where one register allocation
-for all operators lowers occupancy.
+`tune(model, B)` measures, on the current GPU, every candidate configuration
+of each kernel kind and keeps the fastest via fst_model_set_launch. A
+candidate is an environment-to-thread mapping with a block size (32 to 256
+threads):
+  generic      one environment per thread, the tree from shared memory;
+  specialized  one environment per thread, a kernel compiled for the tree;
+  level        32 environments per block, the block's warps splitting each
+               tree level;
+  mixed        (eval) the specialised fused kernel with each role mapped as
+               its own operator is set;
+  path         a lane per root-to-leaf path (trees with at most 8 leaves);
+  pathwarp     a warp per root-to-leaf path (block size fixed by the tree).
+
+`StepPlan(model, B)` then decides how a step of the five forward operators
+runs: one fused launch, ABA beside a fused launch of the other four (the
+fused part whole or split in two, or both pinned to disjoint SM sets), every
+operator on its own stream, or one after another; each at two
+shared-memory carveouts and with its fork-order or stream-priority option.
 
 Timings replay a CUDA graph of repeated launches, so host launch overhead is
 excluded. Choices are cached in a JSON file (FST_TUNE_CACHE, default
-~/.cache/fst_tune.json) keyed by the tree's fingerprint, the kind, B and the
-GPU name.
+~/.cache/fst_tune.json) keyed by the tree's fingerprint, the kind, B, the
+GPU name and the library version.
 """
 from __future__ import annotations
 
