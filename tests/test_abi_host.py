@@ -126,3 +126,27 @@ def test_batch_size_bounds_are_checked_before_the_model_is_used(lib):
         assert "B must" in lib.fst_last_error().decode()
         assert lib.fst_rnea(h, ctypes.c_int64(B), None, None, None, None, None, None) == -1
     assert lib.fst_fk(h, ctypes.c_int64(0), None, None, None) == 0
+
+
+def test_plain_c_caller_compiles_links_and_reports_status(lib, tmp_path):
+    """include/fst.h serves a C program (ISO C11, warnings as errors); run
+    without a GPU, the example stops at model creation with FST_ERR_CUDA and
+    the library's message."""
+    import shutil
+    import subprocess
+    import torch
+    cuda = os.environ.get("CUDA_HOME", "/usr/local/cuda")
+    if shutil.which("gcc") is None or not os.path.isdir(os.path.join(cuda, "include")):
+        pytest.skip("needs gcc and the CUDA headers")
+    pkg = os.path.dirname(_ffi.LIB_PATH)
+    exe = str(tmp_path / "abi_example")
+    r = subprocess.run(["gcc", "-std=c11", "-Wall", "-Wextra", "-Werror", "-pedantic",
+                        f"-I{os.path.join(ROOT, 'include')}", f"-I{cuda}/include",
+                        os.path.join(ROOT, "tests", "host", "abi_example.c"), f"-L{pkg}", "-lfst",
+                        f"-L{cuda}/lib64", "-lcudart", f"-Wl,-rpath,{pkg}", "-o", exe],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr[-3000:]
+    if torch.cuda.is_available():
+        return                                     # the GPU run belongs to the parity tests
+    r = subprocess.run([exe], capture_output=True, text=True, timeout=60)
+    assert r.returncode == 1 and "fst_model_create" in r.stderr and "(-5)" in r.stderr
