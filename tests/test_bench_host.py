@@ -59,3 +59,14 @@ def test_algorithmic_bytes_per_environment():
     # four extra reads of q and the second read of qd, 2332 B
     ops = sum(costs.io_bytes(quad, op, 4) for op in ("fk", "jacobian", "rnea", "crba", "aba"))
     assert ops - 4 * (4 * quad.nq + quad.nv) == 2332
+
+
+def test_reference_arm_other_ranks_exit_quietly():
+    """Under torchrun only rank 0 times the reference arm and prints; the
+    other ranks exit 0 without work or output."""
+    env = dict(os.environ, RANK="1", WORLD_SIZE="2", LOCAL_RANK="1")
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--gpus", "2",
+                        "--steps", "10", "--warmup", "3"], capture_output=True, text=True, timeout=120, cwd=ROOT,
+                       env=env)
+    assert r.returncode == 0, r.stderr[-2000:]
+    assert r.stdout.strip() == ""
