@@ -87,6 +87,52 @@ def fp32_peak_tflops(sm_mhz):
     return N_SM * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
 
 
+def roof_of(bytes_, flops_, seconds, p_alu_tflops, hbm_gbs):
+    """Roofline position of one launch (or step): algorithmic bytes and
+    flops, their rates and the fraction of each ceiling; `bound` is the
+    ceiling the algorithmic cost hits first (the larger time), `frac` the
+    fraction of that one."""
+    t_hbm, t_alu = bytes_ / (hbm_gbs * 1e9), flops_ / (p_alu_tflops * 1e12)
+    hf, af = t_hbm / seconds, t_alu / seconds
+    return {"bytes": int(bytes_), "flops": int(flops_), "us": round(seconds * 1e6, 3),
+            "gbs": round(bytes_ / seconds / 1e9, 1), "tflops": round(flops_ / seconds / 1e12, 3),
+            "hbm_frac": round(hf, 4), "alu_frac": round(af, 4), "bound": "hbm" if t_hbm >= t_alu else "alu",
+            "frac": round(max(hf, af), 4)}
+
+
+def measure_fp32_peak(torch, gpu_index, launches=12, iters=1 << 19):
+    """FP32 FMA throughput of this GPU, measured: the library's FMA probe
+    (fst_fp32_probe: 4 blocks of 256 threads per SM, 16 independent chains
+    per thread) launched back to back for about half a second, each launch
+    timed with CUDA events on the launching stream, with nvidia-smi clocks
+    sampled over the same interval. Returns the best launch's TFLOP/s (a
+    burst figure, like the measured copy bandwidth), the median, and the
+    clocks seen."""
+    from paper_2605_31481_gb300 import api
+    fl, buf = api.fp32_probe(4, 1 << 10)          # first launch: module load, not timed
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    clk = ClockSampler(gpu_index)
+    clk.start()
+    time.sleep(0.15)
+    clk.mark("soak")
+    clk.mark("t0")
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(launches + 1)]
+    ev[0].record(stream)
+    for k in range(launches):
+        fl, buf = api.fp32_probe(4, iters, out=buf)
+        ev[k + 1].record(stream)
+    torch.cuda.synchronize()
+    clk.mark("t1")
+    clocks = clk.stop()
+    tf = [fl / (ev[k].elapsed_time(ev[k + 1]) / 1e3) / 1e12 for k in range(launches)]
+    return {"tflops": round(max(tf), 2), "tflops_median": round(statistics.median(tf), 2),
+            "launch_ms": round(ev[0].elapsed_time(ev[-1]) / launches, 3), "clocks": clocks,
+            "derived_at_max_clock": round(fp32_peak_tflops(2070.0), 2),
+            "how": "fst_fp32_probe: SMs x 4 blocks x 256 threads x 16 FMA chains, best of "
+                   f"{launches} launches of {iters} iterations (CUDA events)"}
+
+
 def workload():
     from paper_2605_31481_gb300 import workloads as w
     tree = w.spined_quadruped(seed=0)
@@ -289,9 +335,9 @@ def run_fst(args):
 
     K = args.steps
     # The timed loop replays CUDA graphs: one graph of R steps (one per
-    # rotating input/output set) n times, then single-step graphs for the
-    # remaining K mod R steps, so exactly K steps run with no host launch
-    # overhead between them.
+    # rotating input/output set) K // R times, then one graph of the
+    # remaining K mod R steps, so exactly K steps run back to back with no
+    # host launch gap between them whatever K is.
     def capture(ks):
         g = torch.cuda.CUDAGraph()
         with torch.cuda.graph(g):
@@ -300,9 +346,11 @@ def run_fst(args):
         return g
 
     g_all = capture(range(R))
-    g_one = [capture([k]) for k in range(K % R)]
+    g_rem = capture(range(K % R)) if K % R else None
     for _ in range(3):
         g_all.replay()
+        if g_rem is not None:      # the first replay of a graph uploads it: keep that out of the timed region
+            g_rem.replay()
     torch.cuda.synchronize()
     clk = ClockSampler(local)
     clk.start()
@@ -323,8 +371,8 @@ def run_fst(args):
     t_start.record(stream)
     for _ in range(K // R):
         g_all.replay()
-    for g in g_one:
-        g.replay()
+    if g_rem is not None:
+        g_rem.replay()
     t_end.record(stream)
     torch.cuda.synchronize()
     clk.mark("t1")
@@ -344,7 +392,8 @@ def run_fst(args):
     e2e["ms"], e2e_value = job_rate(e2e["ms"], world, B, e2e["steps"], dev)
 
     pk = peaks()
-    p_alu = fp32_peak_tflops(pk["sm_max_mhz"])
+    fp32 = measure_fp32_peak(torch, local)
+    p_alu = fp32["tflops"]
     fl = sum(costs.flops(tree, op, links=links if op == "jacobian" else ()) for op in OPS)
     by = 4 * (in_floats + out_floats)
     t_k = kernel_ms / 1e3
@@ -359,7 +408,8 @@ def run_fst(args):
               "kernel_ms": round(kernel_ms, 5),
               "alu_frac": round(fl * B / t_k / 1e12 / p_alu, 5),
               "hbm_frac": round(by * B / t_k / 1e9 / pk["hbm_gbs"], 5),
-              "alu_peak_src": f"derived: 152 SMs x 128 FP32 lanes x 2 x {pk['sm_max_mhz']:.0f} MHz = {p_alu:.1f} TFLOP/s",
+              "alu_peak_src": f"measured: FP32 FMA probe {p_alu:.1f} TFLOP/s (burst) at SM clock "
+                              f"{fp32['clocks'].get('sm_mhz')} MHz",
               "hbm_peak_src": f"{pk['src']} copy bandwidth {pk['hbm_gbs']} GB/s"}
     if bound == "alu":
         achieved = fl * B / t_k / 1e12
@@ -374,7 +424,8 @@ def run_fst(args):
     if rank == 0 and not args.no_extras:
         extras["rnea_fwd_bwd"] = rnea_fwd_bwd(torch, fst, w)
         extras["rl_step_graph"] = rl_step(torch, fst, w)
-        extras["humanoid_sweep"] = humanoid_sweep(torch, fst, w)
+        extras["humanoid_sweep"] = humanoid_sweep(torch, fst, w, p_alu, pk["hbm_gbs"])
+        extras["chain7_b1024"] = chain7_small(torch, fst, w, p_alu, pk["hbm_gbs"])
         extras["multi_tree"] = multi_tree(torch, fst, w)
         extras["sysid"] = sysid(torch, fst, w)
     if rank == 0:
@@ -395,6 +446,10 @@ def run_fst(args):
             "per_op_ms": {k: round(v, 5) for k, v in per_op_ms.items()},
             "per_op_hot_ms": {k: round(v, 5) for k, v in per_op_hot_ms.items()},
             "per_op_env_evals_per_s": {k: round(B / (v / 1e3), 1) for k, v in per_op_ms.items()},
+            "per_op_roofline": {k: roof_of(B * costs.io_bytes(tree, k, len(links)),
+                                           B * costs.flops(tree, k, links=links if k == "jacobian" else ()),
+                                           v / 1e3, p_alu, pk["hbm_gbs"]) for k, v in per_op_ms.items()},
+            "fp32_peak": fp32,
             "roofline": roof,
             "e2e": {"value": round(e2e_value, 1), "unit": "env-evals/s", "h2d_bytes_per_step": e2e["h2d"],
                     "d2h_bytes_per_step": e2e["d2h"], "steps": e2e["steps"],
@@ -467,12 +522,15 @@ def rnea_fwd_bwd(torch, fst, w):
 def rl_step(torch, fst, w, steps=1000):
     """One RL-style controller step on the 11-DOF tree, B = 4096: FK, the four
     foot Jacobians, RNEA and the RNEA adjoint (cotangent tau), run eagerly
-    through the binding and replayed from one captured CUDA graph."""
+    through the binding as four launches and replayed from one captured CUDA
+    graph; then the same step as ONE fused launch (fst_eval with the RNEA
+    adjoint), with the kinematics in blocks of their own beside the
+    RNEA+adjoint blocks, and with everything fed by one forward sweep."""
     tree = w.spined_quadruped(seed=0)
     B = 4096
     m = fst.Model(tree)
     try:
-        m.specialize(["fk", "jacobian", "rnea", "rnea_vjp"])
+        m.specialize(["fk", "jacobian", "rnea", "rnea_vjp", "eval"])
     except Exception:
         pass
     from paper_2605_31481_gb300 import autotune
@@ -512,14 +570,72 @@ def rl_step(torch, fst, w, steps=1000):
     b.record()
     torch.cuda.synchronize()
     graph = a.elapsed_time(b) * 1e3 / steps
+    qb, qdb = torch.empty(tree.nq, B, device="cuda"), torch.empty(tree.nv, B, device="cuda")
+    fused = {}
+    for one_sweep in (False, True):
+        fo = {"poses": poses, "J": J, "tau": tau, "q_bar": qb, "qd_bar": qdb}
+
+        def fstep():
+            fst.api.eval(m, q, qd, qdd, fk=True, links=tree.ee, rnea=True, q_bar=True, qd_bar=True, tau_bar="tau",
+                         one_sweep=one_sweep, out=fo)
+
+        best = {}
+        for blk in (32, 64, 128, 256):          # the fused launch's block size, tuned here
+            m.set_launch(["eval"], blk, "auto")
+            best[blk] = _graph_us(torch, fstep, n=steps // 10, reps=10)
+        blk = min(best, key=best.get)
+        fused["one_sweep" if one_sweep else "kin_beside"] = {"graph_us_per_step": round(best[blk], 3), "block": blk,
+                                                             "speedup_vs_4_launch_graph": round(graph / best[blk], 3)}
     return {"workload": "spined_quadruped11, B=4096: FK + 4 foot Jacobians + RNEA + RNEA adjoint", "steps": steps,
             "eager_us_per_step": round(eager, 3), "graph_us_per_step": round(graph, 3),
-            "graph_steps_per_s": round(1e6 / graph, 1), "speedup": round(eager / graph, 3)}
+            "graph_steps_per_s": round(1e6 / graph, 1), "speedup": round(eager / graph, 3),
+            "fused_one_launch": fused}
 
 
-def humanoid_sweep(torch, fst, w, Bs=(1, 64, 1024, 4096, 16384, 65536)):
+def chain7_small(torch, fst, w, p_alu, hbm_gbs, B=1024):
+    """The plain method on the 7-DOF serial chain, B = 1024: FK of all links,
+    the end-effector Jacobian, RNEA and CRBA in one fused launch (the tuned
+    kernel configuration), graph-replayed over rotating input sets larger
+    than L2. Env-evals/s and the roofline of the step."""
+    from paper_2605_31481_gb300 import autotune, costs
+    tree = w.chain(7, seed=0)
+    m = fst.Model(tree)
+    try:
+        m.specialize(["fk", "jacobian", "rnea", "crba", "eval"])
+    except Exception:
+        pass
+    autotune.tune(m, B, kinds=("eval",), links=[tree.n_bodies - 1], use_cache=False)
+    links = [tree.n_bodies - 1]
+    per_set = 4 * B * (tree.nq + 2 * tree.nv + 12 * tree.n_bodies + 6 * tree.nv + tree.nv + tree.nv ** 2)
+    R = int(np.ceil(2 * L2_BYTES / per_set)) + 1
+    st = w.random_state(tree, B * R, seed=1)
+    cu = lambda x: torch.from_numpy(np.ascontiguousarray(x.T.astype(np.float32))).cuda()
+    sets = [{k: cu(st[k][r * B:(r + 1) * B]) for k in ("q", "qd", "qdd")} for r in range(R)]
+    outs = [{"poses": torch.empty(tree.n_bodies, 12, B, device="cuda"), "J": torch.empty(1, 6, tree.nv, B, device="cuda"),
+             "tau": torch.empty(tree.nv, B, device="cuda"), "M": torch.empty(tree.nv, tree.nv, B, device="cuda")}
+            for _ in range(R)]
+    k = [0]
+
+    def step():
+        d, o = sets[k[0] % R], outs[k[0] % R]
+        k[0] += 1
+        fst.eval(m, d["q"], d["qd"], d["qdd"], fk=True, links=links, rnea=True, crba=True, out=o)
+
+    us = _graph_us(torch, step, n=R, reps=20)
+    ops = ("fk", "jacobian", "rnea", "crba")
+    by = B * sum(costs.io_bytes(tree, op, 1) for op in ops) - 3 * B * 4 * tree.nq   # q read once
+    fl = B * sum(costs.flops(tree, op, links=links if op == "jacobian" else ()) for op in ops)
+    return {"workload": "chain7 (7 revolute DOF serial chain), B=1024: FK + end-effector Jacobian + RNEA + CRBA, "
+                        f"one fused launch, inputs rotating over {R} sets (> 2x L2)",
+            "us": round(us, 3), "env_evals_per_s": round(B / us * 1e6, 1),
+            "roofline": roof_of(by, fl, us / 1e6, p_alu, hbm_gbs)}
+
+
+def humanoid_sweep(torch, fst, w, p_alu, hbm_gbs, Bs=(1, 64, 1024, 4096, 16384, 65536)):
     """The five operators on the floating-base 29-DOF humanoid across batch
-    sizes (tuned plan per B), env-evals/s of the whole step."""
+    sizes (tuned plan per B), env-evals/s of the whole step and its roofline
+    position (algorithmic bytes with q, qd, qdd and tau read once)."""
+    from paper_2605_31481_gb300 import costs
     tree = w.humanoid(seed=0)
     m = fst.Model(tree)
     try:
@@ -537,7 +653,12 @@ def humanoid_sweep(torch, fst, w, Bs=(1, 64, 1024, 4096, 16384, 65536)):
              "J": torch.empty(len(tree.ee), 6, tree.nv, B, device="cuda"), "tau": torch.empty(tree.nv, B, device="cuda"),
              "M": torch.empty(tree.nv, tree.nv, B, device="cuda"), "qdd": torch.empty(tree.nv, B, device="cuda")}
         us = _graph_us(torch, lambda: plan(q, qd, qdd, tau, o))
-        out[str(B)] = {"us": round(us, 3), "env_evals_per_s": round(B / us * 1e6, 1), "plan": plan.mode}
+        links = list(tree.ee)
+        by = B * 4 * (tree.nq + 3 * tree.nv + 12 * tree.n_bodies + 6 * tree.nv * len(links) + tree.nv
+                      + tree.nv ** 2 + tree.nv)
+        fl = B * sum(costs.flops(tree, op, links=links if op == "jacobian" else ()) for op in OPS)
+        out[str(B)] = {"us": round(us, 3), "env_evals_per_s": round(B / us * 1e6, 1), "plan": plan.mode,
+                       "roofline": roof_of(by, fl, us / 1e6, p_alu, hbm_gbs)}
     return {"workload": "humanoid_float29 (free base + 23 revolute, depth 7): FK + 4 Jacobians + RNEA + CRBA + ABA",
             "per_B": out}
 

@@ -202,6 +202,12 @@ FST_API fst_status fst_model_specialize(fst_model* model, uint32_t kinds);
  * overlap in time, except one eval beside one ABA (they count in separate
  * regions). */
 #define FST_VARIANT_PINNED 7
+/* As LEVEL, with two tiles of 32 environments per block (block >= 64
+ * threads, split evenly; the tiles' warps interleaved so that each tile's
+ * busiest warp has an SM sub-partition of its own): half as many blocks,
+ * each twice the shared memory. For trees whose per-tile state fits twice
+ * in shared memory; otherwise the generic kernel runs. */
+#define FST_VARIANT_LEVEL2 8
 FST_API fst_status fst_model_set_launch(fst_model* model, uint32_t kinds, int32_t block, int32_t variant);
 
 /* Roles of the SMs for FST_VARIANT_PINNED launches: role_of_sm[i] is the
@@ -265,9 +271,15 @@ FST_API fst_status fst_aba(const fst_model* model, int64_t B, const float* q,
                    const float* qd, const float* tau, const float* theta,
                    float* qdd, void* stream);
 
+/* fst_eval_io.flags */
+#define FST_EVAL_ONE_SWEEP 1u  /* poses and J come from the RNEA sweep's own joint transforms */
+#define FST_EVAL_PACKED 2u     /* M and J in the packed layouts of fst_packed_layout */
+
 /* Inputs and outputs of fst_eval. Inputs: q always; qd and qdd when tau_out
- * is requested; qd and tau when qdd_out is requested. Outputs: any subset,
- * NULL = not computed. links/n_links (HOST array) are used when J is set. */
+ * or an RNEA cotangent is requested; qd and tau when qdd_out is requested.
+ * Outputs: any subset, NULL = not computed. links/n_links (HOST array) are
+ * used when J is set. Zero-initialise the struct: fields added later are
+ * then off. */
 typedef struct fst_eval_io {
   const float* q;        /* [nq][B] */
   const float* qd;       /* [nv][B] */
@@ -280,13 +292,48 @@ typedef struct fst_eval_io {
   float* tau_out;        /* [nv][B]             as fst_rnea (inputs q, qd, qdd) */
   float* M;              /* [nv][nv][B]         as fst_crba */
   float* qdd_out;        /* [nv][B]             as fst_aba (inputs q, qd, tau) */
+  /* The RNEA adjoint in the same pass (as fst_rnea_vjp without theta_bar):
+   * set any of q_bar / qd_bar / qdd_bar to request it; tau_bar [nv][B] is
+   * then its cotangent, or the computed tau itself when tau_bar == tau_out
+   * (e.g. for the loss |tau|^2 / 2). */
+  const float* tau_bar;
+  float* q_bar;          /* [nq][B] */
+  float* qd_bar;         /* [nv][B] */
+  float* qdd_bar;        /* [nv][B] */
+  uint32_t flags;        /* FST_EVAL_* */
 } fst_eval_io;
+
+/* Sizes of the packed outputs of fst_eval (FST_EVAL_PACKED), which drop
+ * what the full layouts repeat or know to be zero, so that less has to be
+ * copied off the device:
+ *  - M: its upper triangle, row by row: element (r, c), r <= c, is row
+ *    r*nv - r*(r-1)/2 + (c - r) of an [nv*(nv+1)/2][B] array;
+ *  - J: for each link l, only the columns of the DOFs on its support path
+ *    (the joints between it and the root; every other column is zero), in
+ *    DOF order, as a [6][cols[l]] block; the blocks follow each other in
+ *    link order in one [j_rows][B] array, j_rows = 6 * sum of cols.
+ * Host only (no device work). cols (n_links entries), j_rows and m_rows may
+ * be NULL. The paper has no counterpart: it returns dense tensors. */
+FST_API fst_status fst_packed_layout(const fst_model* model, const int32_t* links, int32_t n_links,
+                                     int32_t* cols, int32_t* j_rows, int32_t* m_rows);
 
 /* Every requested operator of one batch in ONE launch. The paper computes
  * only the kinematic tiers a query needs (Sec. 3.1); here the operators
  * whose outputs are NULL are skipped and the others run side by side on the
  * GPU, one group of thread blocks per operator. Results are bit-identical
- * to the per-operator calls. theta as in fst_rnea. */
+ * to the per-operator calls. theta as in fst_rnea.
+ * With an RNEA cotangent requested, the RNEA operator's blocks run its
+ * forward sweep once and feed tau and the adjoint's reverse sweeps from it
+ * (the controller step of the paper's RL experiment, Sec. 4.4: FK,
+ * Jacobians and inverse dynamics, here with RNEA's gradient). With
+ * FST_EVAL_ONE_SWEEP and the RNEA operator requested, poses and J are also
+ * computed by those blocks from the same joint transforms (paper Eq. 4-5
+ * evaluated once per joint) instead of by blocks of their own. Both run the
+ * one-environment-per-thread fused kernel: the one specialised for the tree
+ * when it is compiled (FST_SPEC_EVAL) and the eval kind is not set to
+ * FST_VARIANT_GENERIC, else the generic one. FST_EVAL_PACKED writes M and J
+ * in the layouts of fst_packed_layout (M then has nv*(nv+1)/2 rows), on the
+ * same kernels; values are bit-identical to the full layouts' entries. */
 FST_API fst_status fst_eval(const fst_model* model, int64_t B, const fst_eval_io* io,
                             const float* theta, void* stream);
 
@@ -427,7 +474,11 @@ FST_API fst_status fst_rnea_loss_grad(const fst_model* model, int64_t B, const f
  * theta_bar; sequential calls are fine and need no clearing. The first call
  * on a device looks up the array's device address (cudaGetSymbolAddress with
  * that device current) and caches it; make that first call before any
- * stream capture. */
+ * stream capture. The cached address lives as long as the device's primary
+ * context: do not call this entry point after a cudaDeviceReset. Argument
+ * checks are those of every entry point (B <= 2^31 - 1, the model's device
+ * current, non-null inputs), and the call then runs exactly what
+ * fst_rnea_vjp runs for this model (its specialised kernel, if compiled). */
 FST_API fst_status fst_rnea_vjp_noalloc(const fst_model* model, int64_t B, const float* q,
                                         const float* qd, const float* qdd, const float* theta,
                                         const float* tau_bar, float* q_bar, float* qd_bar,
@@ -468,6 +519,23 @@ FST_API fst_status fst_multi_destroy(fst_multi* multi);
  * group (unordered streams) race on its counter; create one group per
  * stream for that. Results are bit-identical to the per-tree generic calls. */
 FST_API fst_status fst_multi_eval(fst_multi* multi, const fst_multi_io* io, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Measurement. The paper reports speed against other libraries (Sec. 4.2);
+ * this library reports it as a fraction of the GPU's own ceilings, and
+ * this probe measures the arithmetic one.
+ * ------------------------------------------------------------------------- */
+
+/* Launches an FP32 fused multiply-add throughput probe on `stream`:
+ * (SMs x blocks_per_sm) blocks of 256 threads, each thread running 16
+ * independent FMA chains for `iters` iterations, and writes one float per
+ * thread to out (device memory of at least SMs x blocks_per_sm x 256 floats,
+ * so the work cannot be optimised away). *flops (host) receives the flops
+ * the launch executes (2 per FMA). Time the launch with CUDA events and
+ * divide. blocks_per_sm in [1, 64], iters >= 1; FST_ERR_INVALID_ARG
+ * otherwise or when out is too small. */
+FST_API fst_status fst_fp32_probe(int32_t blocks_per_sm, int32_t iters, float* out, size_t out_bytes,
+                                  double* flops, void* stream);
 
 /* Message for the last non-OK status on this thread ("" if none). */
 FST_API const char* fst_last_error(void);

@@ -18,7 +18,8 @@ STATUS_NAMES = {
 }
 MAX_BODIES = 64
 MAX_LINKS = 16
-VARIANTS = {"auto": 0, "generic": 1, "specialized": 2, "level": 3, "mixed": 4, "path": 5, "pathwarp": 6, "pinned": 7}
+VARIANTS = {"auto": 0, "generic": 1, "specialized": 2, "level": 3, "mixed": 4, "path": 5, "pathwarp": 6, "pinned": 7,
+            "level2": 8}
 SPEC_KINDS = ("fk", "jacobian", "rnea", "crba", "aba", "eval", "fk_vjp", "rnea_vjp", "aba_vjp", "loss_grad",
               "eval_mixed", "rnea_store", "rnea_vjp_stored", "rnea_derivatives", "aba_derivatives")
 
@@ -52,7 +53,13 @@ class EvalIO(ctypes.Structure):
         ("q", c_void_p), ("qd", c_void_p), ("qdd", c_void_p), ("tau", c_void_p),
         ("poses", c_void_p), ("J", c_void_p), ("links", ctypes.POINTER(c_int32)), ("n_links", c_int32),
         ("tau_out", c_void_p), ("M", c_void_p), ("qdd_out", c_void_p),
+        ("tau_bar", c_void_p), ("q_bar", c_void_p), ("qd_bar", c_void_p), ("qdd_bar", c_void_p),
+        ("flags", ctypes.c_uint32),
     ]
+
+
+EVAL_ONE_SWEEP = 1     # FST_EVAL_ONE_SWEEP
+EVAL_PACKED = 2        # FST_EVAL_PACKED
 
 
 class MultiIO(ctypes.Structure):
@@ -106,6 +113,9 @@ _SIGS = {
     "fst_multi_create": (c_int32, [ctypes.POINTER(c_void_p), c_int32, ctypes.POINTER(c_void_p)]),
     "fst_multi_destroy": (c_int32, [c_void_p]),
     "fst_multi_eval": (c_int32, [c_void_p, ctypes.POINTER(MultiIO), c_void_p]),
+    "fst_packed_layout": (c_int32, [c_void_p, ctypes.POINTER(c_int32), c_int32, ctypes.POINTER(c_int32),
+                                    ctypes.POINTER(c_int32), ctypes.POINTER(c_int32)]),
+    "fst_fp32_probe": (c_int32, [c_int32, c_int32, c_void_p, ctypes.c_size_t, ctypes.POINTER(c_double), c_void_p]),
     "fst_last_error": (ctypes.c_char_p, []),
     "fst_version": (ctypes.c_char_p, []),
 }

@@ -230,21 +230,33 @@ def aba(model: Model, q, qd, tau, theta=None, out=None):
 
 
 def eval(model: Model, q, qd=None, qdd=None, tau=None, *, fk=False, links=None, rnea=False, crba=False,
-         aba=False, theta=None, out=None):
+         aba=False, theta=None, out=None, tau_bar=None, q_bar=False, qd_bar=False, qdd_bar=False,
+         one_sweep=False, packed=False):
     """Every requested operator in one fused launch (fst_eval).
 
     fk=True requests poses; links=[...] the Jacobians of those bodies;
     rnea=True tau (needs qd, qdd); crba=True M; aba=True qdd (needs qd, tau).
-    Returns a dict with the requested outputs ("poses", "J", "tau", "M",
-    "qdd"); `out` may supply preallocated tensors under the same keys."""
+    q_bar/qd_bar/qdd_bar=True request the RNEA adjoint for the cotangent
+    tau_bar (nv, B) in the same pass; tau_bar="tau" uses the computed tau
+    (with rnea=True). one_sweep=True computes poses and Jacobians from the
+    RNEA sweep's own joint transforms. packed=True writes M as its upper
+    triangle (nv (nv + 1) / 2, B) and J as the support-path columns of each
+    link (packed_layout(), (j_rows, B)). Returns a dict with the requested
+    outputs ("poses", "J", "tau", "M", "qdd", "q_bar", "qd_bar", "qdd_bar");
+    `out` may supply preallocated tensors under the same keys."""
     B = _check_in(q, model.nq, "q", model)
     out = dict(out or {})
     io = _ffi.EvalIO()
     io.q = q.data_ptr()
-    if rnea or aba:
+    vjp = q_bar or qd_bar or qdd_bar
+    if vjp and tau_bar is None:
+        raise ValueError("the RNEA adjoint needs tau_bar (a (nv, B) tensor, or 'tau' with rnea=True)")
+    if isinstance(tau_bar, str) and (tau_bar != "tau" or not rnea):
+        raise ValueError("tau_bar='tau' needs rnea=True")
+    if rnea or aba or vjp:
         _check_in(qd, model.nv, "qd", model)
         io.qd = qd.data_ptr()
-    if rnea:
+    if rnea or vjp:
         _check_in(qdd, model.nv, "qdd", model)
         io.qdd = qdd.data_ptr()
     if aba:
@@ -258,7 +270,8 @@ def eval(model: Model, q, qd=None, qdd=None, tau=None, *, fk=False, links=None, 
     if links:
         links = [int(l) for l in links]
         link_arr = (ctypes.c_int32 * len(links))(*links)
-        res["J"] = _out(out.get("J"), (len(links), 6, model.nv, B), model)
+        jshape = (packed_layout(model, links)[1], B) if packed else (len(links), 6, model.nv, B)
+        res["J"] = _out(out.get("J"), jshape, model)
         io.J = res["J"].data_ptr()
         io.links = link_arr
         io.n_links = len(links)
@@ -266,13 +279,38 @@ def eval(model: Model, q, qd=None, qdd=None, tau=None, *, fk=False, links=None, 
         res["tau"] = _out(out.get("tau"), (model.nv, B), model)
         io.tau_out = res["tau"].data_ptr()
     if crba:
-        res["M"] = _out(out.get("M"), (model.nv, model.nv, B), model)
+        mshape = (model.nv * (model.nv + 1) // 2, B) if packed else (model.nv, model.nv, B)
+        res["M"] = _out(out.get("M"), mshape, model)
         io.M = res["M"].data_ptr()
     if aba:
         res["qdd"] = _out(out.get("qdd"), (model.nv, B), model)
         io.qdd_out = res["qdd"].data_ptr()
+    if vjp:
+        if isinstance(tau_bar, str):
+            io.tau_bar = io.tau_out
+        else:
+            _check_in(tau_bar, model.nv, "tau_bar", model)
+            io.tau_bar = tau_bar.data_ptr()
+        for key, want, rows in (("q_bar", q_bar, model.nq), ("qd_bar", qd_bar, model.nv),
+                                ("qdd_bar", qdd_bar, model.nv)):
+            if want:
+                res[key] = _out(out.get(key), (rows, B), model)
+                setattr(io, key, res[key].data_ptr())
+    io.flags = (_ffi.EVAL_ONE_SWEEP if one_sweep else 0) | (_ffi.EVAL_PACKED if packed else 0)
     check(_ffi.lib().fst_eval(model.handle, B, ctypes.byref(io), _ptr(_theta(theta, model)), _stream()))
     return res
+
+
+def packed_layout(model: Model, links):
+    """The packed Jacobian layout of eval(packed=True) (fst_packed_layout):
+    (support-path columns per link, rows of the packed J, rows of the packed
+    M)."""
+    links = [int(l) for l in links]
+    arr = (ctypes.c_int32 * max(len(links), 1))(*links)
+    cols = (ctypes.c_int32 * max(len(links), 1))()
+    jr, mr = ctypes.c_int32(), ctypes.c_int32()
+    check(_ffi.lib().fst_packed_layout(model.handle, arr, len(links), cols, ctypes.byref(jr), ctypes.byref(mr)))
+    return [cols[k] for k in range(len(links))], jr.value, mr.value
 
 
 # ---------------------------------------------------------------------------
@@ -536,3 +574,17 @@ class MultiBatch:
             results.append(res)
         check(_ffi.lib().fst_multi_eval(self._h, ios, _stream()))
         return results
+
+
+def fp32_probe(blocks_per_sm: int = 4, iters: int = 1 << 16, out=None):
+    """Launches the FP32 FMA throughput probe (fst_fp32_probe) on the current
+    stream. Returns (flops of the launch, the output buffer); time the call
+    with CUDA events around it."""
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    n = sms * blocks_per_sm * 256
+    if out is None or out.numel() < n:
+        out = torch.empty(n, dtype=torch.float32, device="cuda")
+    fl = ctypes.c_double()
+    check(_ffi.lib().fst_fp32_probe(int(blocks_per_sm), int(iters), _ptr(out), out.numel() * 4, ctypes.byref(fl),
+                                    _stream()))
+    return fl.value, out

@@ -8,6 +8,7 @@ threads):
   specialized  one environment per thread, a kernel compiled for the tree;
   level        32 environments per block, the block's warps splitting each
                tree level;
+  level2       the same with two such tiles per block (half the blocks);
   mixed        (eval) the specialised fused kernel with each role mapped as
                its own operator is set;
   path         a lane per root-to-leaf path (trees with at most 8 leaves);
@@ -91,6 +92,57 @@ def graph_time_us(fn, n=20, reps=10, trials=3):
     return best
 
 
+L2_BYTES = 129 * 2 ** 20    # GB300's L2 cache
+
+
+def cold_time_us(fn, R, reps=5, trials=3):
+    """Device time per call of fn(k) in microseconds, from a CUDA graph of the
+    R calls fn(0) .. fn(R - 1) replayed reps times: with fn(k) working on the
+    k-th of R rotating data sets larger than L2 together, every call reads and
+    writes HBM. The best of `trials` measurements."""
+    for k in range(min(R, 2)):
+        fn(k)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        for k in range(R):
+            fn(k)
+    g.replay()
+    torch.cuda.synchronize()
+    best = float("inf")
+    for _ in range(trials):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            g.replay()
+        b.record()
+        torch.cuda.synchronize()
+        best = min(best, a.elapsed_time(b) * 1e3 / (R * reps))
+    return best
+
+
+class ColdSets:
+    """R rotating copies of a five-operator step's inputs and outputs, more
+    than twice the L2 cache together, for timing step plans the way the
+    benchmark runs them (cold inputs every step)."""
+
+    def __init__(self, model, B, links):
+        dev = model.device
+        nq, nv, nb, nl = model.nq, model.nv, model.n_bodies, len(links)
+        per = 4 * B * (nq + 3 * nv + 12 * nb + 6 * nv * nl + nv + nv * nv + nv)
+        self.R = max(2, -(-2 * L2_BYTES // per) + 1)
+        gen = torch.Generator(device=dev).manual_seed(1)
+        r = lambda *sh: torch.randn(*sh, device=dev, generator=gen)
+        self.sets = []
+        for _ in range(self.R):
+            self.sets.append({"q": r(nq, B), "qd": r(nv, B), "qdd": r(nv, B), "tau": r(nv, B),
+                              "out": {"poses": torch.empty(nb, 12, B, device=dev),
+                                      "J": torch.empty(nl, 6, nv, B, device=dev),
+                                      "tau": torch.empty(nv, B, device=dev),
+                                      "M": torch.empty(nv, nv, B, device=dev),
+                                      "qdd": torch.empty(nv, B, device=dev)}})
+
+
 class Buffers:
     """Synthetic device inputs and outputs for timing one model at batch B."""
 
@@ -169,13 +221,15 @@ def tune(model, B, kinds=FORWARD_KINDS + ("eval",), links=None, use_cache=True, 
                 api.rnea_store(model, buf.q, buf.qd, buf.qdd, tape=buf.tape, tau=False)
         fn = _op(model, kind, buf)
         cands = {}
-        variants = ["generic"] + (["specialized"] if kind in spec else []) + (["level"] if kind in LEVEL_KINDS else [])
+        variants = ["generic"] + (["specialized"] if kind in spec else []) + \
+            (["level", "level2"] if kind in LEVEL_KINDS else [])
         if kind == "eval" and "eval_mixed" in spec:
             variants.append("mixed")       # specialised fused kernel, roles mapped as their operators
         if kind in spec and kind in LEVEL_KINDS:
             variants += ["path", "pathwarp"]   # path-parallel, where the tree has at most 8 leaves
         for variant in variants:
-            for block in ((0,) if variant == "pathwarp" else CANDIDATE_BLOCKS):
+            blocks = (0,) if variant == "pathwarp" else CANDIDATE_BLOCKS[1:] if variant == "level2" else CANDIDATE_BLOCKS
+            for block in blocks:
                 try:
                     model.set_launch([kind], block, variant)
                 except _ffi.FstError:
@@ -242,21 +296,20 @@ class StepPlan:
             mode, carveout, alt, ev = fixed
             if ev is None:
                 ev = "|".join(f"{self.tuned[k]['variant']}/{self.tuned[k]['block']}" for k in ("eval", "aba"))
-            buf = Buffers(model, B, self.links)
+            cold = ColdSets(model, B, self.links)
             api.set_smem_carveout(carveout)
             self._set_eval(ev)
             self._set_alt(mode, alt)
-            self.times = {(mode, carveout, alt, ev): graph_time_us(
-                lambda: self(buf.q, buf.qd, buf.qdd, buf.tau, buf.out))}
+            self.times = {(mode, carveout, alt, ev): self._time(cold)}
             self._apply(mode, carveout, alt, ev)
             return
-        key = _key(model, "plan10", B)
+        key = _key(model, "plan11", B)      # plans timed on cold, rotating inputs
         hit = _load_cache().get(key) if use_cache else None
         if hit:
             self.times = {(k, c, a, ev): v for k, c, a, ev, v in hit["times"]}
             self._apply(hit["mode"], hit["carveout"], hit["alt"], hit["eval"])
             return
-        buf = Buffers(model, B, self.links)
+        cold = ColdSets(model, B, self.links)
         # the hybrid's fused kernel carries three roles, not the four the
         # eval tuning measured: try the best few fused configurations there
         ranked = sorted(self.tuned["eval"]["candidates"].items(), key=lambda kv: kv[1])
@@ -290,14 +343,21 @@ class StepPlan:
                         if (carveout >= 0 or alt) and mode in ("fused", "sequential"):
                             continue
                         self._set_alt(mode, alt)
-                        times[(mode, carveout, alt, ev)] = graph_time_us(
-                            lambda: self(buf.q, buf.qd, buf.qdd, buf.tau, buf.out))
+                        times[(mode, carveout, alt, ev)] = self._time(cold)
         self.times = times
         self._apply(*min(times, key=times.get))
         if use_cache:
             _store_cache({key: {"mode": self.mode, "carveout": self.carveout, "alt": self.alt,
                                 "eval": self.eval_config,
                                 "times": [[k, c, p, ev, round(v, 3)] for (k, c, p, ev), v in times.items()]}})
+
+    def _time(self, cold):
+        """Microseconds per step of the current plan, each step on the next of
+        the rotating cold data sets (as the benchmark's timed steps run)."""
+        def step(k):
+            d = cold.sets[k]
+            self(d["q"], d["qd"], d["qdd"], d["tau"], d["out"])
+        return cold_time_us(step, cold.R)
 
     @classmethod
     def parse_key(cls, key):

@@ -202,6 +202,44 @@ __device__ __forceinline__ void rnea_vjp_env(const TP& tp, SV a0, const Col& q, 
   rnea_vjp_reverse<NB>(tp, a0, q, qd, X, v, a, F, tbar, o, B, e);
 }
 
+// The RNEA role of the fused evaluation (fst_eval): ONE forward sweep whose
+// joint transforms, velocities, accelerations and forces feed, as
+// a.rnea_flags requests, the world poses and Jacobians, tau, and the reverse
+// sweeps of the RNEA adjoint for the cotangent in column tb (staged from
+// a.tau_bar, or filled here with the computed tau when EVAL_TBAR_IS_TAU).
+// This is the controller step the paper times in its RL experiment (FK,
+// Jacobians and RNEA each step, Sec. 4.4) with the gradient of RNEA added,
+// in one pass instead of one launch per operator. Each output is
+// bit-identical to the separate operator's (fk_env, jac_env, rnea_env,
+// rnea_vjp_env run the same arithmetic in the same order).
+template <int NB, class TP>
+__device__ __forceinline__ void rnea_role_env(const TP& tp, SV a0, const Col& q, const Col& qd, const Col& qdd,
+                                              float* tb, int tb_ld, int nv, const EvalArgs& a, int64_t B,
+                                              int64_t e) {
+  Xf X[NB];
+  SV v[NB], acc[NB], F[NB];
+  rnea_forward<NB>(tp, a0, q, qd, qdd, X, v, acc, F);
+  if (a.rnea_flags & EVAL_KIN_IN_RNEA)
+    kin_from_X<NB>(tp, X, nv, a.links, a.poses, a.J, B, e, a.packed ? &a.pj : nullptr);
+  rnea_backward<NB>(tp, X, F, a.tau_out, B, e);
+  if (!(a.rnea_flags & EVAL_RNEA_VJP)) return;
+  if (a.rnea_flags & EVAL_TBAR_IS_TAU) {
+    FST_UNROLL
+    for (int i = 0; i < tp.n(); ++i) {
+      const BodyI bi = tp.I(i);
+      if (bi.type == FST_JOINT_REVOLUTE || bi.type == FST_JOINT_PRISMATIC) {
+        tb[bi.vi * tb_ld] = dot(S_of(tp.C(i)), F[i]);
+      } else if (bi.type == FST_JOINT_FREE) {
+        const float f6[6] = {F[i].v.x, F[i].v.y, F[i].v.z, F[i].w.x, F[i].w.y, F[i].w.z};
+#pragma unroll
+        for (int r = 0; r < 6; ++r) tb[(bi.vi + r) * tb_ld] = f6[r];
+      }
+    }
+  }
+  const VjpOut o{a.qbar, a.qdbar, a.qddbar, nullptr, 1.f, true};
+  rnea_vjp_reverse<NB>(tp, a0, q, qd, X, v, acc, F, Col{tb, tb_ld}, o, B, e);
+}
+
 // ---- store variant: the forward state on a tape -----------------------------
 // Instead of recomputing the forward sweep inside the adjoint kernel, the
 // forward kernel can leave, per body, the quantities the reverse sweeps read:

@@ -31,14 +31,6 @@ fst_status set_error(fst_status s, const std::string& msg) {
   return s;
 }
 
-namespace {
-
-fst_status cuda_error(const char* where, cudaError_t err) {
-  std::ostringstream os;
-  os << where << ": " << cudaGetErrorName(err) << ": " << cudaGetErrorString(err);
-  return set_error(FST_ERR_CUDA, os.str());
-}
-
 // Common checks of every compute call. Returns FST_OK when the call may
 // launch; *skip is set when B == 0.
 fst_status check_call(const char* fn, const fst_model* m, int64_t B, bool* skip) {
@@ -56,13 +48,25 @@ fst_status check_call(const char* fn, const fst_model* m, int64_t B, bool* skip)
     return set_error(FST_ERR_INVALID_ARG, std::string(fn) + ": B must be at most 2^31 - 1 per call");
   int dev = -1;
   cudaError_t err = cudaGetDevice(&dev);
-  if (err != cudaSuccess) return cuda_error(fn, err);
+  if (err != cudaSuccess) {
+    std::ostringstream os;
+    os << fn << ": " << cudaGetErrorName(err) << ": " << cudaGetErrorString(err);
+    return set_error(FST_ERR_CUDA, os.str());
+  }
   if (dev != m->device) {
     std::ostringstream os;
     os << fn << ": current device " << dev << " is not the model's device " << m->device;
     return set_error(FST_ERR_INVALID_ARG, os.str());
   }
   return FST_OK;
+}
+
+namespace {
+
+fst_status cuda_error(const char* where, cudaError_t err) {
+  std::ostringstream os;
+  os << where << ": " << cudaGetErrorName(err) << ": " << cudaGetErrorString(err);
+  return set_error(FST_ERR_CUDA, os.str());
 }
 
 fst_status need(const char* fn, const void* p, const char* name) {
@@ -79,8 +83,13 @@ bool use_jit(const fst_model* m, int kind) {
 
 // Whether a call of this kind runs the level-parallel kernel: selected, and
 // its shared memory (which grows with the number of bodies) fits.
+// Tiles of 32 environments per block of a level-parallel launch of this kind.
+int level_tiles(const fst_model* m, int kind) { return m->variant[kind] == FST_VARIANT_LEVEL2 ? 2 : 1; }
+
 bool use_level(const fst_model* m, int kind, int level_kind) {
-  return m->variant[kind] == FST_VARIANT_LEVEL && level_smem_needed(view_of(m, nullptr), level_kind) <= kLevelSmemLimit;
+  const int v = m->variant[kind];
+  return (v == FST_VARIANT_LEVEL || v == FST_VARIANT_LEVEL2) &&
+         level_smem_needed(view_of(m, nullptr), level_kind, level_tiles(m, kind)) <= kLevelSmemLimit;
 }
 
 // The path-parallel kernel slot a call of this kind runs (0: none): 1 for
@@ -116,7 +125,10 @@ cudaError_t path_go(const fst_model* m, int kind, int64_t B, int rows, unsigned 
 
 // Threads per block of a level-parallel launch: a multiple of 32 (one warp
 // per share of a level), 32 environments per block.
-int level_block(const fst_model* m, int kind) { return m->block[kind] ? m->block[kind] : 128; }
+int level_block(const fst_model* m, int kind) {
+  if (m->block[kind]) return m->block[kind];
+  return m->variant[kind] == FST_VARIANT_LEVEL2 ? 256 : 128;
+}
 
 int block_of(const fst_model* m, int kind, int64_t B) { return m->block[kind] ? m->block[kind] : default_block(B); }
 
@@ -236,11 +248,14 @@ fst_status fst_model_set_launch(fst_model* m, uint32_t kinds, int32_t block, int
   if (!m) return set_error(FST_ERR_INVALID_ARG, "fst_model_set_launch: null model");
   if (block != 0 && block != 32 && block != 64 && block != 128 && block != 256)
     return set_error(FST_ERR_INVALID_ARG, "fst_model_set_launch: block must be 0, 32, 64, 128 or 256");
-  if (variant < FST_VARIANT_AUTO || variant > FST_VARIANT_PINNED)
+  if (variant < FST_VARIANT_AUTO || variant > FST_VARIANT_LEVEL2)
     return set_error(FST_ERR_INVALID_ARG, "fst_model_set_launch: unknown variant");
+  if (variant == FST_VARIANT_LEVEL2 && block == 32)
+    return set_error(FST_ERR_INVALID_ARG, "fst_model_set_launch: the two-tile level variant needs block >= 64");
   // "all kinds" with the level or path variant means every kind that has one
   if (kinds == 0)
-    kinds = (variant == FST_VARIANT_LEVEL || variant == FST_VARIANT_PATH || variant == FST_VARIANT_PATH_WARP)
+    kinds = (variant == FST_VARIANT_LEVEL || variant == FST_VARIANT_LEVEL2 || variant == FST_VARIANT_PATH ||
+             variant == FST_VARIANT_PATH_WARP)
                 ? (1u << (JK_EVAL + 1)) - 1u
                 : variant == FST_VARIANT_PINNED ? (1u << JK_EVAL) | (1u << JK_ABA) : FST_SPEC_ALL;
   if (kinds & ~(uint32_t)FST_SPEC_ALL) return set_error(FST_ERR_INVALID_ARG, "fst_model_set_launch: unknown kind bits");
@@ -263,7 +278,7 @@ fst_status fst_model_set_launch(fst_model* m, uint32_t kinds, int32_t block, int
     if (((kinds >> k) & 1u) && variant == FST_VARIANT_PINNED && k == JK_ABA &&
         level_smem_needed(view_of(m, nullptr), LEVEL_ABA) > kLevelSmemLimit)
       return set_error(FST_ERR_INVALID_ARG, "fst_model_set_launch: the tree is too large for pinned ABA");
-    if (((kinds >> k) & 1u) && variant == FST_VARIANT_LEVEL && k > JK_EVAL)
+    if (((kinds >> k) & 1u) && (variant == FST_VARIANT_LEVEL || variant == FST_VARIANT_LEVEL2) && k > JK_EVAL)
       return set_error(FST_ERR_INVALID_ARG, "fst_model_set_launch: the level-parallel variant exists for FK, "
                                             "Jacobian, RNEA, CRBA, ABA and eval only");
   }
@@ -325,7 +340,8 @@ fst_status fst_fk(const fst_model* m, int64_t B, const float* q, float* poses, v
   FST_CHECK(need(fn, poses, "poses"));
   const ModelView mv = view_of(m, nullptr);
   if (use_level(m, JK_FK, LEVEL_FK))
-    return finish(fn, launch_fk_level(mv, B, q, poses, level_block(m, JK_FK), (cudaStream_t)stream));
+    return finish(fn, launch_fk_level(mv, B, q, poses, level_block(m, JK_FK), level_tiles(m, JK_FK),
+                        (cudaStream_t)stream));
   if (use_path(m, JK_FK))
     return finish(fn, path_go(m, JK_FK, B, m->nq, 1, (cudaStream_t)stream, mv, B, q, poses));
   if (use_jit(m, JK_FK))
@@ -352,7 +368,8 @@ fst_status fst_jacobian(const fst_model* m, int64_t B, const float* q, const int
   FST_CHECK(need(fn, J, "J"));
   const ModelView mv = view_of(m, nullptr);
   if (use_level(m, JK_JACOBIAN, LEVEL_JAC))
-    return finish(fn, launch_jac_level(mv, B, q, L, J, level_block(m, JK_JACOBIAN), (cudaStream_t)stream));
+    return finish(fn, launch_jac_level(mv, B, q, L, J, level_block(m, JK_JACOBIAN), level_tiles(m, JK_JACOBIAN),
+                        (cudaStream_t)stream));
   if (use_path(m, JK_JACOBIAN))
     return finish(fn, path_go(m, JK_JACOBIAN, B, m->nq, 1, (cudaStream_t)stream, mv, B, q, L, J));
   if (use_jit(m, JK_JACOBIAN))
@@ -372,7 +389,8 @@ fst_status fst_rnea(const fst_model* m, int64_t B, const float* q, const float* 
   FST_CHECK(need(fn, tau, "tau"));
   const ModelView mv = view_of(m, theta);
   if (use_level(m, JK_RNEA, LEVEL_RNEA))
-    return finish(fn, launch_rnea_level(mv, B, q, qd, qdd, tau, level_block(m, JK_RNEA), (cudaStream_t)stream));
+    return finish(fn, launch_rnea_level(mv, B, q, qd, qdd, tau, level_block(m, JK_RNEA), level_tiles(m, JK_RNEA),
+                        (cudaStream_t)stream));
   if (use_path(m, JK_RNEA))
     return finish(fn, path_go(m, JK_RNEA, B, m->nq + 2 * m->nv, 1, (cudaStream_t)stream, mv, B, q, qd, qdd, tau));
   if (use_jit(m, JK_RNEA))
@@ -390,7 +408,8 @@ fst_status fst_crba(const fst_model* m, int64_t B, const float* q, const float* 
   FST_CHECK(need(fn, M, "M"));
   const ModelView mv = view_of(m, theta);
   if (use_level(m, JK_CRBA, LEVEL_CRBA))
-    return finish(fn, launch_crba_level(mv, B, q, M, level_block(m, JK_CRBA), (cudaStream_t)stream));
+    return finish(fn, launch_crba_level(mv, B, q, M, level_block(m, JK_CRBA), level_tiles(m, JK_CRBA),
+                        (cudaStream_t)stream));
   if (use_path(m, JK_CRBA))
     return finish(fn, path_go(m, JK_CRBA, B, m->nq, 1, (cudaStream_t)stream, mv, B, q, M));
   if (use_jit(m, JK_CRBA))
@@ -410,7 +429,8 @@ fst_status fst_aba(const fst_model* m, int64_t B, const float* q, const float* q
   FST_CHECK(need(fn, qdd, "qdd"));
   const ModelView mv = view_of(m, theta);
   if (use_level(m, JK_ABA, LEVEL_ABA))
-    return finish(fn, launch_aba_level(mv, B, q, qd, tau, qdd, level_block(m, JK_ABA), (cudaStream_t)stream));
+    return finish(fn, launch_aba_level(mv, B, q, qd, tau, qdd, level_block(m, JK_ABA), level_tiles(m, JK_ABA),
+                        (cudaStream_t)stream));
   if (m->variant[JK_ABA] == FST_VARIANT_PINNED) {
     int* counters = m->dpin + kPinTableSize + kPinAbaRegion * kPinRegion;
     cudaError_t err = cudaMemsetAsync(counters, 0, sizeof(int) * kPinRegion, (cudaStream_t)stream);
@@ -425,6 +445,54 @@ fst_status fst_aba(const fst_model* m, int64_t B, const float* q, const float* q
     return finish(fn, jit_go(m, JK_ABA, B, m->nq + 2 * m->nv, 0, 1, (cudaStream_t)stream, nullptr, mv, B, q, qd,
                              tau, qdd));
   return finish(fn, launch_aba(mv, B, q, qd, tau, qdd, launch_of(m, JK_ABA, B, stream)));
+}
+
+}  // extern "C"
+
+namespace fst {
+// Packed Jacobian layout: columns (support-path DOFs) of each link and the
+// first row of its block.
+void packed_cols(const fst_model* m, const LinkList& links, PackedJ& pj) {
+  int off = 0;
+  for (int l = 0; l < links.n; ++l) {
+    int cols = 0;
+    const uint64_t anc = m->ancestors[links.idx[l]];
+    for (int k = 0; k < m->n; ++k)
+      if ((anc >> k) & 1ull) {
+        const int t = m->hi[k].type;
+        cols += t == FST_JOINT_FREE ? 6 : (t == FST_JOINT_FIXED ? 0 : 1);
+      }
+    pj.cols[l] = cols;
+    pj.off[l] = off;
+    off += 6 * cols;
+  }
+}
+}  // namespace fst
+
+extern "C" {
+
+fst_status fst_packed_layout(const fst_model* m, const int32_t* links, int32_t n_links, int32_t* cols, int32_t* j_rows,
+                             int32_t* m_rows) {
+  static const char* fn = "fst_packed_layout";
+  if (!m) return set_error(FST_ERR_INVALID_ARG, std::string(fn) + ": null model");
+  if (n_links < 0 || n_links > FST_MAX_LINKS || (n_links > 0 && !links))
+    return set_error(FST_ERR_INVALID_ARG, std::string(fn) + ": need 0 <= n_links <= FST_MAX_LINKS links");
+  LinkList L{};
+  L.n = n_links;
+  for (int l = 0; l < n_links; ++l) {
+    if (links[l] < 0 || links[l] >= m->n) return set_error(FST_ERR_INVALID_ARG, std::string(fn) + ": link out of range");
+    L.idx[l] = links[l];
+  }
+  PackedJ pj{};
+  packed_cols(m, L, pj);
+  int rows = 0;
+  for (int l = 0; l < n_links; ++l) {
+    if (cols) cols[l] = pj.cols[l];
+    rows += 6 * pj.cols[l];
+  }
+  if (j_rows) *j_rows = rows;
+  if (m_rows) *m_rows = m->nv * (m->nv + 1) / 2;
+  return FST_OK;
 }
 
 fst_status fst_eval(const fst_model* m, int64_t B, const fst_eval_io* io, const float* theta, void* stream) {
@@ -451,28 +519,57 @@ fst_status fst_eval(const fst_model* m, int64_t B, const fst_eval_io* io, const 
       a.links.idx[l] = io->links[l];
     }
   }
+  if (io->flags & ~(FST_EVAL_ONE_SWEEP | FST_EVAL_PACKED))
+    return set_error(FST_ERR_INVALID_ARG, "fst_eval: unknown flags");
+  if (io->flags & FST_EVAL_PACKED) {
+    a.packed = 1;
+    packed_cols(m, a.links, a.pj);
+  }
   const bool dyn = m->nv > 0;
+  const bool vjp = dyn && (io->q_bar || io->qd_bar || io->qdd_bar);
   if (io->qdd_out && dyn) {
     FST_CHECK(need(fn, io->qd, "qd"));
     FST_CHECK(need(fn, io->tau, "tau"));
     a.roles[a.n_roles++] = ROLE_ABA;
   }
   if (io->M && dyn) a.roles[a.n_roles++] = ROLE_CRBA;
-  if (io->tau_out && dyn) {
+  const bool rnea = dyn && (io->tau_out || vjp);
+  if (rnea) {
     FST_CHECK(need(fn, io->qd, "qd"));
     FST_CHECK(need(fn, io->qdd, "qdd"));
+    if (vjp) {
+      FST_CHECK(need(fn, io->tau_bar, "tau_bar"));
+      a.tau_bar = io->tau_bar;
+      a.qbar = m->nq ? io->q_bar : nullptr;
+      a.qdbar = io->qd_bar;
+      a.qddbar = io->qdd_bar;
+      a.rnea_flags |= EVAL_RNEA_VJP;
+      if (io->tau_bar == io->tau_out) a.rnea_flags |= EVAL_TBAR_IS_TAU;
+    }
     a.roles[a.n_roles++] = ROLE_RNEA;
   }
   if (io->poses || (io->J && dyn)) {
     if (!io->poses) a.poses = nullptr;
     if (!dyn) a.J = nullptr;
-    a.roles[a.n_roles++] = ROLE_KIN;
+    if (rnea && (io->flags & FST_EVAL_ONE_SWEEP))
+      a.rnea_flags |= EVAL_KIN_IN_RNEA;
+    else
+      a.roles[a.n_roles++] = ROLE_KIN;
   }
   if (skip || a.n_roles == 0) return FST_OK;
   if (m->nq) FST_CHECK(need(fn, io->q, "q"));
   const ModelView mv = view_of(m, theta);
+  if (a.rnea_flags || a.packed) {
+    // the shared sweep and the packed layouts live in the one-environment-
+    // per-thread fused kernels
+    const int rows = m->nq + (vjp ? 3 : 2) * m->nv;
+    if (jit_has(m, JK_EVAL) && m->variant[JK_EVAL] != FST_VARIANT_GENERIC)
+      return finish(fn, jit_go(m, JK_EVAL, B, rows, 0, (unsigned)a.n_roles, (cudaStream_t)stream, nullptr, mv, B, a));
+    return finish(fn, launch_eval(mv, B, a, launch_of(m, JK_EVAL, B, stream)));
+  }
   if (use_level(m, JK_EVAL, LEVEL_EVAL))
-    return finish(fn, launch_eval_level(mv, B, a, level_block(m, JK_EVAL), (cudaStream_t)stream));
+    return finish(fn, launch_eval_level(mv, B, a, level_block(m, JK_EVAL), level_tiles(m, JK_EVAL),
+                        (cudaStream_t)stream));
   if (m->variant[JK_EVAL] == FST_VARIANT_MIXED && jit_has(m, JK_EVAL_MIXED)) {
     // roles whose own operator is tuned level-parallel run that way here too
     const int T = block_of(m, JK_EVAL, B);

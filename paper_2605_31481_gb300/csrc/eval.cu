@@ -8,7 +8,7 @@
 // operator alone fills only a fraction of the GPU's 152 SMs; the roles
 // together fill it, and the launch takes as long as its slowest role rather
 // than the sum of all of them.
-#include "ops.cuh"
+#include "adjoint.cuh"
 #include "launch.h"
 
 namespace fst {
@@ -28,6 +28,8 @@ __global__ void __launch_bounds__(256) eval_kernel(ModelView mv, int64_t B, Eval
     if (role == ROLE_RNEA) {
       c1 = stage_rows(tile + mv.nq * T, a.qd, mv.nv, B, e);
       c2 = stage_rows(tile + (mv.nq + mv.nv) * T, a.qdd, mv.nv, B, e);
+      if ((a.rnea_flags & EVAL_RNEA_VJP) && !(a.rnea_flags & EVAL_TBAR_IS_TAU))
+        stage_rows(tile + (mv.nq + 2 * mv.nv) * T, a.tau_bar, mv.nv, B, e);
     } else if (role == ROLE_ABA) {
       c1 = stage_rows(tile + mv.nq * T, a.qd, mv.nv, B, e);
       c2 = stage_rows(tile + (mv.nq + mv.nv) * T, a.tau, mv.nv, B, e);
@@ -41,14 +43,21 @@ __global__ void __launch_bounds__(256) eval_kernel(ModelView mv, int64_t B, Eval
       aba_env<NB>(sm, world_accel(mv), cq, c1, c2, a.qdd_out, B, e);
       break;
     case ROLE_CRBA:
-      crba_env<NB>(sm, cq, mv.nv, a.M, B, e);
+      if (a.packed)
+        crba_env<NB, true>(sm, cq, mv.nv, a.M, B, e);
+      else
+        crba_env<NB>(sm, cq, mv.nv, a.M, B, e);
       break;
     case ROLE_RNEA:
-      rnea_env<NB>(sm, world_accel(mv), cq, c1, c2, a.tau_out, B, e);
+      if (a.rnea_flags)
+        rnea_role_env<NB>(sm, world_accel(mv), cq, c1, c2, tile + (mv.nq + 2 * mv.nv) * T + threadIdx.x, T, mv.nv, a,
+                          B, e);
+      else
+        rnea_env<NB>(sm, world_accel(mv), cq, c1, c2, a.tau_out, B, e);
       break;
     default:
       if (a.J)
-        jac_env<NB>(sm, cq, mv.nv, a.links, a.poses, a.J, B, e);
+        jac_env<NB>(sm, cq, mv.nv, a.links, a.poses, a.J, B, e, a.packed ? &a.pj : nullptr);
       else
         fk_env<NB>(sm, cq, a.poses, B, e);
       break;
@@ -58,7 +67,7 @@ __global__ void __launch_bounds__(256) eval_kernel(ModelView mv, int64_t B, Eval
 }  // namespace
 
 cudaError_t launch_eval(const ModelView& mv, int64_t B, const EvalArgs& a, const Launch& L) {
-  const size_t sh = smem_bytes(mv.n, mv.nq + 2 * mv.nv, L.block);
+  const size_t sh = smem_bytes(mv.n, mv.nq + (a.rnea_flags & EVAL_RNEA_VJP ? 3 : 2) * mv.nv, L.block);
   const dim3 grid(grid_for(B, L.block), a.n_roles);
   FST_NB_DISPATCH(mv.n, prepare(eval_kernel<NB>, sh); eval_kernel<NB><<<grid, L.block, sh, L.stream>>>(mv, B, a));
   return cudaGetLastError();

@@ -320,14 +320,17 @@ __device__ __forceinline__ SmemModel stage_model(const ModelView& mv, float4* sm
   const float4* src = reinterpret_cast<const float4*>(mv.c);
   float4* dst = reinterpret_cast<float4*>(sc);
   const int nc4 = mv.n * (int)(sizeof(BodyC) / sizeof(float4));
-  for (int k = threadIdx.x; k < nc4; k += blockDim.x) dst[k] = src[k];
-  for (int k = threadIdx.x; k < mv.n; k += blockDim.x) si[k] = mv.i[k];
+  // every thread of the block, whatever its shape
+  const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+  const int nt = blockDim.x * blockDim.y * blockDim.z;
+  for (int k = tid; k < nc4; k += nt) dst[k] = src[k];
+  for (int k = tid; k < mv.n; k += nt) si[k] = mv.i[k];
   const int* ts = reinterpret_cast<const int*>(mv.topo);
   int* td = reinterpret_cast<int*>(st);
-  for (int k = threadIdx.x; k < (int)(sizeof(TopoLists) / sizeof(int)); k += blockDim.x) td[k] = ts[k];
+  for (int k = tid; k < (int)(sizeof(TopoLists) / sizeof(int)); k += nt) td[k] = ts[k];
   if (mv.theta) {
     __syncthreads();
-    for (int k = threadIdx.x; k < mv.n * 10; k += blockDim.x) sc[k / 10].theta[k % 10] = mv.theta[k];
+    for (int k = tid; k < mv.n * 10; k += nt) sc[k / 10].theta[k % 10] = mv.theta[k];
   }
   __syncthreads();
   return SmemModel{sc, si, mv.n, st, mv.depth};

@@ -34,6 +34,10 @@ struct fst_model {
 namespace fst {
 // Host-side helpers (model.cpp / api.cpp).
 fst_status set_error(fst_status s, const std::string& msg);
+// Checks shared by every compute entry point: a model, 0 <= B <= 2^31 - 1
+// and the model's device current. FST_OK when the call may go on; *skip is
+// set when B == 0 (nothing to launch).
+fst_status check_call(const char* fn, const fst_model* m, int64_t B, bool* skip);
 fst_status build_model_host(const fst_body_desc* bodies, int32_t n, const double gravity[3],
                             fst_model* m);
 inline ModelView view_of(const fst_model* m, const float* theta) {

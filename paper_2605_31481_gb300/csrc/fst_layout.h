@@ -76,6 +76,14 @@ struct LinkList {
   int idx[FST_MAX_LINKS];
 };
 
+// Packed Jacobian layout of fst_eval: link l keeps only the columns of the
+// DOFs on its support path, in DOF order, as a [6][cols[l]] block starting
+// at row off[l] of a [rows][B] array.
+struct PackedJ {
+  int cols[FST_MAX_LINKS];
+  int off[FST_MAX_LINKS];
+};
+
 // Operators of the fused evaluation kernel, in launch order (longest first,
 // so the slowest role's blocks are dispatched first).
 enum Role { ROLE_ABA = 0, ROLE_CRBA = 1, ROLE_RNEA = 2, ROLE_KIN = 3 };
@@ -107,6 +115,22 @@ struct EvalArgs {
   int roles[4];
   int n_roles;
   int level_mask;  // bit r: role r runs level-parallel (32 environments per block)
+  // RNEA role extras (EVAL_* bits in rnea_flags): the kinematics from the
+  // RNEA sweep's own joint transforms, and the RNEA adjoint for tau_bar
+  const float* tau_bar;
+  float* qbar;
+  float* qdbar;
+  float* qddbar;
+  int rnea_flags;
+  int packed;   // M as its upper triangle and J as PackedJ (the KIN, RNEA and CRBA roles)
+  PackedJ pj;
+};
+
+// rnea_flags of EvalArgs
+enum {
+  EVAL_KIN_IN_RNEA = 1,  // the RNEA role writes poses and J (no separate kinematics role)
+  EVAL_RNEA_VJP = 2,     // the RNEA role runs the adjoint sweeps for tau_bar
+  EVAL_TBAR_IS_TAU = 4   // ... with tau_bar = the tau it computed (tau_bar not read)
 };
 
 }  // namespace fst

@@ -149,6 +149,8 @@ extern "C" __global__ void __launch_bounds__(256) FST_JIT_NAME(ModelView mv, int
   if (role == ROLE_RNEA) {
     c1 = stage_rows(tile + mv.nq * T, a.qd, mv.nv, B, e);
     c2 = stage_rows(tile + (mv.nq + mv.nv) * T, a.qdd, mv.nv, B, e);
+    if ((a.rnea_flags & EVAL_RNEA_VJP) && !(a.rnea_flags & EVAL_TBAR_IS_TAU))
+      stage_rows(tile + (mv.nq + 2 * mv.nv) * T, a.tau_bar, mv.nv, B, e);
   } else if (role == ROLE_ABA) {
     c1 = stage_rows(tile + mv.nq * T, a.qd, mv.nv, B, e);
     c2 = stage_rows(tile + (mv.nq + mv.nv) * T, a.tau, mv.nv, B, e);
@@ -160,14 +162,21 @@ extern "C" __global__ void __launch_bounds__(256) FST_JIT_NAME(ModelView mv, int
       aba_env<FST_N>(tp, world_accel(mv), cq, c1, c2, a.qdd_out, B, e);
       break;
     case ROLE_CRBA:
-      crba_env<FST_N>(tp, cq, mv.nv, a.M, B, e);
+      if (a.packed)
+        crba_env<FST_N, true>(tp, cq, mv.nv, a.M, B, e);
+      else
+        crba_env<FST_N>(tp, cq, mv.nv, a.M, B, e);
       break;
     case ROLE_RNEA:
-      rnea_env<FST_N>(tp, world_accel(mv), cq, c1, c2, a.tau_out, B, e);
+      if (a.rnea_flags)
+        rnea_role_env<FST_N>(tp, world_accel(mv), cq, c1, c2, tile + (mv.nq + 2 * mv.nv) * T + threadIdx.x, T,
+                             mv.nv, a, B, e);
+      else
+        rnea_env<FST_N>(tp, world_accel(mv), cq, c1, c2, a.tau_out, B, e);
       break;
     default:
       if (a.J)
-        jac_env<FST_N>(tp, cq, mv.nv, a.links, a.poses, a.J, B, e);
+        jac_env<FST_N>(tp, cq, mv.nv, a.links, a.poses, a.J, B, e, a.packed ? &a.pj : nullptr);
       else
         fk_env<FST_N>(tp, cq, a.poses, B, e);
       break;

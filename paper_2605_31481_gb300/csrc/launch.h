@@ -90,23 +90,28 @@ cudaError_t launch_eval(const ModelView& mv, int64_t B, const EvalArgs& a, const
 cudaError_t launch_aba(const ModelView& mv, int64_t B, const float* q, const float* qd, const float* tau,
                        float* qdd, const Launch& L);
 
-// Level-parallel kernels (level.cu): 32 environments per block, block/32
-// warps splitting each tree level's bodies; per-body state in shared memory.
+// Level-parallel kernels (level.cu): tiles of 32 environments, the warps of
+// a tile splitting each tree level's bodies; per-body state in shared memory.
 enum LevelKind { LEVEL_FK = 0, LEVEL_JAC, LEVEL_RNEA, LEVEL_CRBA, LEVEL_ABA, LEVEL_EVAL };
 constexpr size_t kLevelSmemLimit = 227 * 1024;
 
 // Floats per body and environment on the store-variant RNEA tape (X 12, v 6, a 6, F 6).
 constexpr int kTapeFloatsPerBody = 30;
-size_t level_smem_needed(const ModelView& mv, int kind);
-cudaError_t launch_fk_level(const ModelView& mv, int64_t B, const float* q, float* poses, int block, cudaStream_t s);
+// `tiles` tiles of 32 environments per block (1, or 2 for FST_VARIANT_LEVEL2),
+// `block` threads in all.
+size_t level_smem_needed(const ModelView& mv, int kind, int tiles = 1);
+cudaError_t launch_fk_level(const ModelView& mv, int64_t B, const float* q, float* poses, int block, int tiles,
+                            cudaStream_t s);
 cudaError_t launch_jac_level(const ModelView& mv, int64_t B, const float* q, const LinkList& links, float* J,
-                             int block, cudaStream_t s);
+                             int block, int tiles, cudaStream_t s);
 cudaError_t launch_rnea_level(const ModelView& mv, int64_t B, const float* q, const float* qd, const float* qdd,
-                              float* tau, int block, cudaStream_t s);
-cudaError_t launch_crba_level(const ModelView& mv, int64_t B, const float* q, float* M, int block, cudaStream_t s);
+                              float* tau, int block, int tiles, cudaStream_t s);
+cudaError_t launch_crba_level(const ModelView& mv, int64_t B, const float* q, float* M, int block, int tiles,
+                              cudaStream_t s);
 cudaError_t launch_aba_level(const ModelView& mv, int64_t B, const float* q, const float* qd, const float* tau,
-                             float* qdd, int block, cudaStream_t s);
-cudaError_t launch_eval_level(const ModelView& mv, int64_t B, const EvalArgs& a, int block, cudaStream_t s);
+                             float* qdd, int block, int tiles, cudaStream_t s);
+cudaError_t launch_eval_level(const ModelView& mv, int64_t B, const EvalArgs& a, int block, int tiles,
+                              cudaStream_t s);
 
 // Adjoints (adjoint.cu). scratch: vjp_scratch_floats(n, B) floats of device
 // memory for the per-block partial sums of thetabar (and the loss).

@@ -1,7 +1,9 @@
-// Level-parallel kernels (bodies in level.cuh): 32 environments per block,
-// W = blockDim.x / 32 warps splitting each level's bodies.
+// Level-parallel kernels (bodies in level.cuh): tiles of 32 environments,
+// W warps per tile splitting each tree level's bodies. A block is one tile
+// (1-D, 32 W threads) or T tiles (3-D, (32, T, W); see warp_id()).
 //
-// Shared memory: model | input tile (rows x 32) | per-body state (F x n x 32).
+// Shared memory: model | per tile: input rows (rows x 32) | per-body state
+// (F x n x 32); `stride` floats per tile.
 #include "launch.h"
 #include "level.cuh"
 
@@ -10,13 +12,15 @@ namespace {
 
 __device__ __forceinline__ float* level_tile(float4* smem, int n) { return smem_tile(smem, n); }
 
-#define FST_LEVEL_PROLOGUE(rows, F)                                          \
-  extern __shared__ float4 smem[];                                          \
-  float* tile = level_tile(smem, mv.n);                                     \
-  const LaneState S{tile + (rows) * kLaneEnvs, (F)};                        \
-  const int lane = threadIdx.x & 31;                                        \
-  const int64_t e = (int64_t)blockIdx.x * kLaneEnvs + lane;                 \
+#define FST_LEVEL_PROLOGUE_S(rows, F, stride)                                            \
+  extern __shared__ float4 smem[];                                                       \
+  float* tile = level_tile(smem, mv.n) + (size_t)threadIdx.y * (stride);                 \
+  const LaneState S{tile + (rows) * kLaneEnvs, (F)};                                     \
+  const int lane = threadIdx.x & 31;                                                     \
+  const int64_t e = ((int64_t)blockIdx.x * blockDim.y + threadIdx.y) * kLaneEnvs + lane; \
   const bool act = e < B
+
+#define FST_LEVEL_PROLOGUE(rows, F) FST_LEVEL_PROLOGUE_S(rows, F, ((rows) + (F) * mv.n) * kLaneEnvs)
 
 #define FST_LEVEL_READY                            \
   const SmemModel sm = stage_model(mv, smem);      \
@@ -110,7 +114,8 @@ __global__ void __launch_bounds__(256) aba_level_pin_kernel(ModelView mv, int64_
 __global__ void __launch_bounds__(256) eval_level_kernel(ModelView mv, int64_t B, EvalArgs a) {
   const int role = a.roles[blockIdx.y];
   const int F = role == ROLE_ABA ? kAbaState : role == ROLE_CRBA ? kCrbaState : role == ROLE_RNEA ? kRneaState : kFkState;
-  FST_LEVEL_PROLOGUE(mv.nq + 2 * mv.nv, F);
+  // tiles are sized for the largest role (ABA), as the launch allocates them
+  FST_LEVEL_PROLOGUE_S(mv.nq + 2 * mv.nv, F, (mv.nq + 2 * mv.nv + kAbaState * mv.n) * kLaneEnvs);
   stage_block_rows(tile, a.q, mv.nq, B, e);
   if (role == ROLE_RNEA) {
     stage_block_rows(tile + mv.nq * kLaneEnvs, a.qd, mv.nv, B, e);
@@ -140,54 +145,67 @@ __global__ void __launch_bounds__(256) eval_level_kernel(ModelView mv, int64_t B
   }
 }
 
-size_t level_smem(const ModelView& mv, int rows, int F) {
-  return smem_bytes(mv.n) + (size_t)rows * kLaneEnvs * sizeof(float) + (size_t)F * mv.n * kLaneEnvs * sizeof(float);
+// bytes of shared memory of one tile: input rows and per-body state
+size_t level_tile_bytes(const ModelView& mv, int rows, int F) {
+  return (size_t)rows * kLaneEnvs * sizeof(float) + (size_t)F * mv.n * kLaneEnvs * sizeof(float);
 }
 
+// `block` threads (a multiple of 32 T) as `tiles` tiles of block / (32 T)
+// warps each: a 1-D block for one tile, (32, T, W) for several.
 template <typename K, typename... A>
-cudaError_t go(K* kernel, const ModelView& mv, int64_t B, size_t sh, int block, unsigned gy, cudaStream_t s,
-               A... args) {
-  if (sh > kLevelSmemLimit) return cudaErrorInvalidConfiguration;
+cudaError_t go(K* kernel, const ModelView& mv, int64_t B, size_t sh, int block, int tiles, unsigned gy,
+               cudaStream_t s, A... args) {
+  if (sh > kLevelSmemLimit || tiles < 1 || block < 32 * tiles || block % (32 * tiles))
+    return cudaErrorInvalidConfiguration;
   prepare(kernel, sh);
-  kernel<<<dim3((unsigned)((B + kLaneEnvs - 1) / kLaneEnvs), gy), block, sh, s>>>(mv, B, args...);
+  const int64_t envs = (int64_t)kLaneEnvs * tiles;
+  const dim3 blk = tiles == 1 ? dim3(block) : dim3(32, tiles, block / (32 * tiles));
+  kernel<<<dim3((unsigned)((B + envs - 1) / envs), gy), blk, sh, s>>>(mv, B, args...);
   return cudaGetLastError();
 }
 
 }  // namespace
 
-size_t level_smem_needed(const ModelView& mv, int kind) {
+size_t level_smem_needed(const ModelView& mv, int kind, int tiles) {
+  size_t t;
   switch (kind) {
     case LEVEL_FK:
     case LEVEL_JAC:
-      return level_smem(mv, mv.nq, kFkState);
+      t = level_tile_bytes(mv, mv.nq, kFkState);
+      break;
     case LEVEL_RNEA:
-      return level_smem(mv, mv.nq + 2 * mv.nv, kRneaState);
+      t = level_tile_bytes(mv, mv.nq + 2 * mv.nv, kRneaState);
+      break;
     case LEVEL_CRBA:
-      return level_smem(mv, mv.nq, kCrbaState);
-    case LEVEL_ABA:
-      return level_smem(mv, mv.nq + 2 * mv.nv, kAbaState);
-    default:
-      return level_smem(mv, mv.nq + 2 * mv.nv, kAbaState);
+      t = level_tile_bytes(mv, mv.nq, kCrbaState);
+      break;
+    default:  // ABA, and eval (its tiles are sized for the ABA role)
+      t = level_tile_bytes(mv, mv.nq + 2 * mv.nv, kAbaState);
+      break;
   }
+  return smem_bytes(mv.n) + (size_t)tiles * t;
 }
 
-cudaError_t launch_fk_level(const ModelView& mv, int64_t B, const float* q, float* poses, int block, cudaStream_t s) {
-  return go(fk_level_kernel, mv, B, level_smem_needed(mv, LEVEL_FK), block, 1, s, q, poses);
+cudaError_t launch_fk_level(const ModelView& mv, int64_t B, const float* q, float* poses, int block, int tiles,
+                            cudaStream_t s) {
+  return go(fk_level_kernel, mv, B, level_smem_needed(mv, LEVEL_FK, tiles), block, tiles, 1, s, q, poses);
 }
 cudaError_t launch_jac_level(const ModelView& mv, int64_t B, const float* q, const LinkList& links, float* J,
-                             int block, cudaStream_t s) {
-  return go(jac_level_kernel, mv, B, level_smem_needed(mv, LEVEL_JAC), block, 1, s, q, links, (float*)nullptr, J);
+                             int block, int tiles, cudaStream_t s) {
+  return go(jac_level_kernel, mv, B, level_smem_needed(mv, LEVEL_JAC, tiles), block, tiles, 1, s, q, links,
+            (float*)nullptr, J);
 }
 cudaError_t launch_rnea_level(const ModelView& mv, int64_t B, const float* q, const float* qd, const float* qdd,
-                              float* tau, int block, cudaStream_t s) {
-  return go(rnea_level_kernel, mv, B, level_smem_needed(mv, LEVEL_RNEA), block, 1, s, q, qd, qdd, tau);
+                              float* tau, int block, int tiles, cudaStream_t s) {
+  return go(rnea_level_kernel, mv, B, level_smem_needed(mv, LEVEL_RNEA, tiles), block, tiles, 1, s, q, qd, qdd, tau);
 }
-cudaError_t launch_crba_level(const ModelView& mv, int64_t B, const float* q, float* M, int block, cudaStream_t s) {
-  return go(crba_level_kernel, mv, B, level_smem_needed(mv, LEVEL_CRBA), block, 1, s, q, M);
+cudaError_t launch_crba_level(const ModelView& mv, int64_t B, const float* q, float* M, int block, int tiles,
+                              cudaStream_t s) {
+  return go(crba_level_kernel, mv, B, level_smem_needed(mv, LEVEL_CRBA, tiles), block, tiles, 1, s, q, M);
 }
 cudaError_t launch_aba_level(const ModelView& mv, int64_t B, const float* q, const float* qd, const float* tau,
-                             float* qdd, int block, cudaStream_t s) {
-  return go(aba_level_kernel, mv, B, level_smem_needed(mv, LEVEL_ABA), block, 1, s, q, qd, tau, qdd);
+                             float* qdd, int block, int tiles, cudaStream_t s) {
+  return go(aba_level_kernel, mv, B, level_smem_needed(mv, LEVEL_ABA, tiles), block, tiles, 1, s, q, qd, tau, qdd);
 }
 cudaError_t launch_aba_level_pinned(const ModelView& mv, int64_t B, const float* q, const float* qd,
                                     const float* tau, float* qdd, int block, const PinArgs& p, cudaStream_t s) {
@@ -201,8 +219,10 @@ cudaError_t launch_aba_level_pinned(const ModelView& mv, int64_t B, const float*
   return cudaGetLastError();
 }
 
-cudaError_t launch_eval_level(const ModelView& mv, int64_t B, const EvalArgs& a, int block, cudaStream_t s) {
-  return go(eval_level_kernel, mv, B, level_smem_needed(mv, LEVEL_EVAL), block, (unsigned)a.n_roles, s, a);
+cudaError_t launch_eval_level(const ModelView& mv, int64_t B, const EvalArgs& a, int block, int tiles,
+                              cudaStream_t s) {
+  return go(eval_level_kernel, mv, B, level_smem_needed(mv, LEVEL_EVAL, tiles), block, tiles, (unsigned)a.n_roles, s,
+            a);
 }
 
 }  // namespace fst

@@ -104,11 +104,19 @@ constexpr int kRneaState = 30;   // X 12 | v 6 | a 6 | f 6
 constexpr int kCrbaState = 32;   // X 12 | Ic 10 | contribution 10
 constexpr int kAbaState = 59;    // X 12 | va 6 | c 6 | IA 21 | pA 6 | U 6 | invD | u
 
-// Stages `rows` rows of this block's 32 environments (zeros past B);
+// Warps of one tile of 32 environments (lane = threadIdx.x & 31). A 1-D
+// block of 32 W threads is one tile of W warps. A 3-D block (32, T, W) holds
+// T tiles (threadIdx.y) of W warps (threadIdx.z) each; its hardware warp k
+// belongs to tile k mod T, so each tile's first warp (the one that owns the
+// first body of every level, the busiest) sits on its own SM sub-partition.
+__device__ __forceinline__ int warp_id() { return (threadIdx.x >> 5) + (blockDim.x >> 5) * threadIdx.z; }
+__device__ __forceinline__ int n_warps() { return (blockDim.x >> 5) * blockDim.z; }
+
+// Stages `rows` rows of this tile's 32 environments (zeros past B);
 // call from every thread, then cp_async_wait_all() and __syncthreads().
 __device__ __forceinline__ void stage_block_rows(float* tile, const float* __restrict__ src, int rows, int64_t B,
                                                  int64_t e) {
-  const int W = blockDim.x >> 5, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int W = n_warps(), w = warp_id(), lane = threadIdx.x & 31;
   for (int r = w; r < rows; r += W) {
     float* d = tile + (r << 5) + lane;
     if (e < B)
@@ -131,8 +139,6 @@ __device__ __forceinline__ void stage_block_rows(float* tile, const float* __res
 #define FST_FOR_MY_BODIES(tp, l, k) for (int k = (tp).level_begin(l) + w; k < (tp).level_begin((l) + 1); k += W)
 #endif
 
-__device__ __forceinline__ int warp_id() { return threadIdx.x >> 5; }
-__device__ __forceinline__ int n_warps() { return blockDim.x >> 5; }
 
 // ---- forward kinematics -------------------------------------------------------
 template <class TP>

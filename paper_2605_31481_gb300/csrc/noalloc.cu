@@ -21,7 +21,13 @@
 //    ordering between them) race on the array and give wrong theta_bar;
 //  * the first call on a device looks up the array's device address (one
 //    cudaGetSymbolAddress with that device current) and caches it; make that
-//    first call before any stream capture.
+//    first call before any stream capture. The cached address is valid for
+//    the life of the device's primary context: a process that calls
+//    cudaDeviceReset must not call this entry point afterwards.
+//
+// After these checks the call is fst_rnea_vjp with the built-in array as its
+// scratch, so it runs the same kernel (generic or specialised) that
+// fst_rnea_vjp would run for the model and gives the same results.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -63,8 +69,11 @@ extern "C" fst_status fst_rnea_vjp_noalloc(const fst_model* m, int64_t B, const 
                                            const float* qdd, const float* theta, const float* tau_bar, float* q_bar,
                                            float* qd_bar, float* qdd_bar, float* theta_bar, void* stream) {
   static const char* fn = "fst_rnea_vjp_noalloc";
-  if (!m) return arg_error(std::string(fn) + ": null model");
-  if (B < 0) return arg_error(std::string(fn) + ": B must be >= 0");
+  bool skip = false;
+  // the checks of every entry point (model, B <= 2^31 - 1, current device),
+  // before anything touches the device
+  const fst_status st = fst::check_call(fn, m, B, &skip);
+  if (st != FST_OK) return st;
   const size_t need = fst::vjp_scratch_floats(m->n, B);
   if (theta_bar && need > kStaticScratchFloats) {
     std::ostringstream os;
@@ -72,28 +81,23 @@ extern "C" fst_status fst_rnea_vjp_noalloc(const fst_model* m, int64_t B, const 
        << kStaticScratchFloats << " (use fst_rnea_vjp with a caller-provided scratch buffer)";
     return arg_error(os.str());
   }
-  if (B == 0 || m->nv == 0) {
-    // nothing to differentiate: theta_bar is still overwritten (with zeros), as fst_rnea_vjp does
-    if (theta_bar && m->n) {
-      const cudaError_t zerr = cudaMemsetAsync(theta_bar, 0, sizeof(float) * m->n * 10, (cudaStream_t)stream);
-      if (zerr != cudaSuccess) return fst::set_error(FST_ERR_CUDA, std::string(fn) + ": " + cudaGetErrorString(zerr));
-    }
-    return FST_OK;
-  }
-  int dev = -1;
-  cudaError_t err = cudaGetDevice(&dev);
-  if (err != cudaSuccess) return fst::set_error(FST_ERR_CUDA, std::string(fn) + ": " + cudaGetErrorString(err));
-  if (dev != m->device || dev < 0 || dev >= kMaxDevices)
-    return arg_error(std::string(fn) + ": the current device is not the model's device");
-  if (!q || !qd || !qdd || !tau_bar) return arg_error(std::string(fn) + ": null q, qd, qdd or tau_bar");
+  if (!skip && m->nv > 0 && (!q || !qd || !qdd || !tau_bar))
+    return arg_error(std::string(fn) + ": null q, qd, qdd or tau_bar");
   float* scratch = nullptr;
   if (theta_bar) {
+    int dev = -1;
+    cudaError_t err = cudaGetDevice(&dev);
+    if (err != cudaSuccess) return fst::set_error(FST_ERR_CUDA, std::string(fn) + ": " + cudaGetErrorString(err));
+    if (dev < 0 || dev >= kMaxDevices) {
+      std::ostringstream os;
+      os << fn << ": device ordinal " << dev << " is beyond the " << kMaxDevices
+         << " devices this entry point keeps a scratch address for";
+      return arg_error(os.str());
+    }
     err = static_scratch(dev, &scratch);
     if (err != cudaSuccess)
       return fst::set_error(FST_ERR_CUDA, std::string(fn) + ": cudaGetSymbolAddress: " + cudaGetErrorString(err));
   }
-  err = fst::launch_rnea_vjp(fst::view_of(m, theta), B, q, qd, qdd, tau_bar, q_bar, qd_bar, qdd_bar, theta_bar,
-                             scratch, (cudaStream_t)stream);
-  if (err != cudaSuccess) return fst::set_error(FST_ERR_CUDA, std::string(fn) + ": " + cudaGetErrorString(err));
-  return FST_OK;
+  return fst_rnea_vjp(m, B, q, qd, qdd, theta, tau_bar, q_bar, qd_bar, qdd_bar, theta_bar, scratch,
+                      kStaticScratchFloats * sizeof(float), stream);
 }

@@ -64,57 +64,119 @@ __device__ __forceinline__ void fk_env(const TP& tp, const Col& q, float* __rest
   world_poses<NB>(tp, q, Rw, pw, poses, B, e);
 }
 
-// Jacobian columns straight from the world poses (paper Sec. 3.4, Eq. 6):
-// w = R_k S_w, v = R_k S_v + p_k x w, i.e. [o_k x z_k; z_k] for a revolute
-// joint with o_k on its axis. Rows are [v; w]; off-path DOFs are zero.
+// Body k's columns of one link's Jacobian straight from its world pose
+// (paper Sec. 3.4, Eq. 6): w = R_k S_w, v = R_k S_v + p_k x w, i.e.
+// [o_k x z_k; z_k] for a revolute joint with o_k on its axis. Rows are
+// [v; w]; a DOF off the link's support path gets a zero column. Jl points at
+// the link's [6][stride] block for this environment and the body's first
+// column is `col`.
+template <class TP>
+__device__ __forceinline__ void jac_column(const TP& tp, int k, const float* Rk, const float* pk, bool on_path,
+                                           int stride, int col, float* __restrict__ Jl, int64_t B) {
+  const BodyI bk = tp.I(k);
+  const int nvk = nv_of(bk.type);
+  if (nvk == 0) return;
+  const f3 p = f3{pk[0], pk[1], pk[2]};
+  if (nvk == 1) {
+    float c6[6] = {0, 0, 0, 0, 0, 0};
+    if (on_path) {
+      const SV s = S_of(tp.C(k));
+      const f3 w = Rmul(Rk, s.w);
+      const f3 v = Rmul(Rk, s.v) + cross(p, w);
+      c6[0] = v.x; c6[1] = v.y; c6[2] = v.z;
+      c6[3] = w.x; c6[4] = w.y; c6[5] = w.z;
+    }
+#pragma unroll
+    for (int r = 0; r < 6; ++r) Jl[((int64_t)r * stride + col) * B] = c6[r];
+  } else {  // free base: velocity [v; w] in body coordinates
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+      float c6[6] = {0, 0, 0, 0, 0, 0};
+      if (on_path) {
+        const int a = j % 3;
+        const f3 Re = f3{Rk[a], Rk[3 + a], Rk[6 + a]};  // R e_a
+        if (j < 3) {
+          c6[0] = Re.x; c6[1] = Re.y; c6[2] = Re.z;
+        } else {
+          const f3 v = cross(p, Re);
+          c6[0] = v.x; c6[1] = v.y; c6[2] = v.z;
+          c6[3] = Re.x; c6[4] = Re.y; c6[5] = Re.z;
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < 6; ++r) Jl[((int64_t)r * stride + col + j) * B] = c6[r];
+    }
+  }
+}
+
+// Every link's Jacobian from the world poses Rw/pw. Full layout: link l's
+// [6][nv] block at l * 6 nv, structural zeros included. Packed (PK non-null,
+// see PackedJ): only the columns of the DOFs on link l's support path.
+
 template <int NB, class TP>
-__device__ __forceinline__ void jac_env(const TP& tp, const Col& q, int nv, const LinkList& links,
-                                        float* __restrict__ poses, float* __restrict__ J, int64_t B, int64_t e) {
-  float Rw[NB][9];
-  float pw[NB][3];
-  world_poses<NB>(tp, q, Rw, pw, poses, B, e);
+__device__ __forceinline__ void jac_from_world(const TP& tp, const float (&Rw)[NB][9], const float (&pw)[NB][3], int nv,
+                                               const LinkList& links, const PackedJ* PK, float* __restrict__ J,
+                                               int64_t B, int64_t e) {
   for (int l = 0; l < links.n; ++l) {
     const unsigned long long mask = tp.C(links.idx[l]).anc;
-    float* Jl = J + (int64_t)l * 6 * nv * B + e;
-    FST_UNROLL
-    for (int k = 0; k < tp.n(); ++k) {
-      const BodyI bk = tp.I(k);
-      const int nvk = nv_of(bk.type);
-      if (nvk == 0) continue;
-      const bool on_path = (mask >> k) & 1ull;
-      const f3 p = f3{pw[k][0], pw[k][1], pw[k][2]};
-      if (nvk == 1) {
-        float col[6] = {0, 0, 0, 0, 0, 0};
-        if (on_path) {
-          const SV s = S_of(tp.C(k));
-          const f3 w = Rmul(Rw[k], s.w);
-          const f3 v = Rmul(Rw[k], s.v) + cross(p, w);
-          col[0] = v.x; col[1] = v.y; col[2] = v.z;
-          col[3] = w.x; col[4] = w.y; col[5] = w.z;
-        }
-#pragma unroll
-        for (int r = 0; r < 6; ++r) Jl[((int64_t)r * nv + bk.vi) * B] = col[r];
-      } else {  // free base: velocity [v; w] in body coordinates
-#pragma unroll
-        for (int j = 0; j < 6; ++j) {
-          float col[6] = {0, 0, 0, 0, 0, 0};
-          if (on_path) {
-            const int a = j % 3;
-            const f3 Re = f3{Rw[k][a], Rw[k][3 + a], Rw[k][6 + a]};  // R e_a
-            if (j < 3) {
-              col[0] = Re.x; col[1] = Re.y; col[2] = Re.z;
-            } else {
-              const f3 v = cross(p, Re);
-              col[0] = v.x; col[1] = v.y; col[2] = v.z;
-              col[3] = Re.x; col[4] = Re.y; col[5] = Re.z;
-            }
-          }
-#pragma unroll
-          for (int r = 0; r < 6; ++r) Jl[((int64_t)r * nv + bk.vi + j) * B] = col[r];
-        }
+    if (!PK) {
+      float* Jl = J + (int64_t)l * 6 * nv * B + e;
+      FST_UNROLL
+      for (int k = 0; k < tp.n(); ++k) jac_column(tp, k, Rw[k], pw[k], (mask >> k) & 1ull, nv, tp.I(k).vi, Jl, B);
+    } else {
+      float* Jl = J + (int64_t)PK->off[l] * B + e;
+      int col = 0;
+      FST_UNROLL
+      for (int k = 0; k < tp.n(); ++k) {
+        if (!((mask >> k) & 1ull)) continue;
+        jac_column(tp, k, Rw[k], pw[k], true, PK->cols[l], col, Jl, B);
+        col += nv_of(tp.I(k).type);
       }
     }
   }
+}
+
+template <int NB, class TP>
+__device__ __forceinline__ void jac_env(const TP& tp, const Col& q, int nv, const LinkList& links,
+                                        float* __restrict__ poses, float* __restrict__ J, int64_t B, int64_t e,
+                                        const PackedJ* PK = nullptr) {
+  float Rw[NB][9];
+  float pw[NB][3];
+  world_poses<NB>(tp, q, Rw, pw, poses, B, e);
+  jac_from_world<NB>(tp, Rw, pw, nv, links, PK, J, B, e);
+}
+
+// World poses (and, when J is set, the Jacobian columns) from joint
+// transforms already computed by a dynamics sweep, so a fused kernel
+// evaluates each joint's transform (paper Eq. 4-5) once for all of its
+// operators. The same compositions as world_poses, so the results are
+// bit-identical to fk_env / jac_env.
+template <int NB, class TP>
+__device__ __forceinline__ void kin_from_X(const TP& tp, const Xf (&X)[NB], int nv, const LinkList& links,
+                                           float* __restrict__ poses, float* __restrict__ J, int64_t B, int64_t e,
+                                           const PackedJ* PK = nullptr) {
+  float Rw[NB][9];
+  float pw[NB][3];
+  FST_UNROLL
+  for (int i = 0; i < tp.n(); ++i) {
+    const int par = tp.I(i).parent;
+    if (par < 0) {
+#pragma unroll
+      for (int k = 0; k < 9; ++k) Rw[i][k] = X[i].R[k];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) pw[i][k] = X[i].t[k];
+    } else {
+      compose(Rw[par], pw[par], X[i], Rw[i], pw[i]);
+    }
+    if (poses) {
+      float* out = poses + (int64_t)i * 12 * B + e;
+#pragma unroll
+      for (int k = 0; k < 9; ++k) out[(int64_t)k * B] = Rw[i][k];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) out[(int64_t)(9 + k) * B] = pw[i][k];
+    }
+  }
+  if (J) jac_from_world<NB>(tp, Rw, pw, nv, links, PK, J, B, e);
 }
 
 // Forward sweep of RNEA (paper Sec. 3.3, Eq. 7 for the velocities):
@@ -168,13 +230,40 @@ __device__ __forceinline__ void rnea_env(const TP& tp, SV a0, const Col& q, cons
   rnea_backward<NB>(tp, X, f, tau, B, e);
 }
 
+// Where CRBA writes M for one environment: the full symmetric [nv][nv]
+// matrix, or (PACKED) its upper triangle row by row, element (r, c), r <= c,
+// at row r nv - r (r - 1) / 2 + c - r of a [nv (nv + 1) / 2][B] array.
+template <bool PACKED>
+struct MOut {
+  float* p;  // M + e
+  int nv;
+  int64_t B;
+  __device__ __forceinline__ int64_t row(int r, int c) const {
+    if (!PACKED) return (int64_t)r * nv + c;
+    return (int64_t)r * nv - (int64_t)r * (r - 1) / 2 + (c - r);
+  }
+  // M_rc = M_cr = x
+  __device__ __forceinline__ void sym(int r, int c, float x) const {
+    if (PACKED) {
+      p[row(r < c ? r : c, r < c ? c : r) * B] = x;
+    } else {
+      p[row(r, c) * B] = x;
+      p[row(c, r) * B] = x;
+    }
+  }
+  // M_rc = x where the caller also stores M_cr (a diagonal block)
+  __device__ __forceinline__ void one(int r, int c, float x) const {
+    if (!PACKED || r <= c) p[row(r, c) * B] = x;
+  }
+};
+
 // Composite-rigid-body algorithm: composite inertias leaf to root
 // (I^c_p += X_i^T I^c_i X_i, kept as 10 parameters because a sum of rigid
 // bodies is a rigid body), then F = I^c_i S_i carried up the support path:
 // M_ij = S_j^T F. Ancestors have smaller indices than their descendants, so
 // walking j = i-1 .. 0 over the support-path bitmask visits the path from i
 // to the root in order. Structural zeros are written too.
-template <int NB, class TP>
+template <int NB, bool PACKED = false, class TP>
 __device__ __forceinline__ void crba_env(const TP& tp, const Col& q, int nv, float* __restrict__ M, int64_t B,
                                          int64_t e) {
   Xf X[NB];
@@ -189,13 +278,13 @@ __device__ __forceinline__ void crba_env(const TP& tp, const Col& q, int nv, flo
     const int p = tp.I(i).parent;
     if (p >= 0) in_add(Ic[p], in_to_parent(X[i], Ic[i]));
   }
-  float* Me = M + e;
+  const MOut<PACKED> Me{M + e, nv, B};
   FST_UNROLL
   for (int i = 0; i < tp.n(); ++i) {
     const BodyI bi = tp.I(i);
     if (bi.type == FST_JOINT_REVOLUTE || bi.type == FST_JOINT_PRISMATIC) {
       SV F = in_mul(Ic[i], S_of(tp.C(i)));
-      Me[((int64_t)bi.vi * nv + bi.vi) * B] = dot(S_of(tp.C(i)), F);
+      Me.one(bi.vi, bi.vi, dot(S_of(tp.C(i)), F));
       const unsigned long long anc = tp.C(i).anc;
       int k = i;
       FST_UNROLL
@@ -205,16 +294,11 @@ __device__ __forceinline__ void crba_env(const TP& tp, const Col& q, int nv, flo
         k = j;
         const BodyI bj = tp.I(j);
         if (bj.type == FST_JOINT_REVOLUTE || bj.type == FST_JOINT_PRISMATIC) {
-          const float mij = dot(S_of(tp.C(j)), F);
-          Me[((int64_t)bi.vi * nv + bj.vi) * B] = mij;
-          Me[((int64_t)bj.vi * nv + bi.vi) * B] = mij;
+          Me.sym(bi.vi, bj.vi, dot(S_of(tp.C(j)), F));
         } else if (bj.type == FST_JOINT_FREE) {
           const float col[6] = {F.v.x, F.v.y, F.v.z, F.w.x, F.w.y, F.w.z};
 #pragma unroll
-          for (int r = 0; r < 6; ++r) {
-            Me[((int64_t)(bj.vi + r) * nv + bi.vi) * B] = col[r];
-            Me[((int64_t)bi.vi * nv + bj.vi + r) * B] = col[r];
-          }
+          for (int r = 0; r < 6; ++r) Me.sym(bj.vi + r, bi.vi, col[r]);
         }
       }
     } else if (bi.type == FST_JOINT_FREE) {
@@ -231,7 +315,7 @@ __device__ __forceinline__ void crba_env(const TP& tp, const Col& q, int nv, flo
 #pragma unroll
       for (int r = 0; r < 6; ++r)
 #pragma unroll
-        for (int cc = 0; cc < 6; ++cc) Me[((int64_t)(bi.vi + r) * nv + bi.vi + cc) * B] = blk[r][cc];
+        for (int cc = 0; cc < 6; ++cc) Me.one(bi.vi + r, bi.vi + cc, blk[r][cc]);
     }
   }
   FST_UNROLL
@@ -246,10 +330,7 @@ __device__ __forceinline__ void crba_env(const TP& tp, const Col& q, int nv, flo
       const int nj = nv_of(bj.type);
       if (nj == 0 || ((anc_i >> j) & 1ull)) continue;
       for (int r = 0; r < ni; ++r)
-        for (int cc = 0; cc < nj; ++cc) {
-          Me[((int64_t)(bi.vi + r) * nv + bj.vi + cc) * B] = 0.f;
-          Me[((int64_t)(bj.vi + cc) * nv + bi.vi + r) * B] = 0.f;
-        }
+        for (int cc = 0; cc < nj; ++cc) Me.sym(bi.vi + r, bj.vi + cc, 0.f);
     }
   }
 }

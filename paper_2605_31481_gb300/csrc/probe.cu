@@ -1,0 +1,55 @@
+// fst_fp32_probe: a throughput probe of the FP32 fused multiply-add pipes,
+// the denominator of the roofline fractions that the operators report
+// against arithmetic (their flops are FP32 adds, multiplies and FMAs).
+//
+// Every thread runs kChains independent FMA chains (a = a * m + c, with m
+// and c kernel arguments the compiler cannot fold), so each SM sub-partition
+// always has independent FMAs to issue while earlier ones are in flight.
+// The grid is a whole number of blocks per SM. The caller times the launch
+// with CUDA events and divides the flop count this call returns by it.
+#include <cuda_runtime.h>
+
+#include <string>
+
+#include "fst_internal.h"
+
+namespace {
+
+constexpr int kChains = 16;
+constexpr int kThreads = 256;
+
+__global__ void __launch_bounds__(kThreads) fma_probe_kernel(int iters, float m, float c, float* __restrict__ out) {
+  float a[kChains];
+#pragma unroll
+  for (int k = 0; k < kChains; ++k) a[k] = (float)(threadIdx.x + k);
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int k = 0; k < kChains; ++k) a[k] = fmaf(a[k], m, c);
+  }
+  float s = 0.f;
+#pragma unroll
+  for (int k = 0; k < kChains; ++k) s += a[k];
+  out[(int64_t)blockIdx.x * kThreads + threadIdx.x] = s;
+}
+
+}  // namespace
+
+extern "C" fst_status fst_fp32_probe(int32_t blocks_per_sm, int32_t iters, float* out, size_t out_bytes,
+                                     double* flops, void* stream) {
+  static const char* fn = "fst_fp32_probe";
+  if (blocks_per_sm < 1 || blocks_per_sm > 64 || iters < 1 || !out || !flops)
+    return fst::set_error(FST_ERR_INVALID_ARG, std::string(fn) + ": bad argument");
+  int dev = -1, sms = 0;
+  cudaError_t err = cudaGetDevice(&dev);
+  if (err == cudaSuccess) err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (err != cudaSuccess) return fst::set_error(FST_ERR_CUDA, std::string(fn) + ": " + cudaGetErrorString(err));
+  const int64_t blocks = (int64_t)sms * blocks_per_sm;
+  if (out_bytes < (size_t)blocks * kThreads * sizeof(float))
+    return fst::set_error(FST_ERR_INVALID_ARG, std::string(fn) + ": out smaller than SMs x blocks_per_sm x 256 floats");
+  // m and c keep every chain bounded (|a| converges to c / (1 - m))
+  fma_probe_kernel<<<(unsigned)blocks, kThreads, 0, (cudaStream_t)stream>>>(iters, 0.999f, 0.001f, out);
+  err = cudaGetLastError();
+  if (err != cudaSuccess) return fst::set_error(FST_ERR_CUDA, std::string(fn) + ": " + cudaGetErrorString(err));
+  *flops = 2.0 * kChains * (double)iters * (double)blocks * kThreads;
+  return FST_OK;
+}

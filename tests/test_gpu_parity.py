@@ -183,17 +183,20 @@ def test_fused_eval_is_bitwise_equal_to_per_op_calls(torch_cuda, name):
 
 
 @pytest.mark.parametrize("name", list(TREES))
-@pytest.mark.parametrize("block", [32, 64, 256])
-def test_level_parallel_variant_matches_oracle(torch_cuda, name, block):
-    """Level-parallel kernels (warps split each tree level; 32 environments
-    per block) on every tree, with 1, 2 and 8 warps per block."""
+@pytest.mark.parametrize("variant,block", [("level", 32), ("level", 64), ("level", 256), ("level2", 64),
+                                           ("level2", 256)])
+def test_level_parallel_variant_matches_oracle(torch_cuda, name, variant, block):
+    """Level-parallel kernels (warps split each tree level) on every tree:
+    one tile of 32 environments per block with 1, 2 and 8 warps, and two
+    tiles per block with 1 and 4 warps each (a 333-environment batch leaves
+    the last block's second tile partly and wholly past B)."""
     import torch
     from paper_2605_31481_gb300 import api
     tree = TREES[name]()
     B = 333
     s = w.random_state(tree, B, seed=6)
     m = api.Model(tree)
-    m.set_launch(["fk", "jacobian", "rnea", "crba", "aba", "eval"], block, "level")
+    m.set_launch(["fk", "jacobian", "rnea", "crba", "aba", "eval"], block, variant)
     q, qd, qdd, tau = (to_soa_cuda(s[k], torch) for k in ("q", "qd", "qdd", "tau"))
     ee = list(tree.ee)
     out = {"poses": api.fk(m, q), "J": api.jacobian(m, q, ee), "tau": api.rnea(m, q, qd, qdd), "M": api.crba(m, q),
@@ -201,7 +204,7 @@ def test_level_parallel_variant_matches_oracle(torch_cuda, name, block):
     ev = api.eval(m, q, qd, qdd, tau, fk=True, links=ee, rnea=True, crba=True, aba=True)
     torch.cuda.synchronize()
     ref = _oracle_all(tree, s, ee)
-    _assert_close({k: from_soa(v) for k, v in out.items()}, ref, f"level/{name}/{block}")
+    _assert_close({k: from_soa(v) for k, v in out.items()}, ref, f"{variant}/{name}/{block}")
     for k in out:
         assert torch.equal(ev[k], out[k]), k
 

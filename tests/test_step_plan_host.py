@@ -42,8 +42,7 @@ def fakes(monkeypatch, tmp_path):
     tuned["eval"] = {"variant": "specialized", "block": 128, "us": 17.0, "candidates": cands}
     monkeypatch.setattr(autotune, "tune", lambda *a, **k: tuned)
     monkeypatch.setattr(autotune.torch.cuda, "Stream", lambda *a, **k: object())
-    monkeypatch.setattr(autotune, "Buffers", lambda *a, **k: type("B", (), {"q": 0, "qd": 0, "qdd": 0, "tau": 0,
-                                                                            "out": {}})())
+    monkeypatch.setattr(autotune, "ColdSets", lambda *a, **k: type("C", (), {"R": 1, "sets": [{}]})())
     monkeypatch.setattr(autotune, "_key", lambda model, kind, B: f"{model.fingerprint}|{kind}|{B}")
     calls = []
 
@@ -58,7 +57,7 @@ def fakes(monkeypatch, tmp_path):
         return t
 
     current = {}
-    monkeypatch.setattr(autotune, "graph_time_us", fake_time)
+    monkeypatch.setattr(autotune.StepPlan, "_time", lambda self, cold: fake_time(None))
     monkeypatch.setattr(autotune.StepPlan, "__call__", lambda self, *a: None)
     return {"current": current, "calls": calls, "carve": carve, "tmp": tmp_path}
 
@@ -83,7 +82,7 @@ def test_plan_keeps_the_fastest_combination_and_caches_it(fakes):
         n_measured = len(fakes["calls"])
         assert n_measured > 20
         cache = json.load(open(fakes["tmp"] / "tune.json"))
-        assert any(k.endswith("|plan10|4096") for k in cache)
+        assert any(k.endswith("|plan11|4096") for k in cache)
         # a second planner reads the decision back without measuring
         model2 = FakeModel()
         plan2 = autotune.StepPlan(model2, 4096)
