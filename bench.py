@@ -387,9 +387,14 @@ def run_fst(args):
     ms, value = job_rate(ms, world, B, K, dev)
 
     # end to end through the public binding, host buffers in and out
+    # the packed layouts where the plan computes M and J in fused launches
+    packed = plan.mode not in ("sequential", "concurrent")
     e2e = run_e2e(torch, fst, model, tree, B, links, st, dev, min(K, 5000), args.warmup, plan=plan,
-                  slots=args.e2e_slots, split=args.e2e_split)
+                  slots=args.e2e_slots, split=args.e2e_split, packed=packed)
     e2e["ms"], e2e_value = job_rate(e2e["ms"], world, B, e2e["steps"], dev)
+    e2e_full = run_e2e(torch, fst, model, tree, B, links, st, dev, min(K, 5000), args.warmup, plan=plan,
+                       slots=args.e2e_slots, split=args.e2e_split, packed=False)
+    e2e_full["ms"], e2e_full_value = job_rate(e2e_full["ms"], world, B, e2e_full["steps"], dev)
 
     pk = peaks()
     fp32 = measure_fp32_peak(torch, local)
@@ -453,7 +458,11 @@ def run_fst(args):
             "roofline": roof,
             "e2e": {"value": round(e2e_value, 1), "unit": "env-evals/s", "h2d_bytes_per_step": e2e["h2d"],
                     "d2h_bytes_per_step": e2e["d2h"], "steps": e2e["steps"],
-                    "pipelined_slots": e2e["slots"], "readback_chunks": e2e["readback_chunks"]},
+                    "pipelined_slots": e2e["slots"], "readback_chunks": e2e["readback_chunks"],
+                    "output_layout": e2e["layout"]},
+            "e2e_full_layout": {"value": round(e2e_full_value, 1), "unit": "env-evals/s",
+                                "h2d_bytes_per_step": e2e_full["h2d"], "d2h_bytes_per_step": e2e_full["d2h"],
+                                "steps": e2e_full["steps"]},
             "gpu_launches": K * {"fused": 1, "hybrid": 2, "split": 3, "pinned": 2}.get(plan.mode, len(OPS)),
             "kernels": kernels,
             "plan": desc,
@@ -788,7 +797,7 @@ def ctypes_ptr(t):
     return ctypes.c_void_p(t.data_ptr())
 
 
-def run_e2e(torch, fst, model, tree, B, links, st, dev, K, warmup, plan=None, slots=3, split=1):
+def run_e2e(torch, fst, model, tree, B, links, st, dev, K, warmup, plan=None, slots=3, split=1, packed=False):
     """The same step through the public binding, end to end: every step
     uploads its inputs from pinned host memory, runs the step (the tuned step
     plan) and reads every output back into pinned host memory. Inputs and
@@ -797,13 +806,18 @@ def run_e2e(torch, fst, model, tree, B, links, st, dev, K, warmup, plan=None, sl
     training loop with a fixed step shape would. With slots > 1, that many
     such step graphs (each with its own buffers and stream) alternate, so one
     step's read-back overlaps the next step's upload and compute. The timed
-    region ends when the last step's outputs are on the host."""
+    region ends when the last step's outputs are on the host. packed=True
+    reads back M's upper triangle and the Jacobians' support-path columns
+    only (the packed layouts of fst_eval, the same information)."""
     nq, nv, nb, nl = tree.nq, tree.nv, tree.n_bodies, len(links)
     in_rows = {"q": nq, "qd": nv, "qdd": nv, "tau": nv}
     out_shapes = {"poses": (nb, 12, B), "J": (nl, 6, nv, B), "tau": (nv, B), "M": (nv, nv, B), "qdd": (nv, B)}
+    if packed:
+        _, j_rows, m_rows = fst.api.packed_layout(model, links)
+        out_shapes.update({"J": (j_rows, B), "M": (m_rows, B)})
     n_in = sum(in_rows.values()) * B
     n_out = sum(int(np.prod(sh)) for sh in out_shapes.values())
-    packed = np.concatenate([np.ascontiguousarray(st[k][:B].T.astype(np.float32)).ravel() for k in in_rows])
+    host_in = np.concatenate([np.ascontiguousarray(st[k][:B].T.astype(np.float32)).ravel() for k in in_rows])
 
     def views(flat, layout):
         out, off = {}, 0
@@ -817,7 +831,7 @@ def run_e2e(torch, fst, model, tree, B, links, st, dev, K, warmup, plan=None, sl
     S = []
     for _ in range(slots):
         sl = {"stream": torch.cuda.Stream(device=dev),
-              "host_in": torch.from_numpy(packed.copy()).pin_memory(),
+              "host_in": torch.from_numpy(host_in.copy()).pin_memory(),
               "dev_in": torch.empty(n_in, device=dev), "dev_out": torch.empty(n_out, device=dev),
               "host_out": torch.empty(n_out).pin_memory(),
               "copy_streams": [torch.cuda.Stream(device=dev) for _ in range(split)]}
@@ -829,10 +843,10 @@ def run_e2e(torch, fst, model, tree, B, links, st, dev, K, warmup, plan=None, sl
         sl["dev_in"].copy_(sl["host_in"], non_blocking=True)
         i = sl["in"]
         if plan is not None:
-            plan(i["q"], i["qd"], i["qdd"], i["tau"], sl["out"])
+            plan(i["q"], i["qd"], i["qdd"], i["tau"], sl["out"], packed=packed)
         else:
-            fst.eval(model, i["q"], i["qd"], i["qdd"], i["tau"], fk=True, links=links, rnea=True, crba=True, aba=True,
-                     out=sl["out"])
+            fst.api.eval(model, i["q"], i["qd"], i["qdd"], i["tau"], fk=True, links=links, rnea=True, crba=True,
+                         aba=True, out=sl["out"], packed=packed)
         if split == 1:
             sl["host_out"].copy_(sl["dev_out"], non_blocking=True)
             return
@@ -873,7 +887,7 @@ def run_e2e(torch, fst, model, tree, B, links, st, dev, K, warmup, plan=None, sl
     b.record(cur)
     torch.cuda.synchronize()
     return {"ms": a.elapsed_time(b), "h2d": n_in * 4, "d2h": n_out * 4, "slots": slots, "steps": K,
-            "readback_chunks": split}
+            "readback_chunks": split, "layout": "packed" if packed else "full"}
 
 
 # ---------------------------------------------------------------------------

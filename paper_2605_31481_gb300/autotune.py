@@ -124,13 +124,17 @@ def cold_time_us(fn, R, reps=5, trials=3):
 class ColdSets:
     """R rotating copies of a five-operator step's inputs and outputs, more
     than twice the L2 cache together, for timing step plans the way the
-    benchmark runs them (cold inputs every step)."""
+    benchmark runs them (cold inputs every step). At most MAX_SETS copies:
+    a batch so small that even that many sets fit in L2 is L2-resident in
+    use as well."""
+
+    MAX_SETS = 32
 
     def __init__(self, model, B, links):
         dev = model.device
         nq, nv, nb, nl = model.nq, model.nv, model.n_bodies, len(links)
         per = 4 * B * (nq + 3 * nv + 12 * nb + 6 * nv * nl + nv + nv * nv + nv)
-        self.R = max(2, -(-2 * L2_BYTES // per) + 1)
+        self.R = min(self.MAX_SETS, max(2, -(-2 * L2_BYTES // per) + 1))
         gen = torch.Generator(device=dev).manual_seed(1)
         r = lambda *sh: torch.randn(*sh, device=dev, generator=gen)
         self.sets = []
@@ -434,22 +438,28 @@ class StepPlan:
         for st in self.streams[:len(fns)]:
             cur.wait_stream(st)
 
-    def __call__(self, q, qd, qdd, tau, out):
+    def __call__(self, q, qd, qdd, tau, out, packed=False):
+        """One step into `out`. packed=True writes M and J in the packed
+        layouts of eval(packed=True); only the modes that compute M and J in
+        fused launches (fused, hybrid, split, pinned) have them."""
         m = self.model
+        if packed and self.mode in ("sequential", "concurrent"):
+            raise ValueError(f"the {self.mode} step plan has no packed outputs")
         if self.mode == "fused":
-            return api.eval(m, q, qd, qdd, tau, fk=True, links=self.links, rnea=True, crba=True, aba=True, out=out)
+            return api.eval(m, q, qd, qdd, tau, fk=True, links=self.links, rnea=True, crba=True, aba=True, out=out,
+                            packed=packed)
         ops = self._ops(q, qd, qdd, tau, out)
         if self.mode == "sequential":
             for op in ops:
                 op()
         elif self.mode in ("hybrid", "pinned"):
             fused = [lambda: api.eval(m, q, qd, qdd, tau, fk=True, links=self.links, rnea=True, crba=True, aba=False,
-                                      out=out)]
+                                      out=out, packed=packed)]
             self._fork(fused + [ops[4]] if self.alt else [ops[4]] + fused)
         elif self.mode == "split":
             # ABA beside the fused kernel twice: kinematics alone, RNEA with CRBA
-            fused = [lambda: api.eval(m, q, qd, qdd, tau, fk=True, links=self.links, out=out),
-                     lambda: api.eval(m, q, qd, qdd, tau, fk=False, rnea=True, crba=True, out=out)]
+            fused = [lambda: api.eval(m, q, qd, qdd, tau, fk=True, links=self.links, out=out, packed=packed),
+                     lambda: api.eval(m, q, qd, qdd, tau, fk=False, rnea=True, crba=True, out=out, packed=packed)]
             self._fork(fused + [ops[4]] if self.alt else [ops[4]] + fused)
         else:
             # longest first, so its blocks are dispatched first

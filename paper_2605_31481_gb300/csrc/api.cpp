@@ -156,15 +156,21 @@ fst_status finish(const char* fn, cudaError_t err) {
 // input rows per environment plus `P` floats per warp of reduction slots in
 // shared memory; gy = blockIdx.y extent. *nblk receives the grid's x size.
 template <typename... A>
-cudaError_t jit_go(const fst_model* m, int kind, int64_t B, int rows, int P, unsigned gy, cudaStream_t s,
-                   unsigned* nblk, A... args) {
+cudaError_t jit_go_slot(const fst_model* m, int kind, int slot, int64_t B, int rows, int P, unsigned gy,
+                        cudaStream_t s, unsigned* nblk, A... args) {
   int T = block_of(m, kind, B);
   auto smem = [&](int t) { return (size_t)rows * t * sizeof(float) + (size_t)(t / 32) * P * sizeof(float); };
   while (T > 32 && smem(T) > 96 * 1024) T /= 2;
   const dim3 grid(grid_for(B, T), gy);
   if (nblk) *nblk = grid.x;
   void* argv[] = {(void*)&args...};
-  return jit_launch(m, kind, grid, T, smem(T), s, argv);
+  return jit_launch_slot(m, kind, slot, grid, T, smem(T), s, argv);
+}
+
+template <typename... A>
+cudaError_t jit_go(const fst_model* m, int kind, int64_t B, int rows, int P, unsigned gy, cudaStream_t s,
+                   unsigned* nblk, A... args) {
+  return jit_go_slot(m, kind, 0, B, rows, P, gy, s, nblk, args...);
 }
 
 }  // namespace
@@ -563,8 +569,9 @@ fst_status fst_eval(const fst_model* m, int64_t B, const fst_eval_io* io, const 
     // the shared sweep and the packed layouts live in the one-environment-
     // per-thread fused kernels
     const int rows = m->nq + (vjp ? 3 : 2) * m->nv;
-    if (jit_has(m, JK_EVAL) && m->variant[JK_EVAL] != FST_VARIANT_GENERIC)
-      return finish(fn, jit_go(m, JK_EVAL, B, rows, 0, (unsigned)a.n_roles, (cudaStream_t)stream, nullptr, mv, B, a));
+    if (jit_has_slot(m, JK_EVAL, JK_SLOT_EVAL_EXT) && m->variant[JK_EVAL] != FST_VARIANT_GENERIC)
+      return finish(fn, jit_go_slot(m, JK_EVAL, JK_SLOT_EVAL_EXT, B, rows, 0, (unsigned)a.n_roles,
+                                    (cudaStream_t)stream, nullptr, mv, B, a));
     return finish(fn, launch_eval(mv, B, a, launch_of(m, JK_EVAL, B, stream)));
   }
   if (use_level(m, JK_EVAL, LEVEL_EVAL))

@@ -14,7 +14,11 @@
 namespace fst {
 namespace {
 
-template <int NB>
+// EXT: the extended form (a separate kernel, so that the plain one keeps its
+// registers and code size): the RNEA role with the adjoint and/or the
+// kinematics from its own sweep (a.rnea_flags), and M and J in the packed
+// layouts (a.packed). Its input rows past q, qd and qdd hold tau_bar.
+template <int NB, bool EXT>
 __global__ void __launch_bounds__(256) eval_kernel(ModelView mv, int64_t B, EvalArgs a) {
   extern __shared__ float4 smem[];
   float* tile = smem_tile(smem, mv.n);
@@ -28,7 +32,7 @@ __global__ void __launch_bounds__(256) eval_kernel(ModelView mv, int64_t B, Eval
     if (role == ROLE_RNEA) {
       c1 = stage_rows(tile + mv.nq * T, a.qd, mv.nv, B, e);
       c2 = stage_rows(tile + (mv.nq + mv.nv) * T, a.qdd, mv.nv, B, e);
-      if ((a.rnea_flags & EVAL_RNEA_VJP) && !(a.rnea_flags & EVAL_TBAR_IS_TAU))
+      if (EXT && (a.rnea_flags & EVAL_RNEA_VJP) && !(a.rnea_flags & EVAL_TBAR_IS_TAU))
         stage_rows(tile + (mv.nq + 2 * mv.nv) * T, a.tau_bar, mv.nv, B, e);
     } else if (role == ROLE_ABA) {
       c1 = stage_rows(tile + mv.nq * T, a.qd, mv.nv, B, e);
@@ -43,13 +47,13 @@ __global__ void __launch_bounds__(256) eval_kernel(ModelView mv, int64_t B, Eval
       aba_env<NB>(sm, world_accel(mv), cq, c1, c2, a.qdd_out, B, e);
       break;
     case ROLE_CRBA:
-      if (a.packed)
+      if (EXT && a.packed)
         crba_env<NB, true>(sm, cq, mv.nv, a.M, B, e);
       else
         crba_env<NB>(sm, cq, mv.nv, a.M, B, e);
       break;
     case ROLE_RNEA:
-      if (a.rnea_flags)
+      if (EXT && a.rnea_flags)
         rnea_role_env<NB>(sm, world_accel(mv), cq, c1, c2, tile + (mv.nq + 2 * mv.nv) * T + threadIdx.x, T, mv.nv, a,
                           B, e);
       else
@@ -57,7 +61,7 @@ __global__ void __launch_bounds__(256) eval_kernel(ModelView mv, int64_t B, Eval
       break;
     default:
       if (a.J)
-        jac_env<NB>(sm, cq, mv.nv, a.links, a.poses, a.J, B, e, a.packed ? &a.pj : nullptr);
+        jac_env<NB>(sm, cq, mv.nv, a.links, a.poses, a.J, B, e, EXT && a.packed ? &a.pj : nullptr);
       else
         fk_env<NB>(sm, cq, a.poses, B, e);
       break;
@@ -69,7 +73,12 @@ __global__ void __launch_bounds__(256) eval_kernel(ModelView mv, int64_t B, Eval
 cudaError_t launch_eval(const ModelView& mv, int64_t B, const EvalArgs& a, const Launch& L) {
   const size_t sh = smem_bytes(mv.n, mv.nq + (a.rnea_flags & EVAL_RNEA_VJP ? 3 : 2) * mv.nv, L.block);
   const dim3 grid(grid_for(B, L.block), a.n_roles);
-  FST_NB_DISPATCH(mv.n, prepare(eval_kernel<NB>, sh); eval_kernel<NB><<<grid, L.block, sh, L.stream>>>(mv, B, a));
+  if (a.rnea_flags || a.packed)
+    FST_NB_DISPATCH(mv.n, prepare(eval_kernel<NB, true>, sh);
+                    eval_kernel<NB, true><<<grid, L.block, sh, L.stream>>>(mv, B, a));
+  else
+    FST_NB_DISPATCH(mv.n, prepare(eval_kernel<NB, false>, sh);
+                    eval_kernel<NB, false><<<grid, L.block, sh, L.stream>>>(mv, B, a));
   return cudaGetLastError();
 }
 

@@ -220,6 +220,7 @@ std::string make_source(const fst_model* m, int kind) {
      << "#define FST_JIT_NAME " << kKindName[kind] << "\n#define FST_JIT_PATH_NAME " << kKindName[kind] << "_path\n"
      << "#define FST_JIT_WARP_NAME " << kKindName[kind] << "_pathw\n"
      << "#define FST_JIT_PIN_NAME " << kKindName[kind] << "_pin\n"
+     << "#define FST_JIT_EXT_NAME " << kKindName[kind] << "_ext\n"
      << "#include \"fst_layout.h\"\nnamespace fst {\nstatic __device__ const BodyC kC[" << m->n << "] = {\n";
   for (int i = 0; i < m->n; ++i) {
     const BodyC& c = m->hc[i];
@@ -334,6 +335,14 @@ void compile_one(CompileJob& job, const std::string& arch_opt) {
   for (int h = 0; h < kJitHeaderCount; ++h) key += kJitHeaderSources[h];
   char name[32];
   std::snprintf(name, sizeof(name), "%016llx", (unsigned long long)fnv1a(key));
+  // FST_JIT_DUMP=<dir> writes each generated source (the tree's constants and
+  // the kernel selection; it includes the library's device headers) as
+  // <dir>/<kernel>_<hash>.cu, for offline compilation reports
+  if (const char* d = std::getenv("FST_JIT_DUMP")) {
+    const std::string dump = std::string(d) + "/" + kKindName[job.kind] + "_" + name + ".cu";
+    std::ofstream f(dump);
+    f << job.src;
+  }
   const std::string dir = cache_dir();
   const std::string path = dir.empty() ? "" : dir + "/" + name + ".cubin";
   if (!path.empty() && read_file(path, job.cubin)) return;
@@ -363,10 +372,10 @@ void compile_one(CompileJob& job, const std::string& arch_opt) {
 
 }  // namespace
 
-// Per kind, up to four kernels of one module: the one-environment-per-thread
+// Per kind, up to five kernels of one module: the one-environment-per-thread
 // kernel (slot 0), for trees with at most 8 leaves the path-parallel kernels
 // with a lane per path (slot 1) or a warp per path (slot 2), and for eval the
-// SM-pinned kernel (slot 3).
+// SM-pinned kernel (slot 3) and the extended fused kernel (slot 4).
 struct JitState {
   CUmodule mod[JK_COUNT] = {};
   CUfunction fn[JK_SLOTS][JK_COUNT] = {};
@@ -408,7 +417,7 @@ fst_status jit_specialize(fst_model* m, unsigned mask) {
     }
     m->jit->mod[j.kind] = mod;
     m->jit->fn[0][j.kind] = fn;
-    const char* suffix[JK_SLOTS] = {"", "_path", "_pathw", "_pin"};
+    const char* suffix[JK_SLOTS] = {"", "_path", "_pathw", "_pin", "_ext"};
     for (int v = 1; v < JK_SLOTS; ++v) {
       CUfunction fp;
       const std::string pname = std::string(kKindName[j.kind]) + suffix[v];

@@ -34,8 +34,11 @@ void jit_release(fst_model* m);
 unsigned jit_mask(const fst_model* m);
 bool jit_has(const fst_model* m, int kind);
 // Kernel slots of a kind: 0 one environment per thread, 1 path-parallel with
-// a lane per path, 2 path-parallel with a warp per path, 3 SM-pinned (eval).
-constexpr int JK_SLOTS = 4;
+// a lane per path, 2 path-parallel with a warp per path, 3 SM-pinned (eval),
+// 4 the extended fused kernel (eval with the RNEA adjoint, the shared
+// kinematics sweep or the packed layouts).
+constexpr int JK_SLOTS = 5;
+constexpr int JK_SLOT_EVAL_EXT = 4;
 bool jit_has_slot(const fst_model* m, int kind, int slot);
 int jit_path_lanes(const fst_model* m);   // lanes per environment of slot 1
 int jit_path_count(const fst_model* m);   // warps per block of slot 2

@@ -140,7 +140,47 @@ extern "C" __global__ void __launch_bounds__(256) FST_JIT_NAME(ModelView mv, int
 #endif
 
 #ifdef FST_JIT_EVAL
+// The fused evaluation: blockIdx.y is the role (one operator per group of
+// blocks), one environment per thread.
 extern "C" __global__ void __launch_bounds__(256) FST_JIT_NAME(ModelView mv, int64_t B, EvalArgs a) {
+  FST_JIT_PROLOGUE;
+  if (!act) return;
+  const int role = a.roles[blockIdx.y];
+  const Col cq = stage_rows(tile, a.q, mv.nq, B, e);
+  Col c1{}, c2{};
+  if (role == ROLE_RNEA) {
+    c1 = stage_rows(tile + mv.nq * T, a.qd, mv.nv, B, e);
+    c2 = stage_rows(tile + (mv.nq + mv.nv) * T, a.qdd, mv.nv, B, e);
+  } else if (role == ROLE_ABA) {
+    c1 = stage_rows(tile + mv.nq * T, a.qd, mv.nv, B, e);
+    c2 = stage_rows(tile + (mv.nq + mv.nv) * T, a.tau, mv.nv, B, e);
+  }
+  cp_async_wait_all();
+  const FixedTopo tp = fixed_topo(mv);
+  switch (role) {
+    case ROLE_ABA:
+      aba_env<FST_N>(tp, world_accel(mv), cq, c1, c2, a.qdd_out, B, e);
+      break;
+    case ROLE_CRBA:
+      crba_env<FST_N>(tp, cq, mv.nv, a.M, B, e);
+      break;
+    case ROLE_RNEA:
+      rnea_env<FST_N>(tp, world_accel(mv), cq, c1, c2, a.tau_out, B, e);
+      break;
+    default:
+      if (a.J)
+        jac_env<FST_N>(tp, cq, mv.nv, a.links, a.poses, a.J, B, e);
+      else
+        fk_env<FST_N>(tp, cq, a.poses, B, e);
+      break;
+  }
+}
+
+// The extended fused evaluation (a separate kernel, so that the plain one
+// above keeps its registers and code size): the RNEA role with the adjoint
+// and/or the kinematics from its own sweep (a.rnea_flags), and M and J in
+// the packed layouts (a.packed). The rows past q, qd and qdd hold tau_bar.
+extern "C" __global__ void __launch_bounds__(256) FST_JIT_EXT_NAME(ModelView mv, int64_t B, EvalArgs a) {
   FST_JIT_PROLOGUE;
   if (!act) return;
   const int role = a.roles[blockIdx.y];

@@ -53,7 +53,9 @@ def test_tune_sets_and_caches(torch_cuda, tmp_path, monkeypatch):
     m = api.Model(tree, specialize=["rnea", "aba"])
     res = autotune.tune(m, 2048, kinds=("rnea", "aba", "crba"))
     assert res["crba"]["variant"] in ("generic", "level")       # not specialised: no specialised candidates
-    assert len(res["rnea"]["candidates"]) == 17 and len(res["crba"]["candidates"]) == 8   # + path x4, pathwarp
+    # generic x4, level x4, level2 x3 (block >= 64), and for the specialised RNEA also specialised x4,
+    # path x4 and pathwarp
+    assert len(res["rnea"]["candidates"]) == 20 and len(res["crba"]["candidates"]) == 11
     assert not any(k.startswith("mixed") for k in res["rnea"]["candidates"])
     data = json.load(open(tmp_path / "tune.json"))
     assert len(data) == 3

@@ -205,8 +205,13 @@ def test_level_parallel_variant_matches_oracle(torch_cuda, name, variant, block)
     torch.cuda.synchronize()
     ref = _oracle_all(tree, s, ee)
     _assert_close({k: from_soa(v) for k, v in out.items()}, ref, f"{variant}/{name}/{block}")
-    for k in out:
-        assert torch.equal(ev[k], out[k]), k
+    if variant == "level":
+        for k in out:
+            assert torch.equal(ev[k], out[k]), k
+    else:
+        # two ABA-sized tiles need not fit where one operator's tiles do: the
+        # fused launch may then run another kernel than the per-operator one
+        _assert_close({k: from_soa(v) for k, v in ev.items()}, ref, f"{variant}/{name}/{block}/eval")
 
 
 def test_carveout_change_keeps_shared_memory_limit(torch_cuda):
