@@ -226,8 +226,9 @@ def plan_kernel_name(mode, desc):
                 f"Jacobians; RNEA with CRBA) on parallel graph branches, carveout {carveout}" +
                 (", fused kernels forked first" if desc["fused_forked_first"] else ""))
     if mode == "pinned":
-        return (f"SM-pinned: ABA kernel ({kinds['aba']}) on its share of the SMs beside the fused kernel of the other "
-                f"four ({kinds['eval']}) on the rest, carveout {carveout}")
+        return (f"SM-pinned step ({kinds['eval']}): one launch of one block per SM, each SM serving one operator; "
+                f"ABA level-parallel ({kinds['aba']}: SM counts ABA-KIN-RNEA-CRBA after the @), the others one "
+                f"environment per thread")
     return "5 per-operator kernels in sequence"
 
 
@@ -463,7 +464,7 @@ def run_fst(args):
             "e2e_full_layout": {"value": round(e2e_full_value, 1), "unit": "env-evals/s",
                                 "h2d_bytes_per_step": e2e_full["h2d"], "d2h_bytes_per_step": e2e_full["d2h"],
                                 "steps": e2e_full["steps"]},
-            "gpu_launches": K * {"fused": 1, "hybrid": 2, "split": 3, "pinned": 2}.get(plan.mode, len(OPS)),
+            "gpu_launches": K * {"fused": 1, "hybrid": 2, "split": 3, "pinned": 1}.get(plan.mode, len(OPS)),
             "kernels": kernels,
             "plan": desc,
             "clocks": clocks,

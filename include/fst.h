@@ -198,9 +198,13 @@ FST_API fst_status fst_model_specialize(fst_model* model, uint32_t kinds);
  * warm). Blocks pull tiles of environments from per-call counters; blocks on
  * SMs without a matching role leave at once, and the block that finishes
  * last completes whatever is left, so results never depend on where the
- * hardware placed the blocks. Calls of one model with this variant must not
- * overlap in time, except one eval beside one ABA (they count in separate
- * regions). */
+ * hardware placed the blocks. For eval this is one launch of one block per
+ * SM for every requested operator, ABA included (level-parallel, two tiles
+ * of 32 environments at a time; the others one environment per thread, as
+ * many tiles as the role has SMs); the block argument is ignored, and trees
+ * whose two ABA tiles do not fit in shared memory are refused. Calls of one
+ * model with this variant must not overlap in time, except one eval beside
+ * one ABA (they count in separate regions). */
 #define FST_VARIANT_PINNED 7
 /* As LEVEL, with two tiles of 32 environments per block (block >= 64
  * threads, split evenly; the tiles' warps interleaved so that each tile's

@@ -95,6 +95,11 @@ def graph_time_us(fn, n=20, reps=10, trials=3):
 L2_BYTES = 129 * 2 ** 20    # GB300's L2 cache
 
 
+def sm_count(device):
+    """Streaming multiprocessors of the device."""
+    return torch.cuda.get_device_properties(device).multi_processor_count
+
+
 def cold_time_us(fn, R, reps=5, trials=3):
     """Device time per call of fn(k) in microseconds, from a CUDA graph of the
     R calls fn(0) .. fn(R - 1) replayed reps times: with fn(k) working on the
@@ -262,7 +267,8 @@ class StepPlan:
                   overlapping one fused launch of the four other operators;
       split       the same, with that fused launch split in two (FK with the
                   Jacobians; RNEA with CRBA) on two more branches;
-      pinned      the hybrid pair as SM-pinned launches on disjoint SM sets;
+      pinned      one launch of one block per SM, each SM serving one operator
+                  (fst_eval with FST_VARIANT_PINNED; SM counts tuned);
       concurrent  each operator's own kernel on its own stream;
       sequential  the per-operator kernels one after another.
     Side streams are forked from and joined back into the caller's stream,
@@ -276,7 +282,6 @@ class StepPlan:
     on GB300 the order moves a hybrid step between 14.5 and 22 us)."""
 
     MODES = ("fused", "hybrid", "split", "pinned", "concurrent", "sequential")
-    PIN_SHARES = (0.45, 0.55, 0.65)   # fractions of the SMs pinned to ABA
 
     def __init__(self, model, B, links=None, use_cache=True, verbose=False, modes=MODES, fixed=None):
         """fixed: run this one plan instead of searching, named as the keys of
@@ -327,11 +332,12 @@ class StepPlan:
         best_aba = f"{self.tuned['aba']['variant']}/{self.tuned['aba']['block']}"
         abas = [n for n, _ in sorted(self.tuned["aba"]["candidates"].items(), key=lambda kv: kv[1])[:3]]
         hybrid_cfgs = [f"{ev}|{ab}" for ev in hybrid_evals for ab in abas]
-        # SM-pinned: the specialised fused kernel and the level-parallel ABA on
-        # disjoint SM sets, so each SM keeps running the same code
+        # SM-pinned: the whole step in one launch of one block per SM, every SM
+        # serving one operator (ABA level-parallel, the others one environment
+        # per thread) with the SM counts of the candidates below
         pinned_cfgs = []
         if "specialized" in {c.split("/")[0] for c in self.tuned["eval"]["candidates"]}:
-            pinned_cfgs = [f"pinned/{b}|pinned/256@{sh}" for b in (64, 128) for sh in self.PIN_SHARES]
+            pinned_cfgs = [f"pinned/256|level/256@{c}" for c in self.pin_count_candidates(B)]
         times = {}
         for carveout in (-1, 100):
             api.set_smem_carveout(carveout)
@@ -344,7 +350,7 @@ class StepPlan:
                     except _ffi.FstError:
                         continue                 # not available for this model
                     for alt in (False, True):
-                        if (carveout >= 0 or alt) and mode in ("fused", "sequential"):
+                        if (carveout >= 0 or alt) and mode in ("fused", "sequential", "pinned"):
                             continue
                         self._set_alt(mode, alt)
                         times[(mode, carveout, alt, ev)] = self._time(cold)
@@ -386,23 +392,49 @@ class StepPlan:
         return mode, carveout, opt is not None, ev
 
     def _set_eval(self, config):
-        """config: "<eval variant>/<block>|<aba variant>/<block>[@<ABA share of
-        the SMs>]"; a share sets the SM roles of the pinned variant."""
-        config, _, share = config.partition("@")
+        """config: "<eval variant>/<block>|<aba variant>/<block>[@<SM counts>]";
+        SM counts "a-k-r-c" (ABA, KIN, RNEA, CRBA) set the SM roles of the
+        pinned step."""
+        config, _, counts = config.partition("@")
         for kind, part in zip(("eval", "aba"), config.split("|")):
             variant, block = part.split("/")
             self.model.set_launch([kind], int(block), variant)
-        if share:
-            self.model.set_sm_roles(self.pin_roles(float(share)))
+        if counts:
+            self.model.set_sm_roles(self.pin_roles([int(c) for c in counts.split("-")]))
+
+    def pin_count_candidates(self, B, n_sm=None):
+        """SM counts (ABA, KIN, RNEA, CRBA) to try for the pinned step: ABA
+        gets one SM per 64-environment tile (at most all but 24 SMs); the rest
+        is split between the other three in proportion to their measured
+        times, evenly, and with KIN and CRBA favoured."""
+        n_sm = n_sm or sm_count(self.model.device)
+        n_aba = min(-(-B // 64), n_sm - 24)
+        out = []
+        for a in (n_aba, n_aba - 8):
+            rest = n_sm - a
+            t = [self.tuned[k]["us"] for k in ("jacobian", "rnea", "crba")]
+            for w in (t, (1.0, 1.0, 1.0), (1.0, 0.5, 1.0)):
+                k = [max(1, int(rest * x / sum(w))) for x in w]
+                k[0] += rest - sum(k)
+                out.append(f"{a}-{k[0]}-{k[1]}-{k[2]}")
+        return list(dict.fromkeys(out))
 
     @staticmethod
-    def pin_roles(aba_share, period=20):
-        """Role names for the 256 SM ids: of every `period` consecutive ids,
-        round(aba_share * period) serve ABA and the rest take KIN, RNEA and
-        CRBA in turn, so every role spreads over the whole chip."""
-        n_aba = int(round(aba_share * period))
-        other = ("kin", "rnea", "crba")
-        return ["aba" if i % period < n_aba else other[(i % period - n_aba) % 3] for i in range(256)]
+    def pin_roles(counts, n_ids=256):
+        """Role names for the SM ids 0 .. n_ids - 1 from SM counts (ABA, KIN,
+        RNEA, CRBA): the roles are interleaved along the ids, each spread
+        evenly over the first sum(counts) ids (so over both dies of the GPU);
+        ids beyond them get no role."""
+        names = ("aba", "kin", "rnea", "crba")
+        total = sum(counts)
+        out, acc = [], [0.0] * 4
+        for _ in range(total):
+            for r in range(4):
+                acc[r] += counts[r] / total
+            r = max(range(4), key=lambda j: acc[j])
+            acc[r] -= 1.0
+            out.append(names[r])
+        return out + ["none"] * (n_ids - total)
 
     def _set_alt(self, mode, alt):
         """The plan's binary option: for the concurrent mode, the longest
@@ -452,7 +484,11 @@ class StepPlan:
         if self.mode == "sequential":
             for op in ops:
                 op()
-        elif self.mode in ("hybrid", "pinned"):
+        elif self.mode == "pinned":
+            # the SM-pinned step: all five operators in one launch
+            api.eval(m, q, qd, qdd, tau, fk=True, links=self.links, rnea=True, crba=True, aba=True, out=out,
+                     packed=packed)
+        elif self.mode == "hybrid":
             fused = [lambda: api.eval(m, q, qd, qdd, tau, fk=True, links=self.links, rnea=True, crba=True, aba=False,
                                       out=out, packed=packed)]
             self._fork(fused + [ops[4]] if self.alt else [ops[4]] + fused)

@@ -210,6 +210,7 @@ fst_status fst_model_create(const fst_body_desc* bodies, int32_t n_bodies, const
   if (err == cudaSuccess) err = cudaMemcpy(m->dt, &m->ht, sizeof(TopoLists), cudaMemcpyHostToDevice);
   if (err == cudaSuccess) err = cudaMalloc((void**)&m->dpin, sizeof(int) * (kPinTableSize + 2 * kPinRegion));
   if (err == cudaSuccess) err = cudaMemset(m->dpin, 0xff, sizeof(int) * kPinTableSize);  // no roles: -1
+  for (int i = 0; i < kPinTableSize; ++i) m->pin_table[i] = FST_ROLE_NONE;
   if (err != cudaSuccess) {
     fst_status st = (err == cudaErrorMemoryAllocation) ? set_error(FST_ERR_NO_MEMORY, "fst_model_create: cudaMalloc failed")
                                                        : cuda_error("fst_model_create", err);
@@ -281,6 +282,10 @@ fst_status fst_model_set_launch(fst_model* m, uint32_t kinds, int32_t block, int
       return set_error(FST_ERR_INVALID_ARG, "fst_model_set_launch: the pinned variant is for eval and ABA only");
     if (((kinds >> k) & 1u) && variant == FST_VARIANT_PINNED && k == JK_EVAL && !jit_has_slot(m, JK_EVAL, 3))
       return set_error(FST_ERR_INVALID_ARG, "fst_model_set_launch: pinned eval needs the specialised eval kernel");
+    if (((kinds >> k) & 1u) && variant == FST_VARIANT_PINNED && k == JK_EVAL &&
+        (size_t)2 * (m->nq + 2 * m->nv + kAbaStateFloats * m->n) * 32 * sizeof(float) > kLevelSmemLimit)
+      return set_error(FST_ERR_INVALID_ARG, "fst_model_set_launch: the tree is too large for the pinned step "
+                                            "(two level-parallel ABA tiles do not fit in shared memory)");
     if (((kinds >> k) & 1u) && variant == FST_VARIANT_PINNED && k == JK_ABA &&
         level_smem_needed(view_of(m, nullptr), LEVEL_ABA) > kLevelSmemLimit)
       return set_error(FST_ERR_INVALID_ARG, "fst_model_set_launch: the tree is too large for pinned ABA");
@@ -312,6 +317,8 @@ fst_status fst_model_set_sm_roles(fst_model* m, const int32_t* role_of_sm, int32
   if (err == cudaSuccess && dev != m->device)
     return set_error(FST_ERR_INVALID_ARG, "fst_model_set_sm_roles: the current device is not the model's device");
   if (err == cudaSuccess) err = cudaMemcpy(m->dpin, table, sizeof(table), cudaMemcpyHostToDevice);
+  if (err == cudaSuccess)
+    for (int i = 0; i < kPinTableSize; ++i) m->pin_table[i] = table[i];
   return err == cudaSuccess ? FST_OK : cuda_error("fst_model_set_sm_roles", err);
 }
 
@@ -456,6 +463,37 @@ fst_status fst_aba(const fst_model* m, int64_t B, const float* q, const float* q
 }  // extern "C"
 
 namespace fst {
+// Tiles of the SM-pinned fused step: per role slot, the number of tiles and
+// the environments per tile. ABA runs two level-parallel tiles of 32 at a
+// time (64 environments); the other roles take about as many tiles as they
+// have SMs (pin_table), of a multiple of 32 and at most 256 environments.
+// Returns the launch's dynamic shared memory: the larger of two ABA tiles
+// and 256 environments' staged inputs, and at least 116 KB, so that no two
+// blocks share an SM.
+size_t pinned_step_plan(const fst_model* m, int64_t B, const EvalArgs& a, int sms, PinArgs& p) {
+  const int rows = m->nq + 2 * m->nv;
+  size_t sh = (size_t)rows * 256 * sizeof(float);
+  for (int r = 0; r < a.n_roles; ++r) {
+    const int role = a.roles[r];
+    if (role == ROLE_ABA) {
+      p.envs[r] = 64;
+      p.tiles[r] = (int)((B + 63) / 64);
+      const size_t aba = (size_t)2 * (rows + kAbaStateFloats * m->n) * 32 * sizeof(float);
+      if (aba > sh) sh = aba;
+      continue;
+    }
+    int n_sm = 0;
+    for (int s = 0; s < sms && s < kPinTableSize; ++s) n_sm += m->pin_table[s] == role;
+    int64_t E = (B + (n_sm > 0 ? n_sm : 1) - 1) / (n_sm > 0 ? n_sm : 1);
+    E = (E + 31) / 32 * 32;
+    E = E < 32 ? 32 : (E > 256 ? 256 : E);
+    p.envs[r] = (int)E;
+    p.tiles[r] = (int)((B + E - 1) / E);
+  }
+  const size_t one_per_sm = 116 * 1024;
+  return sh > one_per_sm ? sh : one_per_sm;
+}
+
 // Packed Jacobian layout: columns (support-path DOFs) of each link and the
 // first row of its block.
 void packed_cols(const fst_model* m, const LinkList& links, PackedJ& pj) {
@@ -610,15 +648,16 @@ fst_status fst_eval(const fst_model* m, int64_t B, const fst_eval_io* io, const 
   }
   if (m->variant[JK_EVAL] == FST_VARIANT_PINNED && jit_has_slot(m, JK_EVAL, 3)) {
     int* counters = m->dpin + kPinTableSize + kPinEvalRegion * kPinRegion;
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, m->device);
+    if (sms < 1) sms = 1;
+    PinArgs p{m->dpin, counters, {0, 0, 0, 0}, {0, 0, 0, 0}};
+    const size_t sh = pinned_step_plan(m, B, a, sms, p);
+    if (sh > kLevelSmemLimit) return set_error(FST_ERR_INVALID_ARG, "fst_eval: the tree is too large for the pinned step");
     cudaError_t err = cudaMemsetAsync(counters, 0, sizeof(int) * kPinRegion, (cudaStream_t)stream);
     if (err == cudaSuccess) {
-      int sms = 0;
-      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, m->device);
-      const int T = m->block[JK_EVAL] ? m->block[JK_EVAL] : 128;
-      const PinArgs p{m->dpin, counters};
       void* argv[] = {(void*)&mv, (void*)&B, (void*)&a, (void*)&p};
-      err = jit_launch_slot(m, JK_EVAL, 3, dim3((unsigned)(2 * (sms > 0 ? sms : 1))), T,
-                            (size_t)(m->nq + 2 * m->nv) * T * sizeof(float), (cudaStream_t)stream, argv);
+      err = jit_launch_slot3(m, JK_EVAL, 3, dim3((unsigned)sms), dim3(32, 2, 4), sh, (cudaStream_t)stream, argv);
     }
     return finish(fn, err);
   }

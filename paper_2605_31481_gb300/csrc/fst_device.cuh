@@ -407,26 +407,28 @@ __device__ __forceinline__ int pinned_role(const PinArgs& p) {
 }
 
 // body(slot, tile) for the tiles of `my_slot` (or none if my_slot < 0), then
-// the clean-up described above. One call site of body, so its code is
-// emitted once. Every thread of the block must call it.
+// the clean-up described above; slot s has n_tiles[s] tiles. One call site of
+// body, so its code is emitted once. Every thread of the block (of any
+// shape) must call it.
 template <class F>
-__device__ __forceinline__ void pinned_tiles(const PinArgs& p, int my_slot, int n_slots, int n_tiles, F& body) {
+__device__ __forceinline__ void pinned_tiles(const PinArgs& p, int my_slot, int n_slots, const int* n_tiles, F& body) {
   __shared__ int s_tile, s_last;
+  const bool lead = (threadIdx.x | threadIdx.y | threadIdx.z) == 0;
   int slot = my_slot;
   bool cleanup = false;
   for (;;) {
     if (slot >= 0) {
-      if (threadIdx.x == 0) s_tile = atomicAdd(&p.counters[slot], 1);
+      if (lead) s_tile = atomicAdd(&p.counters[slot], 1);
       __syncthreads();
       const int t = s_tile;
       __syncthreads();
-      if (t < n_tiles) {
+      if (t < n_tiles[slot]) {
         body(slot, t);
         continue;
       }
     }
     if (!cleanup) {  // own tiles done: count this block out; the last one cleans up
-      if (threadIdx.x == 0)
+      if (lead)
         s_last = atomicAdd(&p.counters[kPinRegion - 1], 1) == (int)(gridDim.x * gridDim.y * gridDim.z) - 1;
       __syncthreads();
       if (!s_last) return;
@@ -436,6 +438,13 @@ __device__ __forceinline__ void pinned_tiles(const PinArgs& p, int my_slot, int 
     }
     if (++slot >= n_slots) return;
   }
+}
+
+// The same with n_tiles tiles in every slot.
+template <class F>
+__device__ __forceinline__ void pinned_tiles(const PinArgs& p, int my_slot, int n_slots, int n_tiles, F& body) {
+  const int t[4] = {n_tiles, n_tiles, n_tiles, n_tiles};
+  pinned_tiles(p, my_slot, n_slots, t, body);
 }
 
 // Stages rows [0, rows) of a [rows][B] array for this thread's environment

@@ -26,6 +26,7 @@ struct fst_model {
   fst::TopoLists ht{};               // level and child lists (host copy)
   fst::TopoLists* dt = nullptr;      // device copy
   int* dpin = nullptr;               // SM-pinned launches: role table, then the counter regions
+  int pin_table[256] = {};           // host copy of the role table (FST_ROLE_*, -1 none)
   fst::JitState* jit = nullptr;      // run-time specialised kernels, if any
   int block[16] = {0};               // threads per block per kernel kind (0 = built-in heuristic)
   int variant[16] = {0};             // per kind: 0 auto, 1 generic, 2 specialised (see fst_model_set_launch)

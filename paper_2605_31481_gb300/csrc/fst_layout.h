@@ -84,6 +84,10 @@ struct PackedJ {
   int off[FST_MAX_LINKS];
 };
 
+// Floats of level-parallel ABA state per body and environment (level.cuh):
+// X 12 | va 6 | c 6 | IA 21 | pA 6 | U 6 | invD | u.
+constexpr int kAbaStateFloats = 59;
+
 // Operators of the fused evaluation kernel, in launch order (longest first,
 // so the slowest role's blocks are dispatched first).
 enum Role { ROLE_ABA = 0, ROLE_CRBA = 1, ROLE_RNEA = 2, ROLE_KIN = 3 };
@@ -99,6 +103,11 @@ constexpr int kPinAbaRegion = 1;
 struct PinArgs {
   const int* table;  // [kPinTableSize]
   int* counters;     // [kPinRegion] of this launch
+  // the fused pinned step (eval): per slot of EvalArgs::roles, the number of
+  // tiles and the environments per tile (a multiple of 32; ABA's tiles are
+  // 64 environments, two level-parallel tiles of 32)
+  int tiles[4];
+  int envs[4];
 };
 
 struct EvalArgs {

@@ -457,6 +457,11 @@ int jit_path_count(const fst_model* m) { return m->jit ? m->jit->path_np : 0; }
 
 cudaError_t jit_launch_slot(const fst_model* m, int kind, int slot, dim3 grid, int block, size_t smem,
                             cudaStream_t s, void** args) {
+  return jit_launch_slot3(m, kind, slot, grid, dim3((unsigned)block), smem, s, args);
+}
+
+cudaError_t jit_launch_slot3(const fst_model* m, int kind, int slot, dim3 grid, dim3 block, size_t smem,
+                             cudaStream_t s, void** args) {
   const Driver& D = driver();
   JitState* J = m->jit;
   CUfunction f = J->fn[slot][kind];
@@ -475,7 +480,7 @@ cudaError_t jit_launch_slot(const fst_model* m, int kind, int slot, dim3 grid, i
       D.set_attr(f, CU_FUNC_ATTRIBUTE_PREFERRED_SHARED_MEMORY_CARVEOUT, pct);
     J->carveout_set[slot][kind] = gen;
   }
-  const CUresult r = D.launch(f, grid.x, grid.y, grid.z, (unsigned)block, 1, 1, (unsigned)smem, (CUstream)s, args,
+  const CUresult r = D.launch(f, grid.x, grid.y, grid.z, block.x, block.y, block.z, (unsigned)smem, (CUstream)s, args,
                               nullptr);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorLaunchFailure;
 }

@@ -45,5 +45,8 @@ int jit_path_count(const fst_model* m);   // warps per block of slot 2
 cudaError_t jit_launch_slot(const fst_model* m, int kind, int slot, dim3 grid, int block, size_t smem,
                             cudaStream_t s, void** args);
 cudaError_t jit_launch(const fst_model* m, int kind, dim3 grid, int block, size_t smem, cudaStream_t s, void** args);
+// the same with a block of any shape
+cudaError_t jit_launch_slot3(const fst_model* m, int kind, int slot, dim3 grid, dim3 block, size_t smem,
+                             cudaStream_t s, void** args);
 
 }  // namespace fst

@@ -225,50 +225,76 @@ extern "C" __global__ void __launch_bounds__(256) FST_JIT_EXT_NAME(ModelView mv,
 #endif
 
 #ifdef FST_JIT_EVAL
-// SM-pinned form (FST_VARIANT_PINNED): a block serves the role its SM is
-// pinned to, tile after tile of T environments (pinned_tiles).
+// SM-pinned fused step (FST_VARIANT_PINNED): ONE launch of one block per SM,
+// each block serving the role its SM is pinned to (pinned_role), tile after
+// tile (pinned_tiles), so that an SM runs the same straight-line code from
+// launch to launch and finds it in its instruction caches: when consecutive
+// launches hand an SM another role's code, it refetches that code and the
+// launch takes about twice as long. Blocks are (32, 2, 4): 256 threads, as
+// two tiles of 32 environments with four warps each.
+//  * KIN, RNEA and CRBA: one environment per thread, p.envs[slot] (<= 256)
+//    environments per tile;
+//  * ABA: level-parallel (level.cuh, the tree compiled in), 64 environments
+//    per tile as two tiles of 32, each tile's four warps splitting every level.
+// Dynamic shared memory: two ABA tiles (input rows and per-body state) or the
+// staged input rows of 256 environments, whichever is larger.
 extern "C" __global__ void __launch_bounds__(256) FST_JIT_PIN_NAME(ModelView mv, int64_t B, EvalArgs a, PinArgs p) {
   extern __shared__ float4 smem[];
-  float* tile = reinterpret_cast<float*>(smem);
-  const int T = blockDim.x;
+  float* base = reinterpret_cast<float*>(smem);
+  const int tid = threadIdx.x + 32 * (threadIdx.y + 2 * threadIdx.z);
   const int code = pinned_role(p);
   int my = -1;
   for (int r = 0; r < a.n_roles; ++r)
     if (a.roles[r] == code) my = r;
   const FixedTopo tp = fixed_topo(mv);
+  const int rows = mv.nq + 2 * mv.nv;
   auto body = [&](int slot, int t) {
     const int role = a.roles[slot];
-    const int64_t e = (int64_t)t * T + threadIdx.x;
-    if (e >= B) return;
-    const Col cq = stage_rows(tile, a.q, mv.nq, B, e);
-    Col c1{}, c2{};
-    if (role == ROLE_RNEA) {
-      c1 = stage_rows(tile + mv.nq * T, a.qd, mv.nv, B, e);
-      c2 = stage_rows(tile + (mv.nq + mv.nv) * T, a.qdd, mv.nv, B, e);
-    } else if (role == ROLE_ABA) {
-      c1 = stage_rows(tile + mv.nq * T, a.qd, mv.nv, B, e);
-      c2 = stage_rows(tile + (mv.nq + mv.nv) * T, a.tau, mv.nv, B, e);
+    if (role == ROLE_ABA) {
+      const int lane = threadIdx.x;
+      float* tile = base + (size_t)threadIdx.y * (rows + kAbaState * mv.n) * kLaneEnvs;
+      const LaneState S{tile + rows * kLaneEnvs, kAbaState};
+      const int64_t e = ((int64_t)t * 2 + threadIdx.y) * kLaneEnvs + lane;
+      stage_block_rows(tile, a.q, mv.nq, B, e);
+      stage_block_rows(tile + mv.nq * kLaneEnvs, a.qd, mv.nv, B, e);
+      stage_block_rows(tile + (mv.nq + mv.nv) * kLaneEnvs, a.tau, mv.nv, B, e);
+      cp_async_wait_all();
+      __syncthreads();
+      aba_level(tp, world_accel(mv), Col{tile + lane, kLaneEnvs}, Col{tile + mv.nq * kLaneEnvs + lane, kLaneEnvs},
+                Col{tile + (mv.nq + mv.nv) * kLaneEnvs + lane, kLaneEnvs}, S, a.qdd_out, B, e, e < B);
+    } else {
+      const int E = p.envs[slot];
+      const int64_t e = (int64_t)t * E + tid;
+      if (tid < E && e < B) {
+        float* col = base + tid;
+        for (int k = 0; k < mv.nq; ++k) cp_async4(col + k * 256, a.q + (int64_t)k * B + e);
+        if (role == ROLE_RNEA) {
+          for (int k = 0; k < mv.nv; ++k) {
+            cp_async4(col + (mv.nq + k) * 256, a.qd + (int64_t)k * B + e);
+            cp_async4(col + (mv.nq + mv.nv + k) * 256, a.qdd + (int64_t)k * B + e);
+          }
+        }
+        cp_async_wait_all();
+        const Col cq{col, 256}, c1{col + mv.nq * 256, 256}, c2{col + (mv.nq + mv.nv) * 256, 256};
+        switch (role) {
+          case ROLE_CRBA:
+            crba_env<FST_N>(tp, cq, mv.nv, a.M, B, e);
+            break;
+          case ROLE_RNEA:
+            rnea_env<FST_N>(tp, world_accel(mv), cq, c1, c2, a.tau_out, B, e);
+            break;
+          default:
+            if (a.J)
+              jac_env<FST_N>(tp, cq, mv.nv, a.links, a.poses, a.J, B, e);
+            else
+              fk_env<FST_N>(tp, cq, a.poses, B, e);
+            break;
+        }
+      }
     }
-    cp_async_wait_all();
-    switch (role) {
-      case ROLE_ABA:
-        aba_env<FST_N>(tp, world_accel(mv), cq, c1, c2, a.qdd_out, B, e);
-        break;
-      case ROLE_CRBA:
-        crba_env<FST_N>(tp, cq, mv.nv, a.M, B, e);
-        break;
-      case ROLE_RNEA:
-        rnea_env<FST_N>(tp, world_accel(mv), cq, c1, c2, a.tau_out, B, e);
-        break;
-      default:
-        if (a.J)
-          jac_env<FST_N>(tp, cq, mv.nv, a.links, a.poses, a.J, B, e);
-        else
-          fk_env<FST_N>(tp, cq, a.poses, B, e);
-        break;
-    }
+    __syncthreads();  // the next tile reuses the shared memory
   };
-  pinned_tiles(p, my, a.n_roles, (int)((B + T - 1) / T), body);
+  pinned_tiles(p, my, a.n_roles, p.tiles, body);
 }
 #endif
 

@@ -29,16 +29,19 @@ def test_bench_refuses_too_few_warmup_steps():
     assert r.returncode != 0 and "warmup" in r.stderr
 
 
-def test_pin_roles_proportions():
+def test_pin_roles_counts_and_spread():
+    """The pinned step's SM table: exactly the requested SM count per role
+    over the first sum(counts) ids, every role spread along the ids (each
+    half of the ids holds about half of each role's SMs), no role past them."""
     sys.path.insert(0, ROOT)
     from paper_2605_31481_gb300.autotune import StepPlan
-    for share in (0.45, 0.55, 0.65):
-        roles = StepPlan.pin_roles(share)
-        assert len(roles) == 256 and set(roles) <= {"aba", "kin", "rnea", "crba"}
-        frac = roles.count("aba") / 256
-        assert abs(frac - share) <= 0.05
-        others = [roles.count(r) for r in ("kin", "rnea", "crba")]
-        assert max(others) - min(others) <= 256 // 20 + 1       # the three roles evenly
+    for counts in ((64, 32, 24, 32), (56, 40, 16, 40), (76, 25, 25, 26)):
+        roles = StepPlan.pin_roles(list(counts))
+        n = sum(counts)
+        assert len(roles) == 256 and set(roles[n:]) <= {"none"}
+        for name, c in zip(("aba", "kin", "rnea", "crba"), counts):
+            assert roles[:n].count(name) == c
+            assert abs(roles[:n // 2].count(name) - c / 2) <= 1.5
 
 
 def test_algorithmic_bytes_per_environment():

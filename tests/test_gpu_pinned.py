@@ -1,7 +1,9 @@
-"""SM-pinned launches (FST_VARIANT_PINNED): the fused evaluation and ABA give
-the oracle's results whatever the SM role table, including tables that give
-some role no SM at all (the last block then does that role's work), and the
-pinned pair beside each other equals the plain calls."""
+"""SM-pinned launches (FST_VARIANT_PINNED): the pinned fused step (all five
+operators in one launch of one block per SM, ABA level-parallel inside it)
+and the pinned ABA give the oracle's results whatever the SM role table,
+including tables that give some role no SM at all (the last block then does
+that role's work), and the pinned step replayed from a CUDA graph equals the
+plain calls."""
 import numpy as np
 import pytest
 
@@ -23,7 +25,10 @@ def torch_cuda():
 
 
 TABLES = {
-    "interleaved": lambda: __import__("paper_2605_31481_gb300.autotune", fromlist=["StepPlan"]).StepPlan.pin_roles(0.55),
+    "interleaved": lambda: __import__("paper_2605_31481_gb300.autotune",
+                                      fromlist=["StepPlan"]).StepPlan.pin_roles([64, 32, 24, 32]),
+    "few_sms": lambda: __import__("paper_2605_31481_gb300.autotune",
+                                  fromlist=["StepPlan"]).StepPlan.pin_roles([3, 2, 1, 2]),
     "no_roles": lambda: ["none"] * 256,
     "aba_only": lambda: ["aba"] * 256,
     "kin_only": lambda: ["kin"] * 256,
@@ -35,10 +40,16 @@ TABLES = {
 def test_pinned_matches_oracle(torch_cuda, name, table):
     torch = torch_cuda
     from paper_2605_31481_gb300 import api
+    from paper_2605_31481_gb300 import _ffi
     tree = TREES[name]()
     m = api.Model(tree, specialize=["eval"])
     m.set_sm_roles(TABLES[table]())
-    m.set_launch(["eval"], 128, "pinned")
+    if name == "humanoid29":
+        # two level-parallel ABA tiles of the 24-body tree exceed shared memory
+        with pytest.raises(_ffi.FstError):
+            m.set_launch(["eval"], 256, "pinned")
+    else:
+        m.set_launch(["eval"], 256, "pinned")
     m.set_launch(["aba"], 256, "pinned")
     B = 1000 + 13
     s = w.random_state(tree, B, seed=17)
@@ -53,16 +64,17 @@ def test_pinned_matches_oracle(torch_cuda, name, table):
     assert torch.equal(qdd_pin, api.aba(m, q, qd, tau))     # same level-parallel bodies
 
 
-def test_pinned_pair_side_by_side_in_a_graph(torch_cuda):
-    """The step plan's pinned mode: ABA and the other four on parallel graph
-    branches, replayed, equal to the plain per-operator calls."""
+def test_pinned_step_in_a_graph(torch_cuda):
+    """The step plan's pinned mode: the five operators in one SM-pinned
+    launch, replayed from a CUDA graph, equal to the plain per-operator
+    calls."""
     torch = torch_cuda
     from paper_2605_31481_gb300 import api, autotune
     tree = TREES["quadruped11"]()
     B = 4096
     m = api.Model(tree, specialize=True)
     plan = autotune.StepPlan(m, B, use_cache=False, modes=("fused",))
-    plan._set_eval("pinned/128|pinned/256@0.55")
+    plan._set_eval("pinned/256|level/256@64-32-24-32")
     plan.mode = "pinned"
     s = w.random_state(tree, B, seed=5)
     q, qd, qdd, tau = (to_soa_cuda(s[k], torch) for k in ("q", "qd", "qdd", "tau"))

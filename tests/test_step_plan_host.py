@@ -43,6 +43,7 @@ def fakes(monkeypatch, tmp_path):
     monkeypatch.setattr(autotune, "tune", lambda *a, **k: tuned)
     monkeypatch.setattr(autotune.torch.cuda, "Stream", lambda *a, **k: object())
     monkeypatch.setattr(autotune, "ColdSets", lambda *a, **k: type("C", (), {"R": 1, "sets": [{}]})())
+    monkeypatch.setattr(autotune, "sm_count", lambda device: 152)
     monkeypatch.setattr(autotune, "_key", lambda model, kind, B: f"{model.fingerprint}|{kind}|{B}")
     calls = []
 
@@ -162,7 +163,7 @@ def test_fixed_plan_names_are_checked(bad):
 
 @pytest.mark.parametrize("name", ["hybrid[specialized/128|level/128]@100%+fusedfirst", "fused[specialized/128|level/256]",
                                   "split[specialized/128|level/256]+fusedfirst", "concurrent@100%+prio", "sequential",
-                                  "pinned[pinned/128|pinned/256@0.45]@100%"])
+                                  "pinned[pinned/256|level/256@64-32-24-32]"])
 def test_bench_describes_a_fixed_plan(fakes, name):
     """bench.py's report of the timed step works from a named plan's
     describe(), with or without the per-kind tuning."""
