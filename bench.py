@@ -699,11 +699,20 @@ def multi_tree(torch, fst, w, counts=(4096, 2048, 1024, 512, 256)):
             fst.aba(m, it["q"], it["qd"], it["tau"], out=o["qdd"])
 
     tp, ts = _graph_us(torch, lambda: mb.eval(items)), _graph_us(torch, separate)
+    level = {}
+    for block in (64, 128, 256):          # the level-parallel form of the same launch
+        mb.set_launch(block, "level")
+        level[f"level/{block}"] = round(_graph_us(torch, lambda: mb.eval(items)), 3)
+    mb.set_launch(64, "generic")
+    best = min(level, key=level.get)
     n = sum(counts)
     return {"workload": "5 trees (7/11/12/18/23 DOF) x (4096/2048/1024/512/256 envs): FK+RNEA+CRBA+ABA",
             "persistent_us": round(tp, 3), "separate_us": round(ts, 3),
+            "persistent_level_us": level, "persistent_level_best": best,
             "persistent_env_evals_per_s": round(n / tp * 1e6, 1), "separate_env_evals_per_s": round(n / ts * 1e6, 1),
-            "speedup": round(ts / tp, 3), "launches": {"persistent": 1, "separate": 4 * len(trees)}}
+            "persistent_level_env_evals_per_s": round(n / level[best] * 1e6, 1),
+            "speedup": round(ts / tp, 3), "level_speedup_vs_generic": round(tp / level[best], 3),
+            "launches": {"persistent": 1, "separate": 4 * len(trees)}}
 
 
 def sysid(torch, fst, w, steps=500):

@@ -216,7 +216,8 @@ FST_API fst_status fst_model_set_launch(fst_model* model, uint32_t kinds, int32_
 
 /* Roles of the SMs for FST_VARIANT_PINNED launches: role_of_sm[i] is the
  * role of SM id i (FST_ROLE_*, or FST_ROLE_NONE), for n <= 256 SM ids; ids
- * past n get FST_ROLE_NONE. The roles are the operator groups of fst_eval:
+ * past n get FST_ROLE_NONE. The ids are the hardware's (fst_sm_ids lists
+ * those that exist); the first call also probes them for the pinned step. The roles are the operator groups of fst_eval:
  * ABA, CRBA, RNEA and KIN (FK with the Jacobians). Synchronous (copies the
  * table to the model's device memory): call it before capturing a stream.
  * Until it is called every SM has no role, which is correct but slow (the
@@ -521,8 +522,19 @@ FST_API fst_status fst_multi_destroy(fst_multi* multi);
  * `stream` and can be captured into a CUDA graph). io has n_models entries,
  * in the order given to fst_multi_create. Overlapping calls on the same
  * group (unordered streams) race on its counter; create one group per
- * stream for that. Results are bit-identical to the per-tree generic calls. */
+ * stream for that. Results are bit-identical to the per-tree generic calls
+ * (with the default launch form; see fst_multi_set_launch). */
 FST_API fst_status fst_multi_eval(fst_multi* multi, const fst_multi_io* io, void* stream);
+
+/* Launch form of a group's fst_multi_eval (not in the paper; a tuning knob).
+ * FST_VARIANT_GENERIC (the default, block 64): one environment per thread,
+ * items of `block` environments. FST_VARIANT_LEVEL: the level-parallel
+ * bodies of paper Sec. 3.3, items of 32 environments with the block's
+ * block/32 warps splitting each tree level (results then bit-identical to
+ * the per-tree level-parallel calls at that block); a group whose largest
+ * tree's state does not fit in shared memory then returns
+ * FST_ERR_INVALID_ARG from fst_multi_eval. block: 32, 64, 128 or 256. */
+FST_API fst_status fst_multi_set_launch(fst_multi* multi, int32_t block, int32_t variant);
 
 /* ---------------------------------------------------------------------------
  * Measurement. The paper reports speed against other libraries (Sec. 4.2);
@@ -540,6 +552,13 @@ FST_API fst_status fst_multi_eval(fst_multi* multi, const fst_multi_io* io, void
  * otherwise or when out is too small. */
 FST_API fst_status fst_fp32_probe(int32_t blocks_per_sm, int32_t iters, float* out, size_t out_bytes,
                                   double* flops, void* stream);
+
+/* The ids (PTX %smid) of the current device's SMs, sorted ascending, for
+ * building the role table of fst_model_set_sm_roles: a GPU may number its
+ * SMs with gaps, so they need not be 0 .. SMs - 1. Writes up to `capacity`
+ * ids and sets *n to their number. Synchronous (launches a probe kernel of
+ * one block per SM three times and reads the ids back). */
+FST_API fst_status fst_sm_ids(int32_t* ids, int32_t capacity, int32_t* n);
 
 /* Message for the last non-OK status on this thread ("" if none). */
 FST_API const char* fst_last_error(void);

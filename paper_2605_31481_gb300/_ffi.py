@@ -113,9 +113,11 @@ _SIGS = {
     "fst_multi_create": (c_int32, [ctypes.POINTER(c_void_p), c_int32, ctypes.POINTER(c_void_p)]),
     "fst_multi_destroy": (c_int32, [c_void_p]),
     "fst_multi_eval": (c_int32, [c_void_p, ctypes.POINTER(MultiIO), c_void_p]),
+    "fst_multi_set_launch": (c_int32, [c_void_p, c_int32, c_int32]),
     "fst_packed_layout": (c_int32, [c_void_p, ctypes.POINTER(c_int32), c_int32, ctypes.POINTER(c_int32),
                                     ctypes.POINTER(c_int32), ctypes.POINTER(c_int32)]),
     "fst_fp32_probe": (c_int32, [c_int32, c_int32, c_void_p, ctypes.c_size_t, ctypes.POINTER(c_double), c_void_p]),
+    "fst_sm_ids": (c_int32, [ctypes.POINTER(c_int32), c_int32, ctypes.POINTER(c_int32)]),
     "fst_last_error": (ctypes.c_char_p, []),
     "fst_version": (ctypes.c_char_p, []),
 }

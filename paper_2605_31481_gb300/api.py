@@ -528,6 +528,12 @@ class MultiBatch:
         check(_ffi.lib().fst_multi_create(arr, len(self.models), ctypes.byref(h)))
         self._h = h
 
+    def set_launch(self, block=64, variant="generic"):
+        """Launch form of eval() (fst_multi_set_launch): "generic" (one
+        environment per thread) or "level" (level-parallel, 32 environments
+        per item), with `block` threads per block."""
+        check(_ffi.lib().fst_multi_set_launch(self._h, int(block), _ffi.VARIANTS[variant]))
+
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
             _ffi.lib().fst_multi_destroy(self._h)
@@ -588,3 +594,19 @@ def fp32_probe(blocks_per_sm: int = 4, iters: int = 1 << 16, out=None):
     check(_ffi.lib().fst_fp32_probe(int(blocks_per_sm), int(iters), _ptr(out), out.numel() * 4, ctypes.byref(fl),
                                     _stream()))
     return fl.value, out
+
+
+_SM_IDS = {}
+
+
+def sm_ids(device=None):
+    """The hardware ids of the device's SMs (fst_sm_ids), sorted; probed once
+    per device."""
+    dev = torch.cuda.current_device() if device is None else torch.device(device).index or 0
+    if dev not in _SM_IDS:
+        buf = (ctypes.c_int32 * 1024)()
+        n = ctypes.c_int32()
+        with torch.cuda.device(dev):
+            check(_ffi.lib().fst_sm_ids(buf, 1024, ctypes.byref(n)))
+        _SM_IDS[dev] = [buf[k] for k in range(min(n.value, 1024))]
+    return _SM_IDS[dev]

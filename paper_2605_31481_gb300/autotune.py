@@ -100,6 +100,11 @@ def sm_count(device):
     return torch.cuda.get_device_properties(device).multi_processor_count
 
 
+def sm_ids(device):
+    """The hardware ids of the device's SMs (api.sm_ids)."""
+    return api.sm_ids(device)
+
+
 def cold_time_us(fn, R, reps=5, trials=3):
     """Device time per call of fn(k) in microseconds, from a CUDA graph of the
     R calls fn(0) .. fn(R - 1) replayed reps times: with fn(k) working on the
@@ -400,7 +405,8 @@ class StepPlan:
             variant, block = part.split("/")
             self.model.set_launch([kind], int(block), variant)
         if counts:
-            self.model.set_sm_roles(self.pin_roles([int(c) for c in counts.split("-")]))
+            self.model.set_sm_roles(self.pin_roles([int(c) for c in counts.split("-")],
+                                                   ids=sm_ids(self.model.device)))
 
     def pin_count_candidates(self, B, n_sm=None):
         """SM counts (ABA, KIN, RNEA, CRBA) to try for the pinned step: ABA
@@ -420,21 +426,24 @@ class StepPlan:
         return list(dict.fromkeys(out))
 
     @staticmethod
-    def pin_roles(counts, n_ids=256):
+    def pin_roles(counts, ids=None, n_ids=256):
         """Role names for the SM ids 0 .. n_ids - 1 from SM counts (ABA, KIN,
-        RNEA, CRBA): the roles are interleaved along the ids, each spread
-        evenly over the first sum(counts) ids (so over both dies of the GPU);
-        ids beyond them get no role."""
+        RNEA, CRBA): the roles are interleaved along the given SM ids (the
+        hardware's, api.sm_ids(); by default 0 .. sum(counts) - 1), each
+        spread evenly over them (so over both dies of the GPU); every other
+        id gets no role."""
         names = ("aba", "kin", "rnea", "crba")
         total = sum(counts)
-        out, acc = [], [0.0] * 4
-        for _ in range(total):
+        ids = list(range(total)) if ids is None else list(ids)[:total]
+        out, acc = ["none"] * n_ids, [0.0] * 4
+        for sid in ids:
             for r in range(4):
                 acc[r] += counts[r] / total
             r = max(range(4), key=lambda j: acc[j])
             acc[r] -= 1.0
-            out.append(names[r])
-        return out + ["none"] * (n_ids - total)
+            if sid < n_ids:
+                out[sid] = names[r]
+        return out
 
     def _set_alt(self, mode, alt):
         """The plan's binary option: for the concurrent mode, the longest

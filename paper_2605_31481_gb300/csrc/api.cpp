@@ -283,7 +283,9 @@ fst_status fst_model_set_launch(fst_model* m, uint32_t kinds, int32_t block, int
     if (((kinds >> k) & 1u) && variant == FST_VARIANT_PINNED && k == JK_EVAL && !jit_has_slot(m, JK_EVAL, 3))
       return set_error(FST_ERR_INVALID_ARG, "fst_model_set_launch: pinned eval needs the specialised eval kernel");
     if (((kinds >> k) & 1u) && variant == FST_VARIANT_PINNED && k == JK_EVAL &&
-        (size_t)2 * (m->nq + 2 * m->nv + kAbaStateFloats * m->n) * 32 * sizeof(float) > kLevelSmemLimit)
+        (size_t)2 * (m->nq + 2 * m->nv + kAbaStateFloats * m->n) * 32 * sizeof(float) +
+                (size_t)m->n * (sizeof(BodyC) + sizeof(BodyI)) + sizeof(TopoLists) + 16 >
+            kLevelSmemLimit)
       return set_error(FST_ERR_INVALID_ARG, "fst_model_set_launch: the tree is too large for the pinned step "
                                             "(two level-parallel ABA tiles do not fit in shared memory)");
     if (((kinds >> k) & 1u) && variant == FST_VARIANT_PINNED && k == JK_ABA &&
@@ -319,6 +321,8 @@ fst_status fst_model_set_sm_roles(fst_model* m, const int32_t* role_of_sm, int32
   if (err == cudaSuccess) err = cudaMemcpy(m->dpin, table, sizeof(table), cudaMemcpyHostToDevice);
   if (err == cudaSuccess)
     for (int i = 0; i < kPinTableSize; ++i) m->pin_table[i] = table[i];
+  // the SM ids that exist, for the pinned step's tiles per role (once)
+  if (err == cudaSuccess && m->sm_ids.empty()) err = sm_ids(m->sm_ids);
   return err == cudaSuccess ? FST_OK : cuda_error("fst_model_set_sm_roles", err);
 }
 
@@ -483,13 +487,18 @@ size_t pinned_step_plan(const fst_model* m, int64_t B, const EvalArgs& a, int sm
       continue;
     }
     int n_sm = 0;
-    for (int s = 0; s < sms && s < kPinTableSize; ++s) n_sm += m->pin_table[s] == role;
+    if (m->sm_ids.empty()) {
+      for (int s = 0; s < sms && s < kPinTableSize; ++s) n_sm += m->pin_table[s] == role;
+    } else {
+      for (int s : m->sm_ids) n_sm += s < kPinTableSize && m->pin_table[s] == role;
+    }
     int64_t E = (B + (n_sm > 0 ? n_sm : 1) - 1) / (n_sm > 0 ? n_sm : 1);
     E = (E + 31) / 32 * 32;
     E = E < 32 ? 32 : (E > 256 ? 256 : E);
     p.envs[r] = (int)E;
     p.tiles[r] = (int)((B + E - 1) / E);
   }
+  sh += (size_t)m->n * (sizeof(BodyC) + sizeof(BodyI)) + (sizeof(TopoLists) + 15) / 16 * 16;  // the staged model
   const size_t one_per_sm = 116 * 1024;
   return sh > one_per_sm ? sh : one_per_sm;
 }
@@ -978,7 +987,9 @@ fst_status fst_multi_eval(fst_multi* g, const fst_multi_io* io, void* stream) {
   for (int k = 0; k < n; ++k) order[k] = k;
   for (int i = 1; i < n; ++i)
     for (int j = i; j > 0 && g->models[order[j]]->n > g->models[order[j - 1]]->n; --j) std::swap(order[j], order[j - 1]);
-  const int T = g->block;
+  const bool level = g->variant == FST_VARIANT_LEVEL;
+  const int T = level ? 32 : g->block;  // environments per item
+  size_t state_bytes = 0;               // level: per-body state of the largest (tree, operator) pair
   // every block of the persistent grid draws one item past the last, so the
   // int work counter reaches n_items + grid: keep ample headroom below 2^31
   const int64_t kMaxItems = (int64_t)INT32_MAX - (1 << 24);
@@ -992,6 +1003,12 @@ fst_status fst_multi_eval(fst_multi* g, const fst_multi_io* io, void* stream) {
                        : r == ROLE_CRBA ? (const void*)x.M
                        : r == ROLE_RNEA ? (const void*)x.tau_out : (const void*)x.poses;
       if (!outp || x.B == 0) continue;
+      if (level) {
+        const int F = r == ROLE_ABA ? kAbaStateFloats : r == ROLE_CRBA ? kCrbaStateFloats
+                    : r == ROLE_RNEA ? kRneaStateFloats : kFkStateFloats;
+        const size_t need = (size_t)F * g->models[k]->n * 32 * sizeof(float);
+        if (need > state_bytes) state_bytes = need;
+      }
       a.seg_start[seg] = (int)items;  // within kMaxItems: checked below on every addition
       a.seg_model[seg] = (unsigned char)k;
       a.seg_op[seg] = (unsigned char)r;
@@ -1005,7 +1022,26 @@ fst_status fst_multi_eval(fst_multi* g, const fst_multi_io* io, void* stream) {
   a.model_bytes = (size_t)max_n * (sizeof(BodyC) + sizeof(BodyI)) + (sizeof(TopoLists) + 15) / 16 * 16;
   a.model_bytes = (a.model_bytes + 15) / 16 * 16;
   if (items == 0) return FST_OK;
+  if (level) {
+    const size_t sh = a.model_bytes + (size_t)a.max_rows * 32 * sizeof(float) + state_bytes;
+    if (sh > kLevelSmemLimit)
+      return set_error(FST_ERR_INVALID_ARG, std::string(fn) + ": the level-parallel state of the largest tree "
+                                                              "does not fit in shared memory");
+    return finish(fn, launch_multi_level(a, state_bytes, g->block, (cudaStream_t)stream));
+  }
   return finish(fn, launch_multi(a, max_n, T, (cudaStream_t)stream));
+}
+
+fst_status fst_multi_set_launch(fst_multi* g, int32_t block, int32_t variant) {
+  static const char* fn = "fst_multi_set_launch";
+  if (!g) return set_error(FST_ERR_INVALID_ARG, std::string(fn) + ": null group");
+  if (variant != FST_VARIANT_GENERIC && variant != FST_VARIANT_LEVEL)
+    return set_error(FST_ERR_INVALID_ARG, std::string(fn) + ": the variant must be FST_VARIANT_GENERIC or FST_VARIANT_LEVEL");
+  if (block != 32 && block != 64 && block != 128 && block != 256)
+    return set_error(FST_ERR_INVALID_ARG, std::string(fn) + ": block must be 32, 64, 128 or 256");
+  g->block = block;
+  g->variant = variant;
+  return FST_OK;
 }
 
 }  // extern "C"

@@ -1,6 +1,8 @@
 // Internal layout shared by the host model builder and the kernels.
 #pragma once
 
+#include <cuda_runtime.h>
+
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -27,6 +29,7 @@ struct fst_model {
   fst::TopoLists* dt = nullptr;      // device copy
   int* dpin = nullptr;               // SM-pinned launches: role table, then the counter regions
   int pin_table[256] = {};           // host copy of the role table (FST_ROLE_*, -1 none)
+  std::vector<int> sm_ids;           // the device's SM ids (probed when the role table is set)
   fst::JitState* jit = nullptr;      // run-time specialised kernels, if any
   int block[16] = {0};               // threads per block per kernel kind (0 = built-in heuristic)
   int variant[16] = {0};             // per kind: 0 auto, 1 generic, 2 specialised (see fst_model_set_launch)
@@ -39,6 +42,8 @@ fst_status set_error(fst_status s, const std::string& msg);
 // and the model's device current. FST_OK when the call may go on; *skip is
 // set when B == 0 (nothing to launch).
 fst_status check_call(const char* fn, const fst_model* m, int64_t B, bool* skip);
+// Ids (%smid) of the current device's SMs, sorted (probe.cu; synchronous).
+cudaError_t sm_ids(std::vector<int>& ids);
 fst_status build_model_host(const fst_body_desc* bodies, int32_t n, const double gravity[3],
                             fst_model* m);
 inline ModelView view_of(const fst_model* m, const float* theta) {

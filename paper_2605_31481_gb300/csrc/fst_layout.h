@@ -84,8 +84,12 @@ struct PackedJ {
   int off[FST_MAX_LINKS];
 };
 
-// Floats of level-parallel ABA state per body and environment (level.cuh):
-// X 12 | va 6 | c 6 | IA 21 | pA 6 | U 6 | invD | u.
+// Floats of level-parallel state per body and environment (level.cuh):
+// FK X 12; RNEA X 12 | v 6 | a 6 | f 6; CRBA X 12 | Ic 10 | contribution 10;
+// ABA X 12 | va 6 | c 6 | IA 21 | pA 6 | U 6 | invD | u.
+constexpr int kFkStateFloats = 12;
+constexpr int kRneaStateFloats = 30;
+constexpr int kCrbaStateFloats = 32;
 constexpr int kAbaStateFloats = 59;
 
 // Operators of the fused evaluation kernel, in launch order (longest first,

@@ -234,13 +234,18 @@ extern "C" __global__ void __launch_bounds__(256) FST_JIT_EXT_NAME(ModelView mv,
 // two tiles of 32 environments with four warps each.
 //  * KIN, RNEA and CRBA: one environment per thread, p.envs[slot] (<= 256)
 //    environments per tile;
-//  * ABA: level-parallel (level.cuh, the tree compiled in), 64 environments
-//    per tile as two tiles of 32, each tile's four warps splitting every level.
-// Dynamic shared memory: two ABA tiles (input rows and per-body state) or the
-// staged input rows of 256 environments, whichever is larger.
+//  * ABA: level-parallel (level.cuh), 64 environments per tile as two tiles
+//    of 32, each tile's four warps splitting every level.
+// Dynamic shared memory: the model, then two ABA tiles (input rows and
+// per-body state) or the staged input rows of 256 environments, whichever is
+// larger.
 extern "C" __global__ void __launch_bounds__(256) FST_JIT_PIN_NAME(ModelView mv, int64_t B, EvalArgs a, PinArgs p) {
   extern __shared__ float4 smem[];
-  float* base = reinterpret_cast<float*>(smem);
+  // ABA runs the level-parallel bodies over the model staged in shared memory
+  // (compact loops: the fully unrolled form of the compiled-in tree runs about
+  // twice as long here)
+  const SmemModel sm = stage_model(mv, smem);
+  float* base = smem_tile(smem, mv.n);
   const int tid = threadIdx.x + 32 * (threadIdx.y + 2 * threadIdx.z);
   const int code = pinned_role(p);
   int my = -1;
@@ -260,7 +265,7 @@ extern "C" __global__ void __launch_bounds__(256) FST_JIT_PIN_NAME(ModelView mv,
       stage_block_rows(tile + (mv.nq + mv.nv) * kLaneEnvs, a.tau, mv.nv, B, e);
       cp_async_wait_all();
       __syncthreads();
-      aba_level(tp, world_accel(mv), Col{tile + lane, kLaneEnvs}, Col{tile + mv.nq * kLaneEnvs + lane, kLaneEnvs},
+      aba_level(sm, world_accel(mv), Col{tile + lane, kLaneEnvs}, Col{tile + mv.nq * kLaneEnvs + lane, kLaneEnvs},
                 Col{tile + (mv.nq + mv.nv) * kLaneEnvs + lane, kLaneEnvs}, S, a.qdd_out, B, e, e < B);
     } else {
       const int E = p.envs[slot];

@@ -99,9 +99,9 @@ struct LaneState {
 };
 
 // floats of per-body state per environment
-constexpr int kFkState = 12;
-constexpr int kRneaState = 30;   // X 12 | v 6 | a 6 | f 6
-constexpr int kCrbaState = 32;   // X 12 | Ic 10 | contribution 10
+constexpr int kFkState = kFkStateFloats;
+constexpr int kRneaState = kRneaStateFloats;   // X 12 | v 6 | a 6 | f 6
+constexpr int kCrbaState = kCrbaStateFloats;   // X 12 | Ic 10 | contribution 10
 constexpr int kAbaState = kAbaStateFloats;    // X 12 | va 6 | c 6 | IA 21 | pA 6 | U 6 | invD | u
 
 // Warps of one tile of 32 environments (lane = threadIdx.x & 31). A 1-D

@@ -13,8 +13,8 @@
 // launch, so the pair can be captured into a CUDA graph; there is no
 // inter-block waiting of any kind.
 #include "launch.h"
+#include "level.cuh"
 #include "multi.h"
-#include "ops.cuh"
 
 namespace fst {
 namespace {
@@ -74,6 +74,68 @@ __global__ void __launch_bounds__(256) multi_kernel(MultiArgs a) {
   }
 }
 
+// The same work list run with the level-parallel bodies (level.cuh): an item
+// is 32 environments (one per lane) of one operator on one tree, and the
+// block's warps split each of the tree's levels. Shared memory: the largest
+// tree's model, the staged input rows, then the per-body state of the
+// largest (tree, operator) pair.
+__global__ void __launch_bounds__(256) multi_level_kernel(MultiArgs a) {
+  extern __shared__ float4 smem[];
+  __shared__ int s_item;
+  float* tile = reinterpret_cast<float*>(reinterpret_cast<char*>(smem) + a.model_bytes);
+  const int lane = threadIdx.x & 31;
+  int cur = -1;
+  SmemModel sm{nullptr, nullptr, 0};
+  for (;;) {
+    if (threadIdx.x == 0) s_item = atomicAdd(a.counter, 1);
+    __syncthreads();
+    const int item = s_item;
+    if (item >= a.n_items) break;
+    int sg = 0;
+    while (item >= a.seg_start[sg + 1]) ++sg;
+    const int m = a.seg_model[sg];
+    const int op = a.seg_op[sg];
+    const ModelView& mv = a.mv[m];
+    const MultiIO& io = a.io[m];
+    if (m != cur) {
+      sm = stage_model(mv, smem);  // synchronises the block
+      cur = m;
+    }
+    const int64_t B = io.B;
+    const int64_t e = (int64_t)(item - a.seg_start[sg]) * kLaneEnvs + lane;
+    const bool act = e < B;
+    stage_block_rows(tile, io.q, mv.nq, B, e);
+    if (op == ROLE_RNEA) {
+      stage_block_rows(tile + mv.nq * kLaneEnvs, io.qd, mv.nv, B, e);
+      stage_block_rows(tile + (mv.nq + mv.nv) * kLaneEnvs, io.qdd, mv.nv, B, e);
+    } else if (op == ROLE_ABA) {
+      stage_block_rows(tile + mv.nq * kLaneEnvs, io.qd, mv.nv, B, e);
+      stage_block_rows(tile + (mv.nq + mv.nv) * kLaneEnvs, io.tau, mv.nv, B, e);
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    const Col cq{tile + lane, kLaneEnvs};
+    const Col c1{tile + mv.nq * kLaneEnvs + lane, kLaneEnvs};
+    const Col c2{tile + (mv.nq + mv.nv) * kLaneEnvs + lane, kLaneEnvs};
+    float* state = tile + a.max_rows * kLaneEnvs;
+    switch (op) {
+      case ROLE_ABA:
+        aba_level(sm, world_accel(mv), cq, c1, c2, LaneState{state, kAbaState}, io.qdd_out, B, e, act);
+        break;
+      case ROLE_CRBA:
+        crba_level(sm, cq, mv.nv, LaneState{state, kCrbaState}, io.M, B, e, act);
+        break;
+      case ROLE_RNEA:
+        rnea_level(sm, world_accel(mv), cq, c1, c2, LaneState{state, kRneaState}, io.tau_out, B, e, act);
+        break;
+      default:
+        fk_level(sm, cq, LaneState{state, kFkState}, io.poses, B, e, act);
+        break;
+    }
+    __syncthreads();  // everyone is done with this item's shared memory
+  }
+}
+
 }  // namespace
 
 // Grid = resident blocks per SM x SMs (from the occupancy calculator), but
@@ -95,6 +157,17 @@ cudaError_t launch_multi(const MultiArgs& a, int max_n, int block, cudaStream_t 
   FST_NB_DISPATCH(max_n, prepare(multi_kernel<NB>, sh);
                   const int grid = persistent_grid(multi_kernel<NB>, block, sh, a.n_items);
                   multi_kernel<NB><<<grid, block, sh, s>>>(a));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_multi_level(const MultiArgs& a, size_t state_bytes, int block, cudaStream_t s) {
+  const size_t sh = a.model_bytes + (size_t)a.max_rows * kLaneEnvs * sizeof(float) + state_bytes;
+  if (sh > kLevelSmemLimit) return cudaErrorInvalidConfiguration;
+  cudaError_t err = cudaMemsetAsync(a.counter, 0, sizeof(int), s);
+  if (err != cudaSuccess) return err;
+  prepare(multi_level_kernel, sh);
+  const int grid = persistent_grid(multi_level_kernel, block, sh, a.n_items);
+  multi_level_kernel<<<grid, block, sh, s>>>(a);
   return cudaGetLastError();
 }
 

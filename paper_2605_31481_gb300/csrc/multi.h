@@ -34,7 +34,12 @@ struct MultiArgs {
   int* counter;          // device work counter (reset before each launch)
 };
 
+// Environments per item: `block` for the generic kernel (one environment per
+// thread), 32 for the level-parallel one.
 cudaError_t launch_multi(const MultiArgs& a, int max_n, int block, cudaStream_t s);
+// The level-parallel form: items of 32 environments, the block's warps
+// splitting each tree level; state_bytes of per-body state per block.
+cudaError_t launch_multi_level(const MultiArgs& a, size_t state_bytes, int block, cudaStream_t s);
 
 }  // namespace fst
 
@@ -43,4 +48,5 @@ struct fst_multi {
   int* counter = nullptr;
   int device = -1;
   int block = 64;
+  int variant = FST_VARIANT_GENERIC;  // or FST_VARIANT_LEVEL
 };

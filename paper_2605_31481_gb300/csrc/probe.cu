@@ -10,6 +10,7 @@
 #include <cuda_runtime.h>
 
 #include <string>
+#include <vector>
 
 #include "fst_internal.h"
 
@@ -51,5 +52,69 @@ extern "C" fst_status fst_fp32_probe(int32_t blocks_per_sm, int32_t iters, float
   err = cudaGetLastError();
   if (err != cudaSuccess) return fst::set_error(FST_ERR_CUDA, std::string(fn) + ": " + cudaGetErrorString(err));
   *flops = 2.0 * kChains * (double)iters * (double)blocks * kThreads;
+  return FST_OK;
+}
+
+// ---- SM ids -------------------------------------------------------------------
+// The ids (%smid) of the SMs a launch can land on need not be 0 .. SMs - 1
+// (a GPU may number its SMs with gaps). The SM-pinned launches give roles by
+// SM id, so they need the ids that exist.
+
+namespace {
+
+__global__ void sm_id_kernel(int* out) {
+  if (threadIdx.x == 0) {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%smid;" : "=r"(r));
+    out[blockIdx.x] = (int)r;
+  }
+}
+
+}  // namespace
+
+namespace fst {
+
+// Ids of the SMs of the current device, sorted: one block per SM (a shared
+// memory request larger than half an SM's keeps blocks apart), recorded and
+// deduplicated, three rounds united in case a busy SM missed one.
+// Synchronous.
+cudaError_t sm_ids(std::vector<int>& ids) {
+  int dev = -1, sms = 0;
+  cudaError_t err = cudaGetDevice(&dev);
+  if (err == cudaSuccess) err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (err != cudaSuccess) return err;
+  int* d = nullptr;
+  err = cudaMalloc((void**)&d, sizeof(int) * sms);
+  if (err != cudaSuccess) return err;
+  const int sh = 120 * 1024;
+  err = cudaFuncSetAttribute(sm_id_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, sh);
+  std::vector<int> h(sms);
+  std::vector<bool> seen(1024, false);
+  for (int round = 0; round < 3 && err == cudaSuccess; ++round) {
+    sm_id_kernel<<<sms, 32, sh>>>(d);
+    err = cudaGetLastError();
+    if (err == cudaSuccess) err = cudaMemcpy(h.data(), d, sizeof(int) * sms, cudaMemcpyDeviceToHost);
+    if (err == cudaSuccess)
+      for (int v : h)
+        if (v >= 0 && v < 1024) seen[v] = true;
+  }
+  cudaFree(d);
+  ids.clear();
+  for (int v = 0; v < 1024; ++v)
+    if (seen[v]) ids.push_back(v);
+  return err;
+}
+
+}  // namespace fst
+
+extern "C" fst_status fst_sm_ids(int32_t* ids, int32_t capacity, int32_t* n) {
+  static const char* fn = "fst_sm_ids";
+  if (!n || capacity < 0 || (capacity > 0 && !ids))
+    return fst::set_error(FST_ERR_INVALID_ARG, std::string(fn) + ": bad argument");
+  std::vector<int> v;
+  const cudaError_t err = fst::sm_ids(v);
+  if (err != cudaSuccess) return fst::set_error(FST_ERR_CUDA, std::string(fn) + ": " + cudaGetErrorString(err));
+  *n = (int32_t)v.size();
+  for (int k = 0; k < (int)v.size() && k < capacity; ++k) ids[k] = v[k];
   return FST_OK;
 }

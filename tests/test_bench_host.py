@@ -42,6 +42,11 @@ def test_pin_roles_counts_and_spread():
         for name, c in zip(("aba", "kin", "rnea", "crba"), counts):
             assert roles[:n].count(name) == c
             assert abs(roles[:n // 2].count(name) - c / 2) <= 1.5
+    # over hardware ids with gaps: the roles land on the given ids only
+    ids = [i for i in range(200) if i % 9 != 4][:152]
+    roles = StepPlan.pin_roles([64, 32, 24, 32], ids=ids)
+    assert [roles[i] for i in range(256) if i not in ids] == ["none"] * (256 - 152)
+    assert sorted(roles[i] for i in ids).count("aba") == 64
 
 
 def test_algorithmic_bytes_per_environment():

@@ -99,3 +99,42 @@ def test_mixed_batch_replays_from_a_cuda_graph(torch_cuda):
     for e, o in zip(eager, outs):
         for k in e:
             assert torch.equal(e[k], o[k]), k
+
+
+@pytest.mark.parametrize("block", [64, 256])
+def test_mixed_batch_level_parallel_form(torch_cuda, block):
+    """fst_multi_set_launch(FST_VARIANT_LEVEL): items of 32 environments run
+    with the level-parallel bodies; bit-identical to the per-tree
+    level-parallel calls at the same block, and the oracle's numbers."""
+    torch = torch_cuda
+    from paper_2605_31481_gb300 import api
+    trees = w.mixed_trees()
+    models = [api.Model(t) for t in trees]
+    counts = [c + 5 for c in COUNTS]
+    items, states = _items(torch, trees, counts)
+    mb = api.MultiBatch(models)
+    mb.set_launch(block, "level")
+    res = mb.eval(items)
+    res2 = mb.eval(items)
+    torch.cuda.synchronize()
+    for m, t, it, r, r2, s in zip(models, trees, items, res, res2, states):
+        m.set_launch(["fk", "rnea", "crba", "aba"], block, "level")
+        per = {"poses": api.fk(m, it["q"]), "tau": api.rnea(m, it["q"], it["qd"], it["qdd"]),
+               "M": api.crba(m, it["q"]), "qdd": api.aba(m, it["q"], it["qd"], it["tau"])}
+        for k in per:
+            assert torch.equal(r[k], per[k]), (t.name, k)
+            assert torch.equal(r2[k], per[k]), (t.name, k)
+        idx = np.r_[np.arange(0, s["q"].shape[0], 41), s["q"].shape[0] - 1]
+        ref = {"poses": oracle_poses(t, s["q"][idx]), "tau": rbd.rnea(t, s["q"][idx], s["qd"][idx], s["qdd"][idx]),
+               "M": rbd.crba(t, s["q"][idx]), "qdd": rbd.aba(t, s["q"][idx], s["qd"][idx], s["tau"][idx])}
+        for k in ref:
+            assert env_err(from_soa(r[k])[idx], ref[k]).max() <= TOL[k], (t.name, k)
+
+
+def test_multi_set_launch_rejects_bad_arguments(torch_cuda):
+    from paper_2605_31481_gb300 import api, _ffi
+    mb = api.MultiBatch([api.Model(w.chain(7, seed=0))])
+    with pytest.raises(_ffi.FstError):
+        mb.set_launch(96, "level")
+    with pytest.raises(_ffi.FstError):
+        mb.set_launch(64, "specialized")

@@ -110,3 +110,15 @@ def test_set_sm_roles_rejects_bad_tables(torch_cuda):
         m.set_sm_roles(["aba"] * 300)
     with pytest.raises(_ffi.FstError):
         m.set_launch(["rnea"], 64, "pinned")                 # eval and ABA only
+
+
+def test_sm_ids_lists_every_sm_once(torch_cuda):
+    """fst_sm_ids: as many distinct hardware SM ids as the device has SMs,
+    sorted; a role table over them gives each role its requested SM count."""
+    torch = torch_cuda
+    from paper_2605_31481_gb300 import api, autotune
+    ids = api.sm_ids()
+    n = torch.cuda.get_device_properties(0).multi_processor_count
+    assert len(ids) == n and ids == sorted(set(ids))
+    roles = autotune.StepPlan.pin_roles([n // 2, n // 4, n // 8, n - n // 2 - n // 4 - n // 8], ids=ids)
+    assert sum(roles[i] == "aba" for i in ids if i < 256) == n // 2

@@ -44,6 +44,7 @@ def fakes(monkeypatch, tmp_path):
     monkeypatch.setattr(autotune.torch.cuda, "Stream", lambda *a, **k: object())
     monkeypatch.setattr(autotune, "ColdSets", lambda *a, **k: type("C", (), {"R": 1, "sets": [{}]})())
     monkeypatch.setattr(autotune, "sm_count", lambda device: 152)
+    monkeypatch.setattr(autotune, "sm_ids", lambda device: list(range(152)))
     monkeypatch.setattr(autotune, "_key", lambda model, kind, B: f"{model.fingerprint}|{kind}|{B}")
     calls = []
 
