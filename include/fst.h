@@ -560,6 +560,16 @@ FST_API fst_status fst_fp32_probe(int32_t blocks_per_sm, int32_t iters, float* o
  * one block per SM three times and reads the ids back). */
 FST_API fst_status fst_sm_ids(int32_t* ids, int32_t capacity, int32_t* n);
 
+/* *ok = 1 when the current device can address `ptr` with that same
+ * pointer: device memory of the current device, managed memory, or pinned
+ * host memory mapped into the device's address space (cudaHostAlloc'd
+ * memory under unified addressing). Any output array of the compute calls
+ * may be such pinned host memory: the kernels then write their results
+ * straight to the host (on Grace-Blackwell over the coherent NVLink-C2C
+ * link), with no separate copy. *ok = 0 for anything else, including
+ * ordinary pageable host memory, which must never be passed. */
+FST_API fst_status fst_device_can_access(const void* ptr, int32_t* ok);
+
 /* Message for the last non-OK status on this thread ("" if none). */
 FST_API const char* fst_last_error(void);
 

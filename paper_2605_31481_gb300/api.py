@@ -162,11 +162,26 @@ def _check_shape(x, shape, name, model):
         raise ValueError(f"{name} must be a contiguous float32 {tuple(shape)} tensor on {model.device}")
 
 
+def _host_out_ok(t):
+    """A pinned host tensor the device can write with its own pointer
+    (fst_device_can_access)."""
+    if t.device.type != "cpu" or not t.is_pinned():
+        return False
+    ok = ctypes.c_int32()
+    with torch.cuda.device(torch.cuda.current_device()):
+        check(_ffi.lib().fst_device_can_access(ctypes.c_void_p(t.data_ptr()), ctypes.byref(ok)))
+    return bool(ok.value)
+
+
 def _out(out, shape, model):
+    """An output tensor: on the model's device, or pinned host memory the
+    device addresses directly (the kernels then write to the host)."""
     if out is None:
         return torch.empty(shape, dtype=torch.float32, device=model.device)
-    if out.shape != torch.Size(shape) or out.dtype != torch.float32 or not out.is_contiguous() or out.device != model.device:
-        raise ValueError(f"out must be a contiguous float32 {shape} tensor on {model.device}")
+    if out.shape != torch.Size(shape) or out.dtype != torch.float32 or not out.is_contiguous() or \
+            (out.device != model.device and not _host_out_ok(out)):
+        raise ValueError(f"out must be a contiguous float32 {shape} tensor on {model.device} "
+                         "(or in pinned host memory the device can address)")
     return out
 
 

@@ -118,3 +118,25 @@ extern "C" fst_status fst_sm_ids(int32_t* ids, int32_t capacity, int32_t* n) {
   for (int k = 0; k < (int)v.size() && k < capacity; ++k) ids[k] = v[k];
   return FST_OK;
 }
+
+// ---- addressability ---------------------------------------------------------
+
+extern "C" fst_status fst_device_can_access(const void* ptr, int32_t* ok) {
+  static const char* fn = "fst_device_can_access";
+  if (!ok) return fst::set_error(FST_ERR_INVALID_ARG, std::string(fn) + ": null ok");
+  *ok = 0;
+  if (!ptr) return FST_OK;
+  int dev = -1;
+  cudaError_t err = cudaGetDevice(&dev);
+  if (err != cudaSuccess) return fst::set_error(FST_ERR_CUDA, std::string(fn) + ": " + cudaGetErrorString(err));
+  cudaPointerAttributes a{};
+  err = cudaPointerGetAttributes(&a, ptr);
+  if (err != cudaSuccess) {
+    cudaGetLastError();  // an unregistered host pointer: not addressable, not an error of the caller's stream
+    return FST_OK;
+  }
+  if (a.type == cudaMemoryTypeDevice) *ok = a.device == dev;
+  else if (a.type == cudaMemoryTypeManaged) *ok = 1;
+  else if (a.type == cudaMemoryTypeHost) *ok = a.devicePointer == ptr;  // pinned and mapped at the same address
+  return FST_OK;
+}
