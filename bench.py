@@ -143,11 +143,79 @@ def workload():
 # clocks during the timed region
 # ---------------------------------------------------------------------------
 
+class NvmlPoller:
+    """SM clock and clock-event reasons read through NVML (libnvidia-ml,
+    through ctypes: read-only queries) from a host thread every ~0.2 ms, so
+    that a timed region far shorter than nvidia-smi's sampling period still
+    holds samples. The reason bits are NVML's public clock-event reason
+    masks."""
+    BITS = {"sw_power_cap": 0x4, "hw_slowdown": 0x8, "sw_thermal_slowdown": 0x20, "hw_thermal_slowdown": 0x40}
+
+    def __init__(self, torch_device_index):
+        import ctypes
+        import threading
+        self.rows, self.ok, self._stop = [], False, threading.Event()
+        try:
+            self.lib = ctypes.CDLL("libnvidia-ml.so.1")
+            if self.lib.nvmlInit_v2() != 0:
+                return
+            self.dev = ctypes.c_void_p()
+            uuid = None
+            try:
+                import torch
+                uuid = "GPU-" + str(torch.cuda.get_device_properties(torch_device_index).uuid)
+            except Exception:
+                uuid = None
+            rc = 1
+            if uuid:
+                rc = self.lib.nvmlDeviceGetHandleByUUID(uuid.encode(), ctypes.byref(self.dev))
+            if rc != 0:
+                rc = self.lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(torch_device_index), ctypes.byref(self.dev))
+            if rc != 0:
+                return
+            self.reasons_fn = getattr(self.lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+                self.lib.nvmlDeviceGetCurrentClocksThrottleReasons
+            self.ct = ctypes
+            self.ok = True
+        except (OSError, AttributeError):
+            self.ok = False
+        self.thread = threading.Thread(target=self._run, daemon=True) if self.ok else None
+
+    def _read(self):
+        ct = self.ct
+        mhz, mx, rs = ct.c_uint(0), ct.c_uint(0), ct.c_ulonglong(0)
+        if self.lib.nvmlDeviceGetClockInfo(self.dev, 1, ct.byref(mhz)) != 0:      # NVML_CLOCK_SM
+            return None
+        self.lib.nvmlDeviceGetMaxClockInfo(self.dev, 1, ct.byref(mx))
+        self.reasons_fn(self.dev, ct.byref(rs))
+        return (time.time(), float(mhz.value), float(mx.value), None,
+                [bool(rs.value & self.BITS[n]) for n in ClockSampler.NAMES])
+
+    def _run(self):
+        while not self._stop.is_set():
+            r = self._read()
+            if r is not None:
+                self.rows.append(r)
+            time.sleep(0.0002)
+
+    def start(self):
+        if self.thread is not None:
+            self.thread.start()
+
+    def stop(self):
+        if self.thread is not None:
+            self._stop.set()
+            self.thread.join(timeout=5)
+            self.lib.nvmlShutdown()
+        return self.rows
+
+
 class ClockSampler:
-    """nvidia-smi samples (100 ms period) of SM clock and throttle reasons;
-    stats are taken over the samples whose timestamps fall in the timed
-    region (or, if the region is shorter than the period, over the samples
-    of the loaded soak just before it, flagged in_region=false)."""
+    """nvidia-smi samples (100 ms period) of SM clock and throttle reasons,
+    plus NVML reads every ~0.2 ms (NvmlPoller); stats are taken over the
+    samples whose timestamps fall in the timed region (or, if none does,
+    over the samples of the loaded soak just before it, flagged
+    in_region=false)."""
     FIELDS = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
               "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
               "clocks_event_reasons.sw_power_cap")
@@ -157,8 +225,10 @@ class ClockSampler:
         self.gpu = gpu_index
         self.proc = None
         self.marks = {}
+        self.nvml = NvmlPoller(gpu_index)
 
     def start(self):
+        self.nvml.start()
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
@@ -170,13 +240,16 @@ class ClockSampler:
         self.marks[name] = time.time()
 
     def stop(self):
-        if self.proc is None:
+        nv_rows = self.nvml.stop()
+        if self.proc is None and not nv_rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
-        time.sleep(0.2)
-        self.proc.terminate()
-        out, _ = self.proc.communicate(timeout=10)
+        out = ""
+        if self.proc is not None:
+            time.sleep(0.2)
+            self.proc.terminate()
+            out, _ = self.proc.communicate(timeout=10)
         import datetime
-        rows = []
+        rows = list(nv_rows)
         for line in out.strip().splitlines():
             r = [x.strip() for x in line.split(",")]
             try:
@@ -190,8 +263,10 @@ class ClockSampler:
             if not sel:
                 return None
             reasons = sorted({n for x in sel for n, a in zip(self.NAMES, x[4]) if a})
+            pw = [x[3] for x in sel if x[3] is not None]
             return {"sm_mhz": statistics.median(x[1] for x in sel), "sm_max_mhz": max(x[2] for x in sel),
-                    "power_w_median": statistics.median(x[3] for x in sel), "reasons": reasons, "samples": len(sel)}
+                    "power_w_median": statistics.median(pw) if pw else None, "reasons": reasons,
+                    "samples": len(sel), "nvml_samples": sum(1 for x in sel if x[3] is None)}
 
         st = stats(self.marks.get("t0", 0), self.marks.get("t1", 0))
         if st is not None:
