@@ -239,6 +239,16 @@ class ClockSampler:
     def mark(self, name):
         self.marks[name] = time.time()
 
+    def read_now(self):
+        """One NVML read from the calling thread, stamped now: called while
+        the timed work runs on the device (after it was enqueued, before the
+        host waits for it) and right after it, so that a timed region shorter
+        than the polling period still holds samples."""
+        if self.nvml.ok:
+            r = self.nvml._read()
+            if r is not None:
+                self.nvml.rows.append(r)
+
     def stop(self):
         nv_rows = self.nvml.stop()
         if self.proc is None and not nv_rows:
@@ -450,7 +460,9 @@ def run_fst(args):
     if g_rem is not None:
         g_rem.replay()
     t_end.record(stream)
+    clk.read_now()             # the step graphs are running on the device
     torch.cuda.synchronize()
+    clk.read_now()
     clk.mark("t1")
     if world > 1:
         dist.barrier()

@@ -344,8 +344,7 @@ extern "C" __global__ void __launch_bounds__(256) FST_JIT_NAME(ModelView mv, int
         rnea_level(tp, world_accel(mv), cq, c1, c2, S, a.tau_out, B, e, act);
         break;
       default:
-        fk_level(tp, cq, S, a.poses, B, e, act);
-        if (a.J) jac_columns(tp, mv.nv, a.links, S, a.J, B, e, act);
+        kin_level(tp, cq, mv.nv, a.links, S, a.poses, a.J, B, e, act);
         break;
     }
     return;

@@ -41,8 +41,7 @@ __global__ void __launch_bounds__(256) jac_level_kernel(ModelView mv, int64_t B,
   FST_LEVEL_PROLOGUE(mv.nq, kFkState);
   stage_block_rows(tile, q, mv.nq, B, e);
   FST_LEVEL_READY;
-  fk_level(sm, Col{tile + lane, kLaneEnvs}, S, poses, B, e, act);
-  jac_columns(sm, mv.nv, links, S, J, B, e, act);
+  kin_level(sm, Col{tile + lane, kLaneEnvs}, mv.nv, links, S, poses, J, B, e, act);
 }
 
 __global__ void __launch_bounds__(256) rnea_level_kernel(ModelView mv, int64_t B, const float* __restrict__ q,
@@ -139,8 +138,7 @@ __global__ void __launch_bounds__(256) eval_level_kernel(ModelView mv, int64_t B
       rnea_level(sm, world_accel(mv), cq, c1, c2, S, a.tau_out, B, e, act);
       break;
     default:
-      fk_level(sm, cq, S, a.poses, B, e, act);
-      if (a.J) jac_columns(sm, mv.nv, a.links, S, a.J, B, e, act);
+      kin_level(sm, cq, mv.nv, a.links, S, a.poses, a.J, B, e, act);
       break;
   }
 }

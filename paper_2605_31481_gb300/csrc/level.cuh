@@ -171,7 +171,11 @@ __device__ __forceinline__ void fk_level(const TP& tp, const Col& q, const LaneS
   }
 }
 
-// Jacobians after fk_level: one (link, body) column per work item.
+// Jacobians after fk_level: one (link, body) column per work item; columns
+// of bodies off a link's support path are written as zeros. (Clearing the
+// tile's rows first and writing only the support-path columns, as
+// crba_level does for M, was measured slower here: the columns are cheap to
+// write, and the clear adds L2 writes.)
 template <class TP>
 __device__ __forceinline__ void jac_columns(const TP& tp, int nv, const LinkList& links, const LaneState& S,
                                            float* __restrict__ J, int64_t B, int64_t e, bool act) {
@@ -217,6 +221,15 @@ __device__ __forceinline__ void jac_columns(const TP& tp, int nv, const LinkList
       }
     }
   }
+}
+
+// FK, then the Jacobian columns of `links` when J is given.
+template <class TP>
+__device__ __forceinline__ void kin_level(const TP& tp, const Col& q, int nv, const LinkList& links,
+                                          const LaneState& S, float* __restrict__ poses, float* __restrict__ J,
+                                          int64_t B, int64_t e, bool act) {
+  fk_level(tp, q, S, poses, B, e, act);
+  if (J) jac_columns(tp, nv, links, S, J, B, e, act);
 }
 
 // ---- RNEA -----------------------------------------------------------------------
@@ -266,11 +279,38 @@ __device__ __forceinline__ void rnea_level(const TP& tp, SV a0, const Col& q, co
 }
 
 // ---- CRBA -----------------------------------------------------------------------
+// Zeros rows [0, rows) of a [rows][B] array for the tile's 32 environments
+// e0 .. e0 + 31, shared among the tile's W warps (w = this warp). A full tile
+// of a 16-byte aligned array with B a multiple of 4 is cleared with 16-byte
+// stores (eight threads per row); otherwise with 4-byte stores, skipping
+// environments past B.
+__device__ __forceinline__ void m_clear_tile(float* __restrict__ M, int64_t rows, int64_t B, int64_t e0, int W,
+                                             int w) {
+  const int t = (threadIdx.x & 31) + (w << 5), nt = W << 5;
+  if (e0 + kLaneEnvs <= B && (B & 3) == 0 && ((reinterpret_cast<unsigned long long>(M) & 15ull) == 0)) {
+    const int part = t & 7;
+    const int64_t step = (int64_t)(nt >> 3) * B;
+    float4* p = reinterpret_cast<float4*>(M + (int64_t)(t >> 3) * B + e0 + 4 * part);
+    for (int64_t r = t >> 3; r < rows; r += nt >> 3, p += step >> 2) *p = make_float4(0.f, 0.f, 0.f, 0.f);
+    return;
+  }
+  const int l = t & 31;
+  if (e0 + l >= B) return;
+  float* p = M + (int64_t)(t >> 5) * B + e0 + l;
+  for (int64_t r = t >> 5; r < rows; r += W, p += (int64_t)W * B) *p = 0.f;
+}
+
 template <class TP>
 __device__ __forceinline__ void crba_level(const TP& tp, const Col& q, int nv, const LaneState& S,
                                            float* __restrict__ M, int64_t B, int64_t e, bool act) {
   const int W = n_warps(), w = warp_id();
   enum { X_ = 0, IC_ = 12, CT_ = 22 };
+  // Structural zeros: the tile clears its whole nv x nv block of M first,
+  // and the column phase below overwrites the entries that are not zero.
+  // The block barriers of the composite pass order the two sets of stores.
+  // Nothing is read back, so DRAM sees each line once; the clear costs L2
+  // writes, not a per-entry ancestry test.
+  if (tp.depth() > 0) m_clear_tile(M, (int64_t)nv * nv, B, e - (threadIdx.x & 31), W, w);
   FST_UNROLL
   for (int l = tp.depth() - 1; l >= 0; --l) {
     FST_FOR_MY_BODIES(tp, l, k) {
@@ -293,10 +333,9 @@ __device__ __forceinline__ void crba_level(const TP& tp, const Col& q, int nv, c
       const In10 Ic = S.in10(i, IC_);
       SV F = in_mul(Ic, S_of(tp.C(i)));
       Me[((int64_t)bi.vi * nv + bi.vi) * B] = dot(S_of(tp.C(i)), F);
-      const unsigned long long anc = tp.C(i).anc;
+      // up the support path, parent by parent (parents precede children)
       int kk = i;
-      for (int j = i - 1; j >= 0; --j) {
-        if (!((anc >> j) & 1ull)) continue;
+      for (int j = bi.parent; j >= 0; j = tp.I(j).parent) {
         F = XT_force(S.X(kk, X_), F);
         kk = j;
         const BodyI bj = tp.I(j);
@@ -327,20 +366,6 @@ __device__ __forceinline__ void crba_level(const TP& tp, const Col& q, int nv, c
       for (int r = 0; r < 6; ++r)
 #pragma unroll
         for (int cc = 0; cc < 6; ++cc) Me[((int64_t)(bi.vi + r) * nv + bi.vi + cc) * B] = blk[r][cc];
-    }
-    // structural zeros of row block i against earlier bodies off its path
-    const int ni = nv_of(bi.type);
-    if (ni == 0) continue;
-    const unsigned long long anc_i = tp.C(i).anc;
-    for (int j = 0; j < i; ++j) {
-      const BodyI bj = tp.I(j);
-      const int nj = nv_of(bj.type);
-      if (nj == 0 || ((anc_i >> j) & 1ull)) continue;
-      for (int r = 0; r < ni; ++r)
-        for (int cc = 0; cc < nj; ++cc) {
-          Me[((int64_t)(bi.vi + r) * nv + bj.vi + cc) * B] = 0.f;
-          Me[((int64_t)(bj.vi + cc) * nv + bi.vi + r) * B] = 0.f;
-        }
     }
   }
 }
