@@ -754,8 +754,12 @@ def humanoid_sweep(torch, fst, w, p_alu, hbm_gbs, Bs=(1, 64, 1024, 4096, 16384, 
         by = B * 4 * (tree.nq + 3 * tree.nv + 12 * tree.n_bodies + 6 * tree.nv * len(links) + tree.nv
                       + tree.nv ** 2 + tree.nv)
         fl = B * sum(costs.flops(tree, op, links=links if op == "jacobian" else ()) for op in OPS)
+        tuned = getattr(plan, "tuned", None) or {}
         out[str(B)] = {"us": round(us, 3), "env_evals_per_s": round(B / us * 1e6, 1), "plan": plan.mode,
-                       "roofline": roof_of(by, fl, us / 1e6, p_alu, hbm_gbs)}
+                       "roofline": roof_of(by, fl, us / 1e6, p_alu, hbm_gbs),
+                       # each operator's tuned launch and its time alone (µs, graph replay)
+                       "ops": {k: f"{v['variant']}/{v['block']} {v['us']}" for k, v in tuned.items()
+                               if k in OPS}}
     return {"workload": "humanoid_float29 (free base + 23 revolute, depth 7): FK + 4 Jacobians + RNEA + CRBA + ABA",
             "per_B": out}
 

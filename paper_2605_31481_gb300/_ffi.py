@@ -19,7 +19,7 @@ STATUS_NAMES = {
 MAX_BODIES = 64
 MAX_LINKS = 16
 VARIANTS = {"auto": 0, "generic": 1, "specialized": 2, "level": 3, "mixed": 4, "path": 5, "pathwarp": 6, "pinned": 7,
-            "level2": 8}
+            "level2": 8, "levellean": 9}
 SPEC_KINDS = ("fk", "jacobian", "rnea", "crba", "aba", "eval", "fk_vjp", "rnea_vjp", "aba_vjp", "loss_grad",
               "eval_mixed", "rnea_store", "rnea_vjp_stored", "rnea_derivatives", "aba_derivatives")
 

@@ -255,7 +255,7 @@ fst_status fst_model_set_launch(fst_model* m, uint32_t kinds, int32_t block, int
   if (!m) return set_error(FST_ERR_INVALID_ARG, "fst_model_set_launch: null model");
   if (block != 0 && block != 32 && block != 64 && block != 128 && block != 256)
     return set_error(FST_ERR_INVALID_ARG, "fst_model_set_launch: block must be 0, 32, 64, 128 or 256");
-  if (variant < FST_VARIANT_AUTO || variant > FST_VARIANT_LEVEL2)
+  if (variant < FST_VARIANT_AUTO || variant > FST_VARIANT_LEVEL_LEAN)
     return set_error(FST_ERR_INVALID_ARG, "fst_model_set_launch: unknown variant");
   if (variant == FST_VARIANT_LEVEL2 && block == 32)
     return set_error(FST_ERR_INVALID_ARG, "fst_model_set_launch: the two-tile level variant needs block >= 64");
@@ -264,7 +264,9 @@ fst_status fst_model_set_launch(fst_model* m, uint32_t kinds, int32_t block, int
     kinds = (variant == FST_VARIANT_LEVEL || variant == FST_VARIANT_LEVEL2 || variant == FST_VARIANT_PATH ||
              variant == FST_VARIANT_PATH_WARP)
                 ? (1u << (JK_EVAL + 1)) - 1u
-                : variant == FST_VARIANT_PINNED ? (1u << JK_EVAL) | (1u << JK_ABA) : FST_SPEC_ALL;
+                : variant == FST_VARIANT_PINNED ? (1u << JK_EVAL) | (1u << JK_ABA)
+                : variant == FST_VARIANT_LEVEL_LEAN ? (1u << JK_ABA)
+                                                    : FST_SPEC_ALL;
   if (kinds & ~(uint32_t)FST_SPEC_ALL) return set_error(FST_ERR_INVALID_ARG, "fst_model_set_launch: unknown kind bits");
   for (int k = 0; k < JK_COUNT; ++k) {
     if (((kinds >> k) & 1u) && variant == FST_VARIANT_MIXED && k != JK_EVAL)
@@ -278,6 +280,8 @@ fst_status fst_model_set_launch(fst_model* m, uint32_t kinds, int32_t block, int
       return set_error(FST_ERR_INVALID_ARG, "fst_model_set_launch: no path-parallel kernel for a selected kind "
                                             "(specialise FK, Jacobian, RNEA, CRBA, ABA or eval first; trees with "
                                             "more than 8 leaves have none)");
+    if (((kinds >> k) & 1u) && variant == FST_VARIANT_LEVEL_LEAN && k != JK_ABA)
+      return set_error(FST_ERR_INVALID_ARG, "fst_model_set_launch: the lean level-parallel variant is for ABA only");
     if (((kinds >> k) & 1u) && variant == FST_VARIANT_PINNED && k != JK_EVAL && k != JK_ABA)
       return set_error(FST_ERR_INVALID_ARG, "fst_model_set_launch: the pinned variant is for eval and ABA only");
     if (((kinds >> k) & 1u) && variant == FST_VARIANT_PINNED && k == JK_EVAL && !jit_has_slot(m, JK_EVAL, 3))
@@ -448,6 +452,9 @@ fst_status fst_aba(const fst_model* m, int64_t B, const float* q, const float* q
   if (use_level(m, JK_ABA, LEVEL_ABA))
     return finish(fn, launch_aba_level(mv, B, q, qd, tau, qdd, level_block(m, JK_ABA), level_tiles(m, JK_ABA),
                         (cudaStream_t)stream));
+  if (m->variant[JK_ABA] == FST_VARIANT_LEVEL_LEAN && aba_lean_smem_needed(mv, m->max_width) <= kLevelSmemLimit)
+    return finish(fn, launch_aba_level_lean(mv, B, q, qd, tau, qdd, level_block(m, JK_ABA), m->max_width,
+                                            (cudaStream_t)stream));
   if (m->variant[JK_ABA] == FST_VARIANT_PINNED) {
     int* counters = m->dpin + kPinTableSize + kPinAbaRegion * kPinRegion;
     cudaError_t err = cudaMemsetAsync(counters, 0, sizeof(int) * kPinRegion, (cudaStream_t)stream);

@@ -16,6 +16,7 @@ struct JitState;
 
 struct fst_model {
   int n = 0, nq = 0, nv = 0, depth = 0;
+  int max_width = 0;                 // bodies of the widest tree level
   int device = -1;
   bool has_free = false;
   double gravity[3] = {0, 0, 0};

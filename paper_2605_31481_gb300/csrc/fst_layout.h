@@ -37,7 +37,8 @@ struct BodyC {
   float S[6];
   float theta[10];
   unsigned long long anc;  // bit j set: body j is on this body's support path (itself included)
-  float pad[10];
+  int32_t lpos;            // position of the body within its tree level (level_body order)
+  float pad[9];
 };
 static_assert(sizeof(BodyC) == 256, "BodyC must stay 256 bytes");
 
@@ -91,6 +92,11 @@ constexpr int kFkStateFloats = 12;
 constexpr int kRneaStateFloats = 30;
 constexpr int kCrbaStateFloats = 32;
 constexpr int kAbaStateFloats = 59;
+// The lean level-parallel ABA (FST_VARIANT_LEVEL_LEAN): per body VU 6 (v,
+// then U, then a) | c 6 | invD | u; per level parity and position within the
+// level, the contribution to the parent: X^T I^a X 21 | X^T p^a 6.
+constexpr int kAbaLeanBodyFloats = 14;
+constexpr int kAbaLeanRingFloats = 27;
 
 // Operators of the fused evaluation kernel, in launch order (longest first,
 // so the slowest role's blocks are dispatched first).

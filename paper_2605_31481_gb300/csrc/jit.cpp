@@ -240,7 +240,7 @@ std::string make_source(const fst_model* m, int kind) {
     put_floats(os, c.S, 6);
     os << ",";
     put_floats(os, c.theta, 10);
-    os << "," << c.anc << "ull,{0}}";
+    os << "," << c.anc << "ull," << c.lpos << ",{0}}";
   }
   os << "};\nstatic __device__ const BodyI kI[" << m->n << "] = {";
   for (int i = 0; i < m->n; ++i) {

@@ -76,6 +76,23 @@ __global__ void __launch_bounds__(256) aba_level_kernel(ModelView mv, int64_t B,
             Col{tile + (mv.nq + mv.nv) * kLaneEnvs + lane, kLaneEnvs}, S, qdd, B, e, act);
 }
 
+// ABA with the lean per-tile state (FST_VARIANT_LEVEL_LEAN): per body
+// kAbaLeanBodyFloats, plus a ring of 2 x maxw contribution slots.
+__global__ void __launch_bounds__(256) aba_lean_kernel(ModelView mv, int64_t B, const float* __restrict__ q,
+                                                       const float* __restrict__ qd, const float* __restrict__ tau,
+                                                       float* __restrict__ qdd, int maxw) {
+  const int rows = mv.nq + 2 * mv.nv;
+  FST_LEVEL_PROLOGUE_S(rows, kAbaLeanBodyFloats,
+                       (rows + kAbaLeanBodyFloats * mv.n + 2 * kAbaLeanRingFloats * maxw) * kLaneEnvs);
+  const LaneState R{tile + (rows + kAbaLeanBodyFloats * mv.n) * kLaneEnvs, kAbaLeanRingFloats};
+  stage_block_rows(tile, q, mv.nq, B, e);
+  stage_block_rows(tile + mv.nq * kLaneEnvs, qd, mv.nv, B, e);
+  stage_block_rows(tile + (mv.nq + mv.nv) * kLaneEnvs, tau, mv.nv, B, e);
+  FST_LEVEL_READY;
+  aba_level_lean(sm, world_accel(mv), Col{tile + lane, kLaneEnvs}, Col{tile + mv.nq * kLaneEnvs + lane, kLaneEnvs},
+                 Col{tile + (mv.nq + mv.nv) * kLaneEnvs + lane, kLaneEnvs}, S, R, maxw, qdd, B, e, act);
+}
+
 // SM-pinned ABA (FST_VARIANT_PINNED): blocks on SMs pinned to ABA take
 // tiles of 32 environments until none is left (pinned_tiles). The model is
 // staged only by blocks that get work.
@@ -204,6 +221,15 @@ cudaError_t launch_crba_level(const ModelView& mv, int64_t B, const float* q, fl
 cudaError_t launch_aba_level(const ModelView& mv, int64_t B, const float* q, const float* qd, const float* tau,
                              float* qdd, int block, int tiles, cudaStream_t s) {
   return go(aba_level_kernel, mv, B, level_smem_needed(mv, LEVEL_ABA, tiles), block, tiles, 1, s, q, qd, tau, qdd);
+}
+size_t aba_lean_smem_needed(const ModelView& mv, int maxw, int tiles) {
+  const size_t t = level_tile_bytes(mv, mv.nq + 2 * mv.nv, kAbaLeanBodyFloats) +
+                   (size_t)2 * kAbaLeanRingFloats * maxw * kLaneEnvs * sizeof(float);
+  return smem_bytes(mv.n) + (size_t)tiles * t;
+}
+cudaError_t launch_aba_level_lean(const ModelView& mv, int64_t B, const float* q, const float* qd, const float* tau,
+                                  float* qdd, int block, int maxw, cudaStream_t s) {
+  return go(aba_lean_kernel, mv, B, aba_lean_smem_needed(mv, maxw, 1), block, 1, 1, s, q, qd, tau, qdd, maxw);
 }
 cudaError_t launch_aba_level_pinned(const ModelView& mv, int64_t B, const float* q, const float* qd,
                                     const float* tau, float* qdd, int block, const PinArgs& p, cudaStream_t s) {

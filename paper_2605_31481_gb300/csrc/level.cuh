@@ -473,4 +473,119 @@ __device__ __forceinline__ void aba_level(const TP& tp, SV a0, const Col& q, con
   }
 }
 
+// ---- ABA, lean shared memory ------------------------------------------------------
+// The same three passes with less state per tile, so that a large tree's
+// tiles fit two per SM: per body only VU (v in pass 1, U from pass 2, a in
+// pass 3), c, invD and u stay (kAbaLeanBodyFloats); a body's contribution to
+// its parent (X^T I^a X, X^T p^a) lives in ring R, slot (level parity,
+// position within the level), only until the parent has read it
+// (kAbaLeanRingFloats each, 2 x widest level slots); the rigid inertia and
+// the bias force are formed in pass 2, and the joint transforms recomputed
+// in passes 2 and 3 instead of stored. The root's I^A and p^A, which pass 3
+// needs for a free base, stay in its level-0 ring slot.
+template <class TP>
+__device__ __forceinline__ void aba_level_lean(const TP& tp, SV a0, const Col& q, const Col& qd, const Col& tau,
+                                               const LaneState& S, const LaneState& R, int maxw,
+                                               float* __restrict__ qdd, int64_t B, int64_t e, bool act) {
+  const int W = n_warps(), w = warp_id();
+  enum { VU_ = 0, C_ = 6, ID_ = 12, u_ = 13 };  // per body
+  enum { RI_ = 0, RP_ = 21 };                      // per ring slot
+  // 1. root to leaf: velocities and bias accelerations
+  FST_UNROLL
+  for (int l = 0; l < tp.depth(); ++l) {
+    FST_FOR_MY_BODIES(tp, l, k) {
+      const int i = tp.level_body(k);
+      const BodyC& c = tp.C(i);
+      const BodyI bi = tp.I(i);
+      const SV vJ = S_times(c, bi, qd);
+      SV vi, ci;
+      if (bi.parent < 0) {
+        vi = vJ;
+        ci = sv_zero();
+      } else {
+        vi = X_motion(joint_X(c, bi, q), S.sv(bi.parent, VU_)) + vJ;
+        ci = crm(vi, vJ);
+      }
+      S.put(i, VU_, vi);
+      S.put(i, C_, ci);
+    }
+    __syncthreads();
+  }
+  // 2. leaf to root: articulated inertias; a body of level l leaves its
+  //    contribution in ring slot (l & 1) * maxw + its position in the level
+  FST_UNROLL
+  for (int l = tp.depth() - 1; l >= 0; --l) {
+    FST_FOR_MY_BODIES(tp, l, k) {
+      const int i = tp.level_body(k);
+      const BodyI bi = tp.I(i);
+      const int slot = (l & 1) * maxw + (k - tp.level_begin(l));
+      const int child_ring = ((l + 1) & 1) * maxw;
+      const In10 I = in_load(tp.theta(i));
+      const SV vi = S.sv(i, VU_);
+      Sym6 IA = sym6_from_in(I);
+      SV pA = crf(vi, in_mul(I, vi));
+      for (int ch = tp.child_begin(i); ch < tp.child_begin(i + 1); ++ch) {
+        const int cs = child_ring + tp.C(tp.child(ch)).lpos;
+        sym6_add(IA, R.sym(cs, RI_));
+        pA = pA + R.sv(cs, RP_);
+      }
+      if (bi.type == FST_JOINT_FREE) {
+        R.putsym(slot, RI_, IA);
+        R.put(slot, RP_, pA);
+        continue;
+      }
+      Sym6 Ia = IA;
+      SV pa = pA;
+      if (bi.type != FST_JOINT_FIXED) {
+        const SV Sv = S_of(tp.C(i));
+        const SV Ui = sym6_mul(IA, Sv);
+        const float iD = 1.0f / dot(Sv, Ui);
+        const float ui = tau[bi.vi] - dot(Sv, pA);
+        S.put(i, VU_, Ui);
+        *S.at(i, ID_) = iD;
+        *S.at(i, u_) = ui;
+        if (bi.parent < 0) continue;
+        sym6_rank1_sub(Ia, Ui, iD);
+        pa = pa + sym6_mul(Ia, S.sv(i, C_)) + (ui * iD) * Ui;
+      } else {
+        if (bi.parent < 0) continue;
+        pa = pa + sym6_mul(Ia, S.sv(i, C_));
+      }
+      const Xf X = joint_X(tp.C(i), bi, q);
+      R.putsym(slot, RI_, sym6_to_parent(X, Ia));
+      R.put(slot, RP_, XT_force(X, pa));
+    }
+    __syncthreads();
+  }
+  // 3. root to leaf: accelerations (each body reads its U before it
+  //    overwrites VU with its acceleration)
+  FST_UNROLL
+  for (int l = 0; l < tp.depth(); ++l) {
+    FST_FOR_MY_BODIES(tp, l, k) {
+      const int i = tp.level_body(k);
+      const BodyI bi = tp.I(i);
+      const SV ap = bi.parent < 0 ? a0 : S.sv(bi.parent, VU_);
+      SV ai = X_motion(joint_X(tp.C(i), bi, q), ap) + S.sv(i, C_);
+      if (bi.type == FST_JOINT_REVOLUTE || bi.type == FST_JOINT_PRISMATIC) {
+        const float qi = (*S.at(i, u_) - dot(S.sv(i, VU_), ai)) * *S.at(i, ID_);
+        if (act) qdd[(int64_t)bi.vi * B + e] = qi;
+        ai = ai + qi * S_of(tp.C(i));
+      } else if (bi.type == FST_JOINT_FREE) {
+        const int slot = k - tp.level_begin(l);  // level 0: ring parity 0
+        const SV tf = SV{f3{tau[bi.vi + 3], tau[bi.vi + 4], tau[bi.vi + 5]}, f3{tau[bi.vi], tau[bi.vi + 1], tau[bi.vi + 2]}};
+        const SV anew = sym6_solve(R.sym(slot, RI_), tf - R.sv(slot, RP_));
+        const SV x = anew - ai;
+        if (act) {
+          const float xo[6] = {x.v.x, x.v.y, x.v.z, x.w.x, x.w.y, x.w.z};
+#pragma unroll
+          for (int r = 0; r < 6; ++r) qdd[(int64_t)(bi.vi + r) * B + e] = xo[r];
+        }
+        ai = anew;
+      }
+      S.put(i, VU_, ai);
+    }
+    __syncthreads();
+  }
+}
+
 }  // namespace fst

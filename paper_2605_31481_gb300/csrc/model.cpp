@@ -8,6 +8,7 @@
 //   t0 = R_pre t_post + t_pre,  a = R_pre K t_post,  b = R_pre K^2 t_post,
 // so that at run time R_pc = R0 + sin q A + (1 - cos q) Bm (Eq. 4) and
 // t_pc = t0 + sin q a + (1 - cos q) b (Eq. 5) need no matrix product.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <sstream>
@@ -218,10 +219,15 @@ fst_status build_model_host(const fst_body_desc* bodies, int32_t n, const double
   // level lists (stable: bodies of a level in body order) and child lists
   TopoLists& T = m->ht;
   int k = 0;
+  m->max_width = 0;
   for (int l = 0; l < depth; ++l) {
     T.level_start[l] = k;
     for (int i = 0; i < n; ++i)
-      if (m->level[i] == l + 1) T.level_body[k++] = i;
+      if (m->level[i] == l + 1) {
+        m->hc[i].lpos = k - T.level_start[l];
+        T.level_body[k++] = i;
+      }
+    m->max_width = std::max(m->max_width, k - T.level_start[l]);
   }
   T.level_start[depth] = k;
   k = 0;

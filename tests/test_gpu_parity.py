@@ -214,6 +214,63 @@ def test_level_parallel_variant_matches_oracle(torch_cuda, name, variant, block)
         _assert_close({k: from_soa(v) for k, v in ev.items()}, ref, f"{variant}/{name}/{block}/eval")
 
 
+@pytest.mark.parametrize("name", list(TREES))
+@pytest.mark.parametrize("block", [32, 128, 256])
+def test_lean_level_aba_matches_oracle(torch_cuda, name, block):
+    """The lean level-parallel ABA (14 floats per body, contributions in a
+    two-level ring, transforms recomputed) on every tree, 1, 4 and 8 warps
+    per tile, a ragged 333-environment batch: the oracle's accelerations,
+    and those of the standard level-parallel kernel within rounding."""
+    import torch
+    from paper_2605_31481_gb300 import api
+    tree = TREES[name]()
+    B = 333
+    s = w.random_state(tree, B, seed=16)
+    m = api.Model(tree)
+    q, qd, tau = (to_soa_cuda(s[k], torch) for k in ("q", "qd", "tau"))
+    m.set_launch(["aba"], block, "levellean")
+    lean = api.aba(m, q, qd, tau)
+    m.set_launch(["aba"], block, "level")
+    std = api.aba(m, q, qd, tau)
+    torch.cuda.synchronize()
+    ref = {"qdd": rbd.aba(tree, s["q"], s["qd"], s["tau"])}
+    err = env_err(from_soa(lean), ref["qdd"])
+    assert np.all(np.isfinite(err)) and err.max() <= TOL["qdd"], f"levellean/{name}/{block}: {err.max():.3e}"
+    scale = 1.0 + std.abs().max().item()
+    assert (lean - std).abs().max().item() <= 1e-4 * scale, name
+
+
+def test_lean_level_aba_full_size_sampled(torch_cuda):
+    """humanoid29 at B = 65536 with the lean kernel at the block the tuner
+    tries (256): sampled environments against the oracle, and the NaN of one
+    environment's input stays in that environment."""
+    import torch
+    from paper_2605_31481_gb300 import api
+    tree = TREES["humanoid29"]()
+    B = 65536
+    s = w.random_state(tree, B, seed=17)
+    m = api.Model(tree)
+    m.set_launch(["aba"], 256, "levellean")
+    q, qd, tau = (to_soa_cuda(s[k], torch) for k in ("q", "qd", "tau"))
+    q[0, 777] = float("nan")
+    out = from_soa(api.aba(m, q, qd, tau))
+    idx = np.r_[np.arange(0, B, 997), B - 1]
+    idx = idx[idx != 777]
+    ref = {"qdd": rbd.aba(tree, s["q"][idx], s["qd"][idx], s["tau"][idx])}
+    err = env_err(out[idx], ref["qdd"])
+    assert np.all(np.isfinite(err)) and err.max() <= TOL["qdd"], f"levellean/humanoid29/65536: {err.max():.3e}"
+    assert np.isnan(out[777]).any()
+    assert np.isfinite(out[np.r_[776, 778]]).all()
+
+
+def test_lean_variant_is_for_aba_only(torch_cuda):
+    from paper_2605_31481_gb300 import api, _ffi
+    m = api.Model(TREES["quadruped11"]())
+    with pytest.raises(_ffi.FstError):
+        m.set_launch(["rnea"], 128, "levellean")
+    m.set_launch(None, 128, "levellean")        # "all kinds" means ABA alone
+
+
 def test_carveout_change_keeps_shared_memory_limit(torch_cuda):
     """A change of the shared-memory carveout re-prepares each kernel; a
     smaller model prepared after it must not shrink the dynamic shared-memory

@@ -6,7 +6,7 @@ import pytest
 from scipy.spatial.transform import Rotation
 
 from paper_2605_31481_gb300 import workloads as w
-from tests._helpers import from_soa, to_soa_cuda
+from tests._helpers import TOL, env_err, from_soa, to_soa_cuda
 from tests.test_gpu_parity import _assert_close, _oracle_all
 
 pytestmark = pytest.mark.gpu
@@ -77,6 +77,12 @@ def test_random_tree_every_mapping_matches_oracle(torch_cuda, seed):
         _assert_close({k: from_soa(v) for k, v in out.items()}, ref, f"random{seed}/{variant}")
         _assert_close({k: from_soa(v) for k, v in ev.items()}, ref, f"random{seed}/{variant}/eval")
         ran.append(variant)
+    # the lean level-parallel ABA (fixed and prismatic joints, free roots)
+    m.set_launch(["aba"], 128, "levellean")
+    lean = api.aba(m, q, qd, tau)
+    torch.cuda.synchronize()
+    err = env_err(from_soa(lean), ref["qdd"])
+    assert np.all(np.isfinite(err)) and err.max() <= TOL["qdd"], f"random{seed}/levellean: {err.max():.3e}"
     m.set_sm_roles(autotune.StepPlan.pin_roles([60, 30, 30, 32]))
     try:
         m.set_launch(["eval"], 256, "pinned")
