@@ -212,15 +212,18 @@ FST_API fst_status fst_model_specialize(fst_model* model, uint32_t kinds);
  * each twice the shared memory. For trees whose per-tile state fits twice
  * in shared memory; otherwise the generic kernel runs. */
 #define FST_VARIANT_LEVEL2 8
-/* The level-parallel ABA with less shared memory per tile, so that two tiles
- * of a large tree fit on one SM (FST_VARIANT_LEVEL_LEAN; ABA only): per body
- * 14 floats per environment (v, then U, then a; c; 1/D; u) instead of 59;
- * each body's contribution to its parent (X^T I^a X, X^T p^a: 27 floats)
- * sits in a ring of two levels' slots only until the parent reads it; the
- * joint transforms are recomputed in passes 2 and 3. Same recursion
- * (Sec. 3.3 level-parallel form of the articulated-body algorithm); results
- * agree with FST_VARIANT_LEVEL within FP32 rounding. Where even the lean tile
- * does not fit in shared memory, the generic kernel runs. */
+/* The level-parallel CRBA and ABA with less shared memory per tile, so that
+ * more tiles of a large tree fit on one SM (FST_VARIANT_LEVEL_LEAN; CRBA and
+ * ABA only; "all kinds" means those two). ABA: per body 14 floats per
+ * environment (v, then U, then a; c; 1/D; u) instead of 59; each body's
+ * contribution to its parent (X^T I^a X, X^T p^a: 27 floats) sits in a
+ * ring of two levels' slots only until the parent reads it; the joint
+ * transforms are recomputed in passes 2 and 3. CRBA: per body X and
+ * F = I^c S (18 floats) instead of 32, the composite-inertia contributions
+ * in the same kind of ring, q read from global memory instead of staged.
+ * Same recursions (Sec. 3.3 level-parallel form); results agree with
+ * FST_VARIANT_LEVEL within FP32 rounding. Where even the lean tile does not
+ * fit in shared memory, the generic kernel runs. */
 #define FST_VARIANT_LEVEL_LEAN 9
 FST_API fst_status fst_model_set_launch(fst_model* model, uint32_t kinds, int32_t block, int32_t variant);
 

@@ -9,9 +9,9 @@ threads):
   level        32 environments per block, the block's warps splitting each
                tree level;
   level2       the same with two such tiles per block (half the blocks);
-  levellean    (ABA) the level-parallel ABA with 14 floats of state per body
-               and a two-level ring of contributions, so that two tiles of
-               a large tree fit on one SM;
+  levellean    (CRBA, ABA) the level-parallel kernel with less state per
+               body and a two-level ring of contributions to the parent, so
+               that more tiles of a large tree fit on one SM;
   mixed        (eval) the specialised fused kernel with each role mapped as
                its own operator is set;
   path         a lane per root-to-leaf path (trees with at most 8 leaves);
@@ -239,7 +239,7 @@ def tune(model, B, kinds=FORWARD_KINDS + ("eval",), links=None, use_cache=True, 
         fn = _op(model, kind, buf)
         cands = {}
         variants = ["generic"] + (["specialized"] if kind in spec else []) + \
-            (["level", "level2"] if kind in LEVEL_KINDS else []) + (["levellean"] if kind == "aba" else [])
+            (["level", "level2"] if kind in LEVEL_KINDS else []) + (["levellean"] if kind in ("aba", "crba") else [])
         if kind == "eval" and "eval_mixed" in spec:
             variants.append("mixed")       # specialised fused kernel, roles mapped as their operators
         if kind in spec and kind in LEVEL_KINDS:

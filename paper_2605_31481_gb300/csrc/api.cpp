@@ -265,7 +265,7 @@ fst_status fst_model_set_launch(fst_model* m, uint32_t kinds, int32_t block, int
              variant == FST_VARIANT_PATH_WARP)
                 ? (1u << (JK_EVAL + 1)) - 1u
                 : variant == FST_VARIANT_PINNED ? (1u << JK_EVAL) | (1u << JK_ABA)
-                : variant == FST_VARIANT_LEVEL_LEAN ? (1u << JK_ABA)
+                : variant == FST_VARIANT_LEVEL_LEAN ? (1u << JK_ABA) | (1u << JK_CRBA)
                                                     : FST_SPEC_ALL;
   if (kinds & ~(uint32_t)FST_SPEC_ALL) return set_error(FST_ERR_INVALID_ARG, "fst_model_set_launch: unknown kind bits");
   for (int k = 0; k < JK_COUNT; ++k) {
@@ -280,8 +280,9 @@ fst_status fst_model_set_launch(fst_model* m, uint32_t kinds, int32_t block, int
       return set_error(FST_ERR_INVALID_ARG, "fst_model_set_launch: no path-parallel kernel for a selected kind "
                                             "(specialise FK, Jacobian, RNEA, CRBA, ABA or eval first; trees with "
                                             "more than 8 leaves have none)");
-    if (((kinds >> k) & 1u) && variant == FST_VARIANT_LEVEL_LEAN && k != JK_ABA)
-      return set_error(FST_ERR_INVALID_ARG, "fst_model_set_launch: the lean level-parallel variant is for ABA only");
+    if (((kinds >> k) & 1u) && variant == FST_VARIANT_LEVEL_LEAN && k != JK_ABA && k != JK_CRBA)
+      return set_error(FST_ERR_INVALID_ARG,
+                       "fst_model_set_launch: the lean level-parallel variant is for CRBA and ABA only");
     if (((kinds >> k) & 1u) && variant == FST_VARIANT_PINNED && k != JK_EVAL && k != JK_ABA)
       return set_error(FST_ERR_INVALID_ARG, "fst_model_set_launch: the pinned variant is for eval and ABA only");
     if (((kinds >> k) & 1u) && variant == FST_VARIANT_PINNED && k == JK_EVAL && !jit_has_slot(m, JK_EVAL, 3))
@@ -431,6 +432,9 @@ fst_status fst_crba(const fst_model* m, int64_t B, const float* q, const float* 
   if (use_level(m, JK_CRBA, LEVEL_CRBA))
     return finish(fn, launch_crba_level(mv, B, q, M, level_block(m, JK_CRBA), level_tiles(m, JK_CRBA),
                         (cudaStream_t)stream));
+  if (m->variant[JK_CRBA] == FST_VARIANT_LEVEL_LEAN && crba_lean_smem_needed(mv, m->max_width) <= kLevelSmemLimit)
+    return finish(fn, launch_crba_level_lean(mv, B, q, M, level_block(m, JK_CRBA), m->max_width,
+                                             (cudaStream_t)stream));
   if (use_path(m, JK_CRBA))
     return finish(fn, path_go(m, JK_CRBA, B, m->nq, 1, (cudaStream_t)stream, mv, B, q, M));
   if (use_jit(m, JK_CRBA))

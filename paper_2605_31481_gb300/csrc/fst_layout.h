@@ -97,6 +97,10 @@ constexpr int kAbaStateFloats = 59;
 // level, the contribution to the parent: X^T I^a X 21 | X^T p^a 6.
 constexpr int kAbaLeanBodyFloats = 14;
 constexpr int kAbaLeanRingFloats = 27;
+// The lean level-parallel CRBA: per body X 12 | F = Ic S 6; per ring slot
+// the composite-inertia contribution to the parent (10).
+constexpr int kCrbaLeanBodyFloats = 18;
+constexpr int kCrbaLeanRingFloats = 10;
 
 // Operators of the fused evaluation kernel, in launch order (longest first,
 // so the slowest role's blocks are dispatched first).

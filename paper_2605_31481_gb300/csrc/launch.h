@@ -117,6 +117,10 @@ cudaError_t launch_eval_level(const ModelView& mv, int64_t B, const EvalArgs& a,
 size_t aba_lean_smem_needed(const ModelView& mv, int maxw, int tiles = 1);
 cudaError_t launch_aba_level_lean(const ModelView& mv, int64_t B, const float* q, const float* qd, const float* tau,
                                   float* qdd, int block, int maxw, cudaStream_t s);
+// The lean level-parallel CRBA (FST_VARIANT_LEVEL_LEAN).
+size_t crba_lean_smem_needed(const ModelView& mv, int maxw);
+cudaError_t launch_crba_level_lean(const ModelView& mv, int64_t B, const float* q, float* M, int block, int maxw,
+                                   cudaStream_t s);
 
 // Adjoints (adjoint.cu). scratch: vjp_scratch_floats(n, B) floats of device
 // memory for the per-block partial sums of thetabar (and the loss).

@@ -93,6 +93,18 @@ __global__ void __launch_bounds__(256) aba_lean_kernel(ModelView mv, int64_t B, 
                  Col{tile + (mv.nq + mv.nv) * kLaneEnvs + lane, kLaneEnvs}, S, R, maxw, qdd, B, e, act);
 }
 
+// CRBA with the lean per-tile state (FST_VARIANT_LEVEL_LEAN): no staged
+// rows (q is read from global memory), kCrbaLeanBodyFloats per body, a ring
+// of 2 x maxw contribution slots. Up to three blocks per SM.
+__global__ void __launch_bounds__(256, 3) crba_lean_kernel(ModelView mv, int64_t B, const float* __restrict__ q,
+                                                           float* __restrict__ M, int maxw) {
+  FST_LEVEL_PROLOGUE_S(0, kCrbaLeanBodyFloats,
+                       (kCrbaLeanBodyFloats * mv.n + 2 * kCrbaLeanRingFloats * maxw) * kLaneEnvs);
+  const LaneState R{tile + kCrbaLeanBodyFloats * mv.n * kLaneEnvs, kCrbaLeanRingFloats};
+  FST_LEVEL_READY;
+  crba_level_lean(sm, q, mv.nv, S, R, maxw, M, B, e, act);
+}
+
 // SM-pinned ABA (FST_VARIANT_PINNED): blocks on SMs pinned to ABA take
 // tiles of 32 environments until none is left (pinned_tiles). The model is
 // staged only by blocks that get work.
@@ -230,6 +242,14 @@ size_t aba_lean_smem_needed(const ModelView& mv, int maxw, int tiles) {
 cudaError_t launch_aba_level_lean(const ModelView& mv, int64_t B, const float* q, const float* qd, const float* tau,
                                   float* qdd, int block, int maxw, cudaStream_t s) {
   return go(aba_lean_kernel, mv, B, aba_lean_smem_needed(mv, maxw, 1), block, 1, 1, s, q, qd, tau, qdd, maxw);
+}
+size_t crba_lean_smem_needed(const ModelView& mv, int maxw) {
+  return smem_bytes(mv.n) +
+         (size_t)(kCrbaLeanBodyFloats * mv.n + 2 * kCrbaLeanRingFloats * maxw) * kLaneEnvs * sizeof(float);
+}
+cudaError_t launch_crba_level_lean(const ModelView& mv, int64_t B, const float* q, float* M, int block, int maxw,
+                                   cudaStream_t s) {
+  return go(crba_lean_kernel, mv, B, crba_lean_smem_needed(mv, maxw), block, 1, 1, s, q, M, maxw);
 }
 cudaError_t launch_aba_level_pinned(const ModelView& mv, int64_t B, const float* q, const float* qd,
                                     const float* tau, float* qdd, int block, const PinArgs& p, cudaStream_t s) {

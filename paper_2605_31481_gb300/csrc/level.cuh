@@ -370,6 +370,96 @@ __device__ __forceinline__ void crba_level(const TP& tp, const Col& q, int nv, c
   }
 }
 
+// ---- CRBA, lean shared memory ---------------------------------------------------
+// Joint transform of body i with its coordinates read straight from global
+// memory (rows of B; ec a valid environment index), for kernels that do not
+// stage q in shared memory.
+__device__ __forceinline__ Xf joint_X_rows(const BodyC& c, const BodyI& bi, const float* __restrict__ q, int64_t B,
+                                           int64_t ec) {
+  const int nqb = bi.type == FST_JOINT_FREE ? 7 : bi.type == FST_JOINT_FIXED ? 0 : 1;
+  float qb[7];
+#pragma unroll
+  for (int k = 0; k < 7; ++k) qb[k] = k < nqb ? __ldg(q + (int64_t)(bi.qi + k) * B + ec) : 0.f;
+  BodyI b0 = bi;
+  b0.qi = 0;
+  return joint_X(c, b0, Col{qb, 1});
+}
+
+// The composite-rigid-body algorithm with less shared memory per tile (so
+// that three tiles of a large tree fit on one SM): per body only X and
+// F = I^c S stay (kCrbaLeanBodyFloats); a body's composite inertia moved to
+// its parent lives in ring R, slot (level parity, position within the
+// level), until the parent has added it; the root keeps its own I^c in its
+// level-0 slot for a free base's 6 x 6 block. q is read from global memory,
+// not staged. Same arithmetic, in the same order, as crba_level.
+template <class TP>
+__device__ __forceinline__ void crba_level_lean(const TP& tp, const float* __restrict__ q, int nv,
+                                                const LaneState& S, const LaneState& R, int maxw,
+                                                float* __restrict__ M, int64_t B, int64_t e, bool act) {
+  const int W = n_warps(), w = warp_id();
+  enum { X_ = 0, F_ = 12 };
+  const int64_t ec = act ? e : B - 1;  // lanes past B compute on the last environment and store nothing
+  if (tp.depth() > 0) m_clear_tile(M, (int64_t)nv * nv, B, e - (threadIdx.x & 31), W, w);
+  FST_UNROLL
+  for (int l = tp.depth() - 1; l >= 0; --l) {
+    FST_FOR_MY_BODIES(tp, l, k) {
+      const int i = tp.level_body(k);
+      const BodyI bi = tp.I(i);
+      const int slot = (l & 1) * maxw + (k - tp.level_begin(l));
+      const int child_ring = ((l + 1) & 1) * maxw;
+      const Xf X = joint_X_rows(tp.C(i), bi, q, B, ec);
+      In10 Ic = in_load(tp.theta(i));
+      for (int ch = tp.child_begin(i); ch < tp.child_begin(i + 1); ++ch)
+        in_add(Ic, R.in10(child_ring + tp.C(tp.child(ch)).lpos, 0));
+      S.putX(i, X_, X);
+      if (bi.type == FST_JOINT_REVOLUTE || bi.type == FST_JOINT_PRISMATIC) S.put(i, F_, in_mul(Ic, S_of(tp.C(i))));
+      R.putin(slot, 0, bi.parent >= 0 ? in_to_parent(X, Ic) : Ic);
+    }
+    __syncthreads();
+  }
+  if (!act) return;
+  float* Me = M + e;
+  for (int i = w; i < tp.n(); i += W) {
+    const BodyI bi = tp.I(i);
+    if (bi.type == FST_JOINT_REVOLUTE || bi.type == FST_JOINT_PRISMATIC) {
+      SV F = S.sv(i, F_);
+      Me[((int64_t)bi.vi * nv + bi.vi) * B] = dot(S_of(tp.C(i)), F);
+      int kk = i;
+      for (int j = bi.parent; j >= 0; j = tp.I(j).parent) {
+        F = XT_force(S.X(kk, X_), F);
+        kk = j;
+        const BodyI bj = tp.I(j);
+        if (bj.type == FST_JOINT_REVOLUTE || bj.type == FST_JOINT_PRISMATIC) {
+          const float mij = dot(S_of(tp.C(j)), F);
+          Me[((int64_t)bi.vi * nv + bj.vi) * B] = mij;
+          Me[((int64_t)bj.vi * nv + bi.vi) * B] = mij;
+        } else if (bj.type == FST_JOINT_FREE) {
+          const float col[6] = {F.v.x, F.v.y, F.v.z, F.w.x, F.w.y, F.w.z};
+#pragma unroll
+          for (int r = 0; r < 6; ++r) {
+            Me[((int64_t)(bj.vi + r) * nv + bi.vi) * B] = col[r];
+            Me[((int64_t)bi.vi * nv + bj.vi + r) * B] = col[r];
+          }
+        }
+      }
+    } else if (bi.type == FST_JOINT_FREE) {
+      const In10 I = R.in10(tp.C(i).lpos, 0);  // the root's own slot (level 0, parity 0)
+      const float blk[6][6] = {
+          {I.m, 0.f, 0.f, 0.f, I.h.z, -I.h.y},
+          {0.f, I.m, 0.f, -I.h.z, 0.f, I.h.x},
+          {0.f, 0.f, I.m, I.h.y, -I.h.x, 0.f},
+          {0.f, -I.h.z, I.h.y, I.I[0], I.I[1], I.I[3]},
+          {I.h.z, 0.f, -I.h.x, I.I[1], I.I[2], I.I[4]},
+          {-I.h.y, I.h.x, 0.f, I.I[3], I.I[4], I.I[5]},
+      };
+#pragma unroll
+      for (int r = 0; r < 6; ++r)
+#pragma unroll
+        for (int cc = 0; cc < 6; ++cc) Me[((int64_t)(bi.vi + r) * nv + bi.vi + cc) * B] = blk[r][cc];
+    }
+  }
+}
+
 // ---- ABA ------------------------------------------------------------------------
 template <class TP>
 __device__ __forceinline__ void aba_level(const TP& tp, SV a0, const Col& q, const Col& qd, const Col& tau,

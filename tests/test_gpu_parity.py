@@ -216,11 +216,12 @@ def test_level_parallel_variant_matches_oracle(torch_cuda, name, variant, block)
 
 @pytest.mark.parametrize("name", list(TREES))
 @pytest.mark.parametrize("block", [32, 128, 256])
-def test_lean_level_aba_matches_oracle(torch_cuda, name, block):
-    """The lean level-parallel ABA (14 floats per body, contributions in a
-    two-level ring, transforms recomputed) on every tree, 1, 4 and 8 warps
-    per tile, a ragged 333-environment batch: the oracle's accelerations,
-    and those of the standard level-parallel kernel within rounding."""
+def test_lean_level_crba_aba_match_oracle(torch_cuda, name, block):
+    """The lean level-parallel CRBA (X and I^c S per body, q from global
+    memory) and ABA (14 floats per body, transforms recomputed), both with
+    contributions in a two-level ring, on every tree, 1, 4 and 8 warps per
+    tile, a ragged 333-environment batch: the oracle's M and accelerations,
+    and those of the standard level-parallel kernels within rounding."""
     import torch
     from paper_2605_31481_gb300 import api
     tree = TREES[name]()
@@ -228,20 +229,22 @@ def test_lean_level_aba_matches_oracle(torch_cuda, name, block):
     s = w.random_state(tree, B, seed=16)
     m = api.Model(tree)
     q, qd, tau = (to_soa_cuda(s[k], torch) for k in ("q", "qd", "tau"))
-    m.set_launch(["aba"], block, "levellean")
-    lean = api.aba(m, q, qd, tau)
-    m.set_launch(["aba"], block, "level")
-    std = api.aba(m, q, qd, tau)
+    M_out = torch.full((tree.nv, tree.nv, B), float("nan"), device="cuda")  # every entry must be written
+    m.set_launch(["crba", "aba"], block, "levellean")
+    lean = {"M": api.crba(m, q, out=M_out), "qdd": api.aba(m, q, qd, tau)}
+    m.set_launch(["crba", "aba"], block, "level")
+    std = {"M": api.crba(m, q), "qdd": api.aba(m, q, qd, tau)}
     torch.cuda.synchronize()
-    ref = {"qdd": rbd.aba(tree, s["q"], s["qd"], s["tau"])}
-    err = env_err(from_soa(lean), ref["qdd"])
-    assert np.all(np.isfinite(err)) and err.max() <= TOL["qdd"], f"levellean/{name}/{block}: {err.max():.3e}"
-    scale = 1.0 + std.abs().max().item()
-    assert (lean - std).abs().max().item() <= 1e-4 * scale, name
+    ref = {"M": rbd.crba(tree, s["q"]), "qdd": rbd.aba(tree, s["q"], s["qd"], s["tau"])}
+    for k in ref:
+        err = env_err(from_soa(lean[k]), ref[k])
+        assert np.all(np.isfinite(err)) and err.max() <= TOL[k], f"levellean/{name}/{block}/{k}: {err.max():.3e}"
+        scale = 1.0 + std[k].abs().max().item()
+        assert (lean[k] - std[k]).abs().max().item() <= 1e-4 * scale, (name, k)
 
 
 def test_lean_level_aba_full_size_sampled(torch_cuda):
-    """humanoid29 at B = 65536 with the lean kernel at the block the tuner
+    """humanoid29 at B = 65536 with the lean kernels at the block the tuner
     tries (256): sampled environments against the oracle, and the NaN of one
     environment's input stays in that environment."""
     import torch
@@ -250,25 +253,27 @@ def test_lean_level_aba_full_size_sampled(torch_cuda):
     B = 65536
     s = w.random_state(tree, B, seed=17)
     m = api.Model(tree)
-    m.set_launch(["aba"], 256, "levellean")
+    m.set_launch(["crba", "aba"], 256, "levellean")
     q, qd, tau = (to_soa_cuda(s[k], torch) for k in ("q", "qd", "tau"))
-    q[0, 777] = float("nan")
-    out = from_soa(api.aba(m, q, qd, tau))
+    q[7, 777] = float("nan")                  # the waist joint (q of the free base do not enter M)
+    out = {"qdd": from_soa(api.aba(m, q, qd, tau)), "M": from_soa(api.crba(m, q))}
     idx = np.r_[np.arange(0, B, 997), B - 1]
     idx = idx[idx != 777]
-    ref = {"qdd": rbd.aba(tree, s["q"][idx], s["qd"][idx], s["tau"][idx])}
-    err = env_err(out[idx], ref["qdd"])
-    assert np.all(np.isfinite(err)) and err.max() <= TOL["qdd"], f"levellean/humanoid29/65536: {err.max():.3e}"
-    assert np.isnan(out[777]).any()
-    assert np.isfinite(out[np.r_[776, 778]]).all()
+    ref = {"qdd": rbd.aba(tree, s["q"][idx], s["qd"][idx], s["tau"][idx]), "M": rbd.crba(tree, s["q"][idx])}
+    for k in ref:
+        err = env_err(out[k][idx], ref[k])
+        assert np.all(np.isfinite(err)) and err.max() <= TOL[k], f"levellean/humanoid29/65536/{k}: {err.max():.3e}"
+        assert np.isnan(out[k][777]).any()
+        assert np.isfinite(out[k][np.r_[776, 778]]).all()
 
 
-def test_lean_variant_is_for_aba_only(torch_cuda):
+def test_lean_variant_is_for_crba_and_aba_only(torch_cuda):
     from paper_2605_31481_gb300 import api, _ffi
     m = api.Model(TREES["quadruped11"]())
-    with pytest.raises(_ffi.FstError):
-        m.set_launch(["rnea"], 128, "levellean")
-    m.set_launch(None, 128, "levellean")        # "all kinds" means ABA alone
+    for kind in ("fk", "jacobian", "rnea", "eval"):
+        with pytest.raises(_ffi.FstError):
+            m.set_launch([kind], 128, "levellean")
+    m.set_launch(None, 128, "levellean")        # "all kinds" means CRBA and ABA
 
 
 def test_carveout_change_keeps_shared_memory_limit(torch_cuda):

@@ -77,12 +77,13 @@ def test_random_tree_every_mapping_matches_oracle(torch_cuda, seed):
         _assert_close({k: from_soa(v) for k, v in out.items()}, ref, f"random{seed}/{variant}")
         _assert_close({k: from_soa(v) for k, v in ev.items()}, ref, f"random{seed}/{variant}/eval")
         ran.append(variant)
-    # the lean level-parallel ABA (fixed and prismatic joints, free roots)
-    m.set_launch(["aba"], 128, "levellean")
-    lean = api.aba(m, q, qd, tau)
+    # the lean level-parallel CRBA and ABA (fixed and prismatic joints, free roots)
+    m.set_launch(["crba", "aba"], 128, "levellean")
+    lean = {"M": api.crba(m, q), "qdd": api.aba(m, q, qd, tau)}
     torch.cuda.synchronize()
-    err = env_err(from_soa(lean), ref["qdd"])
-    assert np.all(np.isfinite(err)) and err.max() <= TOL["qdd"], f"random{seed}/levellean: {err.max():.3e}"
+    for k in lean:
+        err = env_err(from_soa(lean[k]), ref[k])
+        assert np.all(np.isfinite(err)) and err.max() <= TOL[k], f"random{seed}/levellean/{k}: {err.max():.3e}"
     m.set_sm_roles(autotune.StepPlan.pin_roles([60, 30, 30, 32]))
     try:
         m.set_launch(["eval"], 256, "pinned")
