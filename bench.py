@@ -480,6 +480,12 @@ def run_fst(args):
     e2e = run_e2e(torch, fst, model, tree, B, links, st, dev, min(K, 5000), args.warmup, plan=plan,
                   slots=args.e2e_slots, split=args.e2e_split, packed=packed)
     e2e["ms"], e2e_value = job_rate(e2e["ms"], world, B, e2e["steps"], dev)
+    link = link_bandwidth(torch, dev)
+    # the end-to-end step against the link: its bytes in each direction per
+    # second of step time, over the measured one-way copy bandwidths
+    e2e_s = e2e["ms"] / e2e["steps"] / 1e3
+    link["d2h_frac"] = round(e2e["d2h"] / e2e_s / 1e9 / link["d2h_gbs"], 4)
+    link["h2d_frac"] = round(e2e["h2d"] / e2e_s / 1e9 / link["h2d_gbs"], 4)
     e2e_full = run_e2e(torch, fst, model, tree, B, links, st, dev, min(K, 5000), args.warmup, plan=plan,
                        slots=args.e2e_slots, split=args.e2e_split, packed=False)
     e2e_full["ms"], e2e_full_value = job_rate(e2e_full["ms"], world, B, e2e_full["steps"], dev)
@@ -547,7 +553,7 @@ def run_fst(args):
             "e2e": {"value": round(e2e_value, 1), "unit": "env-evals/s", "h2d_bytes_per_step": e2e["h2d"],
                     "d2h_bytes_per_step": e2e["d2h"], "steps": e2e["steps"],
                     "pipelined_slots": e2e["slots"], "readback_chunks": e2e["readback_chunks"],
-                    "output_layout": e2e["layout"]},
+                    "output_layout": e2e["layout"], "link": link},
             "e2e_full_layout": {"value": round(e2e_full_value, 1), "unit": "env-evals/s",
                                 "h2d_bytes_per_step": e2e_full["h2d"], "d2h_bytes_per_step": e2e_full["d2h"],
                                 "steps": e2e_full["steps"]},
@@ -896,6 +902,45 @@ def per_op_times(torch, launch, sets, R, stream, K_op, hot=False):
 
 def ctypes_ptr(t):
     return ctypes.c_void_p(t.data_ptr())
+
+
+def link_bandwidth(torch, dev, nbytes=256 << 20, reps=5):
+    """The host link's copy bandwidth, measured: one cudaMemcpyAsync of
+    `nbytes` between pinned host memory and the device each way (and both at
+    once, on two streams), timed with CUDA events, best of `reps`. The
+    end-to-end leg's ceiling: its per-step bytes over its step time against
+    these."""
+    n = nbytes // 4
+    h = torch.empty(n).pin_memory()
+    h2 = torch.empty(n).pin_memory()
+    d = torch.empty(n, device=dev)
+    d2 = torch.empty(n, device=dev)
+    s1, s2 = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
+    res = {}
+    for name in ("h2d", "d2h", "both"):
+        best = float("inf")
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            cur = torch.cuda.current_stream()
+            a.record(cur)
+            s1.wait_stream(cur)
+            s2.wait_stream(cur)
+            with torch.cuda.stream(s1):
+                if name in ("h2d", "both"):
+                    d.copy_(h, non_blocking=True)
+            with torch.cuda.stream(s2):
+                if name in ("d2h", "both"):
+                    h2.copy_(d2, non_blocking=True)
+            cur.wait_stream(s1)
+            cur.wait_stream(s2)
+            b.record(cur)
+            torch.cuda.synchronize()
+            best = min(best, a.elapsed_time(b) / 1e3)
+        res[f"{name}_gbs"] = round((2 if name == "both" else 1) * nbytes / best / 1e9, 1)
+    res["bytes_per_copy"] = nbytes
+    return res
 
 
 def run_e2e(torch, fst, model, tree, B, links, st, dev, K, warmup, plan=None, slots=3, split=1, packed=False):

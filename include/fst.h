@@ -543,8 +543,9 @@ FST_API fst_status fst_multi_eval(fst_multi* multi, const fst_multi_io* io, void
  * FST_VARIANT_GENERIC (the default, block 64): one environment per thread,
  * items of `block` environments. FST_VARIANT_LEVEL: the level-parallel
  * bodies of paper Sec. 3.3, items of 32 environments with the block's
- * block/32 warps splitting each tree level (results then bit-identical to
- * the per-tree level-parallel calls at that block); a group whose largest
+ * block/32 warps splitting each tree level, ABA in its lean form (results
+ * then bit-identical to the per-tree calls at that block with
+ * FST_VARIANT_LEVEL, and FST_VARIANT_LEVEL_LEAN for ABA); a group whose largest
  * tree's state does not fit in shared memory then returns
  * FST_ERR_INVALID_ARG from fst_multi_eval. block: 32, 64, 128 or 256. */
 FST_API fst_status fst_multi_set_launch(fst_multi* multi, int32_t block, int32_t variant);

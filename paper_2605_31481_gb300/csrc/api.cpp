@@ -990,6 +990,7 @@ fst_status fst_multi_eval(fst_multi* g, const fst_multi_io* io, void* stream) {
     a.io[k] = MultiIO{x.q, x.qd, x.qdd, x.tau, x.poses, m->nv ? x.tau_out : nullptr, m->nv ? x.M : nullptr,
                       m->nv ? x.qdd_out : nullptr, x.B};
     if (m->n > max_n) max_n = m->n;
+    a.maxw[k] = m->max_width;
     const int rows = m->nq + 2 * m->nv;
     if (rows > a.max_rows) a.max_rows = rows;
   }
@@ -1015,9 +1016,11 @@ fst_status fst_multi_eval(fst_multi* g, const fst_multi_io* io, void* stream) {
                        : r == ROLE_RNEA ? (const void*)x.tau_out : (const void*)x.poses;
       if (!outp || x.B == 0) continue;
       if (level) {
-        const int F = r == ROLE_ABA ? kAbaStateFloats : r == ROLE_CRBA ? kCrbaStateFloats
-                    : r == ROLE_RNEA ? kRneaStateFloats : kFkStateFloats;
-        const size_t need = (size_t)F * g->models[k]->n * 32 * sizeof(float);
+        const fst_model* m = g->models[k];
+        const size_t floats = r == ROLE_ABA ? (size_t)kAbaLeanBodyFloats * m->n + 2 * kAbaLeanRingFloats * m->max_width
+                              : (size_t)(r == ROLE_CRBA ? kCrbaStateFloats
+                                         : r == ROLE_RNEA ? kRneaStateFloats : kFkStateFloats) * m->n;
+        const size_t need = floats * 32 * sizeof(float);
         if (need > state_bytes) state_bytes = need;
       }
       a.seg_start[seg] = (int)items;  // within kMaxItems: checked below on every addition

@@ -78,7 +78,10 @@ __global__ void __launch_bounds__(256) multi_kernel(MultiArgs a) {
 // is 32 environments (one per lane) of one operator on one tree, and the
 // block's warps split each of the tree's levels. Shared memory: the largest
 // tree's model, the staged input rows, then the per-body state of the
-// largest (tree, operator) pair.
+// largest (tree, operator) pair. ABA runs in its lean form (aba_level_lean:
+// 14 floats per body and a ring of contributions instead of 59 floats per
+// body), so that the block's shared memory, sized for the largest pair, is
+// not set by ABA.
 __global__ void __launch_bounds__(256) multi_level_kernel(MultiArgs a) {
   extern __shared__ float4 smem[];
   __shared__ int s_item;
@@ -120,7 +123,9 @@ __global__ void __launch_bounds__(256) multi_level_kernel(MultiArgs a) {
     float* state = tile + a.max_rows * kLaneEnvs;
     switch (op) {
       case ROLE_ABA:
-        aba_level(sm, world_accel(mv), cq, c1, c2, LaneState{state, kAbaState}, io.qdd_out, B, e, act);
+        aba_level_lean(sm, world_accel(mv), cq, c1, c2, LaneState{state, kAbaLeanBodyFloats},
+                       LaneState{state + kAbaLeanBodyFloats * mv.n * kLaneEnvs, kAbaLeanRingFloats}, a.maxw[m],
+                       io.qdd_out, B, e, act);
         break;
       case ROLE_CRBA:
         crba_level(sm, cq, mv.nv, LaneState{state, kCrbaState}, io.M, B, e, act);

@@ -30,6 +30,7 @@ struct MultiArgs {
   unsigned char seg_op[4 * kMaxMulti];
   int n_items;
   int max_rows;          // staged input rows of the widest item
+  int maxw[kMaxMulti];   // level form: bodies of each tree's widest level (the lean ABA's ring)
   size_t model_bytes;    // shared memory reserved for the largest tree
   int* counter;          // device work counter (reset before each launch)
 };

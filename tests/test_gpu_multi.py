@@ -104,8 +104,9 @@ def test_mixed_batch_replays_from_a_cuda_graph(torch_cuda):
 @pytest.mark.parametrize("block", [64, 256])
 def test_mixed_batch_level_parallel_form(torch_cuda, block):
     """fst_multi_set_launch(FST_VARIANT_LEVEL): items of 32 environments run
-    with the level-parallel bodies; bit-identical to the per-tree
-    level-parallel calls at the same block, and the oracle's numbers."""
+    with the level-parallel bodies (ABA in its lean form); bit-identical to
+    the per-tree level-parallel calls at the same block (lean ABA), and the
+    oracle's numbers."""
     torch = torch_cuda
     from paper_2605_31481_gb300 import api
     trees = w.mixed_trees()
@@ -118,7 +119,8 @@ def test_mixed_batch_level_parallel_form(torch_cuda, block):
     res2 = mb.eval(items)
     torch.cuda.synchronize()
     for m, t, it, r, r2, s in zip(models, trees, items, res, res2, states):
-        m.set_launch(["fk", "rnea", "crba", "aba"], block, "level")
+        m.set_launch(["fk", "rnea", "crba"], block, "level")
+        m.set_launch(["aba"], block, "levellean")
         per = {"poses": api.fk(m, it["q"]), "tau": api.rnea(m, it["q"], it["qd"], it["qdd"]),
                "M": api.crba(m, it["q"]), "qdd": api.aba(m, it["q"], it["qd"], it["tau"])}
         for k in per:
