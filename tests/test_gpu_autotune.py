@@ -52,10 +52,11 @@ def test_tune_sets_and_caches(torch_cuda, tmp_path, monkeypatch):
     tree = w.chain(7, seed=0)
     m = api.Model(tree, specialize=["rnea", "aba"])
     res = autotune.tune(m, 2048, kinds=("rnea", "aba", "crba"))
-    assert res["crba"]["variant"] in ("generic", "level")       # not specialised: no specialised candidates
-    # generic x4, level x4, level2 x3 (block >= 64), and for the specialised RNEA also specialised x4,
-    # path x4 and pathwarp
-    assert len(res["rnea"]["candidates"]) == 20 and len(res["crba"]["candidates"]) == 11
+    # not specialised: no specialised candidates
+    assert res["crba"]["variant"] in ("generic", "level", "level2", "levellean")
+    # generic x4, level x4, level2 x3 (block >= 64), for CRBA also levellean x2 (blocks 128, 256), and for
+    # the specialised RNEA also specialised x4, path x4 and pathwarp
+    assert len(res["rnea"]["candidates"]) == 20 and len(res["crba"]["candidates"]) == 13
     assert not any(k.startswith("mixed") for k in res["rnea"]["candidates"])
     data = json.load(open(tmp_path / "tune.json"))
     assert len(data) == 3
