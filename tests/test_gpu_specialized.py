@@ -97,11 +97,16 @@ def test_specialized_theta_override(torch_cuda):
 
 
 @pytest.mark.parametrize("name", ["quadruped11", "humanoid29", "general8"])
-@pytest.mark.parametrize("level_kinds", [("aba",), ("aba", "crba", "rnea", "jacobian")])
+@pytest.mark.parametrize("level_kinds", [("aba",), ("aba", "crba", "rnea", "jacobian"), ("crba",), ("jacobian",),
+                                         ("crba", "jacobian")])
 def test_specialized_eval_with_level_parallel_roles(torch_cuda, name, level_kinds):
     """The specialised fused kernel runs roles whose operator is tuned
     level-parallel that way (32 environments per block, warps splitting
-    levels) and the others one environment per thread, in one launch."""
+    levels) and the others one environment per thread, in one launch. The
+    cases without ABA have a CRBA or Jacobian role set the launch's shared
+    memory: its state sits after the nq + 2 nv staged rows of the kernel's
+    layout, which the launch must allocate even though the role stages only
+    q."""
     torch = torch_cuda
     from paper_2605_31481_gb300 import api
     tree = TREES[name]()
