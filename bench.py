@@ -309,6 +309,10 @@ def plan_kernel_name(mode, desc):
         return (f"ABA kernel ({kinds['aba']}) beside two launches of the fused kernel ({kinds['eval']}: FK with the "
                 f"Jacobians; RNEA with CRBA) on parallel graph branches, carveout {carveout}" +
                 (", fused kernels forked first" if desc["fused_forked_first"] else ""))
+    if mode == "partitioned":
+        return (f"ABA kernel ({kinds['aba']}), and the fused kernel ({kinds['eval']}) once per operator group (FK with "
+                f"the Jacobians; RNEA; CRBA), each on its own SM partition (green contexts; SM counts ABA-KIN-RNEA-CRBA "
+                f"after the @), carveout {carveout}")
     if mode == "pinned":
         return (f"SM-pinned step ({kinds['eval']}): one launch of one block per SM, each SM serving one operator; "
                 f"ABA level-parallel ({kinds['aba']}: SM counts ABA-KIN-RNEA-CRBA after the @), the others one "
@@ -556,7 +560,8 @@ def run_fst(args):
             "e2e_full_layout": {"value": round(e2e_full_value, 1), "unit": "env-evals/s",
                                 "h2d_bytes_per_step": e2e_full["h2d"], "d2h_bytes_per_step": e2e_full["d2h"],
                                 "steps": e2e_full["steps"]},
-            "gpu_launches": K * {"fused": 1, "hybrid": 2, "split": 3, "pinned": 1}.get(plan.mode, len(OPS)),
+            "gpu_launches": K * {"fused": 1, "hybrid": 2, "split": 3, "pinned": 1, "partitioned": 4}.get(plan.mode,
+                                                                                                  len(OPS)),
             "kernels": kernels,
             "plan": desc,
             "clocks": clocks,

@@ -227,6 +227,32 @@ FST_API fst_status fst_model_specialize(fst_model* model, uint32_t kinds);
 #define FST_VARIANT_LEVEL_LEAN 9
 FST_API fst_status fst_model_set_launch(fst_model* model, uint32_t kinds, int32_t block, int32_t variant);
 
+/* SM partitions (CUDA green contexts): disjoint sets of a device's SMs, each
+ * with a stream whose kernels run only on its SMs, also when the launches
+ * are captured into a CUDA graph from another stream that forks into them.
+ * The operators of one step launched on separate partitions run side by
+ * side without sharing an SM, so no SM refetches another operator's
+ * instructions between launches (the level-parallel propagation of
+ * Sec. 3.3 and the fused launch of the others, as concurrent branches).
+ *
+ * fst_sm_partition_create: device = CUDA ordinal; sm_counts = HOST array of
+ * n (1 <= n <= FST_MAX_PARTITIONS) positive SM counts, each rounded up to
+ * whole groups of 8 SMs; their sum must fit the device. *out receives the
+ * handle (owned by the caller; release with fst_sm_partition_destroy, after
+ * every launch and graph that uses its streams has finished).
+ * FST_ERR_UNSUPPORTED when the driver has no green contexts,
+ * FST_ERR_INVALID_ARG for bad counts or device, FST_ERR_CUDA when a green
+ * context or stream cannot be created. Synchronous.
+ * fst_sm_partition_info: partition k's stream (a CUstream / cudaStream_t,
+ * owned by the partition) and its actual SM count; either output may be
+ * NULL. */
+#define FST_MAX_PARTITIONS 8
+typedef struct fst_sm_partition fst_sm_partition;
+FST_API fst_status fst_sm_partition_create(int32_t device, const int32_t* sm_counts, int32_t n,
+                                           fst_sm_partition** out);
+FST_API fst_status fst_sm_partition_info(const fst_sm_partition* p, int32_t k, void** stream, int32_t* sm_count);
+FST_API fst_status fst_sm_partition_destroy(fst_sm_partition* p);
+
 /* Roles of the SMs for FST_VARIANT_PINNED launches: role_of_sm[i] is the
  * role of SM id i (FST_ROLE_*, or FST_ROLE_NONE), for n <= 256 SM ids; ids
  * past n get FST_ROLE_NONE. The ids are the hardware's (fst_sm_ids lists

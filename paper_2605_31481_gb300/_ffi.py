@@ -119,6 +119,9 @@ _SIGS = {
     "fst_fp32_probe": (c_int32, [c_int32, c_int32, c_void_p, ctypes.c_size_t, ctypes.POINTER(c_double), c_void_p]),
     "fst_sm_ids": (c_int32, [ctypes.POINTER(c_int32), c_int32, ctypes.POINTER(c_int32)]),
     "fst_device_can_access": (c_int32, [c_void_p, ctypes.POINTER(c_int32)]),
+    "fst_sm_partition_create": (c_int32, [c_int32, ctypes.POINTER(c_int32), c_int32, ctypes.POINTER(c_void_p)]),
+    "fst_sm_partition_info": (c_int32, [c_void_p, c_int32, ctypes.POINTER(c_void_p), ctypes.POINTER(c_int32)]),
+    "fst_sm_partition_destroy": (c_int32, [c_void_p]),
     "fst_last_error": (ctypes.c_char_p, []),
     "fst_version": (ctypes.c_char_p, []),
 }

@@ -625,3 +625,52 @@ def sm_ids(device=None):
             check(_ffi.lib().fst_sm_ids(buf, 1024, ctypes.byref(n)))
         _SM_IDS[dev] = [buf[k] for k in range(min(n.value, 1024))]
     return _SM_IDS[dev]
+
+
+class SmPartition:
+    """Disjoint SM sets of one device, each with a stream whose kernels run
+    only on its SMs (fst_sm_partition_create: CUDA green contexts), also
+    inside a CUDA graph captured from another stream that forks into them.
+    `streams[k]` is a torch stream of partition k, `sm_counts[k]` its SMs
+    (each request rounded up to groups of 8). Keep the object alive while
+    any launch or graph that uses its streams can still run."""
+
+    def __init__(self, sm_counts, device=None):
+        dev = torch.cuda.current_device() if device is None else torch.device(device).index or 0
+        counts = [int(c) for c in sm_counts]
+        arr = (ctypes.c_int32 * len(counts))(*counts)
+        h = ctypes.c_void_p()
+        check(_ffi.lib().fst_sm_partition_create(int(dev), arr, len(counts), ctypes.byref(h)))
+        self._h = h
+        self.device = dev
+        self.streams, self.sm_counts = [], []
+        for k in range(len(counts)):
+            s, c = ctypes.c_void_p(), ctypes.c_int32()
+            check(_ffi.lib().fst_sm_partition_info(h, k, ctypes.byref(s), ctypes.byref(c)))
+            self.streams.append(torch.cuda.ExternalStream(s.value, device=torch.device("cuda", dev)))
+            self.sm_counts.append(c.value)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            torch.cuda.synchronize(self.device)
+            _ffi.lib().fst_sm_partition_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+_PARTITIONS = {}
+
+
+def sm_partition(sm_counts, device=None):
+    """A shared SmPartition per (device, SM counts): step plans that use the
+    same split reuse one set of green contexts for the life of the process."""
+    dev = torch.cuda.current_device() if device is None else torch.device(device).index or 0
+    key = (dev, tuple(int(c) for c in sm_counts))
+    if key not in _PARTITIONS:
+        _PARTITIONS[key] = SmPartition(key[1], dev)
+    return _PARTITIONS[key]

@@ -278,6 +278,10 @@ class StepPlan:
                   Jacobians; RNEA with CRBA) on two more branches;
       pinned      one launch of one block per SM, each SM serving one operator
                   (fst_eval with FST_VARIANT_PINNED; SM counts tuned);
+      partitioned ABA, the kinematics (FK with the Jacobians), RNEA and CRBA
+                  as four launches on four disjoint SM partitions (green
+                  contexts, fst_sm_partition_create; SM counts tuned), so no
+                  SM runs two operators' code;
       concurrent  each operator's own kernel on its own stream;
       sequential  the per-operator kernels one after another.
     Side streams are forked from and joined back into the caller's stream,
@@ -290,7 +294,7 @@ class StepPlan:
     (the block scheduler places the first-forked kernel's blocks first, and
     on GB300 the order moves a hybrid step between 14.5 and 22 us)."""
 
-    MODES = ("fused", "hybrid", "split", "pinned", "concurrent", "sequential")
+    MODES = ("fused", "hybrid", "split", "pinned", "partitioned", "concurrent", "sequential")
 
     def __init__(self, model, B, links=None, use_cache=True, verbose=False, modes=MODES, fixed=None):
         """fixed: run this one plan instead of searching, named as the keys of
@@ -347,11 +351,18 @@ class StepPlan:
         pinned_cfgs = []
         if "specialized" in {c.split("/")[0] for c in self.tuned["eval"]["candidates"]}:
             pinned_cfgs = [f"pinned/256|level/256@{c}" for c in self.pin_count_candidates(B)]
+        # SM partitions: the best two fused configurations for the single-role
+        # launches, the best ABA configuration, the SM splits below
+        part_cfgs = []
+        if B <= 16384:
+            part_evals = [n for n in hybrid_evals if n.split("/")[0] in ("specialized", "level")][:2]
+            part_cfgs = [f"{ev}|{abas[0]}@{c}" for ev in part_evals for c in self.partition_count_candidates(B)]
         times = {}
         for carveout in (-1, 100):
             api.set_smem_carveout(carveout)
             for mode in modes:
-                cfgs = {"hybrid": hybrid_cfgs, "split": hybrid_cfgs, "pinned": pinned_cfgs}.get(
+                cfgs = {"hybrid": hybrid_cfgs, "split": hybrid_cfgs, "pinned": pinned_cfgs,
+                        "partitioned": part_cfgs}.get(
                     mode, [f"{best_eval}|{best_aba}"])
                 for ev in cfgs:
                     try:
@@ -359,7 +370,7 @@ class StepPlan:
                     except _ffi.FstError:
                         continue                 # not available for this model
                     for alt in (False, True):
-                        if (carveout >= 0 or alt) and mode in ("fused", "sequential", "pinned"):
+                        if (carveout >= 0 or alt) and mode in ("fused", "sequential", "pinned", "partitioned"):
                             continue
                         self._set_alt(mode, alt)
                         times[(mode, carveout, alt, ev)] = self._time(cold)
@@ -403,14 +414,46 @@ class StepPlan:
     def _set_eval(self, config):
         """config: "<eval variant>/<block>|<aba variant>/<block>[@<SM counts>]";
         SM counts "a-k-r-c" (ABA, KIN, RNEA, CRBA) set the SM roles of the
-        pinned step."""
+        pinned step (eval variant "pinned"), or the SM partitions of the
+        partitioned step (any other eval variant)."""
         config, _, counts = config.partition("@")
         for kind, part in zip(("eval", "aba"), config.split("|")):
             variant, block = part.split("/")
             self.model.set_launch([kind], int(block), variant)
-        if counts:
+        if counts and config.startswith("pinned/"):
             self.model.set_sm_roles(self.pin_roles([int(c) for c in counts.split("-")],
                                                    ids=sm_ids(self.model.device)))
+        elif counts:
+            self.partition = api.sm_partition([int(c) for c in counts.split("-")], self.model.device)
+
+    def partition_count_candidates(self, B, n_sm=None):
+        """SM counts (ABA, KIN, RNEA, CRBA), in groups of 8, for the
+        partitioned step: ABA about one SM per two 32-environment tiles (two
+        level-parallel tiles fit an SM for trees up to about 14 bodies),
+        that less or more one group; the rest split between the other three
+        evenly and in proportion to their measured times."""
+        n_sm = n_sm or sm_count(self.model.device)
+        groups = n_sm // 8
+        tiles = -(-B // 32)
+        a0 = min(max(1, -(-tiles // 16)), groups - 3)    # ceil(tiles / 2 per SM / 8 SMs per group)
+        out = []
+        for a in (a0, a0 - 1, a0 + 1):
+            rest = groups - a
+            if a < 1 or rest < 3:
+                continue
+            t = [self.tuned[k]["us"] for k in ("jacobian", "rnea", "crba")] if self.tuned else [1.0, 1.0, 1.0]
+            for wts in (t, (1.0, 1.0, 1.0)):
+                k = [max(1, int(rest * x / sum(wts))) for x in wts]
+                while sum(k) < rest:     # the next group to the most loaded operator
+                    i = max(range(3), key=lambda j: wts[j] / k[j])
+                    k[i] += 1
+                while sum(k) > rest:
+                    i = min((j for j in range(3) if k[j] > 1), key=lambda j: wts[j] / k[j])
+                    k[i] -= 1
+                c = "-".join(str(8 * g) for g in [a] + k)
+                if c not in out:
+                    out.append(c)
+        return out
 
     def pin_count_candidates(self, B, n_sm=None):
         """SM counts (ABA, KIN, RNEA, CRBA) to try for the pinned step: ABA
@@ -474,19 +517,20 @@ class StepPlan:
                 lambda: api.crba(m, q, out=out["M"]),
                 lambda: api.aba(m, q, qd, tau, out=out["qdd"]))
 
-    def _fork(self, fns):
+    def _fork(self, fns, streams=None):
+        streams = self.streams if streams is None else streams
         cur = torch.cuda.current_stream(self.model.device)
-        for st, fn in zip(self.streams, fns):
+        for st, fn in zip(streams, fns):
             st.wait_stream(cur)
             with torch.cuda.stream(st):
                 fn()
-        for st in self.streams[:len(fns)]:
+        for st in streams[:len(fns)]:
             cur.wait_stream(st)
 
     def __call__(self, q, qd, qdd, tau, out, packed=False):
         """One step into `out`. packed=True writes M and J in the packed
         layouts of eval(packed=True); only the modes that compute M and J in
-        fused launches (fused, hybrid, split, pinned) have them."""
+        fused launches (fused, hybrid, split, pinned, partitioned) have them."""
         m = self.model
         if packed and self.mode in ("sequential", "concurrent"):
             raise ValueError(f"the {self.mode} step plan has no packed outputs")
@@ -501,6 +545,13 @@ class StepPlan:
             # the SM-pinned step: all five operators in one launch
             api.eval(m, q, qd, qdd, tau, fk=True, links=self.links, rnea=True, crba=True, aba=True, out=out,
                      packed=packed)
+        elif self.mode == "partitioned":
+            # ABA, the kinematics, RNEA and CRBA each on its own SMs
+            self._fork([ops[4],
+                        lambda: api.eval(m, q, qd, qdd, tau, fk=True, links=self.links, out=out, packed=packed),
+                        lambda: api.eval(m, q, qd, qdd, tau, fk=False, rnea=True, out=out, packed=packed),
+                        lambda: api.eval(m, q, qd, qdd, tau, fk=False, crba=True, out=out, packed=packed)],
+                       streams=self.partition.streams)
         elif self.mode == "hybrid":
             fused = [lambda: api.eval(m, q, qd, qdd, tau, fk=True, links=self.links, rnea=True, crba=True, aba=False,
                                       out=out, packed=packed)]
@@ -521,7 +572,7 @@ class StepPlan:
         kinds["eval"], kinds["aba"] = self.eval_config.split("|")
         return {"mode": self.mode, "carveout": self.carveout, "priorities": self.prio,
                 "fused_forked_first": self.alt and self.mode != "concurrent",
-                "us": {f"{k[0]}{'[' + k[3] + ']' if k[0] in ('hybrid', 'split', 'pinned') else ''}"
+                "us": {f"{k[0]}{'[' + k[3] + ']' if k[0] in ('hybrid', 'split', 'pinned', 'partitioned') else ''}"
                        f"{'' if k[1] < 0 else f'@{k[1]}%'}"
                        f"{('+prio' if k[0] == 'concurrent' else '+fusedfirst') if k[2] else ''}": round(v, 3)
                        for k, v in self.times.items()},
