@@ -645,12 +645,12 @@ fst_status fst_eval(const fst_model* m, int64_t B, const fst_eval_io* io, const 
       const int role = a.roles[r];
       const int kind = role == ROLE_ABA ? JK_ABA : role == ROLE_CRBA ? JK_CRBA : role == ROLE_RNEA ? JK_RNEA
                                                                      : (a.J ? JK_JACOBIAN : JK_FK);
-      // a level-parallel role of the mixed kernel keeps its per-body state
-      // after nq + 2 nv staged rows whatever rows the role stages (the
-      // kernel's layout), and no model copy (the tree is compiled in)
+      // a level-parallel role of the mixed kernel runs on a model copy in
+      // shared memory and keeps its per-body state after nq + 2 nv staged
+      // rows whatever rows the role stages (the kernel's layout)
       const int F = role == ROLE_ABA ? kAbaStateFloats : role == ROLE_CRBA ? kCrbaStateFloats
                   : role == ROLE_RNEA ? kRneaStateFloats : kFkStateFloats;
-      const size_t level_need = ((size_t)rows + (size_t)F * m->n) * 32 * sizeof(float);
+      const size_t level_need = model_smem_bytes(m->n) + ((size_t)rows + (size_t)F * m->n) * 32 * sizeof(float);
       size_t need;
       int64_t blocks;
       if (m->variant[JK_EVAL] == FST_VARIANT_MIXED && m->variant[kind] == FST_VARIANT_LEVEL &&

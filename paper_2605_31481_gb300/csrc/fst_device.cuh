@@ -311,8 +311,27 @@ struct SmemModel {
   __device__ __forceinline__ int child(int k) const { return t->child[k]; }
 };
 
+// Asynchronous global -> shared copies (no register staging, so a thread
+// issues all of its loads before waiting on any of them): 4 bytes, and 16
+// bytes with both addresses 16-byte aligned.
+__device__ __forceinline__ void cp_async4(void* smem_dst, const void* gmem_src) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 // Copies the model constants (and the inertia override, if any) to shared
-// memory. Every thread of the block must call it (it synchronises).
+// memory. Every thread of the block must call it (it synchronises). All
+// copies are asynchronous, so the whole model arrives in one memory round
+// trip whatever the block size (a load-then-store loop would wait for each
+// of a thread's loads in turn). The wait also completes the calling thread's
+// own earlier cp.async copies (its staged inputs). The BodyC and BodyI
+// arrays are separate device allocations (256-byte aligned) of 256- and
+// 16-byte records, so their 16-byte copies are aligned on both sides.
 __device__ __forceinline__ SmemModel stage_model(const ModelView& mv, float4* smem) {
   BodyC* sc = reinterpret_cast<BodyC*>(smem);
   BodyI* si = reinterpret_cast<BodyI*>(sc + mv.n);
@@ -320,19 +339,22 @@ __device__ __forceinline__ SmemModel stage_model(const ModelView& mv, float4* sm
   const float4* src = reinterpret_cast<const float4*>(mv.c);
   float4* dst = reinterpret_cast<float4*>(sc);
   const int nc4 = mv.n * (int)(sizeof(BodyC) / sizeof(float4));
+  static_assert(sizeof(BodyI) == 16, "BodyI is copied as one 16-byte record");
   // every thread of the block, whatever its shape
   const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
   const int nt = blockDim.x * blockDim.y * blockDim.z;
-  for (int k = tid; k < nc4; k += nt) dst[k] = src[k];
-  for (int k = tid; k < mv.n; k += nt) si[k] = mv.i[k];
+  for (int k = tid; k < nc4; k += nt) cp_async16(dst + k, src + k);
+  for (int k = tid; k < mv.n; k += nt) cp_async16(si + k, mv.i + k);
   const int* ts = reinterpret_cast<const int*>(mv.topo);
   int* td = reinterpret_cast<int*>(st);
-  for (int k = tid; k < (int)(sizeof(TopoLists) / sizeof(int)); k += nt) td[k] = ts[k];
-  if (mv.theta) {
-    __syncthreads();
-    for (int k = tid; k < mv.n * 10; k += nt) sc[k / 10].theta[k % 10] = mv.theta[k];
-  }
+  for (int k = tid; k < (int)(sizeof(TopoLists) / sizeof(int)); k += nt) cp_async4(td + k, ts + k);
+  cp_async_wait_all();
   __syncthreads();
+  if (mv.theta) {  // the override replaces the staged parameters, after they have landed
+    for (int k = tid; k < mv.n * 10; k += nt) cp_async4(&sc[k / 10].theta[k % 10], mv.theta + k);
+    cp_async_wait_all();
+    __syncthreads();
+  }
   return SmemModel{sc, si, mv.n, st, mv.depth};
 }
 
@@ -377,13 +399,6 @@ struct Col {
   __device__ __forceinline__ float operator[](int k) const { return p[k * ld]; }
 };
 
-// Asynchronous 4-byte global -> shared copies (no register staging, so a
-// thread issues all of its environment's loads before waiting on any).
-__device__ __forceinline__ void cp_async4(float* smem_dst, const float* gmem_src) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem_src) : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 // ---- SM-pinned tile loops ---------------------------------------------------
 // The straight-line specialised kernels run fast only while an SM keeps

@@ -308,6 +308,11 @@ extern "C" __global__ void __launch_bounds__(256) FST_JIT_PIN_NAME(ModelView mv,
 // block's warps splitting each tree level); the others one environment per
 // thread. The grid's x extent covers the larger of the two; blocks past a
 // role's last environment leave at once (block-uniform, before any barrier).
+// A level-parallel role runs on a copy of the model staged in shared memory
+// (run-time topology), as the operator's own level-parallel kernel does: its
+// per-level loops are compact code that every warp shares, where the
+// compiled-in tree would unroll every body of every level into each warp's
+// instruction stream; its tile follows the model copy.
 extern "C" __global__ void __launch_bounds__(256) FST_JIT_NAME(ModelView mv, int64_t B, EvalArgs a) {
   extern __shared__ float4 smem[];
   float* tile = reinterpret_cast<float*>(smem);
@@ -318,33 +323,33 @@ extern "C" __global__ void __launch_bounds__(256) FST_JIT_NAME(ModelView mv, int
     const int lane = threadIdx.x & 31;
     const int64_t e = (int64_t)blockIdx.x * kLaneEnvs + lane;
     const bool act = e < B;
+    float* ltile = smem_tile(smem, mv.n);
     const int F = role == ROLE_ABA ? kAbaState : role == ROLE_CRBA ? kCrbaState : role == ROLE_RNEA ? kRneaState : kFkState;
-    const LaneState S{tile + (mv.nq + 2 * mv.nv) * kLaneEnvs, F};
-    stage_block_rows(tile, a.q, mv.nq, B, e);
+    const LaneState S{ltile + (mv.nq + 2 * mv.nv) * kLaneEnvs, F};
+    stage_block_rows(ltile, a.q, mv.nq, B, e);
     if (role == ROLE_RNEA) {
-      stage_block_rows(tile + mv.nq * kLaneEnvs, a.qd, mv.nv, B, e);
-      stage_block_rows(tile + (mv.nq + mv.nv) * kLaneEnvs, a.qdd, mv.nv, B, e);
+      stage_block_rows(ltile + mv.nq * kLaneEnvs, a.qd, mv.nv, B, e);
+      stage_block_rows(ltile + (mv.nq + mv.nv) * kLaneEnvs, a.qdd, mv.nv, B, e);
     } else if (role == ROLE_ABA) {
-      stage_block_rows(tile + mv.nq * kLaneEnvs, a.qd, mv.nv, B, e);
-      stage_block_rows(tile + (mv.nq + mv.nv) * kLaneEnvs, a.tau, mv.nv, B, e);
+      stage_block_rows(ltile + mv.nq * kLaneEnvs, a.qd, mv.nv, B, e);
+      stage_block_rows(ltile + (mv.nq + mv.nv) * kLaneEnvs, a.tau, mv.nv, B, e);
     }
-    cp_async_wait_all();
-    __syncthreads();
-    const Col cq{tile + lane, kLaneEnvs};
-    const Col c1{tile + mv.nq * kLaneEnvs + lane, kLaneEnvs};
-    const Col c2{tile + (mv.nq + mv.nv) * kLaneEnvs + lane, kLaneEnvs};
+    const SmemModel sm = stage_model(mv, smem);  // also waits for the staged rows, and synchronises
+    const Col cq{ltile + lane, kLaneEnvs};
+    const Col c1{ltile + mv.nq * kLaneEnvs + lane, kLaneEnvs};
+    const Col c2{ltile + (mv.nq + mv.nv) * kLaneEnvs + lane, kLaneEnvs};
     switch (role) {
       case ROLE_ABA:
-        aba_level(tp, world_accel(mv), cq, c1, c2, S, a.qdd_out, B, e, act);
+        aba_level(sm, world_accel(mv), cq, c1, c2, S, a.qdd_out, B, e, act);
         break;
       case ROLE_CRBA:
-        crba_level(tp, cq, mv.nv, S, a.M, B, e, act);
+        crba_level(sm, cq, mv.nv, S, a.M, B, e, act);
         break;
       case ROLE_RNEA:
-        rnea_level(tp, world_accel(mv), cq, c1, c2, S, a.tau_out, B, e, act);
+        rnea_level(sm, world_accel(mv), cq, c1, c2, S, a.tau_out, B, e, act);
         break;
       default:
-        kin_level(tp, cq, mv.nv, a.links, S, a.poses, a.J, B, e, act);
+        kin_level(sm, cq, mv.nv, a.links, S, a.poses, a.J, B, e, act);
         break;
     }
     return;

@@ -100,6 +100,8 @@ constexpr int kTapeFloatsPerBody = 30;
 // `tiles` tiles of 32 environments per block (1, or 2 for FST_VARIANT_LEVEL2),
 // `block` threads in all.
 size_t level_smem_needed(const ModelView& mv, int kind, int tiles = 1);
+// Bytes of the model copy a kernel stages in shared memory (stage_model).
+size_t model_smem_bytes(int n);
 cudaError_t launch_fk_level(const ModelView& mv, int64_t B, const float* q, float* poses, int block, int tiles,
                             cudaStream_t s);
 cudaError_t launch_jac_level(const ModelView& mv, int64_t B, const float* q, const LinkList& links, float* J,

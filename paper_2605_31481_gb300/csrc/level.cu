@@ -22,10 +22,9 @@ __device__ __forceinline__ float* level_tile(float4* smem, int n) { return smem_
 
 #define FST_LEVEL_PROLOGUE(rows, F) FST_LEVEL_PROLOGUE_S(rows, F, ((rows) + (F) * mv.n) * kLaneEnvs)
 
-#define FST_LEVEL_READY                            \
-  const SmemModel sm = stage_model(mv, smem);      \
-  cp_async_wait_all();                             \
-  __syncthreads()
+// stage_model waits for the model and for this thread's staged rows, then
+// synchronises the block, so everything staged is visible to every warp.
+#define FST_LEVEL_READY const SmemModel sm = stage_model(mv, smem)
 
 __global__ void __launch_bounds__(256) fk_level_kernel(ModelView mv, int64_t B, const float* __restrict__ q,
                                                        float* __restrict__ poses) {
@@ -192,6 +191,8 @@ cudaError_t go(K* kernel, const ModelView& mv, int64_t B, size_t sh, int block, 
 }
 
 }  // namespace
+
+size_t model_smem_bytes(int n) { return smem_bytes(n); }
 
 size_t level_smem_needed(const ModelView& mv, int kind, int tiles) {
   size_t t;
