@@ -297,6 +297,10 @@ def plan_kernel_name(mode, desc):
     describe() (launch configurations of the kinds it sets)."""
     kinds, carveout = desc["kinds"], desc["carveout"]
     if mode == "fused":
+        if kinds["eval"].startswith("mixed"):
+            lv = [k for k in ("aba", "crba", "rnea") if kinds.get(k, "").startswith("level/")]
+            return (f"fused eval kernel ({kinds['eval']}: " + (", ".join(lv) + " level-parallel, " if lv else "") +
+                    "the other roles one environment per thread)")
         return f"fused eval kernel ({kinds['eval']})"
     if mode == "hybrid":
         return (f"ABA kernel ({kinds['aba']}) on a parallel graph branch beside the fused kernel of the other four "
