@@ -49,7 +49,7 @@ OPS = ("fk", "jacobian", "rnea", "crba", "aba")
 # plan and a hash of the kernel sources at capture time: a source change
 # since the capture makes the entry stale and the reported traffic null.
 NCU_TRAFFIC = {
-    ("hybrid", "level/256", "specialized/128", "de74888568b7"): 781568 + 594944,
+    ("hybrid", "levellean/128", "specialized/128", "15950e7be32c"): 782520 + 594817,
 }
 
 

@@ -173,8 +173,9 @@ FST_API fst_status fst_model_specialize(fst_model* model, uint32_t kinds);
 #define FST_VARIANT_SPECIALIZED 2
 #define FST_VARIANT_LEVEL 3
 /* eval only: the specialised fused kernel, with each role (ABA, CRBA, RNEA,
- * FK/Jacobian) level-parallel where that operator's own kind is set to LEVEL
- * and one environment per thread otherwise. A level-parallel role runs on a
+ * FK/Jacobian) level-parallel (one tile of 32 environments per block) where
+ * that operator's own kind is set to LEVEL, LEVEL2 or LEVEL_LEAN and one
+ * environment per thread otherwise. A level-parallel role runs on a
  * copy of the model staged in shared memory, as the operator's own
  * level-parallel kernel does (compact per-level loops rather than the
  * compiled-in tree unrolled into every warp's instructions). */

@@ -653,7 +653,10 @@ fst_status fst_eval(const fst_model* m, int64_t B, const fst_eval_io* io, const 
       const size_t level_need = model_smem_bytes(m->n) + ((size_t)rows + (size_t)F * m->n) * 32 * sizeof(float);
       size_t need;
       int64_t blocks;
-      if (m->variant[JK_EVAL] == FST_VARIANT_MIXED && m->variant[kind] == FST_VARIANT_LEVEL &&
+      // any level-parallel setting of the operator (one tile, two tiles or
+      // lean state) makes its role level-parallel here, one tile per block
+      const int kv = m->variant[kind];
+      if ((kv == FST_VARIANT_LEVEL || kv == FST_VARIANT_LEVEL2 || kv == FST_VARIANT_LEVEL_LEAN) &&
           level_need <= kLevelSmemLimit) {
         a.level_mask |= 1 << role;
         need = level_need;

@@ -98,7 +98,8 @@ def test_specialized_theta_override(torch_cuda):
 
 @pytest.mark.parametrize("name", ["quadruped11", "humanoid29", "general8"])
 @pytest.mark.parametrize("level_kinds", [("aba",), ("aba", "crba", "rnea", "jacobian"), ("crba",), ("jacobian",),
-                                         ("crba", "jacobian")])
+                                         ("crba", "jacobian"), ("aba:levellean",), ("aba:levellean", "crba:levellean"),
+                                         ("aba:level2", "rnea:level2")])
 def test_specialized_eval_with_level_parallel_roles(torch_cuda, name, level_kinds):
     """The specialised fused kernel runs roles whose operator is tuned
     level-parallel that way (32 environments per block, warps splitting
@@ -106,14 +107,17 @@ def test_specialized_eval_with_level_parallel_roles(torch_cuda, name, level_kind
     cases without ABA have a CRBA or Jacobian role set the launch's shared
     memory: its state sits after the nq + 2 nv staged rows of the kernel's
     layout, which the launch must allocate even though the role stages only
-    q."""
+    q. Any level-parallel setting of an operator (level, level2,
+    levellean) makes its role level-parallel in the fused kernel."""
     torch = torch_cuda
     from paper_2605_31481_gb300 import api
     tree = TREES[name]()
     B = 1000
     s = w.random_state(tree, B, seed=14)
     m = api.Model(tree, specialize=["eval_mixed"])
-    m.set_launch(list(level_kinds), 128, "level")
+    for kv in level_kinds:
+        kind, _, variant = kv.partition(":")
+        m.set_launch([kind], 128, variant or "level")
     m.set_launch(["eval"], 64, "mixed")
     q, qd, qdd, tau = (to_soa_cuda(s[k], torch) for k in ("q", "qd", "qdd", "tau"))
     ee = list(tree.ee)
