@@ -536,9 +536,9 @@ def run_fst(args):
         extras["sysid"] = sysid(torch, fst, w)
     if rank == 0:
         if args.no_cpu_baseline:
-            cpu1 = parity = cpu = None
+            cpu1 = parity = parity_detail = cpu = None
         else:
-            cpu1, parity = cpu_baseline(tree, links, args, st, first)
+            cpu1, parity, parity_detail = cpu_baseline(tree, links, args, st, first)
             cpu = cpu_baseline_all_cores()
         line = {
             "metric": METRIC, "value": round(value, 1), "unit": "env-evals/s", "n_gpus": world, "steps": K,
@@ -572,6 +572,7 @@ def run_fst(args):
             "cpu_baseline": cpu,
             "cpu_baseline_1core": cpu1,
             "parity_vs_oracle": parity,
+            "parity_detail": parity_detail,
             **extras,
         }
         print(json.dumps(line))
@@ -1110,7 +1111,7 @@ def cpu_baseline(tree, links, args, st=None, gpu_first=None, budget_s=12.0, Bs=5
     cpu = {"value": round(n * Bs / dt, 1), "unit": "env-evals/s", "cores": 1, "kind": "oracle",
            "sample": f"{n} passes of FK+4 Jacobians+RNEA+CRBA+ABA over {Bs} envs of the same tree (FP64 numpy, "
                      f"1 thread, {dt:.1f} s)"}
-    parity = None
+    parity = detail = None
     if gpu_first is not None:
         T = rbd.fk(tree, s["q"])
         ref = {"poses": np.concatenate([T[..., :3, :3].reshape(Bs, -1, 9), T[..., :3, 3]], -1),
@@ -1118,15 +1119,28 @@ def cpu_baseline(tree, links, args, st=None, gpu_first=None, budget_s=12.0, Bs=5
                "tau": rbd.rnea(tree, s["q"], s["qd"], s["qdd"]), "M": rbd.crba(tree, s["q"]),
                "qdd": rbd.aba(tree, s["q"], s["qd"], s["tau"])}
         tol = {"poses": 1e-5, "J": 1e-5, "tau": 1e-4, "M": 1e-4, "qdd": 1e-4}
-        parity = {}
+        parity, p999 = {}, {}
         for k, r in ref.items():
             g = np.moveaxis(gpu_first[k], -1, 0)[:Bs].reshape(Bs, -1)
             r = r.reshape(Bs, -1)
-            err = float((np.abs(g - r).max(1) / np.maximum(np.abs(r).max(1), 1.0)).max())
+            env = np.abs(g - r).max(1) / np.maximum(np.abs(r).max(1), 1.0)
+            err = float(env.max())
             if not err <= tol[k]:
                 raise RuntimeError(f"parity check failed: {k} error {err:.3e} > {tol[k]}")
             parity[k] = float(f"{err:.2e}")
-    return cpu, parity
+            p999[k] = float(f"{np.quantile(env, 0.999):.2e}")
+        # forward dynamics: the backward error of the GPU's accelerations
+        # (the torque the oracle's inverse dynamics needs for them, against
+        # the applied torque) and the conditioning of M, per environment
+        qdd_gpu = np.moveaxis(gpu_first["qdd"], -1, 0)[:Bs]
+        tau_back = rbd.rnea(tree, s["q"], s["qd"], qdd_gpu)
+        bwd = np.abs(tau_back - s["tau"]).max(1) / np.maximum(np.abs(s["tau"]).max(1), 1.0)
+        cond = np.linalg.cond(ref["M"])
+        detail = {"envs": Bs, "p99_9": p999,
+                  "qdd_backward_error": {"max": float(f"{bwd.max():.2e}"),
+                                         "p99_9": float(f"{np.quantile(bwd, 0.999):.2e}")},
+                  "cond2_M": {"max": float(f"{cond.max():.3g}"), "median": float(f"{np.median(cond):.3g}")}}
+    return cpu, parity, detail
 
 
 def run_reference(args, budget_s=120.0):

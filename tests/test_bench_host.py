@@ -78,3 +78,37 @@ def test_reference_arm_other_ranks_exit_quietly():
                        env=env)
     assert r.returncode == 0, r.stderr[-2000:]
     assert r.stdout.strip() == ""
+
+
+def test_cpu_baseline_parity_report():
+    """The CPU-baseline leg's parity report on stand-in GPU outputs (the
+    oracle's own results rounded to FP32, in the step's [field][B] layout):
+    the largest and the 99.9th-percentile normwise error per output, the
+    backward error of the accelerations and the conditioning of M; and a
+    wrong output fails the check."""
+    import numpy as np
+    import pytest
+    sys.path.insert(0, ROOT)
+    import bench
+    from oracle import rbd
+    from paper_2605_31481_gb300 import workloads as w
+    tree = w.spined_quadruped(seed=0)
+    links = list(tree.ee)
+    Bs = 24
+    s = w.random_state(tree, Bs, seed=1)
+    T = rbd.fk(tree, s["q"])
+    out = {"poses": np.concatenate([T[..., :3, :3].reshape(Bs, -1, 9), T[..., :3, 3]], -1),
+           "J": np.stack([rbd.jacobian(tree, s["q"], l) for l in links], 1),
+           "tau": rbd.rnea(tree, s["q"], s["qd"], s["qdd"]), "M": rbd.crba(tree, s["q"]),
+           "qdd": rbd.aba(tree, s["q"], s["qd"], s["tau"])}
+    first = {k: np.moveaxis(v.astype(np.float32).astype(np.float64), 0, -1) for k, v in out.items()}
+    cpu, parity, detail = bench.cpu_baseline(tree, links, None, s, first, budget_s=0.05, Bs=Bs)
+    assert cpu["kind"] == "oracle" and cpu["cores"] == 1 and cpu["value"] > 0
+    assert set(parity) == {"poses", "J", "tau", "M", "qdd"} and max(parity.values()) < 1e-6
+    assert detail["envs"] == Bs and set(detail["p99_9"]) == set(parity)
+    assert all(detail["p99_9"][k] <= parity[k] for k in parity)
+    assert 0 < detail["qdd_backward_error"]["max"] < 1e-5
+    assert detail["cond2_M"]["max"] >= detail["cond2_M"]["median"] >= 1.0
+    first["tau"][3] += 1e-2                        # a wrong torque row fails the check
+    with pytest.raises(RuntimeError):
+        bench.cpu_baseline(tree, links, None, s, first, budget_s=0.05, Bs=Bs)
