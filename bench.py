@@ -298,7 +298,8 @@ def plan_kernel_name(mode, desc):
     kinds, carveout = desc["kinds"], desc["carveout"]
     if mode == "fused":
         if kinds["eval"].startswith("mixed"):
-            lv = [k for k in ("aba", "crba", "rnea") if kinds.get(k, "").startswith("level/")]
+            lv = [k for k in ("aba", "crba", "rnea")
+                  if kinds.get(k, "").split("/")[0] in ("level", "level2", "levellean")]
             return (f"fused eval kernel ({kinds['eval']}: " + (", ".join(lv) + " level-parallel, " if lv else "") +
                     "the other roles one environment per thread)")
         return f"fused eval kernel ({kinds['eval']})"

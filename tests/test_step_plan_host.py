@@ -164,7 +164,7 @@ def test_fixed_plan_names_are_checked(bad):
 
 @pytest.mark.parametrize("name", ["hybrid[specialized/128|level/128]@100%+fusedfirst", "fused[specialized/128|level/256]",
                                   "split[specialized/128|level/256]+fusedfirst", "concurrent@100%+prio", "sequential",
-                                  "pinned[pinned/256|level/256@64-32-24-32]"])
+                                  "pinned[pinned/256|level/256@64-32-24-32]", "fused[mixed/128|levellean/128]"])
 def test_bench_describes_a_fixed_plan(fakes, name):
     """bench.py's report of the timed step works from a named plan's
     describe(), with or without the per-kind tuning."""
@@ -183,6 +183,8 @@ def test_bench_describes_a_fixed_plan(fakes, name):
         text = bench.plan_kernel_name(plan.mode, desc)
         assert text and (plan.mode in ("concurrent", "sequential") or desc["kinds"]["eval"] in text)
         assert plan.mode in ("fused", "concurrent", "sequential") or desc["kinds"]["aba"] in text
+        if desc["kinds"]["eval"].startswith("mixed"):
+            assert "aba" in text.split(":")[1].split("level-parallel")[0]   # any level form of ABA is named
         key = (plan.mode, desc["kinds"]["aba"], desc["kinds"]["eval"], bench.kernel_source_hash())
         assert bench.NCU_TRAFFIC.get(key) is None or plan.mode == "hybrid"
         json.dumps(desc)
