@@ -26,7 +26,8 @@ shared-memory carveouts and with its fork-order or stream-priority option.
 Timings replay a CUDA graph of repeated launches, so host launch overhead is
 excluded. Choices are cached in a JSON file (FST_TUNE_CACHE, default
 ~/.cache/fst_tune.json) keyed by the tree's fingerprint, the kind, B, the
-GPU name and the library version.
+GPU name and the library version. FST_AUTOTUNE=0 turns all measurement off
+(autotune_enabled()): built-in launch heuristics and one fused launch.
 """
 from __future__ import annotations
 
@@ -215,9 +216,24 @@ def _key(model, kind, B):
     return f"{model.fingerprint}|{kind}|{B}|{torch.cuda.get_device_name(model.device)}|{_ffi.lib().fst_version().decode()}"
 
 
+def autotune_enabled():
+    """False when FST_AUTOTUNE=0: then nothing is measured. tune() keeps the
+    library's built-in launch heuristics (variant auto: the specialised
+    kernel where compiled, else the generic one; block 0) and StepPlan runs
+    the step as one fused launch."""
+    return os.environ.get("FST_AUTOTUNE", "1").strip() != "0"
+
+
 def tune(model, B, kinds=FORWARD_KINDS + ("eval",), links=None, use_cache=True, verbose=False):
     """Pick and set the fastest (variant, block) for each kind at batch B.
-    Returns {kind: {"variant", "block", "us", "candidates"}}."""
+    Returns {kind: {"variant", "block", "us", "candidates"}} ("us" None and
+    no candidates when FST_AUTOTUNE=0)."""
+    if not autotune_enabled():
+        out = {}
+        for kind in kinds:
+            model.set_launch([kind], 0, "auto")
+            out[kind] = {"variant": "auto", "block": 0, "us": None, "candidates": {}}
+        return out
     links = list(links if links is not None else (model.ee or (model.n_bodies - 1,)))
     cache = _load_cache() if use_cache else {}
     spec = set(model.specialized())
@@ -324,6 +340,11 @@ class StepPlan:
             self._set_alt(mode, alt)
             self.times = {(mode, carveout, alt, ev): self._time(cold)}
             self._apply(mode, carveout, alt, ev)
+            return
+        if not autotune_enabled():          # FST_AUTOTUNE=0: one fused launch, nothing timed
+            ev = "|".join(f"{self.tuned[k]['variant']}/{self.tuned[k]['block']}" for k in ("eval", "aba"))
+            self.times = {("fused", -1, False, ev): None}
+            self._apply("fused", -1, False, ev)
             return
         key = _key(model, "plan11", B)      # plans timed on cold, rotating inputs
         hit = _load_cache().get(key) if use_cache else None
@@ -563,7 +584,7 @@ class StepPlan:
             self._fork(fused + [ops[4]] if self.alt else [ops[4]] + fused)
         else:
             # longest first, so its blocks are dispatched first
-            order = sorted(range(len(ops)), key=lambda k: -self.tuned[FORWARD_KINDS[k]]["us"])
+            order = sorted(range(len(ops)), key=lambda k: -(self.tuned[FORWARD_KINDS[k]]["us"] or 0.0))
             self._fork([ops[k] for k in order])
         return out
 
@@ -574,7 +595,7 @@ class StepPlan:
                 "fused_forked_first": self.alt and self.mode != "concurrent",
                 "us": {f"{k[0]}{'[' + k[3] + ']' if k[0] in ('hybrid', 'split', 'pinned', 'partitioned') else ''}"
                        f"{'' if k[1] < 0 else f'@{k[1]}%'}"
-                       f"{('+prio' if k[0] == 'concurrent' else '+fusedfirst') if k[2] else ''}": round(v, 3)
+                       f"{('+prio' if k[0] == 'concurrent' else '+fusedfirst') if k[2] else ''}": None if v is None else round(v, 3)
                        for k, v in self.times.items()},
                 "kinds": kinds,
                 "eval_candidates_us": self.tuned.get("eval", {}).get("candidates", {})}

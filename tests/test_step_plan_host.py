@@ -190,3 +190,33 @@ def test_bench_describes_a_fixed_plan(fakes, name):
         json.dumps(desc)
     finally:
         autotune.StepPlan.__init__ = orig_init
+
+
+def test_autotune_off_measures_nothing(monkeypatch, tmp_path):
+    """FST_AUTOTUNE=0: tune() sets every kind to the built-in heuristics
+    (variant auto, block 0) without timing anything, and the step planner
+    runs one fused launch, also without timing."""
+    monkeypatch.setenv("FST_AUTOTUNE", "0")
+    monkeypatch.setenv("FST_TUNE_CACHE", str(tmp_path / "tune.json"))
+
+    def no_timing(*a, **k):
+        raise AssertionError("nothing may be timed with FST_AUTOTUNE=0")
+
+    monkeypatch.setattr(autotune, "graph_time_us", no_timing)
+    monkeypatch.setattr(autotune, "cold_time_us", no_timing)
+    monkeypatch.setattr(autotune, "Buffers", no_timing)
+    monkeypatch.setattr(autotune, "ColdSets", no_timing)
+    monkeypatch.setattr(autotune.StepPlan, "_time", no_timing)
+    monkeypatch.setattr(autotune.api, "set_smem_carveout", lambda c: None)
+    monkeypatch.setattr(autotune.torch.cuda, "Stream", lambda *a, **k: object())
+    model = FakeModel()
+    res = autotune.tune(model, 4096)
+    assert set(res) == set(autotune.FORWARD_KINDS + ("eval",))
+    assert all(v == {"variant": "auto", "block": 0, "us": None, "candidates": {}} for v in res.values())
+    assert all(model.launch[k] == ("auto", 0) for k in res)
+    plan = autotune.StepPlan(model, 4096)
+    assert plan.mode == "fused" and plan.expected_us is None and plan.eval_config == "auto/0|auto/0"
+    desc = plan.describe()
+    assert desc["us"] == {"fused": None} and desc["kinds"]["eval"] == "auto/0"
+    json.dumps(desc)
+    assert not (tmp_path / "tune.json").exists()     # nothing measured, nothing cached
