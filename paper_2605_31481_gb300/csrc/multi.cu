@@ -31,6 +31,7 @@ __global__ void __launch_bounds__(256) multi_kernel(MultiArgs a) {
     if (threadIdx.x == 0) s_item = atomicAdd(a.counter, 1);
     __syncthreads();
     const int item = s_item;
+    __syncthreads();  // every thread has read s_item before thread 0 can overwrite it for the next item
     if (item >= a.n_items) break;
     int sg = 0;
     while (item >= a.seg_start[sg + 1]) ++sg;
@@ -93,6 +94,7 @@ __global__ void __launch_bounds__(256) multi_level_kernel(MultiArgs a) {
     if (threadIdx.x == 0) s_item = atomicAdd(a.counter, 1);
     __syncthreads();
     const int item = s_item;
+    __syncthreads();  // every thread has read s_item before thread 0 can overwrite it for the next item
     if (item >= a.n_items) break;
     int sg = 0;
     while (item >= a.seg_start[sg + 1]) ++sg;
