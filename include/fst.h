@@ -102,17 +102,21 @@ typedef struct fst_model fst_model;
 FST_API fst_status fst_model_create(const fst_body_desc* bodies, int32_t n_bodies,
                             const double gravity[3], fst_model** out);
 
-/* Frees the model's device memory. NULL is accepted. */
+/* Frees the model's device memory (and its specialised kernels). NULL is
+ * accepted. Model life cycle: no counterpart in the paper. */
 FST_API fst_status fst_model_destroy(fst_model* model);
 
 /* Sizes of a model: configuration dimension nq, velocity dimension nv,
- * number of bodies and tree depth (bodies on the longest root-leaf path).
- * Any output pointer may be NULL. */
+ * number of bodies and tree depth (bodies on the longest root-leaf path:
+ * the number of level steps of the level-parallel sweeps, Sec. 3.3).
+ * Any output pointer may be NULL; a NULL model returns FST_ERR_INVALID_ARG. */
 FST_API fst_status fst_model_info(const fst_model* model, int32_t* nq, int32_t* nv,
                           int32_t* n_bodies, int32_t* depth);
 
 /* The model's own inertial parameters, theta layout of fst_rnea (about each
- * body origin), copied to HOST memory theta[n_b * 10] (FP32). */
+ * body origin), copied to HOST memory theta[n_b * 10] (FP32): the
+ * parameters that the identification of Sec. 4.3 estimates (the paper
+ * fixes no layout for them). Synchronous; FST_ERR_INVALID_ARG for NULL. */
 FST_API fst_status fst_model_theta(const fst_model* model, float* theta);
 
 /* Kernel kinds for fst_model_specialize (bit masks; 0 = all). */
@@ -272,7 +276,7 @@ FST_API fst_status fst_sm_partition_destroy(fst_sm_partition* p);
 #define FST_ROLE_KIN 3
 FST_API fst_status fst_model_set_sm_roles(fst_model* model, const int32_t* role_of_sm, int32_t n);
 
-/* Shared-memory carveout (percent of the unified L1/shared storage given to
+/* Launch control (no counterpart in the paper). Shared-memory carveout (percent of the unified L1/shared storage given to
  * shared memory) requested for every kernel launched from now on; -1 (the
  * default) lets each kernel ask for what suits it alone. Kernels only share
  * an SM when they ask for the same carveout, so overlapping different
@@ -280,7 +284,9 @@ FST_API fst_status fst_model_set_sm_roles(fst_model* model, const int32_t* role_
  * common value. Process-wide. */
 FST_API fst_status fst_set_smem_carveout(int32_t percent);
 
-/* Bit mask of the specialised kinds currently in use for this model. */
+/* Bit mask (FST_SPEC_*) of the specialised kinds currently in use for this
+ * model, written to *kinds (host). A launch control with no counterpart in
+ * the paper; FST_ERR_INVALID_ARG for NULL arguments. */
 FST_API fst_status fst_model_specialized(const fst_model* model, uint32_t* kinds);
 
 /* Forward kinematics (paper Sec. 3.1, tier 3; Eq. 4-5 for each joint).
@@ -400,29 +406,34 @@ FST_API fst_status fst_eval(const fst_model* model, int64_t B, const fst_eval_io
  * coordinates [x y z qx qy qz qw] (through the quaternion normalisation).
  * ------------------------------------------------------------------------- */
 
-/* Device scratch bytes the adjoints need for B environments. */
+/* Device scratch bytes the adjoints need for theta_bar over B environments
+ * (the per-block partial sums of the deterministic reduction), written to
+ * *bytes (host). Workspace sizing for the gradients of Sec. 4.3. */
 FST_API fst_status fst_adjoint_scratch_bytes(const fst_model* model, int64_t B, size_t* bytes);
 
-/* FK: q_bar [nq][B] = (d poses / d q)^T poses_bar, poses_bar [n_b][12][B]. */
+/* FK (Sec. 3.1, Eq. 4-5): q_bar [nq][B] = (d poses / d q)^T poses_bar,
+ * poses_bar [n_b][12][B] in the layout of fst_fk. */
 FST_API fst_status fst_fk_vjp(const fst_model* model, int64_t B, const float* q,
                               const float* poses_bar, float* q_bar, void* stream);
 
-/* RNEA: cotangents of tau = RNEA(q, qd, qdd; theta) for tau_bar [nv][B]:
- * q_bar [nq][B], qd_bar [nv][B], qdd_bar [nv][B] (= M tau_bar), theta_bar. */
+/* RNEA (Sec. 3.3; its theta-gradient drives the identification of
+ * Sec. 4.3): cotangents of tau = RNEA(q, qd, qdd; theta) for tau_bar
+ * [nv][B]: q_bar [nq][B], qd_bar [nv][B], qdd_bar [nv][B] (= M tau_bar),
+ * theta_bar. */
 FST_API fst_status fst_rnea_vjp(const fst_model* model, int64_t B, const float* q,
                                 const float* qd, const float* qdd, const float* theta,
                                 const float* tau_bar, float* q_bar, float* qd_bar,
                                 float* qdd_bar, float* theta_bar, void* scratch,
                                 size_t scratch_bytes, void* stream);
 
-/* Jacobian: q_bar [nq][B] = sum (d J / d q)^T J_bar for J_bar
+/* Jacobian (Sec. 3.4, Eq. 6): q_bar [nq][B] = sum (d J / d q)^T J_bar for J_bar
  * [n_links][6][nv][B] in the layout of fst_jacobian (the same links).
  * q_bar is required. */
 FST_API fst_status fst_jacobian_vjp(const fst_model* model, int64_t B, const float* q,
                                     const int32_t* links, int32_t n_links, const float* J_bar,
                                     float* q_bar, void* stream);
 
-/* Mass matrix: cotangents of M = CRBA(q; theta) for M_bar [nv][nv][B]:
+/* Mass matrix (the CRBA of Sec. 3.5): cotangents of M = CRBA(q; theta) for M_bar [nv][nv][B]:
  * q_bar [nq][B] (may be NULL) and theta_bar (may be NULL; needs scratch as
  * for fst_rnea_vjp). Uses M e_k = RNEA(q, 0, e_k) without gravity: the sum
  * over columns k of RNEA adjoints with tau_bar = M_bar[:, k]. */
@@ -455,7 +466,7 @@ FST_API fst_status fst_rnea_vjp_stored(const fst_model* model, int64_t B, const 
                                        float* qd_bar, float* qdd_bar, float* theta_bar,
                                        void* scratch, size_t scratch_bytes, void* stream);
 
-/* ABA: cotangents of qdd = ABA(q, qd, tau; theta) for qdd_bar [nv][B].
+/* ABA (forward dynamics, Sec. 4.1): cotangents of qdd = ABA(q, qd, tau; theta) for qdd_bar [nv][B].
  * qdd [nv][B] must be the forward result for the same inputs. Uses
  * tau_bar = M^-1 qdd_bar and {q_bar, qd_bar, theta_bar} = -RNEA-VJP at qdd. */
 FST_API fst_status fst_aba_vjp(const fst_model* model, int64_t B, const float* q,
@@ -477,8 +488,9 @@ FST_API fst_status fst_aba_vjp(const fst_model* model, int64_t B, const float* q
  * degree of freedom.
  * ------------------------------------------------------------------------- */
 
-/* d tau / d q and d tau / d qd of tau = RNEA(q, qd, qdd; theta); either
- * output may be NULL (not computed). d tau / d qdd is M (fst_crba). */
+/* d tau / d q and d tau / d qd of tau = RNEA(q, qd, qdd; theta) (the
+ * analytical derivatives of the section above); either output may be NULL
+ * (not computed). d tau / d qdd is M (fst_crba). */
 FST_API fst_status fst_rnea_derivatives(const fst_model* model, int64_t B, const float* q,
                                         const float* qd, const float* qdd, const float* theta,
                                         float* dtau_dq, float* dtau_dqd, void* stream);
@@ -556,11 +568,16 @@ typedef struct fst_multi_io {
 } fst_multi_io;
 
 /* Groups 1..FST_MAX_MULTI models (same device; they must outlive the group)
- * and allocates its 4-byte device work counter. */
+ * and allocates its 4-byte device work counter; the handle is owned by the
+ * caller and released with fst_multi_destroy (NULL accepted). A batching
+ * form with no counterpart in the paper (which batches one tree at a time).
+ * FST_ERR_INVALID_ARG for a bad count, a NULL model or models on different
+ * devices, FST_ERR_CUDA when the counter cannot be allocated. */
 FST_API fst_status fst_multi_create(const fst_model* const* models, int32_t n_models, fst_multi** out);
 FST_API fst_status fst_multi_destroy(fst_multi* multi);
 
-/* Evaluates the requested operators of every tree in one persistent launch
+/* Evaluates the requested operators (FK Sec. 3.1, RNEA Sec. 3.3, CRBA
+ * Sec. 3.5, ABA Sec. 4.1) of every tree in one persistent launch
  * (plus a 4-byte memset that resets the work counter; both are ordered on
  * `stream` and can be captured into a CUDA graph). io has n_models entries,
  * in the order given to fst_multi_create. Overlapping calls on the same
@@ -586,7 +603,7 @@ FST_API fst_status fst_multi_set_launch(fst_multi* multi, int32_t block, int32_t
  * this probe measures the arithmetic one.
  * ------------------------------------------------------------------------- */
 
-/* Launches an FP32 fused multiply-add throughput probe on `stream`:
+/* Measurement (no counterpart in the paper). Launches an FP32 fused multiply-add throughput probe on `stream`:
  * (SMs x blocks_per_sm) blocks of 256 threads, each thread running 16
  * independent FMA chains for `iters` iterations, and writes one float per
  * thread to out (device memory of at least SMs x blocks_per_sm x 256 floats,
@@ -597,14 +614,14 @@ FST_API fst_status fst_multi_set_launch(fst_multi* multi, int32_t block, int32_t
 FST_API fst_status fst_fp32_probe(int32_t blocks_per_sm, int32_t iters, float* out, size_t out_bytes,
                                   double* flops, void* stream);
 
-/* The ids (PTX %smid) of the current device's SMs, sorted ascending, for
+/* Launch placement (no counterpart in the paper). The ids (PTX %smid) of the current device's SMs, sorted ascending, for
  * building the role table of fst_model_set_sm_roles: a GPU may number its
  * SMs with gaps, so they need not be 0 .. SMs - 1. Writes up to `capacity`
  * ids and sets *n to their number. Synchronous (launches a probe kernel of
  * one block per SM three times and reads the ids back). */
 FST_API fst_status fst_sm_ids(int32_t* ids, int32_t capacity, int32_t* n);
 
-/* *ok = 1 when the current device can address `ptr` with that same
+/* Output placement (no counterpart in the paper). *ok = 1 when the current device can address `ptr` with that same
  * pointer: device memory of the current device, managed memory, or pinned
  * host memory mapped into the device's address space (cudaHostAlloc'd
  * memory under unified addressing). Any output array of the compute calls
@@ -614,10 +631,13 @@ FST_API fst_status fst_sm_ids(int32_t* ids, int32_t capacity, int32_t* n);
  * ordinary pageable host memory, which must never be passed. */
 FST_API fst_status fst_device_can_access(const void* ptr, int32_t* ok);
 
-/* Message for the last non-OK status on this thread ("" if none). */
+/* Message for the last non-OK status on this thread ("" if none); the
+ * string is owned by the library and valid until the next non-OK status on
+ * this thread.
+ * Error reporting: no counterpart in the paper. */
 FST_API const char* fst_last_error(void);
 
-/* Library version string. */
+/* Library version string (static storage, owned by the library). */
 FST_API const char* fst_version(void);
 
 #ifdef __cplusplus
